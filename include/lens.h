@@ -1,0 +1,203 @@
+/*
+ * lens.h -- C ABI of the GB300 parametric strong-lensing evaluator.
+ *
+ * The library evaluates a lens model -- a sum of elliptical dPIE potentials
+ * plus SIS and point-mass terms -- at many image-plane points, and builds on
+ * that evaluation the maps and the chi2 of a parametric cluster-lens fit
+ * (Schaefer, Fourestey & Kneib, "Lenstool-HPC"):
+ *   - deflection (gradient) maps over a rectangular grid          Sec. 4.1, Eq. 10
+ *   - kappa / gamma / magnification maps from the summed Hessian  Sec. 2.4, Eqs. 7-9;
+ *                                                                  Sec. 2.1, Eqs. 4-5
+ *   - chi2 of multiple-image constraints, source-plane form       Sec. 2.2, Eq. 6, Fig. 3
+ *   - chi2 with predicted images from a ray-shot triangulated grid Sec. 2.3, Fig. 4;
+ *                                                                  Sec. 4.2, Fig. 8
+ *
+ * Conventions (all calls):
+ *   - Units are arcsec; angles in radians counter-clockwise from +x to the
+ *     major axis; x to the right.
+ *   - dPIE profile (Eliasdottir et al. 2007, cited in Sec. 2.2):
+ *       kappa = (b0/2)[(rcore^2 + rho^2)^-1/2 - (rcut^2 + rho^2)^-1/2],
+ *       rho^2 = x^2/(1+eps)^2 + y^2/(1-eps)^2 in the halo frame.
+ *     SIS: alpha = b0 theta/|theta|.  Point mass: alpha = b0^2 theta/|theta|^2.
+ *     At the exact centre of an SIS or point mass the deflection and Hessian
+ *     are defined as zero.
+ *   - Deflections and Hessians scale linearly with the distance ratio
+ *     D_ls/D_s ("dls_ds").
+ *   - Grids have inclusive corners: x_i = xmin + i (xmax-xmin)/(nx-1), and
+ *     map planes are row-major [ny][nx] (j along y).
+ *   - Every compute call is asynchronous on the caller's CUDA stream
+ *     ("stream" is a cudaStream_t; NULL means the legacy default stream).
+ *     Output buffers are caller-owned DEVICE memory; host-side descriptors
+ *     (lens_halo, lens_grid, lens_constraints) are read before the call
+ *     returns and may be freed afterwards.
+ *   - Return value: LENS_OK (0) or a negative LENS_E* code; nothing is
+ *     enqueued when a call returns an error.  lens_strerror() names a code;
+ *     lens_last_error() gives a message for the calling thread's last error.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef LENS_H
+#define LENS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- codes */
+#define LENS_OK 0
+#define LENS_EINVAL (-1)    /* bad argument: NULL pointer, size <= 0, non-finite
+                               or out-of-domain halo parameter, bad grid      */
+#define LENS_ENOMEM (-2)    /* device allocation would exceed the context's
+                               memory budget, or cudaMalloc failed            */
+#define LENS_ENOTFOUND (-3) /* unknown model or constraint-set handle        */
+#define LENS_ECAPACITY (-4) /* an internal image buffer overflowed; the chi2
+                               of the affected parameter sets is NaN          */
+#define LENS_ECUDA (-5)     /* a CUDA runtime call failed                     */
+#define LENS_ETIMEOUT (-6)  /* lens_wait: the work did not finish in time, or
+                               a device-side bounded wait gave up            */
+
+/* Halo types. */
+#define LENS_DPIE 0
+#define LENS_SIS 1
+#define LENS_POINT 2
+
+/* Map precision.
+ * LENS_FP64:  every potential in double precision; output planes are double.
+ * LENS_MIXED: potentials whose strength b0 is below the context's FP64
+ *             threshold are evaluated in FP32 with compensated accumulation,
+ *             the others in FP64; output planes are float. */
+#define LENS_FP64 0
+#define LENS_MIXED 1
+
+/* Source-plane chi2 variants (lens_chi2_source). */
+#define LENS_CHI2_SRC_MAPPED 0   /* sum |A (bary - beta)|^2 / sigma^2, A = (I - H)^-1 */
+#define LENS_CHI2_SRC_MU 1       /* sum |bary - beta|^2 |mu| / sigma^2                */
+#define LENS_CHI2_SRC_PLAIN 2    /* sum |bary - beta|^2 / sigma^2                     */
+
+typedef struct lens_ctx lens_ctx;
+typedef int64_t lens_model_t; /* > 0 when valid */
+typedef int64_t lens_cset_t;  /* > 0 when valid */
+
+/* One potential.  dPIE uses every field: 0 <= eps < 1, 0 < rcore < rcut,
+ * b0 > 0.  SIS and point mass use (x0, y0, b0) with b0 > 0; the remaining
+ * fields must be finite and are ignored. */
+typedef struct {
+  int32_t type;
+  double x0, y0, theta, eps, rcore, rcut, b0;
+} lens_halo;
+
+/* Rectangular grid, inclusive corners; nx, ny >= 2, xmax > xmin, ymax > ymin. */
+typedef struct {
+  double xmin, xmax, ymin, ymax;
+  int32_t nx, ny;
+} lens_grid;
+
+/* Multiple-image constraints (HOST pointers).  Source i owns images
+ * img_off[i] .. img_off[i+1]-1 (img_off[0] = 0, non-decreasing); x, y are
+ * image positions, sigma their positional error (> 0), dls_ds[i] the
+ * source's distance ratio D_ls/D_s (> 0). */
+typedef struct {
+  int32_t nsrc;
+  const int32_t *img_off;
+  const double *x;
+  const double *y;
+  const double *sigma;
+  const double *dls_ds;
+} lens_constraints;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
+ * device memory the context may hold (models, constraint sets, caches,
+ * scratch); 0 means no bound.  *out receives the context. */
+int lens_create(lens_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Release every model, constraint set and buffer of the context and free it.
+ * Synchronises the device first.  NULL is accepted. */
+int lens_destroy(lens_ctx *ctx);
+
+/* Potentials with b0 >= threshold_b0 are evaluated in FP64 by LENS_MIXED
+ * maps (default 5 arcsec).  Applies to models uploaded afterwards. */
+int lens_set_fp64_threshold(lens_ctx *ctx, double threshold_b0);
+
+/* Device bytes currently held by the context. */
+size_t lens_mem_used(const lens_ctx *ctx);
+
+/* ------------------------------------------------------------------ models */
+
+/* Upload n >= 1 potentials (host array, copied).  Validates every field
+ * (LENS_EINVAL on the first bad one), precomputes the per-potential
+ * constants on the host in double precision and stores them on the device
+ * (Sec. 3.2 structure-of-arrays discussion; here a packed per-potential
+ * record read by all threads at once).  Synchronous.  The model is immutable
+ * and owned by the context until lens_model_release. */
+int lens_model_upload(lens_ctx *ctx, const lens_halo *h, int32_t n, lens_model_t *out);
+int lens_model_release(lens_ctx *ctx, lens_model_t model);
+
+/* ------------------------------------------------------------------- maps */
+
+/* Deflection map (Sec. 4.1, Eq. 10; lens equation Sec. 2.1 Eq. 1):
+ * d_out holds 2 planes [2][ny][nx] -- alpha_x, alpha_y -- of float
+ * (LENS_MIXED) or double (LENS_FP64), 16-byte aligned. */
+int lens_grad_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                  void *d_out, void *stream);
+
+/* Deflection + Hessian maps (Sec. 2.4, Eqs. 7-9; Sec. 2.1, Eqs. 4-5):
+ * d_out holds 6 planes [6][ny][nx] -- alpha_x, alpha_y, kappa, gamma1,
+ * gamma2, mu -- with kappa = (psi_xx+psi_yy)/2, gamma1 = (psi_xx-psi_yy)/2,
+ * gamma2 = psi_xy of the summed Hessian and mu = 1/((1-kappa)^2 - gamma1^2 -
+ * gamma2^2).  Element type as for lens_grad_map. */
+int lens_hessian_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                     void *d_out, void *stream);
+
+/* ----------------------------------------------------------- chi2 batches */
+
+/* Bind a constraint table to a model for batched chi2 evaluation.
+ * var_halo[0], var_halo[1] (distinct, < n) are the two potentials whose
+ * parameters each parameter set replaces; every other potential is static,
+ * and its FP64 deflection and Hessian at the constraint positions are
+ * computed here once (the static cache).  Synchronous.  The constraint
+ * table is copied. */
+int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *c, const int32_t var_halo[2],
+                     lens_cset_t *out);
+int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
+
+/* Source-plane chi2 of P parameter sets (Sec. 2.2, Eq. 6 and Fig. 3):
+ * each set replaces (x0, y0, eps, theta, rcore, rcut, b0) of var_halo[0]
+ * then var_halo[1] -- d_params is DEVICE double [P][14].  For every image
+ * beta = theta - r alpha(theta) (Sec. 2.1, Eq. 1), the source estimate is the
+ * barycentre of its images, and d_chi2[p] (DEVICE double [P]) receives the
+ * variant's sum.  All arithmetic in FP64.  A parameter set outside the dPIE
+ * domain yields NaN. */
+int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
+                     double *d_chi2, void *stream);
+
+/* Image-plane chi2 of P parameter sets (Sec. 2.2, Eq. 6 with the brute-force
+ * image search of Sec. 2.3, Fig. 4 and Sec. 4.2): per set, the grid is
+ * ray-shot to each source's plane, every triangle containing the source's
+ * barycentre seeds a Newton solve of the lens equation with the full model,
+ * solutions closer than 1e-3 arcsec merge, and each constraint is matched to
+ * the nearest predicted image of its source.  d_chi2: DEVICE double [P];
+ * d_nimg_found: DEVICE int32 [P][nsrc] (may be NULL) receives the number of
+ * distinct images found per source.  A source without images, or a buffer
+ * overflow, makes that set's chi2 NaN (the call then returns
+ * LENS_ECAPACITY after synchronising the stream on overflow). */
+int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
+                    double *d_chi2, int32_t *d_nimg_found, void *stream);
+
+/* --------------------------------------------------------------- control */
+
+/* Wait until all work enqueued on `stream` has finished, polling without
+ * blocking the thread for more than timeout_ms (>= 0) milliseconds.
+ * LENS_ETIMEOUT if it has not finished by then (the work keeps running). */
+int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms);
+
+const char *lens_strerror(int code);
+const char *lens_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LENS_H */

@@ -1,0 +1,300 @@
+"""FP64 CPU oracle for the parametric lens model -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never loads it and
+it shares no code with the CUDA path: the arithmetic lives in
+``lens_oracle.c`` (plain C, double precision), compiled here with gcc and
+called through ctypes.  Each wrapper below names the paper passage the C
+function follows; the formulas themselves are documented at the top of the C
+file.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_pins.py`` (closed forms, invariants, finite differences,
+analytic image positions, brute force).  Bit-level agreement with the original
+Lenstool code is not pinned (no code or worked example is available); the
+pins fix the mathematics instead.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lens_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liblens_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Halo(C.Structure):
+    _fields_ = [("type", C.c_int32), ("x0", C.c_double), ("y0", C.c_double), ("theta", C.c_double),
+                ("eps", C.c_double), ("rcore", C.c_double), ("rcut", C.c_double), ("b0", C.c_double)]
+
+
+class Constraints(C.Structure):
+    _fields_ = [("nsrc", C.c_int32), ("off", C.POINTER(C.c_int32)), ("x", C.POINTER(C.c_double)),
+                ("y", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("dls_ds", C.POINTER(C.c_double))]
+
+
+class Grid(C.Structure):
+    _fields_ = [("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
+                ("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+def build(force=False):
+    """Compile lens_oracle.c into oracle/_build/liblens_oracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+                   check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
+        hp, cp, gp = C.POINTER(Halo), C.POINTER(Constraints), C.POINTER(Grid)
+        sig = {
+            "or_num_threads": (C.c_int, []),
+            "or_halo_eval": (None, [hp, C.c_double, C.c_double, dp]),
+            "or_halo_potential": (C.c_double, [hp, C.c_double, C.c_double]),
+            "or_halo_kappa": (C.c_double, [hp, C.c_double, C.c_double]),
+            "or_model_eval_points": (None, [hp, C.c_int32, dp, dp, C.c_int64, C.c_double, dp]),
+            "or_model_potential_points": (None, [hp, C.c_int32, dp, dp, C.c_int64, C.c_double, dp]),
+            "or_model_kappa_points": (None, [hp, C.c_int32, dp, dp, C.c_int64, C.c_double, dp]),
+            "or_maps": (None, [hp, C.c_int32, gp, C.c_double, C.c_int32, dp]),
+            "or_apply_params": (None, [hp, C.c_int32, ip, dp, hp]),
+            "or_backtrace": (None, [hp, C.c_int32, cp, dp, dp]),
+            "or_chi2_source": (C.c_double, [hp, C.c_int32, cp, C.c_int32]),
+            "or_chi2_source_batch": (None, [hp, C.c_int32, cp, ip, dp, C.c_int32, C.c_int32, dp]),
+            "or_newton": (C.c_int32, [hp, C.c_int32, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int32,
+                                      C.c_double]),
+            "or_find_images": (C.c_int32, [hp, C.c_int32, gp, dp, C.c_double, C.c_double, C.c_double,
+                                           C.c_int32, C.c_double, C.c_double, dp, C.c_int32]),
+            "or_alpha_grid": (None, [hp, C.c_int32, gp, dp]),
+            "or_chi2_image": (C.c_double, [hp, C.c_int32, cp, gp, dp, C.c_int32, C.c_double, C.c_double,
+                                           C.c_int32, ip]),
+            "or_chi2_image_batch": (None, [hp, C.c_int32, cp, gp, ip, dp, C.c_int32, C.c_int32, C.c_double,
+                                           C.c_double, C.c_int32, dp, ip]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------- marshalling
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def halos_from_table(table):
+    """Halo table rows [type, x0, y0, theta, eps, rcore, rcut, b0] -> ctypes array."""
+    t = np.asarray(table, dtype=np.float64).reshape(-1, 8)
+    arr = (Halo * max(len(t), 1))()
+    for k, r in enumerate(t):
+        arr[k] = Halo(int(r[0]), *map(float, r[1:]))
+    return arr, len(t)
+
+
+class _ConstraintsRef:
+    """Keeps the numpy buffers alive for as long as the ctypes struct is used."""
+
+    def __init__(self, cons):
+        self.off = np.ascontiguousarray(cons["img_off"], dtype=np.int32)
+        self.x = np.ascontiguousarray(cons["x"], dtype=np.float64)
+        self.y = np.ascontiguousarray(cons["y"], dtype=np.float64)
+        self.sigma = np.ascontiguousarray(cons["sigma"], dtype=np.float64)
+        self.dls = np.ascontiguousarray(cons["dls_ds"], dtype=np.float64)
+        self.c = Constraints(len(self.off) - 1, _ip(self.off), _dp(self.x), _dp(self.y), _dp(self.sigma),
+                             _dp(self.dls))
+
+
+def _grid(g):
+    return Grid(g["xmin"], g["xmax"], g["ymin"], g["ymax"], g["nx"], g["ny"])
+
+
+def num_threads():
+    return int(_load().or_num_threads())
+
+
+# ------------------------------------------------------------------ evaluation
+
+def halo_eval(row, X, Y):
+    """One potential at one point, D_ls/D_s = 1: (ax, ay, hxx, hyy, hxy).
+    Per-potential derivatives of Sec. 4.1 Eq. 10 / Sec. 2.4 Eqs. 7-9."""
+    lib = _load()
+    h, _ = halos_from_table(row)
+    out = np.zeros(5)
+    lib.or_halo_eval(h, float(X), float(Y), _dp(out))
+    return out
+
+
+def model_eval(table, X, Y, dls_ds=1.0):
+    """Summed (ax, ay, hxx, hyy, hxy) at points X, Y (Sec. 4.1 Eq. 10): [npt, 5]."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    X = np.ascontiguousarray(np.atleast_1d(X), dtype=np.float64)
+    Y = np.ascontiguousarray(np.atleast_1d(Y), dtype=np.float64)
+    out = np.zeros((len(X), 5))
+    lib.or_model_eval_points(h, n, _dp(X), _dp(Y), len(X), float(dls_ds), _dp(out))
+    return out
+
+
+def potential(table, X, Y, dls_ds=1.0):
+    """Lensing potential (Sec. 2.1 Eq. 2, up to a constant) at points."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    X = np.ascontiguousarray(np.atleast_1d(X), dtype=np.float64)
+    Y = np.ascontiguousarray(np.atleast_1d(Y), dtype=np.float64)
+    out = np.zeros(len(X))
+    lib.or_model_potential_points(h, n, _dp(X), _dp(Y), len(X), float(dls_ds), _dp(out))
+    return out
+
+
+def kappa_profile(table, X, Y, dls_ds=1.0):
+    """Surface density from the profile definitions (not from the Hessian)."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    X = np.ascontiguousarray(np.atleast_1d(X), dtype=np.float64)
+    Y = np.ascontiguousarray(np.atleast_1d(Y), dtype=np.float64)
+    out = np.zeros(len(X))
+    lib.or_model_kappa_points(h, n, _dp(X), _dp(Y), len(X), float(dls_ds), _dp(out))
+    return out
+
+
+def maps(table, grid, dls_ds=1.0, nplanes=6):
+    """Map planes [nplanes, ny, nx]: ax, ay (+ kappa, gamma1, gamma2, mu).
+    Sec. 2.4 Eqs. 7-9 and Sec. 2.1 Eqs. 4-5 over the grid of Sec. 4.1."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    g = _grid(grid)
+    out = np.zeros((nplanes, grid["ny"], grid["nx"]))
+    lib.or_maps(h, n, C.byref(g), float(dls_ds), int(nplanes), _dp(out))
+    return out
+
+
+def apply_params(table, var_halo, p14):
+    """Model with halos var_halo[0..1] replaced by the 14 parameters."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    out = (Halo * n)()
+    var = np.asarray(var_halo, dtype=np.int32)
+    p = np.ascontiguousarray(p14, dtype=np.float64)
+    lib.or_apply_params(h, n, _ip(var), _dp(p), out)
+    return np.array([[o.type, o.x0, o.y0, o.theta, o.eps, o.rcore, o.rcut, o.b0] for o in out])
+
+
+def backtrace(table, cons):
+    """beta_ij = theta_ij - alpha(theta_ij) (Sec. 2.1 Eq. 1) and per-source
+    barycentres (Sec. 2.2, Fig. 3).  Returns (beta [nimg, 2], bary [nsrc, 2])."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    cr = _ConstraintsRef(cons)
+    beta = np.zeros((len(cr.x), 2))
+    bary = np.zeros((cr.c.nsrc, 2))
+    lib.or_backtrace(h, n, C.byref(cr.c), _dp(beta), _dp(bary))
+    return beta, bary
+
+
+def chi2_source(table, cons, variant=0):
+    """Source-plane chi2 of one model (Sec. 2.2 Eq. 6, source-plane form)."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    cr = _ConstraintsRef(cons)
+    return float(lib.or_chi2_source(h, n, C.byref(cr.c), int(variant)))
+
+
+def chi2_source_batch(table, cons, var_halo, params, variant=0):
+    lib = _load()
+    h, n = halos_from_table(table)
+    cr = _ConstraintsRef(cons)
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 14)
+    var = np.asarray(var_halo, dtype=np.int32)
+    out = np.zeros(len(params))
+    lib.or_chi2_source_batch(h, n, C.byref(cr.c), _ip(var), _dp(params), len(params), int(variant), _dp(out))
+    return out
+
+
+def newton(table, r, beta_s, theta0, maxit=20, tol=1e-6):
+    """Newton solve of beta_s = theta - r alpha(theta); returns (theta, iters or -1)."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    tx, ty = C.c_double(theta0[0]), C.c_double(theta0[1])
+    it = lib.or_newton(h, n, float(r), float(beta_s[0]), float(beta_s[1]), C.byref(tx), C.byref(ty),
+                       int(maxit), float(tol))
+    return np.array([tx.value, ty.value]), int(it)
+
+
+def alpha_grid(table, grid):
+    lib = _load()
+    h, n = halos_from_table(table)
+    g = _grid(grid)
+    out = np.zeros((grid["ny"], grid["nx"], 2))
+    lib.or_alpha_grid(h, n, C.byref(g), _dp(out))
+    return out
+
+
+def find_images(table, grid, r, beta_s, maxit=20, tol=1e-6, dedup=1e-3, cap=64, ag=None):
+    """Brute-force predicted images of one source (Sec. 2.3 Fig. 4; Sec. 4.2)."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    g = _grid(grid)
+    if ag is None:
+        ag = alpha_grid(table, grid)
+    ag = np.ascontiguousarray(ag, dtype=np.float64)
+    img = np.zeros((cap, 2))
+    nf = lib.or_find_images(h, n, C.byref(g), _dp(ag), float(r), float(beta_s[0]), float(beta_s[1]), int(maxit),
+                            float(tol), float(dedup), _dp(img), int(cap))
+    return img[:min(nf, cap)].copy(), int(nf)
+
+
+def chi2_image(table, cons, grid, maxit=20, tol=1e-6, dedup=1e-3, cap=64, ag=None):
+    """Image-plane chi2 of one model (Sec. 2.2 Eq. 6 with the brute-force
+    search of Sec. 2.3 / Sec. 4.2).  Returns (chi2, nfound[nsrc])."""
+    lib = _load()
+    h, n = halos_from_table(table)
+    cr = _ConstraintsRef(cons)
+    g = _grid(grid)
+    agp = None
+    if ag is not None:
+        ag = np.ascontiguousarray(ag, dtype=np.float64)
+        agp = _dp(ag)
+    nf = np.zeros(cr.c.nsrc, dtype=np.int32)
+    v = lib.or_chi2_image(h, n, C.byref(cr.c), C.byref(g), agp, int(maxit), float(tol), float(dedup), int(cap),
+                          _ip(nf))
+    return float(v), nf
+
+
+def chi2_image_batch(table, cons, grid, var_halo, params, maxit=20, tol=1e-6, dedup=1e-3, cap=64):
+    lib = _load()
+    h, n = halos_from_table(table)
+    cr = _ConstraintsRef(cons)
+    g = _grid(grid)
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 14)
+    var = np.asarray(var_halo, dtype=np.int32)
+    out = np.zeros(len(params))
+    nf = np.zeros((len(params), cr.c.nsrc), dtype=np.int32)
+    lib.or_chi2_image_batch(h, n, C.byref(cr.c), C.byref(g), _ip(var), _dp(params), len(params), int(maxit),
+                            float(tol), float(dedup), int(cap), _dp(out), _ip(nf))
+    return out, nf
