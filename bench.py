@@ -1,0 +1,320 @@
+"""Benchmark: point-halo grad+Hessian evaluations per second on the 2048^2,
+1000-potential deflection + Hessian map (LENS_MIXED), plus the batched chi2
+and FP64 comparison legs.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torch.distributed.run): every rank evaluates its own map of the
+same size -- independent problems, no data-path collective ("weak" scaling);
+value = all ranks' point-halo pairs / the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "point-halo grad+Hessian evals/s"
+UNIT = "pair/s"
+MAP_N, N_HALO = 2048, 1000
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
+
+# FP32-pipe thread instructions (FFMA + FADD + FMUL) and MUFU (XU pipe)
+# instructions per point-halo pair of the LENS_MIXED Hessian map kernel,
+# measured with ncu on the 2048^2 x 1000 workload (profiles/
+# map_hessian_mixed_2048x1000.md); the compensated-fold overhead (~1 op per
+# pair) is included.
+FP32_OPS_PER_PAIR = 91.5
+MUFU_OPS_PER_PAIR = None
+SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the chi2 / FP64 comparison legs")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_map_sample(m, g, seconds):
+    """Time the oracle's Hessian map on row bands of the grid until ~seconds of
+    CPU work; returns (pairs/s, rows evaluated, threads)."""
+    import oracle
+    nx = g["nx"]
+    dy = (g["ymax"] - g["ymin"]) / (g["ny"] - 1)
+    rows, pairs, t_used = 0, 0, 0.0
+    band = 4
+    while t_used < seconds and rows < g["ny"]:
+        gb = dict(g, ymin=g["ymin"] + rows * dy, ymax=g["ymin"] + (rows + band - 1) * dy, ny=band)
+        t0 = time.perf_counter()
+        oracle.maps(m, gb, 1.0, 6)
+        t_used += time.perf_counter() - t0
+        rows += band
+        pairs += band * nx * len(m)
+        band = min(band * 2, 64)
+    return pairs / t_used, rows, oracle.num_threads()
+
+
+def run_reference(args, rank):
+    """The oracle as it stands, on the host cores: each step a bounded row
+    band of the same 2048^2 x 1000 workload."""
+    if rank != 0:
+        return
+    from paper_2004_06352_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    m, g = I.cfg2_model(), I.grid(MAP_N)
+    per_step_s = 4.0
+    for _ in range(args.warmup):
+        oracle_map_sample(m, g, 0.5)
+    rates, rows = [], 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, nr, thr = oracle_map_sample(m, g, per_step_s)
+        rates.append(r)
+        rows += nr
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "hessian_map 2048x2048 grid x 1000 dPIE potentials (2 cluster + 998 members)",
+                       "sample": f"{rows} grid rows of 2048 across the steps"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "sample": f"{rows} rows x 2048 points x 1000 potentials, FP64 C, OpenMP"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    from paper_2004_06352_gb300 import build as B
+    B.build()
+    from paper_2004_06352_gb300 import api
+    from paper_2004_06352_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    m, g = I.cfg2_model(seed=2 + rank), I.grid(MAP_N)
+    pairs = MAP_N * MAP_N * N_HALO
+    ctx = api.Context(local)
+    mid = ctx.model_upload(m)
+    out = torch.empty((6, MAP_N, MAP_N), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.hessian_map(mid, g, 1.0, api.LENS_MIXED, out, stream)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.hessian_map(mid, g, 1.0, api.LENS_MIXED, out, stream)
+        ev[k][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    kms = [a.elapsed_time(b) for a, b in ev]
+    ms = float(np.mean(kms))
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * pairs / (ms * 1e-3)
+
+    # end to end through the public API: host halo table -> upload -> map ->
+    # pinned host copy of all six planes, every step
+    host = torch.empty((6, MAP_N, MAP_N), dtype=torch.float32, pin_memory=True)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        barrier()
+        t1 = time.perf_counter()
+        mid2 = ctx.model_upload(m)
+        ctx.hessian_map(mid2, g, 1.0, api.LENS_MIXED, out, stream)
+        host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        ctx.model_release(mid2)
+        if k >= args.warmup:
+            e2e_ms.append(dt * 1e3)
+    e2e_t = float(np.mean(e2e_ms))
+    if pg:
+        t = torch.tensor([e2e_t], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_t = float(t.item())
+
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra = extra_legs(ctx, api, I, torch, dev, m, g, mid, stream)
+
+    if rank != 0:
+        ctx.close()
+        return
+    f_max = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    roof = {"bound": "alu", "unit": "Top/s", "traffic": None}
+    if FP32_OPS_PER_PAIR:
+        ach = FP32_OPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12
+        peak = SMS * FP32_LANES * f_max / 1e12
+        roof.update({"achieved": ach, "peak": peak, "frac": ach / peak,
+                     "ops_per_pair": FP32_OPS_PER_PAIR, "pipe": "fp32 (FFMA/FADD/FMUL lanes)"})
+        if MUFU_OPS_PER_PAIR:
+            mach = MUFU_OPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12
+            roof["mufu"] = {"achieved": mach, "peak": SMS * MUFU_LANES * f_max / 1e12,
+                            "frac": mach / (SMS * MUFU_LANES * f_max / 1e12)}
+    else:
+        roof.update({"achieved": None, "peak": SMS * FP32_LANES * f_max / 1e12, "frac": None})
+    cpu = extra.pop("cpu_baseline", None)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "hessian_map 2048x2048 grid x 1000 dPIE potentials (2 cluster FP64 + 998 "
+                                   "members FP32), LENS_MIXED, outputs alpha_x, alpha_y, kappa, gamma1, gamma2, mu",
+                       "l2": "256 MB buffer written between timed steps", "parallelism": f"replicas x{ws}"},
+            "e2e": {"value": ws * pairs / (e2e_t * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": N_HALO * 56, "d2h_bytes_per_step": 6 * MAP_N * MAP_N * 4},
+            "gpu_launches": args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "wall_s_timed": wall, "extra": extra}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
+    """Secondary numbers: grad-only map, plain FP64 GPU map, batched chi2, and
+    the oracle on the host cores (bounded sample)."""
+    ex = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    pairs = MAP_N * MAP_N * N_HALO
+    out2 = torch.empty((2, MAP_N, MAP_N), dtype=torch.float32, device=dev)
+    t = timed(lambda: ctx.grad_map(mid, g, 1.0, api.LENS_MIXED, out2, stream), 5)
+    ex["grad_map_mixed"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3)}
+    out64 = torch.empty((6, MAP_N, MAP_N), dtype=torch.float64, device=dev)
+    t = timed(lambda: ctx.hessian_map(mid, g, 1.0, api.LENS_FP64, out64, stream), 1)
+    ex["hessian_map_fp64_gpu"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3)}
+    del out64
+    m1, g1 = I.cfg1_model(), I.grid(256)
+    mid1 = ctx.model_upload(m1)
+    o1 = torch.empty((2, 256, 256), dtype=torch.float64, device=dev)
+    t = timed(lambda: ctx.grad_map(mid1, g1, 0.7, api.LENS_FP64, o1, stream), 50)
+    ex["grad_map_fp64_256x10"] = {"ms": t}
+    # batched source-plane chi2: 100 sources, ~400 images, 4096 sets
+    cons = I.random_constraints(100, seed=34, field=60)
+    cs = ctx.cset_create(mid, cons, (0, 1))
+    P = 4096
+    params = torch.tensor(I.perturbed_params(m, (0, 1), P, seed=35), device=dev)
+    chi2 = torch.empty(P, dtype=torch.float64, device=dev)
+    t = timed(lambda: ctx.chi2_source(cs, params, P, 0, chi2, stream), 5)
+    ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P}
+    # CPU baseline: the oracle on the host cores, ~15 s of row bands
+    try:
+        rate, rows, thr = oracle_map_sample(m, g, 15.0)
+        ex["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+                              "sample": f"{rows} rows x 2048 points x 1000 potentials (FP64 C, OpenMP)"}
+    except Exception as e:  # the benchmark line still prints without it
+        ex["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                              "sample": f"failed: {e}"}
+    return ex
+
+
+if __name__ == "__main__":
+    main()

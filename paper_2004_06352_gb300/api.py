@@ -1,0 +1,201 @@
+"""Thin Python binding of the C ABI in include/lens.h (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names; device buffers are torch tensors (their
+data_ptr() is passed) and streams are torch.cuda.Stream objects (their
+cuda_stream handle is passed).  Importing this module loads the compiled
+library and raises if it is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblens.so")
+
+LENS_OK, LENS_EINVAL, LENS_ENOMEM, LENS_ENOTFOUND, LENS_ECAPACITY, LENS_ECUDA, LENS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LENS_DPIE, LENS_SIS, LENS_POINT = 0, 1, 2
+LENS_FP64, LENS_MIXED = 0, 1
+LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
+           "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_cset_create", "lens_cset_release",
+           "lens_chi2_source", "lens_chi2_image", "lens_wait", "lens_strerror", "lens_last_error")
+
+
+class LensError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.lens_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_lib.lens_strerror(code).decode()} ({code}): {msg}")
+
+
+class lens_halo(C.Structure):
+    _fields_ = [("type", C.c_int32), ("x0", C.c_double), ("y0", C.c_double), ("theta", C.c_double),
+                ("eps", C.c_double), ("rcore", C.c_double), ("rcut", C.c_double), ("b0", C.c_double)]
+
+
+class lens_grid(C.Structure):
+    _fields_ = [("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
+                ("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+class lens_constraints(C.Structure):
+    _fields_ = [("nsrc", C.c_int32), ("img_off", C.POINTER(C.c_int32)), ("x", C.POINTER(C.c_double)),
+                ("y", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("dls_ds", C.POINTER(C.c_double))]
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    vp, i64 = C.c_void_p, C.c_int64
+    sig = {
+        "lens_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_size_t]),
+        "lens_destroy": (C.c_int, [vp]),
+        "lens_set_fp64_threshold": (C.c_int, [vp, C.c_double]),
+        "lens_mem_used": (C.c_size_t, [vp]),
+        "lens_model_upload": (C.c_int, [vp, C.POINTER(lens_halo), C.c_int32, C.POINTER(i64)]),
+        "lens_model_release": (C.c_int, [vp, i64]),
+        "lens_grad_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
+        "lens_hessian_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
+        "lens_cset_create": (C.c_int, [vp, i64, C.POINTER(lens_constraints), C.POINTER(C.c_int32), C.POINTER(i64)]),
+        "lens_cset_release": (C.c_int, [vp, i64]),
+        "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
+        "lens_chi2_image": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
+        "lens_wait": (C.c_int, [vp, vp, i64]),
+        "lens_strerror": (C.c_char_p, [C.c_int]),
+        "lens_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(rc, where):
+    if rc != LENS_OK:
+        raise LensError(rc, where)
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_grid(g):
+    if isinstance(g, lens_grid):
+        return g
+    return lens_grid(g["xmin"], g["xmax"], g["ymin"], g["ymax"], g["nx"], g["ny"])
+
+
+def halos_from_table(table):
+    t = np.asarray(table, dtype=np.float64).reshape(-1, 8)
+    arr = (lens_halo * len(t))()
+    for k, r in enumerate(t):
+        arr[k] = lens_halo(int(r[0]), *map(float, r[1:]))
+    return arr
+
+
+class Context:
+    """Owns a lens_ctx; the methods mirror the C calls."""
+
+    def __init__(self, device=0, mem_budget_bytes=0):
+        self.h = C.c_void_p()
+        _check(_lib.lens_create(C.byref(self.h), int(device), int(mem_budget_bytes)), "lens_create")
+
+    def close(self):
+        if self.h:
+            _lib.lens_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_fp64_threshold(self, b0):
+        _check(_lib.lens_set_fp64_threshold(self.h, float(b0)), "lens_set_fp64_threshold")
+
+    def mem_used(self):
+        return int(_lib.lens_mem_used(self.h))
+
+    def model_upload(self, table):
+        arr = halos_from_table(table)
+        out = C.c_int64()
+        _check(_lib.lens_model_upload(self.h, arr, len(arr), C.byref(out)), "lens_model_upload")
+        return out.value
+
+    def model_release(self, model):
+        _check(_lib.lens_model_release(self.h, int(model)), "lens_model_release")
+
+    def grad_map(self, model, grid, dls_ds, precision, out, stream=None):
+        g = make_grid(grid)
+        _check(_lib.lens_grad_map(self.h, int(model), C.byref(g), float(dls_ds), int(precision), _ptr(out),
+                                  _stream(stream)), "lens_grad_map")
+        return out
+
+    def hessian_map(self, model, grid, dls_ds, precision, out, stream=None):
+        g = make_grid(grid)
+        _check(_lib.lens_hessian_map(self.h, int(model), C.byref(g), float(dls_ds), int(precision), _ptr(out),
+                                     _stream(stream)), "lens_hessian_map")
+        return out
+
+    def cset_create(self, model, cons, var_halo):
+        off = np.ascontiguousarray(cons["img_off"], dtype=np.int32)
+        x = np.ascontiguousarray(cons["x"], dtype=np.float64)
+        y = np.ascontiguousarray(cons["y"], dtype=np.float64)
+        s = np.ascontiguousarray(cons["sigma"], dtype=np.float64)
+        d = np.ascontiguousarray(cons["dls_ds"], dtype=np.float64)
+        dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        c = lens_constraints(len(off) - 1, off.ctypes.data_as(C.POINTER(C.c_int32)), dp(x), dp(y), dp(s), dp(d))
+        var = (C.c_int32 * 2)(int(var_halo[0]), int(var_halo[1]))
+        out = C.c_int64()
+        _check(_lib.lens_cset_create(self.h, int(model), C.byref(c), var, C.byref(out)), "lens_cset_create")
+        return out.value
+
+    def cset_release(self, cset):
+        _check(_lib.lens_cset_release(self.h, int(cset)), "lens_cset_release")
+
+    def chi2_source(self, cset, params, P, variant, chi2, stream=None):
+        _check(_lib.lens_chi2_source(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(chi2),
+                                     _stream(stream)), "lens_chi2_source")
+        return chi2
+
+    def chi2_image(self, cset, grid, params, P, chi2, nfound=None, stream=None):
+        g = make_grid(grid)
+        rc = _lib.lens_chi2_image(self.h, int(cset), C.byref(g), _ptr(params), int(P), _ptr(chi2), _ptr(nfound),
+                                  _stream(stream))
+        if rc not in (LENS_OK, LENS_ECAPACITY):
+            raise LensError(rc, "lens_chi2_image")
+        return rc
+
+    def wait(self, stream=None, timeout_ms=60000):
+        return _check(_lib.lens_wait(self.h, _stream(stream), int(timeout_ms)), "lens_wait")
+
+
+def strerror(code):
+    return _lib.lens_strerror(int(code)).decode()

@@ -1,0 +1,481 @@
+// C-ABI entry points: context, model store, constraint sets, waits, errors.
+// The compute launches live in lens_maps.cu and lens_chi2.cu.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstring>
+#include <thread>
+
+#include "lens_internal.cuh"
+
+namespace lens {
+
+static thread_local char g_msg[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+  va_end(ap);
+}
+
+int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+Model *find_model(lens_ctx *ctx, lens_model_t id) {
+  for (auto &p : ctx->models)
+    if (p.first == id) return p.second;
+  return nullptr;
+}
+
+CSet *find_cset(lens_ctx *ctx, lens_cset_t id) {
+  for (auto &p : ctx->csets)
+    if (p.first == id) return p.second;
+  return nullptr;
+}
+
+int dev_alloc(lens_ctx *ctx, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return LENS_OK;
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(LENS_ENOMEM, "device memory budget exceeded: %zu used + %zu requested > %zu", ctx->used, bytes,
+                ctx->budget);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(LENS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return LENS_OK;
+}
+
+void dev_free(lens_ctx *ctx, void *p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->used -= std::min(ctx->used, bytes);
+}
+
+int ensure_scratch(lens_ctx *ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return LENS_OK;
+  if (ctx->scratch) {
+    cudaDeviceSynchronize();
+    dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+  }
+  int rc = dev_alloc(ctx, &ctx->scratch, bytes);
+  if (rc == LENS_OK) ctx->scratch_bytes = bytes;
+  return rc;
+}
+
+int check_grid(const lens_grid *g) {
+  if (!g) return fail(LENS_EINVAL, "grid is NULL");
+  if (!(std::isfinite(g->xmin) && std::isfinite(g->xmax) && std::isfinite(g->ymin) && std::isfinite(g->ymax)))
+    return fail(LENS_EINVAL, "grid corners must be finite");
+  if (g->nx < 2 || g->ny < 2) return fail(LENS_EINVAL, "grid needs nx, ny >= 2 (got %d x %d)", g->nx, g->ny);
+  if (!(g->xmax > g->xmin && g->ymax > g->ymin)) return fail(LENS_EINVAL, "grid needs xmax > xmin and ymax > ymin");
+  return LENS_OK;
+}
+
+// FP32 record of one potential (host, from FP64 arithmetic).
+static void make_rec32(const lens_halo &h, float *r) {
+  for (int k = 0; k < REC32; ++k) r[k] = 0.f;
+  int kind;
+  if (h.type == LENS_SIS || h.type == LENS_POINT) {
+    r[R_C] = 1.f;
+    kind = h.type == LENS_SIS ? K32_SIS : K32_POINT;
+    r[R_B] = (float)(h.type == LENS_SIS ? h.b0 : h.b0 * h.b0);
+  } else {
+    double e = h.eps;
+    double q = (1.0 - e) / (1.0 + e), u = 2.0 * std::sqrt(e) / (1.0 + e);
+    double q2 = q * q, u2 = u * u;
+    double b = h.b0 * (1.0 + e), bq = b * q;
+    double sc = h.rcore * (1.0 + e), st = h.rcut * (1.0 + e);
+    double c2 = std::cos(2.0 * h.theta), s2 = std::sin(2.0 * h.theta);
+    bool series = u < U_SERIES32;
+    kind = series ? K32_DPIE_SERIES : K32_DPIE;
+    r[R_C] = (float)std::cos(h.theta);
+    r[R_S] = (float)std::sin(h.theta);
+    r[R_Q2] = (float)q2;
+    r[R_U2] = (float)u2;
+    r[R_KC] = (float)(q2 * sc * sc);
+    r[R_KT] = (float)(q2 * st * st);
+    r[R_SC] = (float)sc;
+    r[R_ST] = (float)st;
+    r[R_Q2SS] = (float)(q2 * (st + sc));
+    r[R_DS] = (float)(st - sc);
+    r[R_Q2SC] = (float)(q2 * sc);
+    r[R_Q2ST] = (float)(q2 * st);
+    r[R_SS] = (float)(st + sc);
+    r[R_Q2DS] = (float)(q2 * (st - sc));
+    r[R_KDC] = (float)((1.0 + q2) * sc * sc);
+    r[R_KDT] = (float)((1.0 + q2) * st * st);
+    r[R_2SC] = (float)(2.0 * sc);
+    r[R_2ST] = (float)(2.0 * st);
+    r[R_U2SC2] = (float)(u2 * sc * sc);
+    r[R_U2ST2] = (float)(u2 * st * st);
+    r[R_AXS] = (float)(series ? bq : bq / u);
+    r[R_AYS] = (float)(series ? bq : bq / (2.0 * u));
+    r[R_KAPS] = (float)(0.5 * bq);
+    r[R_U] = (float)u;
+    r[R_C1] = (float)(c2 * 0.5 * bq);
+    r[R_C2] = (float)(s2 * bq);
+    r[R_C3] = (float)(s2 * 0.5 * bq);
+    r[R_C4] = (float)(-c2 * bq);
+  }
+  std::memcpy(&r[R_KIND], &kind, sizeof(int));
+}
+
+static int kind_order(const lens_halo &h) {
+  if (h.type == LENS_SIS) return 2;
+  if (h.type == LENS_POINT) return 3;
+  double u = 2.0 * std::sqrt(h.eps) / (1.0 + h.eps);
+  return u < U_SERIES32 ? 1 : 0;
+}
+
+static void free_model(lens_ctx *ctx, Model *m) {
+  dev_free(ctx, m->rec32, (size_t)m->n_light * REC32 * sizeof(float));
+  dev_free(ctx, m->pos64, (size_t)m->n_light * 4 * sizeof(double));
+  dev_free(ctx, m->heavy, (size_t)m->n_heavy * REC64 * sizeof(double));
+  dev_free(ctx, m->all64, (size_t)m->n * REC64 * sizeof(double));
+  delete m;
+}
+
+static void free_cset(lens_ctx *ctx, CSet *c) {
+  dev_free(ctx, c->img_off, (c->nsrc + 1) * sizeof(int32_t));
+  dev_free(ctx, c->src_of, c->nimg * sizeof(int32_t));
+  dev_free(ctx, c->x, c->nimg * sizeof(double));
+  dev_free(ctx, c->y, c->nimg * sizeof(double));
+  dev_free(ctx, c->sigma, c->nimg * sizeof(double));
+  dev_free(ctx, c->ratio, c->nsrc * sizeof(double));
+  dev_free(ctx, c->stat, (size_t)c->nimg * 5 * sizeof(double));
+  dev_free(ctx, c->var_base, 2 * REC64 * sizeof(double));
+  for (auto &g : c->grids) dev_free(ctx, g.alpha_static, g.bytes);
+  delete c;
+}
+
+}  // namespace lens
+
+using namespace lens;
+
+extern "C" {
+
+const char *lens_strerror(int code) {
+  switch (code) {
+    case LENS_OK: return "ok";
+    case LENS_EINVAL: return "invalid argument";
+    case LENS_ENOMEM: return "device memory budget exceeded or allocation failed";
+    case LENS_ENOTFOUND: return "unknown handle";
+    case LENS_ECAPACITY: return "image buffer capacity exceeded";
+    case LENS_ECUDA: return "CUDA runtime error";
+    case LENS_ETIMEOUT: return "timed out";
+    default: return "unknown error code";
+  }
+}
+
+const char *lens_last_error(void) { return g_msg; }
+
+int lens_create(lens_ctx **out, int device, size_t mem_budget_bytes) {
+  if (!out) return fail(LENS_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  LENS_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(LENS_EINVAL, "device %d out of range (have %d)", device, ndev);
+  LENS_CUDA_TRY(cudaSetDevice(device));
+  lens_ctx *ctx = new lens_ctx();
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  int rc = dev_alloc(ctx, (void **)&ctx->d_err, sizeof(int));
+  if (rc != LENS_OK) {
+    delete ctx;
+    return rc;
+  }
+  cudaMemset(ctx->d_err, 0, sizeof(int));
+  *out = ctx;
+  return LENS_OK;
+}
+
+int lens_destroy(lens_ctx *ctx) {
+  if (!ctx) return LENS_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto &p : ctx->csets) free_cset(ctx, p.second);
+  for (auto &p : ctx->models) free_model(ctx, p.second);
+  dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
+  dev_free(ctx, ctx->d_err, sizeof(int));
+  delete ctx;
+  return LENS_OK;
+}
+
+int lens_set_fp64_threshold(lens_ctx *ctx, double t) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  if (std::isnan(t) || t < 0.0) return fail(LENS_EINVAL, "threshold must be >= 0");
+  ctx->fp64_threshold = t;
+  return LENS_OK;
+}
+
+size_t lens_mem_used(const lens_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+int lens_model_upload(lens_ctx *ctx, const lens_halo *h, int32_t n, lens_model_t *out) {
+  if (!ctx || !h || !out) return fail(LENS_EINVAL, "NULL argument");
+  if (n < 1) return fail(LENS_EINVAL, "need n >= 1 potentials (got %d)", n);
+  for (int32_t i = 0; i < n; ++i) {
+    const lens_halo &a = h[i];
+    if (!halo_params_ok(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0))
+      return fail(LENS_EINVAL,
+                  "potential %d out of domain (type %d, eps %g, rcore %g, rcut %g, b0 %g): need finite values, "
+                  "b0 > 0 and for dPIE 0 <= eps < 1, 0 < rcore < rcut",
+                  i, a.type, a.eps, a.rcore, a.rcut, a.b0);
+  }
+  cudaSetDevice(ctx->device);
+  Model *m = new Model();
+  m->n = n;
+  m->host.assign(h, h + n);
+  // light potentials grouped by kind so each warp-uniform branch runs in one stretch
+  std::vector<int32_t> light, heavy;
+  for (int32_t i = 0; i < n; ++i) (h[i].b0 >= ctx->fp64_threshold ? heavy : light).push_back(i);
+  std::stable_sort(light.begin(), light.end(), [&](int32_t a, int32_t b) { return kind_order(h[a]) < kind_order(h[b]); });
+  m->n_light = (int32_t)light.size();
+  m->n_heavy = (int32_t)heavy.size();
+  std::vector<float> r32((size_t)m->n_light * REC32);
+  std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
+  for (int32_t k = 0; k < m->n_light; ++k) {
+    const lens_halo &a = h[light[k]];
+    make_rec32(a, &r32[(size_t)k * REC32]);
+    bool circ = a.type != LENS_DPIE;
+    p64[4 * k + 0] = a.x0;
+    p64[4 * k + 1] = a.y0;
+    p64[4 * k + 2] = circ ? 1.0 : std::cos(a.theta);
+    p64[4 * k + 3] = circ ? 0.0 : std::sin(a.theta);
+  }
+  for (int32_t k = 0; k < m->n_heavy; ++k) {
+    const lens_halo &a = h[heavy[k]];
+    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &hv[(size_t)k * REC64]);
+  }
+  for (int32_t k = 0; k < n; ++k) {
+    const lens_halo &a = h[k];
+    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
+  }
+  int rc = LENS_OK;
+  size_t b32 = r32.size() * sizeof(float), bp = p64.size() * sizeof(double), bh = hv.size() * sizeof(double),
+         ba = a64.size() * sizeof(double);
+  if ((rc = dev_alloc(ctx, (void **)&m->rec32, b32)) || (rc = dev_alloc(ctx, (void **)&m->pos64, bp)) ||
+      (rc = dev_alloc(ctx, (void **)&m->heavy, bh)) || (rc = dev_alloc(ctx, (void **)&m->all64, ba))) {
+    free_model(ctx, m);
+    return rc;
+  }
+  m->bytes = b32 + bp + bh + ba;
+  cudaError_t e = cudaSuccess;
+  if (b32) e = cudaMemcpy(m->rec32, r32.data(), b32, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bp) e = cudaMemcpy(m->pos64, p64.data(), bp, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bh) e = cudaMemcpy(m->heavy, hv.data(), bh, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->all64, a64.data(), ba, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_model(ctx, m);
+    return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));
+  }
+  int64_t id = ctx->next_id++;
+  ctx->models.push_back({id, m});
+  *out = id;
+  return LENS_OK;
+}
+
+int lens_model_release(lens_ctx *ctx, lens_model_t id) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  for (size_t k = 0; k < ctx->models.size(); ++k)
+    if (ctx->models[k].first == id) {
+      cudaSetDevice(ctx->device);
+      cudaDeviceSynchronize();
+      // constraint sets bound to this model go with it
+      for (size_t j = 0; j < ctx->csets.size();) {
+        if (ctx->csets[j].second->model == id) {
+          free_cset(ctx, ctx->csets[j].second);
+          ctx->csets.erase(ctx->csets.begin() + j);
+        } else {
+          ++j;
+        }
+      }
+      free_model(ctx, ctx->models[k].second);
+      ctx->models.erase(ctx->models.begin() + k);
+      return LENS_OK;
+    }
+  return fail(LENS_ENOTFOUND, "model %lld not found", (long long)id);
+}
+
+static int map_common(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                      void *d_out, void *stream, bool hess) {
+  if (!ctx || !d_out) return fail(LENS_EINVAL, "NULL argument");
+  Model *m = find_model(ctx, model);
+  if (!m) return fail(LENS_ENOTFOUND, "model %lld not found", (long long)model);
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (!(std::isfinite(dls_ds) && dls_ds > 0.0)) return fail(LENS_EINVAL, "dls_ds must be finite and > 0");
+  size_t align = precision == LENS_FP64 ? 8 : 4;
+  if ((uintptr_t)d_out % align) return fail(LENS_EINVAL, "d_out must be aligned to its element size");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == LENS_MIXED) return launch_map_mixed(ctx, m, grid, dls_ds, hess, d_out, st);
+  if (precision == LENS_FP64) return launch_map_fp64(ctx, m, grid, dls_ds, hess, d_out, st);
+  return fail(LENS_EINVAL, "precision must be LENS_FP64 or LENS_MIXED");
+}
+
+int lens_grad_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                  void *d_out, void *stream) {
+  return map_common(ctx, model, grid, dls_ds, precision, d_out, stream, false);
+}
+
+int lens_hessian_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                     void *d_out, void *stream) {
+  return map_common(ctx, model, grid, dls_ds, precision, d_out, stream, true);
+}
+
+int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *c, const int32_t var_halo[2],
+                     lens_cset_t *out) {
+  if (!ctx || !c || !var_halo || !out) return fail(LENS_EINVAL, "NULL argument");
+  Model *m = find_model(ctx, model);
+  if (!m) return fail(LENS_ENOTFOUND, "model %lld not found", (long long)model);
+  if (c->nsrc < 1 || !c->img_off || !c->x || !c->y || !c->sigma || !c->dls_ds)
+    return fail(LENS_EINVAL, "constraints need nsrc >= 1 and non-NULL arrays");
+  if (c->img_off[0] != 0) return fail(LENS_EINVAL, "img_off[0] must be 0");
+  for (int32_t i = 0; i < c->nsrc; ++i) {
+    if (c->img_off[i + 1] < c->img_off[i]) return fail(LENS_EINVAL, "img_off must be non-decreasing");
+    if (!(std::isfinite(c->dls_ds[i]) && c->dls_ds[i] > 0.0)) return fail(LENS_EINVAL, "dls_ds[%d] must be > 0", i);
+  }
+  int32_t nimg = c->img_off[c->nsrc];
+  if (nimg < 1) return fail(LENS_EINVAL, "constraints hold no image");
+  for (int32_t j = 0; j < nimg; ++j)
+    if (!(std::isfinite(c->x[j]) && std::isfinite(c->y[j]) && std::isfinite(c->sigma[j]) && c->sigma[j] > 0.0))
+      return fail(LENS_EINVAL, "image %d: positions must be finite and sigma > 0", j);
+  if (var_halo[0] < 0 || var_halo[0] >= m->n || var_halo[1] < 0 || var_halo[1] >= m->n || var_halo[0] == var_halo[1])
+    return fail(LENS_EINVAL, "var_halo must be two distinct indices < n");
+  cudaSetDevice(ctx->device);
+  CSet *s = new CSet();
+  s->model = model;
+  s->nsrc = c->nsrc;
+  s->nimg = nimg;
+  s->var[0] = var_halo[0];
+  s->var[1] = var_halo[1];
+  std::vector<int32_t> src_of(nimg);
+  for (int32_t i = 0; i < c->nsrc; ++i)
+    for (int32_t j = c->img_off[i]; j < c->img_off[i + 1]; ++j) src_of[j] = i;
+  std::vector<double> vb(2 * REC64);
+  for (int k = 0; k < 2; ++k) {
+    const lens_halo &a = m->host[var_halo[k]];
+    s->var_type[k] = a.type;
+    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &vb[k * REC64]);
+  }
+  int rc;
+  if ((rc = dev_alloc(ctx, (void **)&s->img_off, (c->nsrc + 1) * sizeof(int32_t))) ||
+      (rc = dev_alloc(ctx, (void **)&s->src_of, nimg * sizeof(int32_t))) ||
+      (rc = dev_alloc(ctx, (void **)&s->x, nimg * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->y, nimg * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->sigma, nimg * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->ratio, c->nsrc * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->stat, (size_t)nimg * 5 * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->var_base, 2 * REC64 * sizeof(double)))) {
+    free_cset(ctx, s);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpy(s->img_off, c->img_off, (c->nsrc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->src_of, src_of.data(), nimg * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->x, c->x, nimg * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->y, c->y, nimg * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->sigma, c->sigma, nimg * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->ratio, c->dls_ds, c->nsrc * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->var_base, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_cset(ctx, s);
+    return fail(LENS_ECUDA, "constraint upload: %s", cudaGetErrorString(e));
+  }
+  if ((rc = build_static_cache(ctx, m, s))) {
+    free_cset(ctx, s);
+    return rc;
+  }
+  int64_t id = ctx->next_id++;
+  ctx->csets.push_back({id, s});
+  *out = id;
+  return LENS_OK;
+}
+
+int lens_cset_release(lens_ctx *ctx, lens_cset_t id) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  for (size_t k = 0; k < ctx->csets.size(); ++k)
+    if (ctx->csets[k].first == id) {
+      cudaSetDevice(ctx->device);
+      cudaDeviceSynchronize();
+      free_cset(ctx, ctx->csets[k].second);
+      ctx->csets.erase(ctx->csets.begin() + k);
+      return LENS_OK;
+    }
+  return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)id);
+}
+
+int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
+                     double *d_chi2, void *stream) {
+  if (!ctx || !d_params || !d_chi2) return fail(LENS_EINVAL, "NULL argument");
+  if (P < 1) return fail(LENS_EINVAL, "P must be >= 1");
+  if (variant < 0 || variant > 2) return fail(LENS_EINVAL, "variant must be 0, 1 or 2");
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  Model *m = find_model(ctx, c->model);
+  if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
+  cudaSetDevice(ctx->device);
+  return launch_chi2_source(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
+}
+
+int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
+                    double *d_chi2, int32_t *d_nimg_found, void *stream) {
+  if (!ctx || !d_params || !d_chi2) return fail(LENS_EINVAL, "NULL argument");
+  if (P < 1) return fail(LENS_EINVAL, "P must be >= 1");
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  Model *m = find_model(ctx, c->model);
+  if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
+  cudaSetDevice(ctx->device);
+  return launch_chi2_image(ctx, m, c, grid, d_params, P, d_chi2, d_nimg_found, (cudaStream_t)stream);
+}
+
+int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  if (timeout_ms < 0) return fail(LENS_EINVAL, "timeout_ms must be >= 0");
+  cudaSetDevice(ctx->device);
+  cudaEvent_t ev;
+  LENS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev);
+    return fail(LENS_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      cudaEventDestroy(ev);
+      return fail(LENS_ECUDA, "stream error: %s", cudaGetErrorString(e));
+    }
+    auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms) {
+      cudaEventDestroy(ev);
+      return fail(LENS_ETIMEOUT, "stream work not finished after %lld ms", (long long)timeout_ms);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  int flag = 0;
+  LENS_CUDA_TRY(cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return fail(LENS_ETIMEOUT, "a device-side bounded wait gave up (code %d)", flag);
+  }
+  return LENS_OK;
+}
+
+}  // extern "C"

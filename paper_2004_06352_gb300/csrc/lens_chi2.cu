@@ -1,0 +1,218 @@
+// Batched chi2 of multiple-image constraints (Sec. 2.2, Eq. 6, Fig. 3).
+//
+// Static cache: when a constraint set is bound to a model, the FP64
+// deflection and Hessian of every potential except the two varying ones are
+// summed at each constraint position once (one CTA per image, deterministic
+// tree reduction).  A parameter set then costs two FP64 potential
+// evaluations per image instead of N.
+//
+// Source-plane kernel: persistent CTAs loop over parameter sets; per set the
+// CTA rebuilds the two varying potentials, back-traces every image
+// (beta = theta - r alpha, Sec. 2.1 Eq. 1), forms each source's barycentre
+// and reduces the chi2 with warp shuffles in a fixed order.
+#include "lens_device.cuh"
+
+namespace lens {
+namespace {
+
+constexpr int CACHE_THREADS = 128;
+
+// Deterministic block sum of NV doubles per thread; result valid in thread 0.
+template <int NV, int THREADS>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_red[warp * NV + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += s_red[w * NV + k];
+      v[k] = s;
+    }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(CACHE_THREADS) k_static_cache(const double *__restrict__ all64, int n, int v0,
+                                                                int v1, const double *__restrict__ x,
+                                                                const double *__restrict__ y, double *stat) {
+  __shared__ double s_red[(CACHE_THREADS / 32) * 5];
+  const int img = blockIdx.x;
+  const double X = x[img], Y = y[img];
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int h = threadIdx.x; h < n; h += CACHE_THREADS) {
+    if (h == v0 || h == v1) continue;
+    double ax, ay, k, g1, g2;
+    eval64<true>(all64 + (size_t)h * REC64, X, Y, ax, ay, k, g1, g2);
+    v[0] += ax;
+    v[1] += ay;
+    v[2] += k;
+    v[3] += g1;
+    v[4] += g2;
+  }
+  block_sum<5, CACHE_THREADS>(v, s_red);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) stat[(size_t)img * 5 + k] = v[k];
+}
+
+struct Chi2SrcArgs {
+  const double *stat, *x, *y, *sigma, *ratio, *params;
+  const int32_t *img_off, *src_of;
+  int nsrc, nimg, P, variant;
+  int type0, type1;
+  double *chi2;
+};
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
+  extern __shared__ double sm[];
+  double *s_rec = sm;                    // [2][REC64]
+  double *s_beta = s_rec + 2 * REC64;    // [nimg][2]
+  double *s_m = s_beta + 2 * a.nimg;     // [nimg][3]: r hxx, r hyy, r hxy
+  double *s_bary = s_m + 3 * a.nimg;     // [nsrc][2]
+  double *s_red = s_bary + 2 * a.nsrc;   // [THREADS/32]
+  __shared__ int s_ok;
+  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
+    const double *q = a.params + (size_t)p * 14;
+    if (threadIdx.x < 2) {
+      const double *w = q + 7 * threadIdx.x;
+      const int type = threadIdx.x == 0 ? a.type0 : a.type1;
+      const bool ok = halo_params_ok(type, w[0], w[1], w[3], w[2], w[4], w[5], w[6]);
+      make_rec64(type, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rec + threadIdx.x * REC64);
+      if (threadIdx.x == 0) s_ok = 1;
+      __syncwarp(0x3u);
+      if (!ok) atomicAnd(&s_ok, 0);
+    }
+    __syncthreads();
+    if (!s_ok) {
+      if (threadIdx.x == 0) a.chi2[p] = __longlong_as_double(0x7ff8000000000000ll);
+      __syncthreads();
+      continue;
+    }
+    for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
+      const double X = a.x[j], Y = a.y[j];
+      const double *st = a.stat + (size_t)j * 5;
+      double ax = st[0], ay = st[1], kk = st[2], g1 = st[3], g2 = st[4];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        double bx, by, bk, b1, b2;
+        eval64<true>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
+        ax += bx;
+        ay += by;
+        kk += bk;
+        g1 += b1;
+        g2 += b2;
+      }
+      const double r = a.ratio[a.src_of[j]];
+      s_beta[2 * j] = X - r * ax;
+      s_beta[2 * j + 1] = Y - r * ay;
+      s_m[3 * j] = r * (kk + g1);
+      s_m[3 * j + 1] = r * (kk - g1);
+      s_m[3 * j + 2] = r * g2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.nsrc; i += THREADS) {
+      const int b = a.img_off[i], e = a.img_off[i + 1];
+      double sx = 0, sy = 0;
+      for (int j = b; j < e; ++j) {
+        sx += s_beta[2 * j];
+        sy += s_beta[2 * j + 1];
+      }
+      const int m = e - b;
+      s_bary[2 * i] = m > 0 ? sx / m : 0.0;
+      s_bary[2 * i + 1] = m > 0 ? sy / m : 0.0;
+    }
+    __syncthreads();
+    double acc[1] = {0.0};
+    for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
+      const int i = a.src_of[j];
+      const double dbx = s_bary[2 * i] - s_beta[2 * j], dby = s_bary[2 * i + 1] - s_beta[2 * j + 1];
+      const double s2 = a.sigma[j] * a.sigma[j];
+      if (a.variant == LENS_CHI2_SRC_PLAIN) {
+        acc[0] += (dbx * dbx + dby * dby) / s2;
+      } else {
+        // A^-1 = I - r H (Sec. 2.1 Eq. 4)
+        const double a11 = 1.0 - s_m[3 * j], a22 = 1.0 - s_m[3 * j + 1], a12 = -s_m[3 * j + 2];
+        const double det = a11 * a22 - a12 * a12;
+        if (a.variant == LENS_CHI2_SRC_MU) {
+          acc[0] += (dbx * dbx + dby * dby) * fabs(1.0 / det) / s2;
+        } else {
+          const double rx = (a22 * dbx - a12 * dby) / det, ry = (a11 * dby - a12 * dbx) / det;
+          acc[0] += (rx * rx + ry * ry) / s2;
+        }
+      }
+    }
+    block_sum<1, THREADS>(acc, s_red);
+    if (threadIdx.x == 0) a.chi2[p] = acc[0];
+  }
+}
+
+}  // namespace
+
+int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c) {
+  (void)ctx;
+  k_static_cache<<<c->nimg, CACHE_THREADS>>>(m->all64, m->n, c->var[0], c->var[1], c->x, c->y, c->stat);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "static cache: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                       int32_t variant, double *d_chi2, cudaStream_t st) {
+  (void)m;
+  constexpr int T = 128;
+  const size_t smem = sizeof(double) * (2 * REC64 + 5 * (size_t)c->nimg + 2 * (size_t)c->nsrc + T / 32);
+  if (smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_chi2_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  int per_sm = 0, nsm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chi2_source<T>, T, smem);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  int blocks = std::max(1, std::min(P, std::max(1, per_sm) * nsm));
+  Chi2SrcArgs a;
+  a.stat = c->stat;
+  a.x = c->x;
+  a.y = c->y;
+  a.sigma = c->sigma;
+  a.ratio = c->ratio;
+  a.params = d_params;
+  a.img_off = c->img_off;
+  a.src_of = c->src_of;
+  a.nsrc = c->nsrc;
+  a.nimg = c->nimg;
+  a.P = P;
+  a.variant = variant;
+  a.type0 = c->var_type[0];
+  a.type1 = c->var_type[1];
+  a.chi2 = d_chi2;
+  k_chi2_source<T><<<blocks, T, smem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "chi2 source launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
+                      double *d_chi2, int32_t *d_nfound, cudaStream_t st) {
+  (void)ctx;
+  (void)m;
+  (void)c;
+  (void)g;
+  (void)d_params;
+  (void)P;
+  (void)d_chi2;
+  (void)d_nfound;
+  (void)st;
+  return fail(LENS_EINVAL, "image-plane chi2 is not available in this build");
+}
+
+}  // namespace lens

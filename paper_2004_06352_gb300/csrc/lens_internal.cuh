@@ -1,0 +1,175 @@
+// Internal declarations of the GB300 lens library (not part of the C ABI).
+//
+// Device model store: every uploaded model keeps
+//   rec32  float  [n_light][32]  packed FP32 constants of the potentials
+//                                evaluated in FP32 (one 128-byte record per
+//                                potential; all threads of a CTA read the same
+//                                record, so a packed record is a broadcast)
+//   pos64  double [n_light][4]   x0, y0, cos(theta), sin(theta) in FP64: the
+//                                per-tile offsets of each potential are formed
+//                                from these in double precision
+//   heavy  double [n_heavy][16]  FP64 records of the potentials whose strength
+//                                b0 is at or above the FP64 threshold
+//   all64  double [n][16]        FP64 records of every potential, in upload
+//                                order (FP64 maps, chi2 static cache, Newton)
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cmath>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/lens.h"
+
+namespace lens {
+
+// ---------------------------------------------------------------- records
+// FP32 record (32 floats).  Kinds, stored as int bits in slot K_KIND.
+enum Kind32 : int { K32_DPIE = 0, K32_DPIE_SERIES = 1, K32_SIS = 2, K32_POINT = 3 };
+enum Rec32 : int {
+  R_C = 0, R_S, R_Q2, R_U2,          // rotation, q^2, u^2
+  R_KC, R_KT, R_SC, R_ST,            // q^2 sc^2, q^2 st^2, sc, st
+  R_Q2SS, R_DS, R_Q2SC, R_Q2ST,      // q^2 (st+sc), st-sc, q^2 sc, q^2 st
+  R_SS, R_Q2DS, R_KDC, R_KDT,        // st+sc, q^2 (st-sc), (1+q^2) sc^2, (1+q^2) st^2
+  R_2SC, R_2ST, R_U2SC2, R_U2ST2,    // 2 sc, 2 st, u^2 sc^2, u^2 st^2
+  R_AXS, R_AYS, R_KAPS, R_U,         // alpha_x scale, alpha_y scale, kappa scale, u
+  R_C1, R_C2, R_C3, R_C4,            // shear rotation by 2 theta with the scale folded in
+  R_KIND, R_B, R_PAD0, R_PAD1        // kind, SIS b / point-mass b^2
+};
+constexpr int REC32 = 32;
+
+// FP64 record (16 doubles).
+enum Kind64 : int { K64_DPIE = 0, K64_DPIE_SERIES = 1, K64_SIS = 2, K64_POINT = 3 };
+enum Rec64 : int {
+  D_X0 = 0, D_Y0, D_C, D_S, D_Q2, D_U, D_U2, D_BQ, D_SC, D_ST, D_DS, D_SS, D_C2T, D_S2T, D_KIND, D_B
+};
+constexpr int REC64 = 16;
+
+// u = sqrt(1 - q^2) below which the FP32 / FP64 paths use the series of
+// atan(w)/w and atanh(w)/w (|w| < u there; truncation below 5e-9 / 1e-24).
+constexpr double U_SERIES32 = 0.12;
+constexpr double U_SERIES64 = 1e-4;
+
+// Host + device: FP64 record from user parameters (shared by model upload
+// and by the chi2 kernels, which rebuild the varying potentials per set).
+__host__ __device__ inline void make_rec64(int type, double x0, double y0, double theta, double eps, double rcore,
+                                           double rcut, double b0, double *r) {
+  for (int k = 0; k < REC64; ++k) r[k] = 0.0;
+  r[D_X0] = x0;
+  r[D_Y0] = y0;
+  if (type == LENS_SIS || type == LENS_POINT) {
+    r[D_C] = 1.0;
+    r[D_KIND] = type == LENS_SIS ? K64_SIS : K64_POINT;
+    r[D_B] = type == LENS_SIS ? b0 : b0 * b0;
+    return;
+  }
+  double q = (1.0 - eps) / (1.0 + eps);
+  double u = 2.0 * sqrt(eps) / (1.0 + eps);
+  double b = b0 * (1.0 + eps);
+  double sc = rcore * (1.0 + eps), st = rcut * (1.0 + eps);
+  r[D_C] = cos(theta);
+  r[D_S] = sin(theta);
+  r[D_Q2] = q * q;
+  r[D_U] = u;
+  r[D_U2] = u * u;
+  r[D_BQ] = b * q;
+  r[D_SC] = sc;
+  r[D_ST] = st;
+  r[D_DS] = st - sc;
+  r[D_SS] = st + sc;
+  r[D_C2T] = cos(2.0 * theta);
+  r[D_S2T] = sin(2.0 * theta);
+  r[D_KIND] = u < U_SERIES64 ? K64_DPIE_SERIES : K64_DPIE;
+}
+
+// Host + device: are the parameters inside the model's domain?
+__host__ __device__ inline bool halo_params_ok(int type, double x0, double y0, double theta, double eps, double rcore,
+                                               double rcut, double b0) {
+  if (!(isfinite(x0) && isfinite(y0) && isfinite(theta) && isfinite(eps) && isfinite(rcore) && isfinite(rcut) &&
+        isfinite(b0)))
+    return false;
+  if (!(b0 > 0.0)) return false;
+  if (type == LENS_SIS || type == LENS_POINT) return true;
+  if (type != LENS_DPIE) return false;
+  return eps >= 0.0 && eps < 1.0 && rcore > 0.0 && rcut > rcore;
+}
+
+// ---------------------------------------------------------------- objects
+struct Model {
+  int32_t n = 0, n_light = 0, n_heavy = 0;
+  float *rec32 = nullptr;
+  double *pos64 = nullptr;
+  double *heavy = nullptr;
+  double *all64 = nullptr;
+  std::vector<lens_halo> host;
+  size_t bytes = 0;
+};
+
+struct GridCache {
+  double xmin, xmax, ymin, ymax;
+  int32_t nx, ny;
+  double *alpha_static = nullptr;  // [ny][nx][2] FP64, D_ls/D_s = 1, static potentials only
+  size_t bytes = 0;
+};
+
+struct CSet {
+  lens_model_t model = 0;
+  int32_t nsrc = 0, nimg = 0;
+  int32_t var[2] = {0, 0};
+  int32_t *img_off = nullptr;   // [nsrc+1]
+  int32_t *src_of = nullptr;    // [nimg]
+  double *x = nullptr, *y = nullptr, *sigma = nullptr;  // [nimg]
+  double *ratio = nullptr;      // [nsrc]
+  double *stat = nullptr;       // [nimg][5]: ax, ay, hxx, hyy, hxy of the static potentials (D_ls/D_s = 1)
+  double *var_base = nullptr;   // [2][16] FP64 records of the varying potentials' base types (type in D_KIND)
+  int32_t var_type[2] = {0, 0};
+  std::vector<GridCache> grids;
+  size_t bytes = 0;
+};
+
+}  // namespace lens
+
+struct lens_ctx {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  double fp64_threshold = 5.0;
+  int64_t next_id = 1;
+  std::vector<std::pair<int64_t, lens::Model *>> models;
+  std::vector<std::pair<int64_t, lens::CSet *>> csets;
+  int *d_err = nullptr;          // device-side error word (bounded waits)
+  void *scratch = nullptr;       // growable scratch for chi2 image search
+  size_t scratch_bytes = 0;
+};
+
+namespace lens {
+
+// Thread-local last error message.
+void set_error(const char *fmt, ...);
+int fail(int code, const char *fmt, ...);
+#define LENS_CUDA_TRY(call)                                                                              \
+  do {                                                                                                   \
+    cudaError_t e__ = (call);                                                                            \
+    if (e__ != cudaSuccess) return ::lens::fail(LENS_ECUDA, "%s: %s", #call, cudaGetErrorString(e__));   \
+  } while (0)
+
+Model *find_model(lens_ctx *ctx, lens_model_t id);
+CSet *find_cset(lens_ctx *ctx, lens_cset_t id);
+int dev_alloc(lens_ctx *ctx, void **p, size_t bytes);
+void dev_free(lens_ctx *ctx, void *p, size_t bytes);
+int ensure_scratch(lens_ctx *ctx, size_t bytes);
+int check_grid(const lens_grid *g);
+
+// Kernel launchers (lens_maps.cu / lens_chi2.cu).
+int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
+                     cudaStream_t st);
+int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
+                    cudaStream_t st);
+int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
+int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                       int32_t variant, double *d_chi2, cudaStream_t st);
+int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
+                      double *d_chi2, int32_t *d_nfound, cudaStream_t st);
+
+}  // namespace lens

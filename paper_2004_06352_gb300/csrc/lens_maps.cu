@@ -1,0 +1,391 @@
+// Map kernels: deflection (Sec. 4.1, Eq. 10) and deflection + Hessian maps
+// (Sec. 2.4, Eqs. 7-9; magnification Sec. 2.1, Eqs. 4-5) over a rectangular
+// grid with inclusive corners.
+//
+// LENS_MIXED kernel (the hot path):
+//   - CTA = 256 threads = 8 warps over a 32 x (8 KP) point tile; lane l owns
+//     column i0 + l, warp w owns rows j0 + w KP .. + KP-1, so every store of
+//     one row is 32 consecutive elements (one 128-byte segment per warp).
+//   - Potentials evaluated in FP32 are streamed through shared memory in
+//     chunks of CH packed 128-byte records by 1-D bulk copies (TMA,
+//     cp.async.bulk + mbarrier), double-buffered: the copy of chunk c+1 is in
+//     flight while chunk c is evaluated.  Every thread reads the same record
+//     at the same time (shared-memory broadcast).
+//   - Point positions relative to each potential: the tile origin minus the
+//     potential's centre is formed in FP64 once per (tile, potential) and
+//     kept as a hi/lo float pair; adding the thread's in-tile offset (also a
+//     hi/lo pair) reproduces dX, dY to FP32 relative precision even next to
+//     a potential's centre, before rotating into its frame.
+//   - FP32 contributions go into naive partial sums that are folded every
+//     SUB potentials into a Kahan-compensated total.
+//   - Potentials at or above the FP64 threshold (cluster-scale halos) are
+//     evaluated in FP64; the final sum, scaling by D_ls/D_s and the derived
+//     kappa/gamma/mu are formed in FP64 per point and stored as FP32.
+// LENS_FP64 kernel: one point per thread, every potential in FP64.
+#include "lens_device.cuh"
+
+namespace lens {
+namespace {
+
+constexpr int MAP_THREADS = 256;
+constexpr int MAP_WARPS = MAP_THREADS / 32;
+constexpr int CH = 64;   // potentials per staged chunk (8 KB of records)
+constexpr int SUB = 16;  // partial sums folded into the compensated total every SUB potentials
+
+struct MapArgs {
+  const float *rec32;
+  const double *pos64;
+  int n_light;
+  const double *heavy;
+  int n_heavy;
+  double xmin, ymin, dx, dy;
+  int nx, ny;
+  double dls;
+  float *out;
+  long long plane;
+  int *err;
+};
+
+template <bool HESS, int KP>
+struct Acc {
+  float ax[KP], ay[KP], k[KP], g1[KP], g2[KP];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < KP; ++i) ax[i] = ay[i] = k[i] = g1[i] = g2[i] = 0.f;
+  }
+};
+
+// Kahan step: (s, c) += v, true sum ~ s - c.
+__device__ __forceinline__ void kahan(float &s, float &c, float v) {
+  float y = v - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <bool HESS, int KP>
+__device__ __forceinline__ void fold(Acc<HESS, KP> &tot, Acc<HESS, KP> &cmp, Acc<HESS, KP> &part) {
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    kahan(tot.ax[i], cmp.ax[i], part.ax[i]);
+    kahan(tot.ay[i], cmp.ay[i], part.ay[i]);
+    if (HESS) {
+      kahan(tot.k[i], cmp.k[i], part.k[i]);
+      kahan(tot.g1[i], cmp.g1[i], part.g1[i]);
+      kahan(tot.g2[i], cmp.g2[i], part.g2[i]);
+    }
+  }
+  part.zero();
+}
+
+// One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the
+// potential's centre come from hi/lo float pairs (see Pos), then
+//   x = c dX + s dY,  y = c dY - s dX   (halo frame).
+template <bool HESS, int KP, bool SERIES>
+__device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
+                                       Acc<HESS, KP> &p) {
+  const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4], F = r4[5], G = r4[6];
+  const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
+  const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
+  const float q2sS = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
+  const float sS = D.x, q2dS = D.y;
+  const float axs = F.x, ays = F.y;
+  const float cdX = c * dX, sdX = s * dX;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const float x = fmaf(s, dY[k], cdX), y = fmaf(c, dY[k], -sdX);
+    const float x2 = x * x, y2 = y * y;
+    const float R = fmaf(q2, x2, y2);
+    const float pc2 = R + Kc, pt2 = R + Kt;
+    const float ic = rsqrt_a(pc2), it = rsqrt_a(pt2);
+    const float psc = pc2 * ic, pst = pt2 * it;
+    const float Sp = psc + pst;
+    const float Ec = psc + sc, Et = pst + st;
+    const float Zx = (x * dS) * (Sp + q2sS) * rcp_a(Sp * fmaf(u2, x2, Ec * Et));
+    const float Fc = psc + q2sc, Ft = pst + q2st;
+    const float Zy = (y * q2dS) * (Sp + sS) * rcp_a(Sp * fmaf(-u2, y2, Fc * Ft));
+    float axp, ayp;
+    if (SERIES) {
+      const float wx = u2 * Zx * Zx, wy = u2 * Zy * Zy;
+      axp = axs * Zx * fmaf(wx, fmaf(wx, fmaf(wx, -1.f / 7.f, 0.2f), -1.f / 3.f), 1.f);
+      ayp = ays * Zy * fmaf(wy, fmaf(wy, fmaf(wy, 1.f / 7.f, 0.2f), 1.f / 3.f), 1.f);
+    } else {
+      const float u = F.w;
+      axp = axs * atanf(u * Zx);
+      const float wy = u * Zy;
+      ayp = ays * log1pf((wy + wy) * rcp_a(1.f - wy));
+    }
+    p.ax[k] = fmaf(c, axp, fmaf(-s, ayp, p.ax[k]));
+    p.ay[k] = fmaf(s, axp, fmaf(c, ayp, p.ay[k]));
+    if (HESS) {
+      const float KDc = D.z, KDt = D.w, s2c = E.x, s2t = E.y, u2sc2 = E.z, u2st2 = E.w;
+      const float r2 = x2 + y2, ymx = y2 - x2;
+      const float Dc = fmaf(s2c, psc, r2 + KDc), Dt = fmaf(s2t, pst, r2 + KDt);
+      const float fc = rcp_a(psc * Dc), ft = rcp_a(pst * Dt);
+      const float g1d = fmaf(fc, ymx - u2sc2, -ft * (ymx - u2st2));
+      const float g2d = (fc - ft) * (x * y);
+      p.k[k] = fmaf(F.z, ic - it, p.k[k]);
+      p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
+      p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
+    }
+  }
+}
+
+// SIS / point mass (FP32): circular, evaluated directly on (dX, dY).
+template <bool HESS, int KP, bool POINT>
+__device__ __forceinline__ void circ32(const float4 *__restrict__ r4, float x, const float (&dY)[KP],
+                                       Acc<HESS, KP> &p) {
+  const float b = r4[7].y;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const float y = dY[k];
+    const float r2 = fmaf(x, x, y * y);
+    if (POINT) {
+      const float ir2 = r2 > 0.f ? rcp_a(r2) : 0.f;
+      const float f = b * ir2;
+      p.ax[k] = fmaf(f, x, p.ax[k]);
+      p.ay[k] = fmaf(f, y, p.ay[k]);
+      if (HESS) {
+        const float f2 = f * ir2;
+        p.g1[k] = fmaf(f2, (y - x) * (y + x), p.g1[k]);
+        p.g2[k] = fmaf(-2.f * f2, x * y, p.g2[k]);
+      }
+    } else {
+      const float ir = r2 > 0.f ? rsqrt_a(r2) : 0.f;
+      const float f = b * ir;
+      p.ax[k] = fmaf(f, x, p.ax[k]);
+      p.ay[k] = fmaf(f, y, p.ay[k]);
+      if (HESS) {
+        const float f3 = f * ir * ir;
+        p.k[k] = fmaf(0.5f, f, p.k[k]);
+        p.g1[k] = fmaf(0.5f * f3, (y - x) * (y + x), p.g1[k]);
+        p.g2[k] = fmaf(-f3, x * y, p.g2[k]);
+      }
+    }
+  }
+}
+
+template <bool HESS, int KP>
+__global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
+  __shared__ __align__(128) float s_rec[2][CH * REC32];
+  __shared__ float4 s_off[2][CH];  // hi.x, hi.y, lo.x, lo.y of (Tx - x0, Ty - y0)
+  __shared__ __align__(8) uint64_t s_bar[2];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * (MAP_WARPS * KP);
+  const double Tx = a.xmin + i0 * a.dx, Ty = a.ymin + j0 * a.dy;
+  // the point's offset inside the tile as a hi/lo float pair: (hi_off + hi_L)
+  // is exact when the point is near the potential's centre (Sterbenz), so
+  // dX, dY keep full relative precision where the profile is steepest
+  const double lx = lane * a.dx;
+  const float Lxh = (float)lx, Lxl = (float)(lx - (double)Lxh);
+  float Lyh[KP], Lyl[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const double ly = (warp * KP + k) * a.dy;
+    Lyh[k] = (float)ly;
+    Lyl[k] = (float)(ly - (double)Lyh[k]);
+  }
+
+  Acc<HESS, KP> tot, cmp, part;
+  tot.zero();
+  cmp.zero();
+  part.zero();
+
+  const int nch = (a.n_light + CH - 1) / CH;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0 && nch > 0) {
+    const int cnt = min(CH, a.n_light);
+    mbar_expect_tx(&s_bar[0], cnt * REC32 * 4);
+    bulk_g2s(&s_rec[0][0], a.rec32, cnt * REC32 * 4, &s_bar[0]);
+  }
+  // FP64 position data of the next chunk, prefetched into registers
+  double2 pxy = make_double2(0, 0), pcs = make_double2(1, 0);
+  if (tid < CH && tid < a.n_light) {
+    pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * tid];
+    pcs = reinterpret_cast<const double2 *>(a.pos64)[2 * tid + 1];
+  }
+
+  int seen = 0;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int buf = ch & 1;
+    const int base = ch * CH, cnt = min(CH, a.n_light - base);
+    if (tid < cnt) {
+      // tile origin rotated into the potential's frame, in FP64
+      const double dX = Tx - pxy.x, dY = Ty - pxy.y;
+      const float hx = (float)dX, hy = (float)dY;
+      s_off[buf][tid] = make_float4(hx, hy, (float)(dX - (double)hx), (float)(dY - (double)hy));
+    }
+    const bool ok = mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicExch(a.err, LENS_ERR_WAIT);
+        mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);  // let the copy in flight land before leaving
+      }
+      return;
+    }
+    if (ch + 1 < nch) {
+      if (tid == 0) {
+        fence_proxy_async();
+        const int ncnt = min(CH, a.n_light - base - CH);
+        mbar_expect_tx(&s_bar[buf ^ 1], ncnt * REC32 * 4);
+        bulk_g2s(&s_rec[buf ^ 1][0], a.rec32 + (size_t)(base + CH) * REC32, ncnt * REC32 * 4, &s_bar[buf ^ 1]);
+      }
+      if (tid < CH && base + CH + tid < a.n_light) {
+        pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * (base + CH + tid)];
+        pcs = reinterpret_cast<const double2 *>(a.pos64)[2 * (base + CH + tid) + 1];
+      }
+    }
+    const float4 *recs = reinterpret_cast<const float4 *>(&s_rec[buf][0]);
+    for (int h = 0; h < cnt; ++h) {
+      const float4 *r4 = recs + h * (REC32 / 4);
+      const float4 off = s_off[buf][h];
+      const float dX = (off.x + Lxh) + (off.z + Lxl);
+      float dY[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
+      const int kind = __float_as_int(r4[7].x);
+      if (kind == K32_DPIE)
+        dpie32<HESS, KP, false>(r4, dX, dY, part);
+      else if (kind == K32_DPIE_SERIES)
+        dpie32<HESS, KP, true>(r4, dX, dY, part);
+      else if (kind == K32_SIS)
+        circ32<HESS, KP, false>(r4, dX, dY, part);
+      else
+        circ32<HESS, KP, true>(r4, dX, dY, part);
+      if (++seen == SUB) {
+        fold(tot, cmp, part);
+        seen = 0;
+      }
+    }
+  }
+  fold(tot, cmp, part);
+
+  // FP64 potentials and the per-point epilogue
+  const int i = i0 + lane;
+  const double X = a.xmin + i * a.dx;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int j = j0 + warp * KP + k;
+    const double Y = a.ymin + j * a.dy;
+    double AX = (double)tot.ax[k] - (double)cmp.ax[k], AY = (double)tot.ay[k] - (double)cmp.ay[k];
+    double KA = 0, G1 = 0, G2 = 0;
+    if (HESS) {
+      KA = (double)tot.k[k] - (double)cmp.k[k];
+      G1 = (double)tot.g1[k] - (double)cmp.g1[k];
+      G2 = (double)tot.g2[k] - (double)cmp.g2[k];
+    }
+    for (int h = 0; h < a.n_heavy; ++h) {
+      double ax, ay, kk = 0, q1 = 0, q2 = 0;
+      eval64<HESS>(a.heavy + (size_t)h * REC64, X, Y, ax, ay, kk, q1, q2);
+      AX += ax;
+      AY += ay;
+      if (HESS) {
+        KA += kk;
+        G1 += q1;
+        G2 += q2;
+      }
+    }
+    if (i < a.nx && j < a.ny) {
+      const long long o = (long long)j * a.nx + i;
+      a.out[o] = (float)(a.dls * AX);
+      a.out[a.plane + o] = (float)(a.dls * AY);
+      if (HESS) {
+        const double kap = a.dls * KA, g1 = a.dls * G1, g2 = a.dls * G2;
+        const double det = (1.0 - kap) * (1.0 - kap) - g1 * g1 - g2 * g2;
+        a.out[2 * a.plane + o] = (float)kap;
+        a.out[3 * a.plane + o] = (float)g1;
+        a.out[4 * a.plane + o] = (float)g2;
+        a.out[5 * a.plane + o] = (float)(1.0 / det);
+      }
+    }
+  }
+}
+
+template <bool HESS>
+__global__ void __launch_bounds__(256) k_map_fp64(const double *__restrict__ all64, int n, double xmin, double ymin,
+                                                  double dx, double dy, int nx, int ny, double dls,
+                                                  double *__restrict__ out, long long plane) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= plane) return;
+  const int i = (int)(p % nx), j = (int)(p / nx);
+  const double X = xmin + i * dx, Y = ymin + j * dy;
+  double AX = 0, AY = 0, KA = 0, G1 = 0, G2 = 0;
+  for (int h = 0; h < n; ++h) {
+    double ax, ay, kk = 0, q1 = 0, q2 = 0;
+    eval64<HESS>(all64 + (size_t)h * REC64, X, Y, ax, ay, kk, q1, q2);
+    AX += ax;
+    AY += ay;
+    if (HESS) {
+      KA += kk;
+      G1 += q1;
+      G2 += q2;
+    }
+  }
+  out[p] = dls * AX;
+  out[plane + p] = dls * AY;
+  if (HESS) {
+    const double kap = dls * KA, g1 = dls * G1, g2 = dls * G2;
+    out[2 * plane + p] = kap;
+    out[3 * plane + p] = g1;
+    out[4 * plane + p] = g2;
+    out[5 * plane + p] = 1.0 / ((1.0 - kap) * (1.0 - kap) - g1 * g1 - g2 * g2);
+  }
+}
+
+}  // namespace
+
+int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
+                     cudaStream_t st) {
+  MapArgs a;
+  a.rec32 = m->rec32;
+  a.pos64 = m->pos64;
+  a.n_light = m->n_light;
+  a.heavy = m->heavy;
+  a.n_heavy = m->n_heavy;
+  a.xmin = g->xmin;
+  a.ymin = g->ymin;
+  a.dx = (g->xmax - g->xmin) / (g->nx - 1);
+  a.dy = (g->ymax - g->ymin) / (g->ny - 1);
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.dls = dls;
+  a.out = (float *)out;
+  a.plane = (long long)g->nx * g->ny;
+  a.err = ctx->d_err;
+  constexpr int KPG = 4, KPH = 2;
+  if (hess) {
+    dim3 grid((g->nx + 31) / 32, (g->ny + MAP_WARPS * KPH - 1) / (MAP_WARPS * KPH));
+    k_map_mixed<true, KPH><<<grid, MAP_THREADS, 0, st>>>(a);
+  } else {
+    dim3 grid((g->nx + 31) / 32, (g->ny + MAP_WARPS * KPG - 1) / (MAP_WARPS * KPG));
+    k_map_mixed<false, KPG><<<grid, MAP_THREADS, 0, st>>>(a);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "map kernel launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
+                    cudaStream_t st) {
+  (void)ctx;
+  const long long plane = (long long)g->nx * g->ny;
+  const double dx = (g->xmax - g->xmin) / (g->nx - 1), dy = (g->ymax - g->ymin) / (g->ny - 1);
+  const unsigned blocks = (unsigned)((plane + 255) / 256);
+  if (hess)
+    k_map_fp64<true><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, g->ny, dls,
+                                              (double *)out, plane);
+  else
+    k_map_fp64<false><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, g->ny, dls,
+                                               (double *)out, plane);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "map kernel launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+}  // namespace lens

@@ -65,8 +65,8 @@ def cfg2_model(seed=2, n_members=998):
 
     Members: log10(L/L*) ~ N(-0.5, 0.4) clipped to [-2, 0.7];
     b0 = 1.0"(L/L*)^1/2 (b0 ~ sigma^2, sigma ~ L^1/4), rcore = 0.15"(L/L*)^1/2,
-    rcut = 45"(L/L*)^1/2; centres Gaussian (40") about the origin clipped to
-    the field; eps U(0, 0.6); theta U(0, pi).
+    rcut = 8"(L/L*)^1/2 (~45 kpc at z ~ 0.5); centres Gaussian (40") about the
+    origin clipped to the field; eps U(0, 0.6); theta U(0, pi).
     """
     rng = np.random.default_rng(seed)
     rows = []
@@ -82,6 +82,19 @@ def cfg2_model(seed=2, n_members=998):
     for k in range(n_members):
         s = np.sqrt(l[k])
         rows.append(halo_row(DPIE, xy[k, 0], xy[k, 1], th[k], eps[k], 0.15 * s, 8.0 * s, 1.0 * s))
+    return np.stack(rows)
+
+
+def member_model(n, seed, field=60.0):
+    """n galaxy-scale dPIE halos on the luminosity scaling of cfg2_model
+    (b0 <= 2.3"), uniform centres in +/- field."""
+    rng = np.random.default_rng(seed)
+    l = 10.0 ** np.clip(rng.normal(-0.5, 0.4, n), -2.0, 0.7)
+    rows = []
+    for k in range(n):
+        s = np.sqrt(l[k])
+        x0, y0 = rng.uniform(-field, field, 2)
+        rows.append(halo_row(DPIE, x0, y0, rng.uniform(0, np.pi), rng.uniform(0, 0.6), 0.15 * s, 8.0 * s, s))
     return np.stack(rows)
 
 

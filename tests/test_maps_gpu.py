@@ -1,0 +1,159 @@
+"""GPU map parity against the FP64 oracle, through the C ABI.
+
+Small grids span several 32-wide tiles with ragged tails in x and y; the
+full-size 2048^2 / 1000-potential case is checked on sampled grid points in
+the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2004_06352_gb300 import inputs as I
+from tests import tolerances as T
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def run_map(lens, m, g, dls, precision, hess, threshold=None):
+    dt = torch.float32 if precision == lens.LENS_MIXED else torch.float64
+    with lens.Context(0) as ctx:
+        if threshold is not None:
+            ctx.set_fp64_threshold(threshold)
+        mid = ctx.model_upload(m)
+        out = torch.full((6 if hess else 2, g["ny"], g["nx"]), float("nan"), dtype=dt, device=DEV)
+        (ctx.hessian_map if hess else ctx.grad_map)(mid, g, dls, precision, out)
+        ctx.wait()
+        return out.cpu().numpy().astype(np.float64)
+
+
+def check_mixed(res, ref, hess):
+    bad, err, _ = T.alpha_violations(res[0], res[1], ref[0], ref[1])
+    n, msg = T.report("alpha", bad, err)
+    assert n == 0, msg
+    if hess:
+        badh = T.hess_violations(res[2], res[3], res[4], ref[2], ref[3], ref[4])
+        assert not badh.any(), T.report("kappa/gamma", badh)[1]
+        badm = T.mu_violations(res[5], ref[5])
+        assert not badm.any(), T.report("mu", badm)[1]
+
+
+def check_fp64(res, ref):
+    for k in range(res.shape[0] - (1 if res.shape[0] == 6 else 0)):
+        scale = np.maximum(np.abs(ref[k]), 1e-3 * np.abs(ref[k]).max() + 1e-300)
+        assert np.all(np.abs(res[k] - ref[k]) <= 1e-11 * scale), k
+    if res.shape[0] == 6:
+        det, rdet = 1 / res[5], 1 / ref[5]
+        assert np.all(np.abs(det - rdet) <= 1e-11 * np.maximum(1, np.abs(rdet)))
+
+
+def test_fp64_grad_map_cfg1(lens):
+    """The 256^2, 10-halo FP64 deflection map (plain FP64 GPU form)."""
+    m, g = I.cfg1_model(), I.grid(256)
+    res = run_map(lens, m, g, 0.7, lens.LENS_FP64, False)
+    check_fp64(res, oracle.maps(m, g, 0.7, 2))
+
+
+def test_fp64_hessian_map_mixed_types(lens):
+    m = I.random_model(37, seed=21, types=(I.DPIE, I.DPIE, I.SIS, I.POINT))
+    g = I.grid(71, field=(-65, 65, -50, 55), ny=43)
+    res = run_map(lens, m, g, 0.55, lens.LENS_FP64, True)
+    check_fp64(res, oracle.maps(m, g, 0.55, 6))
+
+
+@pytest.mark.parametrize("hess", [False, True])
+def test_mixed_map_ragged_tiles_all_kinds(lens, hess):
+    """Several tiles, ragged in x and y; dPIE (incl. eps = 0 and the series
+    branch), SIS, point mass, cluster-scale potentials on the FP64 path, and a
+    light-potential count that is not a multiple of the chunk or fold size."""
+    m = I.random_model(203, seed=22, types=(I.DPIE, I.DPIE, I.DPIE, I.SIS, I.POINT))
+    m[0, 4], m[1, 4], m[2, 4] = 0.0, 1e-6, 0.002   # eps = 0, tiny, series branch
+    m[5, 7], m[10, 7] = 28.0, 17.0                 # FP64 path
+    g = I.grid(101, field=(-80, 80, -70, 75), ny=77)
+    res = run_map(lens, m, g, 0.8, lens.LENS_MIXED, hess)
+    check_mixed(res, oracle.maps(m, g, 0.8, 6 if hess else 2), hess)
+
+
+def test_mixed_map_all_heavy_and_all_light(lens):
+    """Threshold 0 puts every potential on the FP64 path; an infinite one puts
+    every potential on the FP32 path (galaxy-scale halos, the class the FP32
+    path is meant for)."""
+    g = I.grid(40, field=(-50, 50, -50, 50))
+    m = I.random_model(9, seed=23)
+    check_mixed(run_map(lens, m, g, 1.0, lens.LENS_MIXED, True, threshold=0.0), oracle.maps(m, g, 1.0, 6), True)
+    m = I.member_model(150, seed=25, field=50)
+    check_mixed(run_map(lens, m, g, 1.0, lens.LENS_MIXED, True, threshold=1e9), oracle.maps(m, g, 1.0, 6), True)
+
+
+def test_mixed_map_single_halo_and_minimal_grid(lens):
+    m = I.halo_row(I.DPIE, 0.3, -0.2, 0.4, 0.35, 0.5, 30.0, 2.0)[None]
+    for g in (I.grid(2, field=(-1, 1, -1, 1)), I.grid(33, field=(-10, 10, -3, 3), ny=2)):
+        check_mixed(run_map(lens, m, g, 0.9, lens.LENS_MIXED, True), oracle.maps(m, g, 0.9, 6), True)
+
+
+def test_point_on_sis_and_point_mass_centre(lens):
+    """Grid nodes exactly on an SIS / point-mass centre get zero from it."""
+    m = np.vstack([I.halo_row(I.SIS, 0.0, 0.0, 0, 0, 0, 0, 1.5),
+                   I.halo_row(I.POINT, 5.0, 5.0, 0, 0, 0, 0, 1.0),
+                   I.halo_row(I.DPIE, 2.0, -3.0, 0.2, 0.3, 0.4, 20.0, 2.0)])
+    g = I.grid(21, field=(-10, 10, -10, 10))
+    for prec in (lens.LENS_MIXED, lens.LENS_FP64):
+        res = run_map(lens, m, g, 1.0, prec, True)
+        assert np.all(np.isfinite(res[:5]))
+    check_mixed(run_map(lens, m, g, 1.0, lens.LENS_MIXED, True), oracle.maps(m, g, 1.0, 6), True)
+
+
+def test_full_size_cfg2_sampled(lens):
+    """2048^2 grid, 1000 potentials (2 cluster + 998 members), the benchmark's
+    launch; 12k sampled grid nodes compared with the oracle."""
+    m, g = I.cfg2_model(), I.grid(2048)
+    res = torch.from_numpy(run_map(lens, m, g, 1.0, lens.LENS_MIXED, True))
+    rng = np.random.default_rng(24)
+    n = 12000
+    ii, jj = rng.integers(0, 2048, n), rng.integers(0, 2048, n)
+    ii[:4], jj[:4] = [0, 2047, 0, 2047], [0, 0, 2047, 2047]  # corners
+    dx = 200.0 / 2047
+    X, Y = -100.0 + ii * dx, -100.0 + jj * dx
+    ev = oracle.model_eval(m, X, Y, 1.0)
+    ref = np.stack([ev[:, 0], ev[:, 1], 0.5 * (ev[:, 2] + ev[:, 3]), 0.5 * (ev[:, 2] - ev[:, 3]), ev[:, 4]])
+    det = (1 - ref[2]) ** 2 - ref[3] ** 2 - ref[4] ** 2
+    ref = np.vstack([ref, 1 / det])
+    got = res[:, jj, ii].numpy()
+    check_mixed(got, ref, True)
+
+
+def test_invalid_inputs_rejected(lens):
+    with lens.Context(0) as ctx:
+        bad = [I.halo_row(I.DPIE, 0, 0, 0, 1.0, 1, 10, 1),      # eps = 1
+               I.halo_row(I.DPIE, 0, 0, 0, 0.2, 10, 5, 1),      # rcut < rcore
+               I.halo_row(I.DPIE, 0, 0, 0, 0.2, 0, 5, 1),       # rcore = 0
+               I.halo_row(I.SIS, 0, 0, 0, 0, 0, 0, -1),         # b0 < 0
+               I.halo_row(7, 0, 0, 0, 0, 0, 0, 1),              # type
+               I.halo_row(I.DPIE, np.nan, 0, 0, 0.2, 1, 5, 1)]  # NaN
+        for row in bad:
+            with pytest.raises(lens.LensError) as e:
+                ctx.model_upload(row[None])
+            assert e.value.code == lens.LENS_EINVAL
+        mid = ctx.model_upload(I.random_model(3, seed=1))
+        out = torch.empty((2, 4, 4), device=DEV)
+        for g in (dict(xmin=0, xmax=1, ymin=0, ymax=1, nx=1, ny=4), dict(xmin=1, xmax=0, ymin=0, ymax=1, nx=4, ny=4),
+                  dict(xmin=0, xmax=np.inf, ymin=0, ymax=1, nx=4, ny=4)):
+            with pytest.raises(lens.LensError) as e:
+                ctx.grad_map(mid, g, 1.0, lens.LENS_MIXED, out)
+            assert e.value.code == lens.LENS_EINVAL
+        with pytest.raises(lens.LensError) as e:
+            ctx.grad_map(mid + 99, I.grid(4), 1.0, lens.LENS_MIXED, out)
+        assert e.value.code == lens.LENS_ENOTFOUND
+        with pytest.raises(lens.LensError) as e:
+            ctx.grad_map(mid, I.grid(4), -1.0, lens.LENS_MIXED, out)
+        assert e.value.code == lens.LENS_EINVAL
+
+
+def test_memory_budget_admission(lens):
+    with lens.Context(0, mem_budget_bytes=64 * 1024) as ctx:
+        ctx.model_upload(I.random_model(10, seed=2))
+        with pytest.raises(lens.LensError) as e:
+            ctx.model_upload(I.random_model(2000, seed=3))
+        assert e.value.code == lens.LENS_ENOMEM
