@@ -82,55 +82,6 @@ int check_grid(const lens_grid *g) {
   return LENS_OK;
 }
 
-// FP32 record of one potential (host, from FP64 arithmetic).
-static void make_rec32(const lens_halo &h, float *r) {
-  for (int k = 0; k < REC32; ++k) r[k] = 0.f;
-  int kind;
-  if (h.type == LENS_SIS || h.type == LENS_POINT) {
-    r[R_C] = 1.f;
-    kind = h.type == LENS_SIS ? K32_SIS : K32_POINT;
-    r[R_B] = (float)(h.type == LENS_SIS ? h.b0 : h.b0 * h.b0);
-  } else {
-    double e = h.eps;
-    double q = (1.0 - e) / (1.0 + e), u = 2.0 * std::sqrt(e) / (1.0 + e);
-    double q2 = q * q, u2 = u * u;
-    double b = h.b0 * (1.0 + e), bq = b * q;
-    double sc = h.rcore * (1.0 + e), st = h.rcut * (1.0 + e);
-    double c2 = std::cos(2.0 * h.theta), s2 = std::sin(2.0 * h.theta);
-    bool series = u < U_SERIES32;
-    kind = series ? K32_DPIE_SERIES : K32_DPIE;
-    r[R_C] = (float)std::cos(h.theta);
-    r[R_S] = (float)std::sin(h.theta);
-    r[R_Q2] = (float)q2;
-    r[R_U2] = (float)u2;
-    r[R_KC] = (float)(q2 * sc * sc);
-    r[R_KT] = (float)(q2 * st * st);
-    r[R_SC] = (float)sc;
-    r[R_ST] = (float)st;
-    r[R_Q2SS] = (float)(q2 * (st + sc));
-    r[R_DS] = (float)(st - sc);
-    r[R_Q2SC] = (float)(q2 * sc);
-    r[R_Q2ST] = (float)(q2 * st);
-    r[R_SS] = (float)(st + sc);
-    r[R_Q2DS] = (float)(q2 * (st - sc));
-    r[R_KDC] = (float)((1.0 + q2) * sc * sc);
-    r[R_KDT] = (float)((1.0 + q2) * st * st);
-    r[R_2SC] = (float)(2.0 * sc);
-    r[R_2ST] = (float)(2.0 * st);
-    r[R_U2SC2] = (float)(u2 * sc * sc);
-    r[R_U2ST2] = (float)(u2 * st * st);
-    r[R_AXS] = (float)(series ? bq : bq / u);
-    r[R_AYS] = (float)(series ? bq : bq / (2.0 * u));
-    r[R_KAPS] = (float)(0.5 * bq);
-    r[R_U] = (float)u;
-    r[R_C1] = (float)(c2 * 0.5 * bq);
-    r[R_C2] = (float)(s2 * bq);
-    r[R_C3] = (float)(s2 * 0.5 * bq);
-    r[R_C4] = (float)(-c2 * bq);
-  }
-  std::memcpy(&r[R_KIND], &kind, sizeof(int));
-}
-
 static int kind_order(const lens_halo &h) {
   if (h.type == LENS_SIS) return 2;
   if (h.type == LENS_POINT) return 3;
@@ -138,12 +89,73 @@ static int kind_order(const lens_halo &h) {
   return u < U_SERIES32 ? 1 : 0;
 }
 
-static void free_model(lens_ctx *ctx, Model *m) {
+void free_model(lens_ctx *ctx, Model *m) {
   dev_free(ctx, m->rec32, (size_t)m->n_light * REC32 * sizeof(float));
   dev_free(ctx, m->pos64, (size_t)m->n_light * 4 * sizeof(double));
+  dev_free(ctx, m->cen32, (size_t)m->n_light * 4 * sizeof(float));
   dev_free(ctx, m->heavy, (size_t)m->n_heavy * REC64 * sizeof(double));
   dev_free(ctx, m->all64, (size_t)m->n * REC64 * sizeof(double));
   delete m;
+}
+
+// Device store of n (already validated) potentials; n may be 0.
+int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
+  Model *m = new Model();
+  m->n = n;
+  m->host.assign(h, h + n);
+  // light potentials grouped by kind so each warp-uniform branch runs in one stretch
+  std::vector<int32_t> light, heavy;
+  for (int32_t i = 0; i < n; ++i) (h[i].b0 >= ctx->fp64_threshold ? heavy : light).push_back(i);
+  std::stable_sort(light.begin(), light.end(),
+                   [&](int32_t a, int32_t b) { return kind_order(h[a]) < kind_order(h[b]); });
+  m->n_light = (int32_t)light.size();
+  m->n_heavy = (int32_t)heavy.size();
+  std::vector<float> r32((size_t)m->n_light * REC32), c32((size_t)m->n_light * 4);
+  std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
+  for (int32_t k = 0; k < m->n_light; ++k) {
+    const lens_halo &a = h[light[k]];
+    make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, &r32[(size_t)k * REC32]);
+    bool circ = a.type != LENS_DPIE;
+    p64[4 * k + 0] = a.x0;
+    p64[4 * k + 1] = a.y0;
+    p64[4 * k + 2] = circ ? 1.0 : std::cos(a.theta);
+    p64[4 * k + 3] = circ ? 0.0 : std::sin(a.theta);
+    float xh = (float)a.x0, yh = (float)a.y0;
+    c32[4 * k + 0] = xh;
+    c32[4 * k + 1] = yh;
+    c32[4 * k + 2] = (float)(a.x0 - (double)xh);
+    c32[4 * k + 3] = (float)(a.y0 - (double)yh);
+  }
+  for (int32_t k = 0; k < m->n_heavy; ++k) {
+    const lens_halo &a = h[heavy[k]];
+    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &hv[(size_t)k * REC64]);
+  }
+  for (int32_t k = 0; k < n; ++k) {
+    const lens_halo &a = h[k];
+    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
+  }
+  int rc = LENS_OK;
+  size_t b32 = r32.size() * sizeof(float), bp = p64.size() * sizeof(double), bc = c32.size() * sizeof(float),
+         bh = hv.size() * sizeof(double), ba = a64.size() * sizeof(double);
+  if ((rc = dev_alloc(ctx, (void **)&m->rec32, b32)) || (rc = dev_alloc(ctx, (void **)&m->pos64, bp)) ||
+      (rc = dev_alloc(ctx, (void **)&m->cen32, bc)) || (rc = dev_alloc(ctx, (void **)&m->heavy, bh)) ||
+      (rc = dev_alloc(ctx, (void **)&m->all64, ba))) {
+    free_model(ctx, m);
+    return rc;
+  }
+  m->bytes = b32 + bp + bc + bh + ba;
+  cudaError_t e = cudaSuccess;
+  if (b32) e = cudaMemcpy(m->rec32, r32.data(), b32, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bp) e = cudaMemcpy(m->pos64, p64.data(), bp, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bc) e = cudaMemcpy(m->cen32, c32.data(), bc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bh) e = cudaMemcpy(m->heavy, hv.data(), bh, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && ba) e = cudaMemcpy(m->all64, a64.data(), ba, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_model(ctx, m);
+    return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));
+  }
+  *out = m;
+  return LENS_OK;
 }
 
 static void free_cset(lens_ctx *ctx, CSet *c) {
@@ -155,7 +167,11 @@ static void free_cset(lens_ctx *ctx, CSet *c) {
   dev_free(ctx, c->ratio, c->nsrc * sizeof(double));
   dev_free(ctx, c->stat, (size_t)c->nimg * 5 * sizeof(double));
   dev_free(ctx, c->var_base, 2 * REC64 * sizeof(double));
-  for (auto &g : c->grids) dev_free(ctx, g.alpha_static, g.bytes);
+  dev_free(ctx, c->grp_off, (c->ng + 1) * sizeof(int32_t));
+  dev_free(ctx, c->grp_src, c->nsrc * sizeof(int32_t));
+  dev_free(ctx, c->grp_ratio, c->ng * sizeof(double));
+  for (auto &g : c->grids) dev_free(ctx, g.alpha32, g.bytes);
+  if (c->stat_model) free_model(ctx, c->stat_model);
   delete c;
 }
 
@@ -233,52 +249,9 @@ int lens_model_upload(lens_ctx *ctx, const lens_halo *h, int32_t n, lens_model_t
                   i, a.type, a.eps, a.rcore, a.rcut, a.b0);
   }
   cudaSetDevice(ctx->device);
-  Model *m = new Model();
-  m->n = n;
-  m->host.assign(h, h + n);
-  // light potentials grouped by kind so each warp-uniform branch runs in one stretch
-  std::vector<int32_t> light, heavy;
-  for (int32_t i = 0; i < n; ++i) (h[i].b0 >= ctx->fp64_threshold ? heavy : light).push_back(i);
-  std::stable_sort(light.begin(), light.end(), [&](int32_t a, int32_t b) { return kind_order(h[a]) < kind_order(h[b]); });
-  m->n_light = (int32_t)light.size();
-  m->n_heavy = (int32_t)heavy.size();
-  std::vector<float> r32((size_t)m->n_light * REC32);
-  std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
-  for (int32_t k = 0; k < m->n_light; ++k) {
-    const lens_halo &a = h[light[k]];
-    make_rec32(a, &r32[(size_t)k * REC32]);
-    bool circ = a.type != LENS_DPIE;
-    p64[4 * k + 0] = a.x0;
-    p64[4 * k + 1] = a.y0;
-    p64[4 * k + 2] = circ ? 1.0 : std::cos(a.theta);
-    p64[4 * k + 3] = circ ? 0.0 : std::sin(a.theta);
-  }
-  for (int32_t k = 0; k < m->n_heavy; ++k) {
-    const lens_halo &a = h[heavy[k]];
-    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &hv[(size_t)k * REC64]);
-  }
-  for (int32_t k = 0; k < n; ++k) {
-    const lens_halo &a = h[k];
-    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
-  }
-  int rc = LENS_OK;
-  size_t b32 = r32.size() * sizeof(float), bp = p64.size() * sizeof(double), bh = hv.size() * sizeof(double),
-         ba = a64.size() * sizeof(double);
-  if ((rc = dev_alloc(ctx, (void **)&m->rec32, b32)) || (rc = dev_alloc(ctx, (void **)&m->pos64, bp)) ||
-      (rc = dev_alloc(ctx, (void **)&m->heavy, bh)) || (rc = dev_alloc(ctx, (void **)&m->all64, ba))) {
-    free_model(ctx, m);
-    return rc;
-  }
-  m->bytes = b32 + bp + bh + ba;
-  cudaError_t e = cudaSuccess;
-  if (b32) e = cudaMemcpy(m->rec32, r32.data(), b32, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bp) e = cudaMemcpy(m->pos64, p64.data(), bp, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bh) e = cudaMemcpy(m->heavy, hv.data(), bh, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->all64, a64.data(), ba, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    free_model(ctx, m);
-    return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));
-  }
+  Model *m = nullptr;
+  int rc = build_model(ctx, h, n, &m);
+  if (rc) return rc;
   int64_t id = ctx->next_id++;
   ctx->models.push_back({id, m});
   *out = id;
@@ -392,6 +365,35 @@ int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *
     free_cset(ctx, s);
     return fail(LENS_ECUDA, "constraint upload: %s", cudaGetErrorString(e));
   }
+  // sources grouped by distance ratio (the image search ray-shoots the grid
+  // once per distinct ratio), and the model without the varying potentials
+  std::vector<double> ratios(c->dls_ds, c->dls_ds + c->nsrc);
+  std::sort(ratios.begin(), ratios.end());
+  ratios.erase(std::unique(ratios.begin(), ratios.end()), ratios.end());
+  s->ng = (int32_t)ratios.size();
+  std::vector<int32_t> goff(s->ng + 1, 0), gsrc;
+  for (int32_t g = 0; g < s->ng; ++g) {
+    for (int32_t i = 0; i < c->nsrc; ++i)
+      if (c->dls_ds[i] == ratios[g]) gsrc.push_back(i);
+    goff[g + 1] = (int32_t)gsrc.size();
+  }
+  std::vector<lens_halo> stat_h;
+  for (int32_t k = 0; k < m->n; ++k)
+    if (k != var_halo[0] && k != var_halo[1]) stat_h.push_back(m->host[k]);
+  if ((rc = dev_alloc(ctx, (void **)&s->grp_off, (s->ng + 1) * sizeof(int32_t))) ||
+      (rc = dev_alloc(ctx, (void **)&s->grp_src, c->nsrc * sizeof(int32_t))) ||
+      (rc = dev_alloc(ctx, (void **)&s->grp_ratio, s->ng * sizeof(double))) ||
+      (rc = build_model(ctx, stat_h.data(), (int32_t)stat_h.size(), &s->stat_model))) {
+    free_cset(ctx, s);
+    return rc;
+  }
+  e = cudaMemcpy(s->grp_off, goff.data(), goff.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->grp_src, gsrc.data(), gsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->grp_ratio, ratios.data(), ratios.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_cset(ctx, s);
+    return fail(LENS_ECUDA, "constraint upload: %s", cudaGetErrorString(e));
+  }
   if ((rc = build_static_cache(ctx, m, s))) {
     free_cset(ctx, s);
     return rc;
@@ -473,7 +475,8 @@ int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms) {
   LENS_CUDA_TRY(cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
-    return fail(LENS_ETIMEOUT, "a device-side bounded wait gave up (code %d)", flag);
+    if (flag & ERRBIT_WAIT) return fail(LENS_ETIMEOUT, "a device-side bounded wait gave up");
+    return fail(LENS_ECAPACITY, "an image buffer overflowed; the affected chi2 values are NaN");
   }
   return LENS_OK;
 }

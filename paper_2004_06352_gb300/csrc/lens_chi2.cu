@@ -17,28 +17,6 @@ namespace {
 
 constexpr int CACHE_THREADS = 128;
 
-// Deterministic block sum of NV doubles per thread; result valid in thread 0.
-template <int NV, int THREADS>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double *s_red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) s_red[warp * NV + k] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < THREADS / 32; ++w) s += s_red[w * NV + k];
-      v[k] = s;
-    }
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(CACHE_THREADS) k_static_cache(const double *__restrict__ all64, int n, int v0,
                                                                 int v1, const double *__restrict__ x,
                                                                 const double *__restrict__ y, double *stat) {
@@ -80,55 +58,17 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
   __shared__ int s_ok;
   for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
     const double *q = a.params + (size_t)p * 14;
-    if (threadIdx.x < 2) {
-      const double *w = q + 7 * threadIdx.x;
-      const int type = threadIdx.x == 0 ? a.type0 : a.type1;
-      const bool ok = halo_params_ok(type, w[0], w[1], w[3], w[2], w[4], w[5], w[6]);
-      make_rec64(type, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rec + threadIdx.x * REC64);
-      if (threadIdx.x == 0) s_ok = 1;
-      __syncwarp(0x3u);
-      if (!ok) atomicAnd(&s_ok, 0);
-    }
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    if (threadIdx.x < 2 && !load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
     __syncthreads();
     if (!s_ok) {
       if (threadIdx.x == 0) a.chi2[p] = __longlong_as_double(0x7ff8000000000000ll);
       __syncthreads();
       continue;
     }
-    for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
-      const double X = a.x[j], Y = a.y[j];
-      const double *st = a.stat + (size_t)j * 5;
-      double ax = st[0], ay = st[1], kk = st[2], g1 = st[3], g2 = st[4];
-#pragma unroll
-      for (int v = 0; v < 2; ++v) {
-        double bx, by, bk, b1, b2;
-        eval64<true>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
-        ax += bx;
-        ay += by;
-        kk += bk;
-        g1 += b1;
-        g2 += b2;
-      }
-      const double r = a.ratio[a.src_of[j]];
-      s_beta[2 * j] = X - r * ax;
-      s_beta[2 * j + 1] = Y - r * ay;
-      s_m[3 * j] = r * (kk + g1);
-      s_m[3 * j + 1] = r * (kk - g1);
-      s_m[3 * j + 2] = r * g2;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < a.nsrc; i += THREADS) {
-      const int b = a.img_off[i], e = a.img_off[i + 1];
-      double sx = 0, sy = 0;
-      for (int j = b; j < e; ++j) {
-        sx += s_beta[2 * j];
-        sy += s_beta[2 * j + 1];
-      }
-      const int m = e - b;
-      s_bary[2 * i] = m > 0 ? sx / m : 0.0;
-      s_bary[2 * i + 1] = m > 0 ? sy / m : 0.0;
-    }
-    __syncthreads();
+    backtrace_set<THREADS>(a.stat, a.x, a.y, a.ratio, a.src_of, a.img_off, a.nimg, a.nsrc, s_rec, s_beta,
+                           a.variant == LENS_CHI2_SRC_PLAIN ? nullptr : s_m, s_bary);
     double acc[1] = {0.0};
     for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
       const int i = a.src_of[j];
@@ -199,20 +139,6 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "chi2 source launch: %s", cudaGetErrorString(e));
   return LENS_OK;
-}
-
-int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
-                      double *d_chi2, int32_t *d_nfound, cudaStream_t st) {
-  (void)ctx;
-  (void)m;
-  (void)c;
-  (void)g;
-  (void)d_params;
-  (void)P;
-  (void)d_chi2;
-  (void)d_nfound;
-  (void)st;
-  return fail(LENS_EINVAL, "image-plane chi2 is not available in this build");
 }
 
 }  // namespace lens

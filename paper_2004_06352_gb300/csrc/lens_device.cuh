@@ -8,9 +8,9 @@
 namespace lens {
 
 // Bound on any spin on an mbarrier: ~2^24 try_wait polls (seconds), after
-// which the kernel records LENS_ERR_WAIT and leaves instead of hanging.
+// which the kernel sets ERRBIT_WAIT in the context's error word and leaves
+// instead of hanging.
 constexpr unsigned WAIT_LIMIT = 1u << 24;
-constexpr int LENS_ERR_WAIT = 1;
 
 __device__ __forceinline__ float rcp_a(float x) {
   float y;
@@ -133,6 +133,266 @@ __device__ __forceinline__ void eval64(const double *__restrict__ r, double X, d
     g1 = c2 * g1p - s2 * g2p;
     g2 = s2 * g1p + c2 * g2p;
   }
+}
+
+
+// ----------------------------------------------------------------- FP32 path
+template <bool HESS, int KP>
+struct Acc {
+  float ax[KP], ay[KP], k[KP], g1[KP], g2[KP];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < KP; ++i) ax[i] = ay[i] = k[i] = g1[i] = g2[i] = 0.f;
+  }
+};
+
+// Kahan step: (s, c) += v, true sum ~ s - c.
+__device__ __forceinline__ void kahan(float &s, float &c, float v) {
+  float y = v - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <bool HESS, int KP>
+__device__ __forceinline__ void fold(Acc<HESS, KP> &tot, Acc<HESS, KP> &cmp, Acc<HESS, KP> &part) {
+#pragma unroll
+  for (int i = 0; i < KP; ++i) {
+    kahan(tot.ax[i], cmp.ax[i], part.ax[i]);
+    kahan(tot.ay[i], cmp.ay[i], part.ay[i]);
+    if (HESS) {
+      kahan(tot.k[i], cmp.k[i], part.k[i]);
+      kahan(tot.g1[i], cmp.g1[i], part.g1[i]);
+      kahan(tot.g2[i], cmp.g2[i], part.g2[i]);
+    }
+  }
+  part.zero();
+}
+
+// atan(w)/w and atanh(w)/w as Maclaurin series in t = w^2,
+//   atan(w)/w  = sum_k (-1)^k t^k / (2k+1),   atanh(w)/w = sum_k t^k / (2k+1),
+// ten terms (Horner, FMA).  For t < T_SERIES = 0.16 the first dropped term is
+// below 0.16^10/21 = 5e-10, under half an FP32 ulp.
+constexpr float T_SERIES = 0.16f;
+__device__ __forceinline__ float atan_over_w(float t) {
+  float p = -1.f / 19.f;
+  p = fmaf(p, t, 1.f / 17.f);
+  p = fmaf(p, t, -1.f / 15.f);
+  p = fmaf(p, t, 1.f / 13.f);
+  p = fmaf(p, t, -1.f / 11.f);
+  p = fmaf(p, t, 1.f / 9.f);
+  p = fmaf(p, t, -1.f / 7.f);
+  p = fmaf(p, t, 1.f / 5.f);
+  p = fmaf(p, t, -1.f / 3.f);
+  return fmaf(p, t, 1.f);
+}
+__device__ __forceinline__ float atanh_over_w(float t) {
+  float p = 1.f / 19.f;
+  p = fmaf(p, t, 1.f / 17.f);
+  p = fmaf(p, t, 1.f / 15.f);
+  p = fmaf(p, t, 1.f / 13.f);
+  p = fmaf(p, t, 1.f / 11.f);
+  p = fmaf(p, t, 1.f / 9.f);
+  p = fmaf(p, t, 1.f / 7.f);
+  p = fmaf(p, t, 1.f / 5.f);
+  p = fmaf(p, t, 1.f / 3.f);
+  return fmaf(p, t, 1.f);
+}
+
+// One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the
+// potential's centre are formed by the caller from hi/lo float pairs, then
+//   x = c dX + s dY,  y = c dY - s dX   (halo frame).
+template <bool HESS, int KP, bool SERIES>
+__device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
+                                       Acc<HESS, KP> &p) {
+  const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4], F = r4[5], G = r4[6];
+  const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
+  const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
+  const float q2sS = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
+  const float sS = D.x, q2dS = D.y;
+  const float axs = F.x, ays = F.y;
+  const float cdX = c * dX, sdX = s * dX;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const float x = fmaf(s, dY[k], cdX), y = fmaf(c, dY[k], -sdX);
+    const float x2 = x * x, y2 = y * y;
+    const float R = fmaf(q2, x2, y2);
+    const float pc2 = R + Kc, pt2 = R + Kt;
+    const float ic = rsqrt_a(pc2), it = rsqrt_a(pt2);
+    const float psc = pc2 * ic, pst = pt2 * it;
+    const float Sp = psc + pst;
+    const float Ec = psc + sc, Et = pst + st;
+    const float Zx = (x * dS) * (Sp + q2sS) * rcp_a(Sp * fmaf(u2, x2, Ec * Et));
+    const float Fc = psc + q2sc, Ft = pst + q2st;
+    const float Zy = (y * q2dS) * (Sp + sS) * rcp_a(Sp * fmaf(-u2, y2, Fc * Ft));
+    float axp, ayp;
+    if (SERIES) {
+      // u < 0.12: t = w^2 < 0.0144 always
+      axp = axs * Zx * atan_over_w(u2 * Zx * Zx);
+      ayp = ays * Zy * atanh_over_w(u2 * Zy * Zy);
+    } else {
+      const float u = F.w;
+      const float wx = u * Zx, wy = u * Zy;
+      const float tx = wx * wx, ty = wy * wy;
+      if (fmaxf(tx, ty) < T_SERIES) {
+        const float bq = 2.f * F.z;  // (bq/u) atan(u Z) = bq Z atan(w)/w
+        axp = bq * Zx * atan_over_w(tx);
+        ayp = bq * Zy * atanh_over_w(ty);
+      } else {
+        axp = axs * atanf(wx);
+        ayp = ays * log1pf((wy + wy) * rcp_a(1.f - wy));
+      }
+    }
+    p.ax[k] = fmaf(c, axp, fmaf(-s, ayp, p.ax[k]));
+    p.ay[k] = fmaf(s, axp, fmaf(c, ayp, p.ay[k]));
+    if (HESS) {
+      const float KDc = D.z, KDt = D.w, s2c = E.x, s2t = E.y, u2sc2 = E.z, u2st2 = E.w;
+      const float r2 = x2 + y2, ymx = y2 - x2;
+      const float Dc = fmaf(s2c, psc, r2 + KDc), Dt = fmaf(s2t, pst, r2 + KDt);
+      const float fc = rcp_a(psc * Dc), ft = rcp_a(pst * Dt);
+      const float g1d = fmaf(fc, ymx - u2sc2, -ft * (ymx - u2st2));
+      const float g2d = (fc - ft) * (x * y);
+      p.k[k] = fmaf(F.z, ic - it, p.k[k]);
+      p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
+      p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
+    }
+  }
+}
+
+// SIS / point mass (FP32): circular, evaluated directly on (dX, dY).
+template <bool HESS, int KP, bool POINT>
+__device__ __forceinline__ void circ32(const float4 *__restrict__ r4, float x, const float (&dY)[KP],
+                                       Acc<HESS, KP> &p) {
+  const float b = r4[7].y;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const float y = dY[k];
+    const float r2 = fmaf(x, x, y * y);
+    if (POINT) {
+      const float ir2 = r2 > 0.f ? rcp_a(r2) : 0.f;
+      const float f = b * ir2;
+      p.ax[k] = fmaf(f, x, p.ax[k]);
+      p.ay[k] = fmaf(f, y, p.ay[k]);
+      if (HESS) {
+        const float f2 = f * ir2;
+        p.g1[k] = fmaf(f2, (y - x) * (y + x), p.g1[k]);
+        p.g2[k] = fmaf(-2.f * f2, x * y, p.g2[k]);
+      }
+    } else {
+      const float ir = r2 > 0.f ? rsqrt_a(r2) : 0.f;
+      const float f = b * ir;
+      p.ax[k] = fmaf(f, x, p.ax[k]);
+      p.ay[k] = fmaf(f, y, p.ay[k]);
+      if (HESS) {
+        const float f3 = f * ir * ir;
+        p.k[k] = fmaf(0.5f, f, p.k[k]);
+        p.g1[k] = fmaf(0.5f * f3, (y - x) * (y + x), p.g1[k]);
+        p.g2[k] = fmaf(-f3, x * y, p.g2[k]);
+      }
+    }
+  }
+}
+
+// Any FP32 potential at KP points sharing dX (kind is warp-uniform in the
+// map kernel; per-lane in the image kernels).
+template <bool HESS, int KP>
+__device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
+                                           Acc<HESS, KP> &p) {
+  const int kind = __float_as_int(r4[7].x);
+  if (kind == K32_DPIE)
+    dpie32<HESS, KP, false>(r4, dX, dY, p);
+  else if (kind == K32_DPIE_SERIES)
+    dpie32<HESS, KP, true>(r4, dX, dY, p);
+  else if (kind == K32_SIS)
+    circ32<HESS, KP, false>(r4, dX, dY, p);
+  else
+    circ32<HESS, KP, true>(r4, dX, dY, p);
+}
+
+// --------------------------------------------------------- constraint sets
+// Back-trace every constraint of one parameter set in FP64 (Sec. 2.1 Eq. 1):
+// beta_j = theta_j - r alpha(theta_j), with alpha = static cache + the two
+// varying potentials (records in s_rec), then each source's barycentre
+// (Sec. 2.2, Fig. 3).  Fills s_beta [nimg][2], s_bary [nsrc][2] and, when
+// s_m is not NULL, r H at every image in s_m [nimg][3] (hxx, hyy, hxy).
+// Must be called by all THREADS threads of the CTA; ends synchronised.
+template <int THREADS>
+__device__ __forceinline__ void backtrace_set(const double *__restrict__ stat, const double *__restrict__ x,
+                                              const double *__restrict__ y, const double *__restrict__ ratio,
+                                              const int32_t *__restrict__ src_of, const int32_t *__restrict__ img_off,
+                                              int nimg, int nsrc, const double *s_rec, double *s_beta, double *s_m,
+                                              double *s_bary) {
+  for (int j = threadIdx.x; j < nimg; j += THREADS) {
+    const double X = x[j], Y = y[j];
+    const double *st = stat + (size_t)j * 5;
+    double ax = st[0], ay = st[1], kk = st[2], g1 = st[3], g2 = st[4];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      double bx, by, bk = 0, b1 = 0, b2 = 0;
+      if (s_m)
+        eval64<true>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
+      else
+        eval64<false>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
+      ax += bx;
+      ay += by;
+      kk += bk;
+      g1 += b1;
+      g2 += b2;
+    }
+    const double r = ratio[src_of[j]];
+    s_beta[2 * j] = X - r * ax;
+    s_beta[2 * j + 1] = Y - r * ay;
+    if (s_m) {
+      s_m[3 * j] = r * (kk + g1);
+      s_m[3 * j + 1] = r * (kk - g1);
+      s_m[3 * j + 2] = r * g2;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nsrc; i += THREADS) {
+    const int b = img_off[i], e = img_off[i + 1];
+    double sx = 0, sy = 0;
+    for (int j = b; j < e; ++j) {
+      sx += s_beta[2 * j];
+      sy += s_beta[2 * j + 1];
+    }
+    const int m = e - b;
+    s_bary[2 * i] = m > 0 ? sx / m : 0.0;
+    s_bary[2 * i + 1] = m > 0 ? sy / m : 0.0;
+  }
+  __syncthreads();
+}
+
+// Deterministic CTA sum of NV doubles per thread; the result is valid in
+// thread 0.  s_red holds (THREADS/32) * NV doubles.  Ends synchronised.
+template <int NV, int THREADS>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *s_red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_red[warp * NV + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < THREADS / 32; ++w) s += s_red[w * NV + k];
+      v[k] = s;
+    }
+  __syncthreads();
+}
+
+// Varying-potential records of parameter set q (14 numbers) into s_rec[2][16];
+// returns (to threads 0 and 1) whether the set is inside the model's domain.
+__device__ __forceinline__ bool load_var_rec64(const double *q, int type0, int type1, int v, double *s_rec) {
+  const double *w = q + 7 * v;
+  const int type = v == 0 ? type0 : type1;
+  make_rec64(type, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rec + v * REC64);
+  return halo_params_ok(type, w[0], w[1], w[3], w[2], w[4], w[5], w[6]);
 }
 
 }  // namespace lens

@@ -1,0 +1,562 @@
+// Image-plane chi2 with brute-force image finding (Sec. 2.2 Eq. 6; Sec. 2.3,
+// Fig. 4; Sec. 4.2, Fig. 8), batched over parameter sets.
+//
+// Per batch of parameter sets, six launches on the caller's stream:
+//   1. k_img_sources  per set: back-trace the constraints in FP64 and form
+//                     each source's barycentre (the source estimate).
+//   2. k_img_search   per (grid tile, set): deflection at the tile's nodes =
+//                     cached static part + the two varying potentials (FP32);
+//                     for each distance ratio the nodes are mapped to the
+//                     source plane, both triangles of every cell are tested
+//                     against that ratio's sources (bounding box, then
+//                     barycentric weights with a small tolerance so that a
+//                     source on a shared edge is never lost), and every hit
+//                     is appended to the set's candidate buffer.
+//   3. k_img_newton   one warp per candidate: Newton on the lens equation with
+//                     the full model, FP32 potentials (lanes split the
+//                     potentials) plus FP64 cluster-scale and varying ones.
+//   4. k_img_dedup    per set: candidates of the same source closer than
+//                     1e-3" are one image.
+//   5. k_img_polish   one warp per distinct image: Newton steps whose residual
+//                     uses the full model in FP64, until the step is < 1e-7".
+//   6. k_img_chi2     per set: each constraint takes the nearest image of its
+//                     own source (ties: lower y, then lower x); chi2 reduced in
+//                     a fixed order.
+// Candidate buffers live in scratch memory (IMG_CAP per set); an overflow
+// makes that set's chi2 NaN and sets ERRBIT_CAPACITY.
+#include "lens_device.cuh"
+
+namespace lens {
+namespace {
+
+constexpr int IMG_CAP = 4096;       // candidate images per parameter set
+constexpr int IMG_BATCH = 64;       // parameter sets per batch
+constexpr int MAX_SRC = 1024;
+constexpr double DEDUP = 1e-3;      // images closer than this are one image (arcsec)
+constexpr double NEWTON32_TOL = 1e-4;
+constexpr double POLISH_TOL = 1e-7;
+constexpr double ACCEPT_TOL = 1e-6;  // same criterion as the FP64 Newton of the definition
+constexpr int NEWTON_MAXIT = 20, POLISH_MAXIT = 6;
+constexpr float BARY_TOL = 1e-3f;
+constexpr int CT_X = 32, CT_Y = 8, NX_T = CT_X + 1, NY_T = CT_Y + 1;
+constexpr int ST_PENDING = 0, ST_NEWTON = 1, ST_FINAL = 2, ST_FAILED = -1;
+
+struct Hit {
+  double tx, ty;       // image position
+  float sx, sy;        // seed from the triangle
+  float h11, h22, h12; // r H at the last FP32 Newton step
+  int src;
+  int status;
+  int pad;
+};
+
+struct Layout {
+  size_t cnt, valid, nuniq, bary, hits, uniq, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+__host__ __device__ inline Layout layout(int B, int nsrc) {
+  Layout L;
+  size_t o = 0;
+  L.cnt = o;
+  o = align_up(o + (size_t)B * sizeof(int));
+  L.valid = o;
+  o = align_up(o + (size_t)B * sizeof(int));
+  L.nuniq = o;
+  o = align_up(o + (size_t)B * sizeof(int));
+  L.bary = o;
+  o = align_up(o + (size_t)B * nsrc * 2 * sizeof(double));
+  L.hits = o;
+  o = align_up(o + (size_t)B * IMG_CAP * sizeof(Hit));
+  L.uniq = o;
+  o = align_up(o + (size_t)B * IMG_CAP * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+struct Bufs {
+  int *cnt, *valid, *nuniq, *uniq;
+  double *bary;
+  Hit *hits;
+};
+
+__host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc) {
+  Layout L = layout(B, nsrc);
+  char *b = (char *)scratch;
+  Bufs r;
+  r.cnt = (int *)(b + L.cnt);
+  r.valid = (int *)(b + L.valid);
+  r.nuniq = (int *)(b + L.nuniq);
+  r.bary = (double *)(b + L.bary);
+  r.hits = (Hit *)(b + L.hits);
+  r.uniq = (int *)(b + L.uniq);
+  return r;
+}
+
+struct SetArgs {  // what every kernel needs to know about the batch
+  const double *params;
+  int p0, B, type0, type1;
+  int nsrc, nimg;
+  Bufs s;
+};
+
+// ---------------------------------------------------------------- 1. sources
+constexpr int SRC_THREADS = 128;
+
+__global__ void __launch_bounds__(SRC_THREADS) k_img_sources(const SetArgs a, const double *__restrict__ stat,
+                                                             const double *__restrict__ x,
+                                                             const double *__restrict__ y,
+                                                             const double *__restrict__ ratio,
+                                                             const int32_t *__restrict__ src_of,
+                                                             const int32_t *__restrict__ img_off) {
+  extern __shared__ double sm[];
+  double *s_rec = sm;
+  double *s_beta = s_rec + 2 * REC64;
+  double *s_bary = s_beta + 2 * a.nimg;
+  __shared__ int s_ok;
+  const int b = blockIdx.x;
+  const double *q = a.params + (size_t)(a.p0 + b) * 14;
+  if (threadIdx.x == 0) s_ok = 1;
+  __syncthreads();
+  if (threadIdx.x < 2 && !load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.s.valid[b] = s_ok;
+    a.s.cnt[b] = 0;
+    a.s.nuniq[b] = 0;
+  }
+  if (!s_ok) return;
+  backtrace_set<SRC_THREADS>(stat, x, y, ratio, src_of, img_off, a.nimg, a.nsrc, s_rec, s_beta, nullptr, s_bary);
+  for (int i = threadIdx.x; i < 2 * a.nsrc; i += SRC_THREADS) a.s.bary[(size_t)b * a.nsrc * 2 + i] = s_bary[i];
+}
+
+// ----------------------------------------------------------------- 2. search
+struct SearchArgs {
+  const float *ax, *ay;  // static deflection planes [ny][nx]
+  double xmin, ymin, dx, dy;
+  int nx, ny;
+  const int32_t *grp_off, *grp_src;
+  const double *grp_ratio;
+  int ng;
+};
+
+__device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 tA, float2 tB, float2 tC,
+                                         const float2 *s_src, const int32_t *__restrict__ gsrc, int g0, int g1,
+                                         float tiny, int *cnt, Hit *hits) {
+  const float lox = fminf(A.x, fminf(Bv.x, Cv.x)), hix = fmaxf(A.x, fmaxf(Bv.x, Cv.x));
+  const float loy = fminf(A.y, fminf(Bv.y, Cv.y)), hiy = fmaxf(A.y, fmaxf(Bv.y, Cv.y));
+  const float padx = BARY_TOL * (hix - lox) + 1e-6f, pady = BARY_TOL * (hiy - loy) + 1e-6f;
+  const float e1x = Bv.x - A.x, e1y = Bv.y - A.y, e2x = Cv.x - A.x, e2y = Cv.y - A.y;
+  const float area2 = e1x * e2y - e1y * e2x;
+  if (!(fabsf(area2) > tiny)) return;
+  const float inv = 1.f / area2;
+  for (int k = g0; k < g1; ++k) {
+    const int src = gsrc[k];
+    const float2 P = s_src[src];
+    if (P.x < lox - padx || P.x > hix + padx || P.y < loy - pady || P.y > hiy + pady) continue;
+    const float px = P.x - A.x, py = P.y - A.y;
+    const float wb = (px * e2y - py * e2x) * inv, wc = (e1x * py - e1y * px) * inv, wa = 1.f - wb - wc;
+    if (wa < -BARY_TOL || wb < -BARY_TOL || wc < -BARY_TOL) continue;
+    const int slot = atomicAdd(cnt, 1);
+    if (slot < IMG_CAP) {
+      Hit *h = hits + slot;
+      h->src = src;
+      h->sx = wa * tA.x + wb * tB.x + wc * tC.x;
+      h->sy = wa * tA.y + wb * tB.y + wc * tC.y;
+      h->status = ST_PENDING;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const SearchArgs g) {
+  __shared__ __align__(16) float s_rec[2][REC32];
+  __shared__ double s_cen[2][2];
+  __shared__ float2 s_al[NX_T * NY_T];
+  __shared__ float2 s_src[MAX_SRC];
+  const int b = blockIdx.z;
+  if (!a.s.valid[b]) return;
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * CT_X, j0 = blockIdx.y * CT_Y;
+  if (tid < 2) {
+    const double *w = a.params + (size_t)(a.p0 + b) * 14 + 7 * tid;
+    make_rec32(tid == 0 ? a.type0 : a.type1, w[3], w[2], w[4], w[5], w[6], s_rec[tid]);
+    s_cen[tid][0] = w[0];
+    s_cen[tid][1] = w[1];
+  }
+  const double *bary = a.s.bary + (size_t)b * a.nsrc * 2;
+  for (int i = tid; i < a.nsrc; i += 256) s_src[i] = make_float2((float)bary[2 * i], (float)bary[2 * i + 1]);
+  __syncthreads();
+  for (int n = tid; n < NX_T * NY_T; n += 256) {
+    const int ii = min(i0 + n % NX_T, g.nx - 1), jj = min(j0 + n / NX_T, g.ny - 1);
+    const size_t o = (size_t)jj * g.nx + ii;
+    const double X = g.xmin + ii * g.dx, Y = g.ymin + jj * g.dy;
+    float tx = g.ax[o], ty = g.ay[o];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      Acc<false, 1> acc;
+      acc.zero();
+      const float dY[1] = {(float)(Y - s_cen[v][1])};
+      eval32_any<false, 1>(reinterpret_cast<const float4 *>(s_rec[v]), (float)(X - s_cen[v][0]), dY, acc);
+      tx += acc.ax[0];
+      ty += acc.ay[0];
+    }
+    s_al[n] = make_float2(tx, ty);
+  }
+  __syncthreads();
+  const int ci = tid % CT_X, cj = tid / CT_X;
+  const int gi = i0 + ci, gj = j0 + cj;
+  if (gi >= g.nx - 1 || gj >= g.ny - 1) return;
+  const float X0 = (float)(g.xmin + gi * g.dx), X1 = (float)(g.xmin + (gi + 1) * g.dx);
+  const float Y0 = (float)(g.ymin + gj * g.dy), Y1 = (float)(g.ymin + (gj + 1) * g.dy);
+  const int n00 = cj * NX_T + ci;
+  const float2 a00 = s_al[n00], a10 = s_al[n00 + 1], a01 = s_al[n00 + NX_T], a11 = s_al[n00 + NX_T + 1];
+  const float tiny = (float)(1e-10 * g.dx * g.dy);
+  int *cnt = a.s.cnt + b;
+  Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
+  const float2 t00 = make_float2(X0, Y0), t10 = make_float2(X1, Y0), t11 = make_float2(X1, Y1),
+               t01 = make_float2(X0, Y1);
+  for (int q = 0; q < g.ng; ++q) {
+    const float r = (float)g.grp_ratio[q];
+    const float2 b00 = make_float2(X0 - r * a00.x, Y0 - r * a00.y), b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
+                 b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y), b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
+    const int g0 = g.grp_off[q], g1 = g.grp_off[q + 1];
+    tri_test(b00, b10, b11, t00, t10, t11, s_src, g.grp_src, g0, g1, tiny, cnt, hits);
+    tri_test(b00, b11, b01, t00, t11, t01, s_src, g.grp_src, g0, g1, tiny, cnt, hits);
+  }
+}
+
+// ----------------------------------------------------------------- 3. Newton
+struct NewtonArgs {
+  const float *rec32, *cen32;  // static potentials on the FP32 path
+  int n_light;
+  const double *heavy;         // static potentials on the FP64 path
+  int n_heavy;
+  const double *all64;         // every static potential in FP64 (polish)
+  int n_stat;
+  const double *ratio;         // per source
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int NW_THREADS = 256, NW_WARPS = NW_THREADS / 32;
+
+__global__ void __launch_bounds__(NW_THREADS) k_img_newton(const SetArgs a, const NewtonArgs n) {
+  __shared__ double s_var[NW_WARPS][2 * REC64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nwarps = (long long)gridDim.x * NW_WARPS;
+  for (long long task = (long long)blockIdx.x * NW_WARPS + w; task < (long long)a.B * IMG_CAP; task += nwarps) {
+    const int b = (int)(task / IMG_CAP), k = (int)(task % IMG_CAP);
+    if (!a.s.valid[b] || k >= min(a.s.cnt[b], IMG_CAP)) continue;
+    Hit *h = a.s.hits + (size_t)b * IMG_CAP + k;
+    const double *q = a.params + (size_t)(a.p0 + b) * 14;
+    if (lane < 2) load_var_rec64(q, a.type0, a.type1, lane, s_var[w]);
+    __syncwarp();
+    const int src = h->src;
+    const double r = n.ratio[src];
+    const double bx = a.s.bary[((size_t)b * a.nsrc + src) * 2], by = a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1];
+    double tx = h->sx, ty = h->sy;
+    int status = ST_FAILED;
+    float h11 = 0.f, h22 = 0.f, h12 = 0.f;
+    for (int it = 0; it < NEWTON_MAXIT; ++it) {
+      const float hx = (float)tx, hy = (float)ty;
+      const float lx = (float)(tx - (double)hx), ly = (float)(ty - (double)hy);
+      Acc<true, 1> part;
+      part.zero();
+      for (int j = lane; j < n.n_light; j += 32) {
+        const float4 c = reinterpret_cast<const float4 *>(n.cen32)[j];
+        const float dY[1] = {(hy - c.y) + (ly - c.w)};
+        eval32_any<true, 1>(reinterpret_cast<const float4 *>(n.rec32) + (size_t)j * (REC32 / 4), (hx - c.x) + (lx - c.z),
+                            dY, part);
+      }
+      double v[5] = {part.ax[0], part.ay[0], part.k[0], part.g1[0], part.g2[0]};
+      for (int j = lane; j < n.n_heavy + 2; j += 32) {
+        const double *rec = j < n.n_heavy ? n.heavy + (size_t)j * REC64 : s_var[w] + (j - n.n_heavy) * REC64;
+        double e0, e1, e2, e3, e4;
+        eval64<true>(rec, tx, ty, e0, e1, e2, e3, e4);
+        v[0] += e0;
+        v[1] += e1;
+        v[2] += e2;
+        v[3] += e3;
+        v[4] += e4;
+      }
+#pragma unroll
+      for (int c = 0; c < 5; ++c) v[c] = warp_sum(v[c]);
+      const double fx = bx - (tx - r * v[0]), fy = by - (ty - r * v[1]);
+      const double m11 = r * (v[2] + v[3]), m22 = r * (v[2] - v[3]), m12 = r * v[4];
+      const double a11 = 1.0 - m11, a22 = 1.0 - m22, a12 = -m12;
+      const double det = a11 * a22 - a12 * a12;
+      if (!(det != 0.0) || !isfinite(det)) break;
+      const double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+      tx += dx;
+      ty += dy;
+      h11 = (float)m11;
+      h22 = (float)m22;
+      h12 = (float)m12;
+      if (!isfinite(tx) || !isfinite(ty)) break;
+      if (sqrt(dx * dx + dy * dy) < NEWTON32_TOL) {
+        status = ST_NEWTON;
+        break;
+      }
+    }
+    if (lane == 0) {
+      h->tx = tx;
+      h->ty = ty;
+      h->h11 = h11;
+      h->h22 = h22;
+      h->h12 = h12;
+      h->status = status;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------ 4. dedup
+constexpr int DD_THREADS = 256;
+
+__global__ void __launch_bounds__(DD_THREADS) k_img_dedup(const SetArgs a) {
+  __shared__ int s_scan[DD_THREADS];
+  __shared__ int s_base;
+  const int b = blockIdx.x;
+  if (!a.s.valid[b]) return;
+  const int n = min(a.s.cnt[b], IMG_CAP);
+  const Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
+  int *uniq = a.s.uniq + (size_t)b * IMG_CAP;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += DD_THREADS) {
+    const int k = k0 + threadIdx.x;
+    int keep = 0;
+    if (k < n && hits[k].status == ST_NEWTON) {
+      keep = 1;
+      const int src = hits[k].src;
+      const double x = hits[k].tx, y = hits[k].ty;
+      for (int j = 0; j < k; ++j) {
+        if (hits[j].status != ST_NEWTON || hits[j].src != src) continue;
+        const double ex = hits[j].tx - x, ey = hits[j].ty - y;
+        if (ex * ex + ey * ey < DEDUP * DEDUP) {
+          keep = 0;
+          break;
+        }
+      }
+    }
+    // inclusive scan of keep flags (Hillis-Steele), keeps the candidates' order
+    s_scan[threadIdx.x] = keep;
+    __syncthreads();
+    for (int o = 1; o < DD_THREADS; o <<= 1) {
+      const int t = threadIdx.x >= o ? s_scan[threadIdx.x - o] : 0;
+      __syncthreads();
+      s_scan[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (keep) uniq[s_base + s_scan[threadIdx.x] - 1] = k;
+    __syncthreads();
+    if (threadIdx.x == DD_THREADS - 1) s_base += s_scan[DD_THREADS - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.s.nuniq[b] = s_base;
+}
+
+// ----------------------------------------------------------------- 5. polish
+__global__ void __launch_bounds__(NW_THREADS) k_img_polish(const SetArgs a, const NewtonArgs n) {
+  __shared__ double s_var[NW_WARPS][2 * REC64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nwarps = (long long)gridDim.x * NW_WARPS;
+  for (long long task = (long long)blockIdx.x * NW_WARPS + w; task < (long long)a.B * IMG_CAP; task += nwarps) {
+    const int b = (int)(task / IMG_CAP), u = (int)(task % IMG_CAP);
+    if (!a.s.valid[b] || u >= a.s.nuniq[b]) continue;
+    Hit *h = a.s.hits + (size_t)b * IMG_CAP + a.s.uniq[(size_t)b * IMG_CAP + u];
+    const double *q = a.params + (size_t)(a.p0 + b) * 14;
+    if (lane < 2) load_var_rec64(q, a.type0, a.type1, lane, s_var[w]);
+    __syncwarp();
+    const int src = h->src;
+    const double r = n.ratio[src];
+    const double bx = a.s.bary[((size_t)b * a.nsrc + src) * 2], by = a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1];
+    const double a11 = 1.0 - h->h11, a22 = 1.0 - h->h22, a12 = -h->h12;
+    const double det = a11 * a22 - a12 * a12;
+    double tx = h->tx, ty = h->ty, step = 1e30;
+    for (int it = 0; it < POLISH_MAXIT && step >= POLISH_TOL; ++it) {
+      double sx = 0.0, sy = 0.0, e2, e3, e4, ex, ey;
+      for (int j = lane; j < n.n_stat + 2; j += 32) {
+        const double *rec = j < n.n_stat ? n.all64 + (size_t)j * REC64 : s_var[w] + (j - n.n_stat) * REC64;
+        eval64<false>(rec, tx, ty, ex, ey, e2, e3, e4);
+        sx += ex;
+        sy += ey;
+      }
+      sx = warp_sum(sx);
+      sy = warp_sum(sy);
+      const double fx = bx - (tx - r * sx), fy = by - (ty - r * sy);
+      const double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+      tx += dx;
+      ty += dy;
+      step = sqrt(dx * dx + dy * dy);
+    }
+    if (lane == 0) {
+      h->tx = tx;
+      h->ty = ty;
+      h->status = (step < ACCEPT_TOL && isfinite(tx) && isfinite(ty)) ? ST_FINAL : ST_FAILED;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------- 6. match, chi2
+constexpr int C2_THREADS = 128;
+
+__global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const double *__restrict__ x,
+                                                         const double *__restrict__ y,
+                                                         const double *__restrict__ sigma,
+                                                         const int32_t *__restrict__ src_of, double *chi2,
+                                                         int32_t *nfound, int *err) {
+  __shared__ double s_red[C2_THREADS / 32];
+  const int b = blockIdx.x, p = a.p0 + b;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  if (!a.s.valid[b]) {
+    if (threadIdx.x == 0) chi2[p] = nan;
+    if (nfound)
+      for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) nfound[(size_t)p * a.nsrc + i] = 0;
+    return;
+  }
+  const bool overflow = a.s.cnt[b] > IMG_CAP;
+  const Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
+  const int *uniq = a.s.uniq + (size_t)b * IMG_CAP;
+  const int nu = a.s.nuniq[b];
+  if (nfound)
+    for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) {
+      int c = 0;
+      for (int u = 0; u < nu; ++u) {
+        const Hit &h = hits[uniq[u]];
+        c += (h.status == ST_FINAL && h.src == i);
+      }
+      nfound[(size_t)p * a.nsrc + i] = overflow ? -1 : c;
+    }
+  double acc[1] = {0.0};
+  for (int j = threadIdx.x; j < a.nimg; j += C2_THREADS) {
+    const int i = src_of[j];
+    double best = INFINITY, bx = 0.0, by = 0.0;
+    for (int u = 0; u < nu; ++u) {
+      const Hit &h = hits[uniq[u]];
+      if (h.status != ST_FINAL || h.src != i) continue;
+      const double ex = x[j] - h.tx, ey = y[j] - h.ty, d2 = ex * ex + ey * ey;
+      if (d2 < best || (d2 == best && (h.ty < by || (h.ty == by && h.tx < bx)))) {
+        best = d2;
+        bx = h.tx;
+        by = h.ty;
+      }
+    }
+    acc[0] += best / (sigma[j] * sigma[j]);  // no image of this source: +inf -> NaN below
+  }
+  block_sum<1, C2_THREADS>(acc, s_red);
+  if (threadIdx.x == 0) {
+    chi2[p] = (overflow || !isfinite(acc[0])) ? nan : acc[0];
+    if (overflow) atomicOr(err, ERRBIT_CAPACITY);
+  }
+}
+
+}  // namespace
+
+size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch) { return layout(batch, c->nsrc).total; }
+
+int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P, double *d_chi2,
+                   int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st) {
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  const Model *sm = c->stat_model;
+  NewtonArgs n;
+  n.rec32 = sm->rec32;
+  n.cen32 = sm->cen32;
+  n.n_light = sm->n_light;
+  n.heavy = sm->heavy;
+  n.n_heavy = sm->n_heavy;
+  n.all64 = sm->all64;
+  n.n_stat = sm->n;
+  n.ratio = c->ratio;
+  SearchArgs g;
+  g.ax = gc->alpha32;
+  g.ay = gc->alpha32 + (size_t)gc->nx * gc->ny;
+  g.xmin = gc->xmin;
+  g.ymin = gc->ymin;
+  g.dx = (gc->xmax - gc->xmin) / (gc->nx - 1);
+  g.dy = (gc->ymax - gc->ymin) / (gc->ny - 1);
+  g.nx = gc->nx;
+  g.ny = gc->ny;
+  g.grp_off = c->grp_off;
+  g.grp_src = c->grp_src;
+  g.grp_ratio = c->grp_ratio;
+  g.ng = c->ng;
+  const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_img_sources, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  for (int32_t p0 = 0; p0 < P; p0 += batch) {
+    SetArgs a;
+    a.params = d_params;
+    a.p0 = p0;
+    a.B = std::min(batch, P - p0);
+    a.type0 = c->var_type[0];
+    a.type1 = c->var_type[1];
+    a.nsrc = c->nsrc;
+    a.nimg = c->nimg;
+    a.s = bufs(scratch, batch, c->nsrc);
+    k_img_sources<<<a.B, SRC_THREADS, src_smem, st>>>(a, c->stat, c->x, c->y, c->ratio, c->src_of, c->img_off);
+    dim3 sg((gc->nx - 1 + CT_X - 1) / CT_X, (gc->ny - 1 + CT_Y - 1) / CT_Y, a.B);
+    k_img_search<<<sg, 256, 0, st>>>(a, g);
+    k_img_newton<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
+    k_img_dedup<<<a.B, DD_THREADS, 0, st>>>(a);
+    k_img_polish<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
+    k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LENS_ECUDA, "image-plane chi2 launch: %s", cudaGetErrorString(e));
+  }
+  return LENS_OK;
+}
+
+int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
+                      double *d_chi2, int32_t *d_nfound, cudaStream_t st) {
+  (void)m;
+  if (c->nsrc > MAX_SRC) return fail(LENS_EINVAL, "image-plane chi2 supports at most %d sources", MAX_SRC);
+  const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
+  if (src_smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
+  if ((long long)(g->nx - 1) * (g->ny - 1) > (1ll << 30)) return fail(LENS_EINVAL, "grid too large");
+  // static deflection on this grid, cached per constraint set
+  GridCache *gc = nullptr;
+  for (auto &x : c->grids)
+    if (x.xmin == g->xmin && x.xmax == g->xmax && x.ymin == g->ymin && x.ymax == g->ymax && x.nx == g->nx &&
+        x.ny == g->ny)
+      gc = &x;
+  if (!gc) {
+    GridCache n;
+    n.xmin = g->xmin;
+    n.xmax = g->xmax;
+    n.ymin = g->ymin;
+    n.ymax = g->ymax;
+    n.nx = g->nx;
+    n.ny = g->ny;
+    n.bytes = 2 * sizeof(float) * (size_t)g->nx * g->ny;
+    int rc = dev_alloc(ctx, (void **)&n.alpha32, n.bytes);
+    if (rc) return rc;
+    if (c->stat_model->n > 0) {
+      rc = launch_map_mixed(ctx, c->stat_model, g, 1.0, false, n.alpha32, st);
+    } else {
+      rc = cudaMemsetAsync(n.alpha32, 0, n.bytes, st) == cudaSuccess ? LENS_OK : LENS_ECUDA;
+    }
+    if (rc) {
+      dev_free(ctx, n.alpha32, n.bytes);
+      return rc;
+    }
+    c->grids.push_back(n);
+    gc = &c->grids.back();
+  }
+  const int32_t batch = std::min<int32_t>(IMG_BATCH, P);
+  int rc = ensure_scratch(ctx, chi2_image_scratch_bytes(c, batch));
+  if (rc) return rc;
+  return run_chi2_image(ctx, c, gc, d_params, P, d_chi2, d_nfound, ctx->scratch, batch, st);
+}
+
+}  // namespace lens

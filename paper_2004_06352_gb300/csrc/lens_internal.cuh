@@ -17,6 +17,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
@@ -84,6 +85,61 @@ __host__ __device__ inline void make_rec64(int type, double x0, double y0, doubl
   r[D_KIND] = u < U_SERIES64 ? K64_DPIE_SERIES : K64_DPIE;
 }
 
+// Host + device: FP32 record of one potential (constants formed in FP64).
+__host__ __device__ inline void make_rec32(int type, double theta, double eps, double rcore, double rcut, double b0,
+                                           float *r) {
+  for (int k = 0; k < REC32; ++k) r[k] = 0.f;
+  int kind;
+  if (type == LENS_SIS || type == LENS_POINT) {
+    r[R_C] = 1.f;
+    kind = type == LENS_SIS ? K32_SIS : K32_POINT;
+    r[R_B] = (float)(type == LENS_SIS ? b0 : b0 * b0);
+  } else {
+    double e = eps;
+    double q = (1.0 - e) / (1.0 + e), u = 2.0 * sqrt(e) / (1.0 + e);
+    double q2 = q * q, u2 = u * u;
+    double b = b0 * (1.0 + e), bq = b * q;
+    double sc = rcore * (1.0 + e), st = rcut * (1.0 + e);
+    double c2 = cos(2.0 * theta), s2 = sin(2.0 * theta);
+    bool series = u < U_SERIES32;
+    kind = series ? K32_DPIE_SERIES : K32_DPIE;
+    r[R_C] = (float)cos(theta);
+    r[R_S] = (float)sin(theta);
+    r[R_Q2] = (float)q2;
+    r[R_U2] = (float)u2;
+    r[R_KC] = (float)(q2 * sc * sc);
+    r[R_KT] = (float)(q2 * st * st);
+    r[R_SC] = (float)sc;
+    r[R_ST] = (float)st;
+    r[R_Q2SS] = (float)(q2 * (st + sc));
+    r[R_DS] = (float)(st - sc);
+    r[R_Q2SC] = (float)(q2 * sc);
+    r[R_Q2ST] = (float)(q2 * st);
+    r[R_SS] = (float)(st + sc);
+    r[R_Q2DS] = (float)(q2 * (st - sc));
+    r[R_KDC] = (float)((1.0 + q2) * sc * sc);
+    r[R_KDT] = (float)((1.0 + q2) * st * st);
+    r[R_2SC] = (float)(2.0 * sc);
+    r[R_2ST] = (float)(2.0 * st);
+    r[R_U2SC2] = (float)(u2 * sc * sc);
+    r[R_U2ST2] = (float)(u2 * st * st);
+    r[R_AXS] = (float)(series ? bq : bq / u);
+    r[R_AYS] = (float)(series ? bq : bq / (2.0 * u));
+    r[R_KAPS] = (float)(0.5 * bq);
+    r[R_U] = (float)u;
+    r[R_C1] = (float)(c2 * 0.5 * bq);
+    r[R_C2] = (float)(s2 * bq);
+    r[R_C3] = (float)(s2 * 0.5 * bq);
+    r[R_C4] = (float)(-c2 * bq);
+  }
+#ifdef __CUDA_ARCH__
+  r[R_KIND] = __int_as_float(kind);
+#else
+  std::memcpy(&r[R_KIND], &kind, sizeof(int));
+#endif
+}
+
+
 // Host + device: are the parameters inside the model's domain?
 __host__ __device__ inline bool halo_params_ok(int type, double x0, double y0, double theta, double eps, double rcore,
                                                double rcut, double b0) {
@@ -101,6 +157,7 @@ struct Model {
   int32_t n = 0, n_light = 0, n_heavy = 0;
   float *rec32 = nullptr;
   double *pos64 = nullptr;
+  float *cen32 = nullptr;   // [n_light][4]: x0, y0 as hi/lo float pairs (hi x, hi y, lo x, lo y)
   double *heavy = nullptr;
   double *all64 = nullptr;
   std::vector<lens_halo> host;
@@ -110,7 +167,7 @@ struct Model {
 struct GridCache {
   double xmin, xmax, ymin, ymax;
   int32_t nx, ny;
-  double *alpha_static = nullptr;  // [ny][nx][2] FP64, D_ls/D_s = 1, static potentials only
+  float *alpha32 = nullptr;  // [2][ny][nx] deflection of the static potentials, D_ls/D_s = 1 (LENS_MIXED map)
   size_t bytes = 0;
 };
 
@@ -125,6 +182,11 @@ struct CSet {
   double *stat = nullptr;       // [nimg][5]: ax, ay, hxx, hyy, hxy of the static potentials (D_ls/D_s = 1)
   double *var_base = nullptr;   // [2][16] FP64 records of the varying potentials' base types (type in D_KIND)
   int32_t var_type[2] = {0, 0};
+  Model *stat_model = nullptr;  // every potential except the two varying ones
+  int32_t ng = 0;               // distinct source distance ratios
+  int32_t *grp_off = nullptr;   // [ng+1] sources of ratio group g: grp_src[grp_off[g] .. grp_off[g+1]-1]
+  int32_t *grp_src = nullptr;   // [nsrc]
+  double *grp_ratio = nullptr;  // [ng]
   std::vector<GridCache> grids;
   size_t bytes = 0;
 };
@@ -159,6 +221,8 @@ CSet *find_cset(lens_ctx *ctx, lens_cset_t id);
 int dev_alloc(lens_ctx *ctx, void **p, size_t bytes);
 void dev_free(lens_ctx *ctx, void *p, size_t bytes);
 int ensure_scratch(lens_ctx *ctx, size_t bytes);
+int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out);
+void free_model(lens_ctx *ctx, Model *m);
 int check_grid(const lens_grid *g);
 
 // Kernel launchers (lens_maps.cu / lens_chi2.cu).
@@ -171,5 +235,12 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
                        int32_t variant, double *d_chi2, cudaStream_t st);
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
                       double *d_chi2, int32_t *d_nfound, cudaStream_t st);
+size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch);
+int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P,
+                   double *d_chi2, int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st);
+
+// device error word bits (read and cleared by lens_wait)
+constexpr int ERRBIT_WAIT = 1;
+constexpr int ERRBIT_CAPACITY = 2;
 
 }  // namespace lens

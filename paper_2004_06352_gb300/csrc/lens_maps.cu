@@ -47,125 +47,6 @@ struct MapArgs {
 };
 
 template <bool HESS, int KP>
-struct Acc {
-  float ax[KP], ay[KP], k[KP], g1[KP], g2[KP];
-  __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int i = 0; i < KP; ++i) ax[i] = ay[i] = k[i] = g1[i] = g2[i] = 0.f;
-  }
-};
-
-// Kahan step: (s, c) += v, true sum ~ s - c.
-__device__ __forceinline__ void kahan(float &s, float &c, float v) {
-  float y = v - c;
-  float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-template <bool HESS, int KP>
-__device__ __forceinline__ void fold(Acc<HESS, KP> &tot, Acc<HESS, KP> &cmp, Acc<HESS, KP> &part) {
-#pragma unroll
-  for (int i = 0; i < KP; ++i) {
-    kahan(tot.ax[i], cmp.ax[i], part.ax[i]);
-    kahan(tot.ay[i], cmp.ay[i], part.ay[i]);
-    if (HESS) {
-      kahan(tot.k[i], cmp.k[i], part.k[i]);
-      kahan(tot.g1[i], cmp.g1[i], part.g1[i]);
-      kahan(tot.g2[i], cmp.g2[i], part.g2[i]);
-    }
-  }
-  part.zero();
-}
-
-// One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the
-// potential's centre come from hi/lo float pairs (see Pos), then
-//   x = c dX + s dY,  y = c dY - s dX   (halo frame).
-template <bool HESS, int KP, bool SERIES>
-__device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
-                                       Acc<HESS, KP> &p) {
-  const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4], F = r4[5], G = r4[6];
-  const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
-  const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
-  const float q2sS = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
-  const float sS = D.x, q2dS = D.y;
-  const float axs = F.x, ays = F.y;
-  const float cdX = c * dX, sdX = s * dX;
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    const float x = fmaf(s, dY[k], cdX), y = fmaf(c, dY[k], -sdX);
-    const float x2 = x * x, y2 = y * y;
-    const float R = fmaf(q2, x2, y2);
-    const float pc2 = R + Kc, pt2 = R + Kt;
-    const float ic = rsqrt_a(pc2), it = rsqrt_a(pt2);
-    const float psc = pc2 * ic, pst = pt2 * it;
-    const float Sp = psc + pst;
-    const float Ec = psc + sc, Et = pst + st;
-    const float Zx = (x * dS) * (Sp + q2sS) * rcp_a(Sp * fmaf(u2, x2, Ec * Et));
-    const float Fc = psc + q2sc, Ft = pst + q2st;
-    const float Zy = (y * q2dS) * (Sp + sS) * rcp_a(Sp * fmaf(-u2, y2, Fc * Ft));
-    float axp, ayp;
-    if (SERIES) {
-      const float wx = u2 * Zx * Zx, wy = u2 * Zy * Zy;
-      axp = axs * Zx * fmaf(wx, fmaf(wx, fmaf(wx, -1.f / 7.f, 0.2f), -1.f / 3.f), 1.f);
-      ayp = ays * Zy * fmaf(wy, fmaf(wy, fmaf(wy, 1.f / 7.f, 0.2f), 1.f / 3.f), 1.f);
-    } else {
-      const float u = F.w;
-      axp = axs * atanf(u * Zx);
-      const float wy = u * Zy;
-      ayp = ays * log1pf((wy + wy) * rcp_a(1.f - wy));
-    }
-    p.ax[k] = fmaf(c, axp, fmaf(-s, ayp, p.ax[k]));
-    p.ay[k] = fmaf(s, axp, fmaf(c, ayp, p.ay[k]));
-    if (HESS) {
-      const float KDc = D.z, KDt = D.w, s2c = E.x, s2t = E.y, u2sc2 = E.z, u2st2 = E.w;
-      const float r2 = x2 + y2, ymx = y2 - x2;
-      const float Dc = fmaf(s2c, psc, r2 + KDc), Dt = fmaf(s2t, pst, r2 + KDt);
-      const float fc = rcp_a(psc * Dc), ft = rcp_a(pst * Dt);
-      const float g1d = fmaf(fc, ymx - u2sc2, -ft * (ymx - u2st2));
-      const float g2d = (fc - ft) * (x * y);
-      p.k[k] = fmaf(F.z, ic - it, p.k[k]);
-      p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
-      p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
-    }
-  }
-}
-
-// SIS / point mass (FP32): circular, evaluated directly on (dX, dY).
-template <bool HESS, int KP, bool POINT>
-__device__ __forceinline__ void circ32(const float4 *__restrict__ r4, float x, const float (&dY)[KP],
-                                       Acc<HESS, KP> &p) {
-  const float b = r4[7].y;
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    const float y = dY[k];
-    const float r2 = fmaf(x, x, y * y);
-    if (POINT) {
-      const float ir2 = r2 > 0.f ? rcp_a(r2) : 0.f;
-      const float f = b * ir2;
-      p.ax[k] = fmaf(f, x, p.ax[k]);
-      p.ay[k] = fmaf(f, y, p.ay[k]);
-      if (HESS) {
-        const float f2 = f * ir2;
-        p.g1[k] = fmaf(f2, (y - x) * (y + x), p.g1[k]);
-        p.g2[k] = fmaf(-2.f * f2, x * y, p.g2[k]);
-      }
-    } else {
-      const float ir = r2 > 0.f ? rsqrt_a(r2) : 0.f;
-      const float f = b * ir;
-      p.ax[k] = fmaf(f, x, p.ax[k]);
-      p.ay[k] = fmaf(f, y, p.ay[k]);
-      if (HESS) {
-        const float f3 = f * ir * ir;
-        p.k[k] = fmaf(0.5f, f, p.k[k]);
-        p.g1[k] = fmaf(0.5f * f3, (y - x) * (y + x), p.g1[k]);
-        p.g2[k] = fmaf(-f3, x * y, p.g2[k]);
-      }
-    }
-  }
-}
-
-template <bool HESS, int KP>
 __global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
   __shared__ __align__(128) float s_rec[2][CH * REC32];
   __shared__ float4 s_off[2][CH];  // hi.x, hi.y, lo.x, lo.y of (Tx - x0, Ty - y0)
@@ -224,7 +105,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
     const bool ok = mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);
     if (!__syncthreads_and(ok)) {
       if (tid == 0) {
-        atomicExch(a.err, LENS_ERR_WAIT);
+        atomicOr(a.err, ERRBIT_WAIT);
         mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);  // let the copy in flight land before leaving
       }
       return;
@@ -249,15 +130,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
       float dY[KP];
 #pragma unroll
       for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
-      const int kind = __float_as_int(r4[7].x);
-      if (kind == K32_DPIE)
-        dpie32<HESS, KP, false>(r4, dX, dY, part);
-      else if (kind == K32_DPIE_SERIES)
-        dpie32<HESS, KP, true>(r4, dX, dY, part);
-      else if (kind == K32_SIS)
-        circ32<HESS, KP, false>(r4, dX, dY, part);
-      else
-        circ32<HESS, KP, true>(r4, dX, dY, part);
+      eval32_any<HESS, KP>(r4, dX, dY, part);
       if (++seen == SUB) {
         fold(tot, cmp, part);
         seen = 0;
