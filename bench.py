@@ -297,14 +297,22 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     o1 = torch.empty((2, 256, 256), dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.grad_map(mid1, g1, 0.7, api.LENS_FP64, o1, stream), 50)
     ex["grad_map_fp64_256x10"] = {"ms": t}
-    # batched source-plane chi2: 100 sources, ~400 images, 4096 sets
-    cons = I.random_constraints(100, seed=34, field=60)
+    # batched chi2 on the 1000-potential model with its multiple-image
+    # constraints (100 sources, 372 images at 5 distance ratios)
+    cons = I.load_constraints(os.path.join(ROOT, "tests", "golden", "cfg2_constraints.json"))
     cs = ctx.cset_create(mid, cons, (0, 1))
     P = 4096
     params = torch.tensor(I.perturbed_params(m, (0, 1), P, seed=35), device=dev)
     chi2 = torch.empty(P, dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.chi2_source(cs, params, P, 0, chi2, stream), 5)
-    ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P}
+    ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P,
+                         "workload": "source-plane chi2, 4096 parameter sets, 1000 potentials"}
+    Pi = 256
+    gi = I.grid(1024)
+    chi2i = torch.empty(Pi, dtype=torch.float64, device=dev)
+    t = timed(lambda: ctx.chi2_image(cs, gi, params[:Pi], Pi, chi2i, None, stream), 2)
+    ex["chi2_image"] = {"ms": t, "models_per_s": Pi / (t * 1e-3), "P": Pi,
+                        "workload": "image-plane chi2, 1024^2 triangulated grid, 256 parameter sets, 1000 potentials"}
     # CPU baseline: the oracle on the host cores, ~15 s of row bands
     try:
         rate, rows, thr = oracle_map_sample(m, g, 15.0)

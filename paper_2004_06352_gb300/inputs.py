@@ -176,5 +176,15 @@ def source_candidates(n, seed, radius=25.0, ratios=(0.5, 0.6, 0.7, 0.8, 0.9)):
     return r * np.cos(a), r * np.sin(a), rng.choice(np.asarray(ratios, dtype=np.float64), n)
 
 
+def load_constraints(path):
+    """A constraint table stored as JSON (img_off, x, y, dls_ds, sigma)."""
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    n = len(d["x"])
+    sig = d["sigma"]
+    return constraints_dict(d["img_off"], d["x"], d["y"], np.full(n, sig) if np.isscalar(sig) else sig, d["dls_ds"])
+
+
 def gaussian_noise(n, seed, sigma):
     return np.random.default_rng(seed).normal(0.0, sigma, (n, 2))

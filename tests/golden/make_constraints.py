@@ -60,10 +60,7 @@ def main():
 
 def load():
     """The stored constraint table as the dict the bindings take."""
-    with open(OUT) as f:
-        d = json.load(f)
-    n = len(d["x"])
-    return I.constraints_dict(d["img_off"], d["x"], d["y"], np.full(n, d["sigma"]), d["dls_ds"])
+    return I.load_constraints(OUT)
 
 
 if __name__ == "__main__":
