@@ -187,6 +187,26 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
 int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
                     double *d_chi2, int32_t *d_nimg_found, void *stream);
 
+/* Image-plane chi2 that allocates nothing (the paper has no counterpart).
+ * For callers that reserve all device memory up front and may not call
+ * cudaMalloc/cudaFree at call time -- e.g. a long-running sampler or request
+ * loop: those calls can synchronise the whole device and can fail under
+ * memory pressure mid-run.  Same arguments, results and error behaviour as
+ * lens_chi2_image, but every working buffer lives in one fixed file-scope
+ * device array of LENS_NOALLOC_SCRATCH_BYTES, held by every GPU that loads
+ * the library until the process exits.  The context, model and constraint
+ * set must already exist (they allocate when created).
+ *   - The first call on a device looks up that array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; each
+ *     call rewrites everything it reads.  Calls whose work overlaps on the
+ *     GPU (different streams, or different contexts on one device) race.
+ *   - LENS_EINVAL, with a message, when the grid's static deflection
+ *     (8 bytes per node) plus the buffers of one parameter set do not fit. */
+#define LENS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params,
+                            int32_t P, double *d_chi2, int32_t *d_nimg_found, void *stream);
+
 /* --------------------------------------------------------------- control */
 
 /* Wait until all work enqueued on `stream` has finished, polling without

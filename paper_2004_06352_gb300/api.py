@@ -24,7 +24,8 @@ LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_cset_create", "lens_cset_release",
-           "lens_chi2_source", "lens_chi2_image", "lens_wait", "lens_strerror", "lens_last_error")
+           "lens_chi2_source", "lens_chi2_image", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
+           "lens_last_error")
 
 
 class LensError(RuntimeError):
@@ -68,6 +69,7 @@ def load_library(path=LIB_PATH):
         "lens_cset_release": (C.c_int, [vp, i64]),
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_image": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
+        "lens_chi2_image_noalloc": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
         "lens_wait": (C.c_int, [vp, vp, i64]),
         "lens_strerror": (C.c_char_p, [C.c_int]),
         "lens_last_error": (C.c_char_p, []),
@@ -191,6 +193,17 @@ class Context:
                                   _stream(stream))
         if rc not in (LENS_OK, LENS_ECAPACITY):
             raise LensError(rc, "lens_chi2_image")
+        return rc
+
+    def chi2_image_noalloc(self, cset, grid, params, P, chi2, nfound=None, stream=None):
+        """lens_chi2_image with all working memory in the library's fixed
+        device array: for loops that may not allocate device memory at call
+        time.  Overlapping calls race on that array."""
+        g = make_grid(grid)
+        rc = _lib.lens_chi2_image_noalloc(self.h, int(cset), C.byref(g), _ptr(params), int(P), _ptr(chi2),
+                                          _ptr(nfound), _stream(stream))
+        if rc not in (LENS_OK, LENS_ECAPACITY):
+            raise LensError(rc, "lens_chi2_image_noalloc")
         return rc
 
     def wait(self, stream=None, timeout_ms=60000):
