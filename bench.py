@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the chi2 / FP64 comparison legs")
+    ap.add_argument("--profile-leg", default=None, choices=["map", "chi2_source", "chi2_image"],
+                    help="run only this workload `--steps` times (for ncu launch lists); prints nothing")
     return ap.parse_args()
 
 
@@ -159,6 +161,9 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.profile_leg:
+        profile_leg(args)
         return
     import torch
     from paper_2004_06352_gb300 import build as B
@@ -313,6 +318,11 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     t = timed(lambda: ctx.chi2_image(cs, gi, params[:Pi], Pi, chi2i, None, stream), 2)
     ex["chi2_image"] = {"ms": t, "models_per_s": Pi / (t * 1e-3), "P": Pi,
                         "workload": "image-plane chi2, 1024^2 triangulated grid, 256 parameter sets, 1000 potentials"}
+    # request loop: mixed Poisson stream over 8 resident models
+    try:
+        ex["serving"] = serving_leg(ctx, api, torch)
+    except Exception as e:  # keep the line
+        ex["serving"] = {"error": str(e)}
     # CPU baseline: the oracle on the host cores, ~15 s of row bands
     try:
         rate, rows, thr = oracle_map_sample(m, g, 15.0)
@@ -322,6 +332,81 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
         ex["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                               "sample": f"failed: {e}"}
     return ex
+
+
+def profile_leg(args):
+    """One workload, warmup + steps launches, for profilers."""
+    import torch
+    from paper_2004_06352_gb300 import build as B
+    B.build()
+    from paper_2004_06352_gb300 import api
+    from paper_2004_06352_gb300 import inputs as I
+    dev = torch.device("cuda", 0)
+    ctx = api.Context(0)
+    m = I.cfg2_model()
+    mid = ctx.model_upload(m)
+    if args.profile_leg == "map":
+        g = I.grid(MAP_N)
+        out = torch.empty((6, MAP_N, MAP_N), dtype=torch.float32, device=dev)
+        run = lambda: ctx.hessian_map(mid, g, 1.0, api.LENS_MIXED, out)
+    else:
+        cons = I.load_constraints(os.path.join(ROOT, "tests", "golden", "cfg2_constraints.json"))
+        cs = ctx.cset_create(mid, cons, (0, 1))
+        P = 4096 if args.profile_leg == "chi2_source" else 256
+        params = torch.tensor(I.perturbed_params(m, (0, 1), P, seed=35), device=dev)
+        chi2 = torch.empty(P, dtype=torch.float64, device=dev)
+        if args.profile_leg == "chi2_source":
+            run = lambda: ctx.chi2_source(cs, params, P, 0, chi2)
+        else:
+            gi = I.grid(1024)
+            run = lambda: ctx.chi2_image(cs, gi, params, P, chi2)
+    for _ in range(args.warmup + args.steps):
+        run()
+    ctx.wait()
+    ctx.close()
+
+
+def serving_leg(ctx, api, torch):
+    """Capacity (closed loop, <= 8 outstanding) and p50/p99 latency of Poisson
+    streams at 50/80/95 % of capacity: 60 % Hessian maps 512^2-8192^2 on
+    models of 10-2000 potentials, 40 % source-plane chi2 of 16-4096 sets;
+    plus the same requests (maps <= 2048^2) served by the plain FP64 form."""
+    from paper_2004_06352_gb300 import serving as S
+    out = {}
+    models = S.resident_models(8, seed=11)
+    sess = S.Session(ctx, models)
+    srv = api.Server(ctx, slots=4, pool_bytes=12 << 30)
+    pool = S.PinnedPool()
+    for side in S.MAP_SIDES:   # page-lock the result buffers before timing
+        for _ in range(4 if side == 8192 else 6):
+            pool.give(torch.empty((6, side, side), dtype=torch.float32, pin_memory=True))
+    warm = S.mixed_requests(8, seed=12, n_models=8, sides=(512, 1024))
+    S.run_stream(srv, sess, warm, pool=pool, max_outstanding=8, keep_results=False)
+    # one request list (200 requests) for the capacity and every load level
+    reqs = S.mixed_requests(200, seed=13, n_models=8)
+    lat, wall, _, _ = S.run_stream(srv, sess, reqs, pool=pool, max_outstanding=8, keep_results=False)
+    cap = len(reqs) / wall
+    out["capacity_req_per_s"] = cap
+    out["closed_loop"] = S.percentiles(lat)
+    for frac in (0.5, 0.8, 0.95):
+        arr = S.poisson_arrivals(len(reqs), frac * cap, seed=int(1000 * frac))
+        lat, wall, _, _ = S.run_stream(srv, sess, reqs, arr, pool=pool, keep_results=False)
+        out[f"load_{int(100 * frac)}"] = dict(S.percentiles(lat), offered_req_per_s=frac * cap,
+                                               served_req_per_s=len(reqs) / wall, n=len(reqs))
+    srv.close()
+    # same small-map requests through the mixed and the plain FP64 forms
+    small = S.mixed_requests(24, seed=14, n_models=8, sides=(512, 1024, 2048))
+    res = {}
+    for name, prec in (("mixed", api.LENS_MIXED), ("fp64", api.LENS_FP64)):
+        s2 = S.Session(ctx, models, precision=prec)
+        srv = api.Server(ctx, slots=4, pool_bytes=4 << 30)
+        lat, wall, _, _ = S.run_stream(srv, s2, small, max_outstanding=8, keep_results=False)
+        res[name] = dict(S.percentiles(lat), req_per_s=len(small) / wall)
+        srv.close()
+    out["mixed_vs_fp64_same_requests"] = res
+    out["workload"] = ("Poisson mix: 60% Hessian maps side 512-8192 (uniform over powers of 2), 8 resident models "
+                       "of 10-2000 potentials; 40% source-plane chi2 with 16-4096 sets; 4 slots, 12 GiB pool")
+    return out
 
 
 if __name__ == "__main__":

@@ -207,6 +207,64 @@ int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, cons
 int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params,
                             int32_t P, double *d_chi2, int32_t *d_nimg_found, void *stream);
 
+/* ---------------------------------------------------------- request loop */
+/* A server runs map and chi2 requests of uneven sizes on `slots` CUDA
+ * streams of its own, admitting queued requests (in arrival order; a request
+ * that does not fit may be overtaken by smaller ones until it has waited 64
+ * rounds) whenever a slot is free and its device buffers fit in the server's
+ * pool -- one allocation of pool_bytes made at creation and counted against
+ * the context budget.  Work of different slots overlaps on the device; each
+ * request runs the same kernels as the direct calls on its own buffers, so
+ * its result does not depend on what else is in flight.  Models and
+ * constraint sets stay resident in the context.  Not part of the paper's
+ * method: it serves the maps (Sec. 2.4) and chi2 (Sec. 2.2) above. */
+#define LENS_REQ_MAP 0
+#define LENS_REQ_CHI2_SOURCE 1
+#define LENS_REQ_CHI2_IMAGE 2
+
+typedef struct lens_server lens_server;
+
+typedef struct {
+  int32_t kind;          /* LENS_REQ_*                                          */
+  int64_t handle;        /* model (maps) or constraint set (chi2)               */
+  lens_grid grid;        /* maps and image-plane chi2                           */
+  double dls_ds;         /* maps                                                */
+  int32_t precision;     /* maps: LENS_MIXED or LENS_FP64                       */
+  int32_t hessian;       /* maps: 0 = 2 deflection planes, 1 = all 6 planes      */
+  int32_t variant;       /* source-plane chi2                                   */
+  int32_t P;             /* chi2: number of parameter sets                      */
+  const double *params;  /* chi2: HOST double [P][14], copied at submit         */
+  void *result;          /* PAGE-LOCKED host destination: the map planes (as
+                            lens_grad_map / lens_hessian_map lay them out) or
+                            double [P] chi2; written when the ticket completes */
+} lens_request;
+
+typedef struct {
+  int64_t ticket;
+  int32_t status;        /* LENS_OK or the error that ended the request         */
+  double queue_ms;       /* submit -> admitted onto a slot                      */
+  double latency_ms;     /* submit -> completion observed by lens_server_progress */
+} lens_completion;
+
+typedef struct {
+  int32_t queued, inflight;
+  size_t pool_bytes, pool_used, pool_peak;
+} lens_server_info;
+
+int lens_server_create(lens_ctx *ctx, int32_t slots, size_t pool_bytes, lens_server **out);
+/* Waits for the work in flight, drops queued requests, frees the pool. */
+int lens_server_destroy(lens_server *s);
+/* Validate and queue; never blocks on the GPU (the first image-plane request
+ * for a new (constraint set, grid) pair builds that pair's static deflection
+ * synchronously).  LENS_ENOMEM if the request can never fit in the pool. */
+int lens_server_submit(lens_server *s, const lens_request *r, int64_t *ticket);
+/* Non-blocking: retire finished requests into done[0..cap) (*n_done of them),
+ * then admit queued requests onto free slots. */
+int lens_server_progress(lens_server *s, lens_completion *done, int32_t cap, int32_t *n_done);
+/* Remove a request that has not been admitted yet (LENS_ENOTFOUND otherwise). */
+int lens_server_cancel(lens_server *s, int64_t ticket);
+int lens_server_stats(const lens_server *s, lens_server_info *info);
+
 /* --------------------------------------------------------------- control */
 
 /* Wait until all work enqueued on `stream` has finished, polling without

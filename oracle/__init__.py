@@ -29,6 +29,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblens_oracle.so")
 _lock = threading.Lock()
 _lib = None
+_override = None  # path of an alternative build (the mutation tests load mutants)
 
 
 class Halo(C.Structure):
@@ -64,7 +65,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        lib = C.CDLL(_override or build())
         dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
         hp, cp, gp = C.POINTER(Halo), C.POINTER(Constraints), C.POINTER(Grid)
         sig = {
@@ -96,6 +97,30 @@ def _load():
             f.argtypes = args
         _lib = lib
         return lib
+
+
+def use_library(path):
+    """Route every wrapper to the library at `path` (None: the normal build).
+    Used by the tests that load deliberately broken copies of the oracle."""
+    global _lib, _override
+    with _lock:
+        _override = path
+        _lib = None
+
+
+def build_variant(src_text, out_path):
+    """Compile C source text (a modified copy of lens_oracle.c) to out_path."""
+    src = out_path[:-3] + ".c"
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", out_path, src, "-lm"],
+                   check=True)
+    return out_path
+
+
+def source_text():
+    with open(_SRC) as f:
+        return f.read()
 
 
 # ----------------------------------------------------------------- marshalling

@@ -25,7 +25,9 @@ LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_cset_create", "lens_cset_release",
            "lens_chi2_source", "lens_chi2_image", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
-           "lens_last_error")
+           "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
+           "lens_server_progress", "lens_server_cancel", "lens_server_stats")
+LENS_REQ_MAP, LENS_REQ_CHI2_SOURCE, LENS_REQ_CHI2_IMAGE = 0, 1, 2
 
 
 class LensError(RuntimeError):
@@ -51,6 +53,21 @@ class lens_constraints(C.Structure):
                 ("dls_ds", C.POINTER(C.c_double))]
 
 
+class lens_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("handle", C.c_int64), ("grid", lens_grid), ("dls_ds", C.c_double),
+                ("precision", C.c_int32), ("hessian", C.c_int32), ("variant", C.c_int32), ("P", C.c_int32),
+                ("params", C.POINTER(C.c_double)), ("result", C.c_void_p)]
+
+
+class lens_completion(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("status", C.c_int32), ("queue_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
+class lens_server_info(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("inflight", C.c_int32), ("pool_bytes", C.c_size_t),
+                ("pool_used", C.c_size_t), ("pool_peak", C.c_size_t)]
+
+
 def load_library(path=LIB_PATH):
     if not os.path.exists(path):
         raise ImportError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
@@ -71,6 +88,12 @@ def load_library(path=LIB_PATH):
         "lens_chi2_image": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
         "lens_chi2_image_noalloc": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
         "lens_wait": (C.c_int, [vp, vp, i64]),
+        "lens_server_create": (C.c_int, [vp, C.c_int32, C.c_size_t, C.POINTER(vp)]),
+        "lens_server_destroy": (C.c_int, [vp]),
+        "lens_server_submit": (C.c_int, [vp, C.POINTER(lens_request), C.POINTER(i64)]),
+        "lens_server_progress": (C.c_int, [vp, C.POINTER(lens_completion), C.c_int32, C.POINTER(C.c_int32)]),
+        "lens_server_cancel": (C.c_int, [vp, i64]),
+        "lens_server_stats": (C.c_int, [vp, C.POINTER(lens_server_info)]),
         "lens_strerror": (C.c_char_p, [C.c_int]),
         "lens_last_error": (C.c_char_p, []),
     }
@@ -208,6 +231,71 @@ class Context:
 
     def wait(self, stream=None, timeout_ms=60000):
         return _check(_lib.lens_wait(self.h, _stream(stream), int(timeout_ms)), "lens_wait")
+
+
+class Server:
+    """Request loop of a context (lens_server_*): map and chi2 requests run on
+    `slots` streams of its own, admitted by the device memory of its pool.
+    Results land in page-locked host tensors given at submit."""
+
+    def __init__(self, ctx, slots=4, pool_bytes=1 << 30):
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        _check(_lib.lens_server_create(ctx.h, int(slots), int(pool_bytes), C.byref(self.h)), "lens_server_create")
+        self._done = (lens_completion * 256)()
+
+    def close(self):
+        if self.h:
+            _lib.lens_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _submit(self, req, keep=None):
+        t = C.c_int64()
+        _check(_lib.lens_server_submit(self.h, C.byref(req), C.byref(t)), "lens_server_submit")
+        return t.value
+
+    def submit_map(self, model, grid, dls_ds, precision, hessian, result):
+        """result: pinned host tensor of (6 if hessian else 2) x ny x nx elements."""
+        r = lens_request(LENS_REQ_MAP, int(model), make_grid(grid), float(dls_ds), int(precision), int(bool(hessian)),
+                         0, 0, None, C.c_void_p(result.data_ptr()))
+        return self._submit(r)
+
+    def submit_chi2_source(self, cset, params, variant, result):
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 14)
+        r = lens_request(LENS_REQ_CHI2_SOURCE, int(cset), lens_grid(), 0.0, 0, 0, int(variant), len(p),
+                         p.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(result.data_ptr()))
+        return self._submit(r)
+
+    def submit_chi2_image(self, cset, grid, params, result):
+        p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 14)
+        r = lens_request(LENS_REQ_CHI2_IMAGE, int(cset), make_grid(grid), 0.0, 0, 0, 0, len(p),
+                         p.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(result.data_ptr()))
+        return self._submit(r)
+
+    def progress(self):
+        """Retire finished requests and admit queued ones; returns a list of
+        (ticket, status, queue_ms, latency_ms)."""
+        n = C.c_int32()
+        rc = _lib.lens_server_progress(self.h, self._done, len(self._done), C.byref(n))
+        out = [(d.ticket, d.status, d.queue_ms, d.latency_ms) for d in self._done[:n.value]]
+        if rc != LENS_OK and not out:
+            raise LensError(rc, "lens_server_progress")
+        return out
+
+    def cancel(self, ticket):
+        _check(_lib.lens_server_cancel(self.h, int(ticket)), "lens_server_cancel")
+
+    def stats(self):
+        i = lens_server_info()
+        _check(_lib.lens_server_stats(self.h, C.byref(i)), "lens_server_stats")
+        return {"queued": i.queued, "inflight": i.inflight, "pool_bytes": i.pool_bytes, "pool_used": i.pool_used,
+                "pool_peak": i.pool_peak}
 
 
 def strerror(code):

@@ -517,6 +517,40 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   return LENS_OK;
 }
 
+const GridCache *find_grid_cache(const CSet *c, const lens_grid *g) {
+  for (auto &x : c->grids)
+    if (x.xmin == g->xmin && x.xmax == g->xmax && x.ymin == g->ymin && x.ymax == g->ymax && x.nx == g->nx &&
+        x.ny == g->ny)
+      return &x;
+  return nullptr;
+}
+
+// Static deflection of the constraint set's model on grid g (LENS_MIXED map
+// of the static potentials, D_ls/D_s = 1), enqueued on st and kept with the
+// constraint set.
+int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st) {
+  GridCache n;
+  n.xmin = g->xmin;
+  n.xmax = g->xmax;
+  n.ymin = g->ymin;
+  n.ymax = g->ymax;
+  n.nx = g->nx;
+  n.ny = g->ny;
+  n.bytes = 2 * sizeof(float) * (size_t)g->nx * g->ny;
+  int rc = dev_alloc(ctx, (void **)&n.alpha32, n.bytes);
+  if (rc) return rc;
+  if (c->stat_model->n > 0)
+    rc = launch_map_mixed(ctx, c->stat_model, g, 1.0, false, n.alpha32, st);
+  else
+    rc = cudaMemsetAsync(n.alpha32, 0, n.bytes, st) == cudaSuccess ? LENS_OK : fail(LENS_ECUDA, "memset failed");
+  if (rc) {
+    dev_free(ctx, n.alpha32, n.bytes);
+    return rc;
+  }
+  c->grids.push_back(n);
+  return LENS_OK;
+}
+
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
                       double *d_chi2, int32_t *d_nfound, cudaStream_t st) {
   (void)m;
@@ -524,37 +558,14 @@ int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g
   const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
   if (src_smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
   if ((long long)(g->nx - 1) * (g->ny - 1) > (1ll << 30)) return fail(LENS_EINVAL, "grid too large");
-  // static deflection on this grid, cached per constraint set
-  GridCache *gc = nullptr;
-  for (auto &x : c->grids)
-    if (x.xmin == g->xmin && x.xmax == g->xmax && x.ymin == g->ymin && x.ymax == g->ymax && x.nx == g->nx &&
-        x.ny == g->ny)
-      gc = &x;
+  const GridCache *gc = find_grid_cache(c, g);
   if (!gc) {
-    GridCache n;
-    n.xmin = g->xmin;
-    n.xmax = g->xmax;
-    n.ymin = g->ymin;
-    n.ymax = g->ymax;
-    n.nx = g->nx;
-    n.ny = g->ny;
-    n.bytes = 2 * sizeof(float) * (size_t)g->nx * g->ny;
-    int rc = dev_alloc(ctx, (void **)&n.alpha32, n.bytes);
+    int rc = build_grid_cache(ctx, c, g, st);
     if (rc) return rc;
-    if (c->stat_model->n > 0) {
-      rc = launch_map_mixed(ctx, c->stat_model, g, 1.0, false, n.alpha32, st);
-    } else {
-      rc = cudaMemsetAsync(n.alpha32, 0, n.bytes, st) == cudaSuccess ? LENS_OK : LENS_ECUDA;
-    }
-    if (rc) {
-      dev_free(ctx, n.alpha32, n.bytes);
-      return rc;
-    }
-    c->grids.push_back(n);
-    gc = &c->grids.back();
+    gc = find_grid_cache(c, g);
   }
   const int32_t batch = std::min<int32_t>(IMG_BATCH, P);
-  int rc = ensure_scratch(ctx, chi2_image_scratch_bytes(c, batch));
+  const int rc = ensure_scratch(ctx, chi2_image_scratch_bytes(c, batch));
   if (rc) return rc;
   return run_chi2_image(ctx, c, gc, d_params, P, d_chi2, d_nfound, ctx->scratch, batch, st);
 }

@@ -48,8 +48,8 @@ enum Rec64 : int {
 };
 constexpr int REC64 = 16;
 
-// u = sqrt(1 - q^2) below which the FP32 / FP64 paths use the series of
-// atan(w)/w and atanh(w)/w (|w| < u there; truncation below 5e-9 / 1e-24).
+// u = sqrt(1 - q^2) below which the FP32 / FP64 paths always use the
+// polynomial / series forms of atan(w)/w and atanh(w)/w (|w| < u there).
 constexpr double U_SERIES32 = 0.12;
 constexpr double U_SERIES64 = 1e-4;
 
@@ -236,6 +236,8 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
                       double *d_chi2, int32_t *d_nfound, cudaStream_t st);
 size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch);
+const GridCache *find_grid_cache(const CSet *c, const lens_grid *g);
+int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st);
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P,
                    double *d_chi2, int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st);
 
