@@ -82,9 +82,9 @@ def _load():
             "or_chi2_source": (C.c_double, [hp, C.c_int32, cp, C.c_int32]),
             "or_chi2_source_batch": (None, [hp, C.c_int32, cp, ip, dp, C.c_int32, C.c_int32, dp]),
             "or_newton": (C.c_int32, [hp, C.c_int32, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int32,
-                                      C.c_double]),
+                                      C.c_double, C.c_double]),
             "or_find_images": (C.c_int32, [hp, C.c_int32, gp, dp, C.c_double, C.c_double, C.c_double,
-                                           C.c_int32, C.c_double, C.c_double, dp, C.c_int32]),
+                                           C.c_int32, C.c_double, C.c_double, dp, C.c_int32, ip]),
             "or_alpha_grid": (None, [hp, C.c_int32, gp, dp]),
             "or_chi2_image": (C.c_double, [hp, C.c_int32, cp, gp, dp, C.c_int32, C.c_double, C.c_double,
                                            C.c_int32, ip]),
@@ -261,13 +261,13 @@ def chi2_source_batch(table, cons, var_halo, params, variant=0):
     return out
 
 
-def newton(table, r, beta_s, theta0, maxit=20, tol=1e-6):
+def newton(table, r, beta_s, theta0, maxit=40, tol=1e-6, step_max=0.0):
     """Newton solve of beta_s = theta - r alpha(theta); returns (theta, iters or -1)."""
     lib = _load()
     h, n = halos_from_table(table)
     tx, ty = C.c_double(theta0[0]), C.c_double(theta0[1])
     it = lib.or_newton(h, n, float(r), float(beta_s[0]), float(beta_s[1]), C.byref(tx), C.byref(ty),
-                       int(maxit), float(tol))
+                       int(maxit), float(tol), float(step_max))
     return np.array([tx.value, ty.value]), int(it)
 
 
@@ -280,8 +280,10 @@ def alpha_grid(table, grid):
     return out
 
 
-def find_images(table, grid, r, beta_s, maxit=20, tol=1e-6, dedup=1e-3, cap=64, ag=None):
-    """Brute-force predicted images of one source (Sec. 2.3 Fig. 4; Sec. 4.2)."""
+def find_images(table, grid, r, beta_s, maxit=40, tol=1e-6, dedup=1e-3, cap=64, ag=None, with_difficulty=False):
+    """Brute-force predicted images of one source (Sec. 2.3 Fig. 4; Sec. 4.2).
+    With with_difficulty, also each image's difficulty (100 x refinement cut
+    short + Newton iterations of its easiest candidate)."""
     lib = _load()
     h, n = halos_from_table(table)
     g = _grid(grid)
@@ -289,12 +291,16 @@ def find_images(table, grid, r, beta_s, maxit=20, tol=1e-6, dedup=1e-3, cap=64, 
         ag = alpha_grid(table, grid)
     ag = np.ascontiguousarray(ag, dtype=np.float64)
     img = np.zeros((cap, 2))
+    diff = np.zeros(cap, dtype=np.int32)
     nf = lib.or_find_images(h, n, C.byref(g), _dp(ag), float(r), float(beta_s[0]), float(beta_s[1]), int(maxit),
-                            float(tol), float(dedup), _dp(img), int(cap))
-    return img[:min(nf, cap)].copy(), int(nf)
+                            float(tol), float(dedup), _dp(img), int(cap), _ip(diff))
+    k = min(nf, cap)
+    if with_difficulty:
+        return img[:k].copy(), int(nf), diff[:k].copy()
+    return img[:k].copy(), int(nf)
 
 
-def chi2_image(table, cons, grid, maxit=20, tol=1e-6, dedup=1e-3, cap=64, ag=None):
+def chi2_image(table, cons, grid, maxit=40, tol=1e-6, dedup=1e-3, cap=64, ag=None):
     """Image-plane chi2 of one model (Sec. 2.2 Eq. 6 with the brute-force
     search of Sec. 2.3 / Sec. 4.2).  Returns (chi2, nfound[nsrc])."""
     lib = _load()
@@ -311,7 +317,7 @@ def chi2_image(table, cons, grid, maxit=20, tol=1e-6, dedup=1e-3, cap=64, ag=Non
     return float(v), nf
 
 
-def chi2_image_batch(table, cons, grid, var_halo, params, maxit=20, tol=1e-6, dedup=1e-3, cap=64):
+def chi2_image_batch(table, cons, grid, var_halo, params, maxit=40, tol=1e-6, dedup=1e-3, cap=64):
     lib = _load()
     h, n = halos_from_table(table)
     cr = _ConstraintsRef(cons)

@@ -16,7 +16,8 @@
  *   - chi2 = sum_i sum_j |c_ij - x_ij|^2 / sigma_ij^2          (Sec. 2.2, Eq. 6)
  *   - source estimate = barycentre of the back-traced images   (Sec. 2.2, Fig. 3)
  *   - brute-force image search: ray-shoot a triangulated image-plane grid to
- *     the source plane and test each triangle for the source  (Sec. 2.3, Fig. 4;
+ *     the source plane, test each triangle for the source and refine a hit by
+ *     subdividing it                                             (Sec. 2.3, Fig. 4;
  *     Sec. 4.2, Fig. 8)
  *
  * The paper gives no profile formulas; it cites Eliasdottir et al. (2007) for
@@ -51,6 +52,14 @@
 #endif
 
 enum { OR_DPIE = 0, OR_SIS = 1, OR_POINT = 2 };
+
+/* Image search: subdivisions of a hit triangle before Newton, how far
+ * outside every sub-triangle (in barycentric weight) the source may be
+ * before the refinement stops, and how far (in cell sizes) a root may lie
+ * from the hit triangle's centroid. */
+#define SUBDIV_LEVELS 6
+#define SUBDIV_TOL 1e-3
+#define LOCAL_CELLS 2.0
 
 /* One potential, same field order as the halo table rows. */
 typedef struct {
@@ -358,10 +367,11 @@ void or_chi2_source_batch(const or_halo *base, int32_t n, const or_constraints *
 /* ---------------- brute-force image finding (Sec. 2.3, Fig. 4) ----------- */
 
 /* Newton iteration on the lens equation with the full model:
- * theta <- theta + A(theta) (beta_s - theta + r alpha(theta)), A = (I - r H)^-1.
+ * theta <- theta + A(theta) (beta_s - theta + r alpha(theta)), A = (I - r H)^-1,
+ * each step shortened to at most step_max (no limit if step_max <= 0).
  * Returns the iteration count on convergence (|step| < tol), -1 otherwise. */
 int32_t or_newton(const or_halo *h, int32_t n, double r, double bx, double by, double *tx, double *ty,
-                  int32_t maxit, double tol) {
+                  int32_t maxit, double tol, double step_max) {
   double x = *tx, y = *ty;
   for (int32_t it = 1; it <= maxit; ++it) {
     double v[5];
@@ -372,6 +382,11 @@ int32_t or_newton(const or_halo *h, int32_t n, double r, double bx, double by, d
     if (det == 0.0 || !isfinite(det)) return -1;
     double dx = (a22 * fx - a12 * fy) / det;
     double dy = (-a12 * fx + a11 * fy) / det;
+    double len = sqrt(dx * dx + dy * dy);
+    if (step_max > 0.0 && len > step_max) { /* trust region: at most step_max per step */
+      dx *= step_max / len;
+      dy *= step_max / len;
+    }
     x += dx;
     y += dy;
     *tx = x;
@@ -399,16 +414,97 @@ static int in_triangle(const double a[2], const double b[2], const double c[2], 
   return 1;
 }
 
+/* Refine a hit (Sec. 2.3 and Sec. 4.2: the triangle holding the source is
+ * subdivided): `levels` times, split the triangle into its four midpoint
+ * sub-triangles (corners 0, 1, 2, then the middle one), map the three new
+ * vertices to the source plane with the full model, and keep the sub-triangle
+ * whose smallest barycentric weight of the source is largest (the first on a
+ * tie; degenerate sub-triangles are never kept).  When no sub-triangle holds
+ * the source the refinement stops at the current triangle.  th/be: image- and
+ * source-plane vertices, updated in place; w: the source's barycentric
+ * weights in the final triangle.  Returns the number of levels refined. */
+static void tri_weights(double be[3][2], const double p[2], double tiny, double w[3]) {
+  double area2 = (be[1][0] - be[0][0]) * (be[2][1] - be[0][1]) - (be[1][1] - be[0][1]) * (be[2][0] - be[0][0]);
+  if (fabs(area2) <= tiny) {
+    w[0] = w[1] = w[2] = 1.0 / 3.0;
+    return;
+  }
+  w[0] = ((be[1][0] - p[0]) * (be[2][1] - p[1]) - (be[1][1] - p[1]) * (be[2][0] - p[0])) / area2;
+  w[1] = ((be[2][0] - p[0]) * (be[0][1] - p[1]) - (be[2][1] - p[1]) * (be[0][0] - p[0])) / area2;
+  w[2] = 1.0 - w[0] - w[1];
+}
+
+static int subdivide(const or_halo *h, int32_t n, double r, const double p[2], double th[3][2], double be[3][2],
+                     int32_t levels, double tiny, double w[3]) {
+  static const int sub[4][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}, {3, 4, 5}};
+  static const int mid[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+  for (int32_t lev = 0;; ++lev) {
+    if (lev == levels) {
+      tri_weights(be, p, tiny, w);
+      return lev;
+    }
+    double t6[6][2], b6[6][2];
+    for (int k = 0; k < 3; ++k) {
+      double v[5];
+      t6[k][0] = th[k][0];
+      t6[k][1] = th[k][1];
+      b6[k][0] = be[k][0];
+      b6[k][1] = be[k][1];
+      t6[3 + k][0] = 0.5 * (th[mid[k][0]][0] + th[mid[k][1]][0]);
+      t6[3 + k][1] = 0.5 * (th[mid[k][0]][1] + th[mid[k][1]][1]);
+      or_model_eval(h, n, t6[3 + k][0], t6[3 + k][1], r, v);
+      b6[3 + k][0] = t6[3 + k][0] - v[0];
+      b6[3 + k][1] = t6[3 + k][1] - v[1];
+    }
+    const double tiny_sub = 0.25 * tiny;
+    int best = -1;
+    double best_score = -INFINITY;
+    for (int s = 0; s < 4; ++s) {
+      const double *a = b6[sub[s][0]], *b = b6[sub[s][1]], *c = b6[sub[s][2]];
+      double area2 = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]);
+      if (fabs(area2) <= tiny_sub) continue;
+      double wa = ((b[0] - p[0]) * (c[1] - p[1]) - (b[1] - p[1]) * (c[0] - p[0])) / area2;
+      double wb = ((c[0] - p[0]) * (a[1] - p[1]) - (c[1] - p[1]) * (a[0] - p[0])) / area2;
+      double wc = 1.0 - wa - wb;
+      double score = fmin(wa, fmin(wb, wc));
+      if (score > best_score) {
+        best_score = score;
+        best = s;
+      }
+    }
+    if (best < 0 || best_score < -SUBDIV_TOL) {
+      /* no sub-triangle holds the source: the map is far from linear on this
+       * triangle (a galaxy core or a fold inside); stop refining here */
+      tri_weights(be, p, tiny, w);
+      return lev;
+    }
+    for (int k = 0; k < 3; ++k) {
+      th[k][0] = t6[sub[best][k]][0];
+      th[k][1] = t6[sub[best][k]][1];
+      be[k][0] = b6[sub[best][k]][0];
+      be[k][1] = b6[sub[best][k]][1];
+    }
+    tiny = tiny_sub;
+  }
+}
+
 /* Predicted images of one source at beta_s for distance ratio r.
  * alpha_grid: [ny][nx][2] deflection at the grid nodes for D_ls/D_s = 1.
  * Each grid cell (i, j) splits into triangles {(i,j),(i+1,j),(i+1,j+1)} and
- * {(i,j),(i+1,j+1),(i,j+1)}, visited in (j, i, k) order.  A hit seeds Newton
- * at the barycentric interpolation of the image-plane vertices; converged
- * images closer than dedup to an earlier one are dropped.
+ * {(i,j),(i+1,j+1),(i,j+1)}, visited in (j, i, k) order.  A triangle holding
+ * the source is refined by SUBDIV_LEVELS subdivisions; Newton starts at the
+ * source's barycentric position in the final sub-triangle.  A converged root
+ * counts only if it lies within LOCAL_CELLS cell sizes of the hit triangle's
+ * centroid (a root further away belongs to another triangle's search), and
+ * images closer than dedup to an earlier one are dropped.  Newton steps are
+ * limited to one cell size.  difficulty (may be NULL) receives per image the
+ * smallest, over the candidates that reached it, of 100 x (refinement cut
+ * short) + Newton iterations.
  * Returns the number of images written to img (capacity cap), or the number
  * found if it exceeds cap (the caller treats that as an overflow). */
 int32_t or_find_images(const or_halo *h, int32_t n, const or_grid *g, const double *alpha_grid, double r,
-                       double bx, double by, int32_t maxit, double tol, double dedup, double *img, int32_t cap) {
+                       double bx, double by, int32_t maxit, double tol, double dedup, double *img, int32_t cap,
+                       int32_t *difficulty) {
   int32_t found = 0;
   double dx = (g->xmax - g->xmin) / (g->nx - 1), dy = (g->ymax - g->ymin) / (g->ny - 1);
   double tiny = 1e-14 * fabs(dx * dy);
@@ -429,21 +525,38 @@ int32_t or_find_images(const or_halo *h, int32_t n, const or_grid *g, const doub
         const int *v = tri[t];
         double w[3];
         if (!in_triangle(be[v[0]], be[v[1]], be[v[2]], p, tiny, w)) continue;
-        double tx = w[0] * th[v[0]][0] + w[1] * th[v[1]][0] + w[2] * th[v[2]][0];
-        double ty = w[0] * th[v[0]][1] + w[1] * th[v[1]][1] + w[2] * th[v[2]][1];
-        if (or_newton(h, n, r, bx, by, &tx, &ty, maxit, tol) < 0) continue;
-        int dup = 0;
+        double tt[3][2], bb[3][2];
+        for (int k = 0; k < 3; ++k) {
+          tt[k][0] = th[v[k]][0];
+          tt[k][1] = th[v[k]][1];
+          bb[k][0] = be[v[k]][0];
+          bb[k][1] = be[v[k]][1];
+        }
+        double cx = (tt[0][0] + tt[1][0] + tt[2][0]) / 3.0, cy = (tt[0][1] + tt[1][1] + tt[2][1]) / 3.0;
+        const int32_t lev = subdivide(h, n, r, p, tt, bb, SUBDIV_LEVELS, tiny, w);
+        double tx = w[0] * tt[0][0] + w[1] * tt[1][0] + w[2] * tt[2][0];
+        double ty = w[0] * tt[0][1] + w[1] * tt[1][1] + w[2] * tt[2][1];
+        const int32_t it = or_newton(h, n, r, bx, by, &tx, &ty, maxit, tol, fmax(dx, dy));
+        if (it < 0) continue;
+        if (hypot(tx - cx, ty - cy) > LOCAL_CELLS * fmax(dx, dy)) continue;
+        /* how hard this candidate was: refinement cut short, Newton iterations */
+        const int32_t diff = (lev < SUBDIV_LEVELS ? 100 : 0) + it;
+        int dup = -1;
         for (int32_t k = 0; k < found && k < cap; ++k) {
           double ex = img[2 * k] - tx, ey = img[2 * k + 1] - ty;
           if (sqrt(ex * ex + ey * ey) < dedup) {
-            dup = 1;
+            dup = k;
             break;
           }
         }
-        if (dup) continue;
+        if (dup >= 0) {
+          if (difficulty && diff < difficulty[dup]) difficulty[dup] = diff;
+          continue;
+        }
         if (found < cap) {
           img[2 * found] = tx;
           img[2 * found + 1] = ty;
+          if (difficulty) difficulty[found] = diff;
         }
         ++found;
       }
@@ -491,7 +604,7 @@ double or_chi2_image(const or_halo *h, int32_t n, const or_constraints *c, const
 #pragma omp for schedule(dynamic, 1)
     for (int32_t i = 0; i < c->nsrc; ++i) {
       int32_t nf = or_find_images(h, n, g, alpha_grid, c->dls_ds[i], bary[2 * i], bary[2 * i + 1], maxit, tol,
-                                  dedup, img, cap);
+                                  dedup, img, cap, NULL);
       if (nfound) nfound[i] = nf;
       double ci = 0.0;
       if (nf > cap || (nf == 0 && c->off[i + 1] > c->off[i])) ci = NAN;
