@@ -174,6 +174,15 @@ int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
 int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                      double *d_chi2, void *stream);
 
+/* Autotuner of lens_chi2_source's launch shape (threads per CTA x CTAs per
+ * SM, 8 candidates) for this constraint set: runs each candidate on d_params
+ * (DEVICE [P][14]) into d_chi2 (DEVICE [P]) on `stream`, times it (best of
+ * 3 after a warm-up), and keeps the fastest for every later lens_chi2_source
+ * call on the set.  Synchronous.  *chosen (may be NULL) = threads*100 +
+ * CTAs-per-SM cap (0 = no cap); *best_ms (may be NULL) its time. */
+int lens_chi2_autotune(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, double *d_chi2,
+                       void *stream, int32_t *chosen, float *best_ms);
+
 /* Image-plane chi2 of P parameter sets (Sec. 2.2, Eq. 6 with the brute-force
  * image search of Sec. 2.3, Fig. 4 and Sec. 4.2): per set, the grid is
  * ray-shot to each source's plane, every triangle containing the source's
@@ -186,6 +195,16 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
  * LENS_ECAPACITY after synchronising the stream on overflow). */
 int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
                     double *d_chi2, int32_t *d_nimg_found, void *stream);
+
+/* Predicted images of P parameter sets: the search of lens_chi2_image
+ * (Sec. 2.3, Fig. 4; Sec. 4.2) without the matching.  Per set p, d_images
+ * (DEVICE double [P][max_per_set][3]) receives (x, y, source index) of each
+ * distinct image of every source's barycentre, in no particular order, and
+ * d_count[p] (DEVICE int32 [P]) their number (-1 on a candidate-buffer
+ * overflow, 0 for a set outside the model's domain; only the first
+ * max_per_set are written). */
+int lens_find_images(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
+                     double *d_images, int32_t max_per_set, int32_t *d_count, void *stream);
 
 /* Image-plane chi2 that allocates nothing (the paper has no counterpart).
  * For callers that reserve all device memory up front and may not call

@@ -24,7 +24,7 @@ LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_cset_create", "lens_cset_release",
-           "lens_chi2_source", "lens_chi2_image", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
+           "lens_chi2_source", "lens_chi2_autotune", "lens_chi2_image", "lens_find_images", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
            "lens_server_progress", "lens_server_cancel", "lens_server_stats")
 LENS_REQ_MAP, LENS_REQ_CHI2_SOURCE, LENS_REQ_CHI2_IMAGE = 0, 1, 2
@@ -85,7 +85,10 @@ def load_library(path=LIB_PATH):
         "lens_cset_create": (C.c_int, [vp, i64, C.POINTER(lens_constraints), C.POINTER(C.c_int32), C.POINTER(i64)]),
         "lens_cset_release": (C.c_int, [vp, i64]),
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
+        "lens_chi2_autotune": (C.c_int, [vp, i64, vp, C.c_int32, vp, vp, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_float)]),
         "lens_chi2_image": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
+        "lens_find_images": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, C.c_int32, vp, vp]),
         "lens_chi2_image_noalloc": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
         "lens_wait": (C.c_int, [vp, vp, i64]),
         "lens_server_create": (C.c_int, [vp, C.c_int32, C.c_size_t, C.POINTER(vp)]),
@@ -210,12 +213,29 @@ class Context:
                                      _stream(stream)), "lens_chi2_source")
         return chi2
 
+    def chi2_autotune(self, cset, params, P, chi2, stream=None):
+        """Pick and keep the fastest launch shape of chi2_source for this set;
+        returns (threads*100 + CTAs-per-SM cap, best ms)."""
+        cfg, ms = C.c_int32(), C.c_float()
+        _check(_lib.lens_chi2_autotune(self.h, int(cset), _ptr(params), int(P), _ptr(chi2), _stream(stream),
+                                       C.byref(cfg), C.byref(ms)), "lens_chi2_autotune")
+        return cfg.value, ms.value
+
     def chi2_image(self, cset, grid, params, P, chi2, nfound=None, stream=None):
         g = make_grid(grid)
         rc = _lib.lens_chi2_image(self.h, int(cset), C.byref(g), _ptr(params), int(P), _ptr(chi2), _ptr(nfound),
                                   _stream(stream))
         if rc not in (LENS_OK, LENS_ECAPACITY):
             raise LensError(rc, "lens_chi2_image")
+        return rc
+
+    def find_images(self, cset, grid, params, P, images, count, stream=None):
+        """images: device double [P][max_per_set][3]; count: device int32 [P]."""
+        g = make_grid(grid)
+        rc = _lib.lens_find_images(self.h, int(cset), C.byref(g), _ptr(params), int(P), _ptr(images),
+                                   int(images.shape[1]), _ptr(count), _stream(stream))
+        if rc not in (LENS_OK, LENS_ECAPACITY):
+            raise LensError(rc, "lens_find_images")
         return rc
 
     def chi2_image_noalloc(self, cset, grid, params, P, chi2, nfound=None, stream=None):

@@ -1,0 +1,54 @@
+"""Coefficients of the FP32 polynomials for atan(w)/w and atanh(w)/w in
+t = w^2 on [0, T] used by lens_device.cuh (atan_over_w / atanh_over_w).
+
+Chebyshev interpolation of the exact functions at the DEG+1 Chebyshev nodes
+of [0, T], converted to monomial coefficients in t; prints the coefficients
+and the worst relative error over a dense grid, exact (float64) and with the
+coefficients rounded to float32 and evaluated by FP32 Horner.
+
+  python paper_2004_06352_gb300/csrc/fit_series.py
+"""
+import numpy as np
+from numpy.polynomial import chebyshev as Ch
+from numpy.polynomial import polynomial as Pn
+
+T, DEG = 0.16, 5
+
+
+def f_atan(t):
+    w = np.sqrt(t)
+    return np.where(t > 0, np.arctan(w) / np.where(w > 0, w, 1), 1.0)
+
+
+def f_atanh(t):
+    w = np.sqrt(t)
+    return np.where(t > 0, np.arctanh(w) / np.where(w > 0, w, 1), 1.0)
+
+
+def fit(f):
+    k = np.arange(DEG + 1)
+    x = np.cos(np.pi * (k + 0.5) / (DEG + 1))
+    c = Ch.chebfit(x, f(0.5 * T * (x + 1)), DEG)
+    P = np.zeros(DEG + 1)
+    for i, a in enumerate(Ch.cheb2poly(c)):          # x = 2t/T - 1
+        P = Pn.polyadd(P, a * Pn.polypow([-1.0, 2.0 / T], i))[:DEG + 1]
+    return P
+
+
+def fp32_horner(P, t):
+    c = P.astype(np.float32)
+    acc = np.full(t.shape, c[-1], dtype=np.float32)
+    for a in c[-2::-1]:
+        acc = (acc.astype(np.float64) * t + a).astype(np.float32)
+    return acc
+
+
+if __name__ == "__main__":
+    tt = np.linspace(0, T, 200001)
+    t32 = tt.astype(np.float32).astype(np.float64)
+    for name, f in (("atan", f_atan), ("atanh", f_atanh)):
+        P = fit(f)
+        e = np.max(np.abs(Pn.polyval(tt, P) / f(tt) - 1))
+        e32 = np.max(np.abs(fp32_horner(P, t32) / f(t32) - 1))
+        print(f"{name}: max rel err {e:.2e} (exact arithmetic), {e32:.2e} (FP32 Horner)")
+        print("  " + ", ".join(f"{v:.9e}f" for v in P))

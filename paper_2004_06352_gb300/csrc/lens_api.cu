@@ -430,6 +430,16 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
   return launch_chi2_source(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
 }
 
+int lens_chi2_autotune(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, double *d_chi2,
+                       void *stream, int32_t *chosen, float *best_ms) {
+  if (!ctx || !d_params || !d_chi2) return fail(LENS_EINVAL, "NULL argument");
+  if (P < 1) return fail(LENS_EINVAL, "P must be >= 1");
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  cudaSetDevice(ctx->device);
+  return autotune_chi2_source(ctx, c, d_params, P, d_chi2, (cudaStream_t)stream, chosen, best_ms);
+}
+
 int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
                     double *d_chi2, int32_t *d_nimg_found, void *stream) {
   if (!ctx || !d_params || !d_chi2) return fail(LENS_EINVAL, "NULL argument");
@@ -442,6 +452,21 @@ int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, cons
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
   return launch_chi2_image(ctx, m, c, grid, d_params, P, d_chi2, d_nimg_found, (cudaStream_t)stream);
+}
+
+int lens_find_images(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
+                     double *d_images, int32_t max_per_set, int32_t *d_count, void *stream) {
+  if (!ctx || !d_params || !d_images || !d_count) return fail(LENS_EINVAL, "NULL argument");
+  if (P < 1 || max_per_set < 1) return fail(LENS_EINVAL, "P and max_per_set must be >= 1");
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  Model *m = find_model(ctx, c->model);
+  if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
+  cudaSetDevice(ctx->device);
+  return launch_chi2_image(ctx, m, c, grid, d_params, P, nullptr, nullptr, (cudaStream_t)stream, d_images,
+                           max_per_set, d_count);
 }
 
 int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms) {

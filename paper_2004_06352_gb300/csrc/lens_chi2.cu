@@ -104,10 +104,9 @@ int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c) {
   return LENS_OK;
 }
 
-int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
-                       int32_t variant, double *d_chi2, cudaStream_t st) {
-  (void)m;
-  constexpr int T = 128;
+template <int T>
+static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, int32_t P, int32_t variant,
+                          double *d_chi2, cudaStream_t st, int blocks_per_sm) {
   const size_t smem = sizeof(double) * (2 * REC64 + 5 * (size_t)c->nimg + 2 * (size_t)c->nsrc + T / 32);
   if (smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
   static bool attr_set = false;
@@ -118,7 +117,9 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
   int per_sm = 0, nsm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chi2_source<T>, T, smem);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-  int blocks = std::max(1, std::min(P, std::max(1, per_sm) * nsm));
+  per_sm = std::max(1, per_sm);
+  if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
+  const int blocks = std::max(1, std::min(P, per_sm * nsm));
   Chi2SrcArgs a;
   a.stat = c->stat;
   a.x = c->x;
@@ -138,6 +139,60 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
   k_chi2_source<T><<<blocks, T, smem, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "chi2 source launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+// Launch shapes the autotuner chooses from: threads per CTA x CTAs per SM
+// (0 = as many as fit).
+static const int SRC_CFG[][2] = {{64, 0}, {64, 8}, {128, 0}, {128, 4}, {128, 2}, {256, 0}, {256, 2}, {256, 1}};
+constexpr int N_SRC_CFG = sizeof(SRC_CFG) / sizeof(SRC_CFG[0]);
+
+static int launch_src_idx(lens_ctx *ctx, const CSet *c, const double *d_params, int32_t P, int32_t variant,
+                          double *d_chi2, cudaStream_t st, int idx) {
+  const int t = SRC_CFG[idx][0], b = SRC_CFG[idx][1];
+  if (t == 64) return launch_src_cfg<64>(ctx, c, d_params, P, variant, d_chi2, st, b);
+  if (t == 256) return launch_src_cfg<256>(ctx, c, d_params, P, variant, d_chi2, st, b);
+  return launch_src_cfg<128>(ctx, c, d_params, P, variant, d_chi2, st, b);
+}
+
+int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                       int32_t variant, double *d_chi2, cudaStream_t st) {
+  (void)m;
+  const int idx = (c->tuned_cfg >= 0 && c->tuned_cfg < N_SRC_CFG) ? c->tuned_cfg : 2;
+  return launch_src_idx(ctx, c, d_params, P, variant, d_chi2, st, idx);
+}
+
+// Time every launch shape on this constraint set and P (each once to warm
+// up, then best of 3), keep the fastest.  Synchronous on st.
+int autotune_chi2_source(lens_ctx *ctx, CSet *c, const double *d_params, int32_t P, double *d_chi2, cudaStream_t st,
+                         int32_t *chosen, float *best_ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(LENS_ECUDA, "event creation failed");
+  int best = -1;
+  float best_t = 1e30f;
+  int rc = LENS_OK;
+  for (int k = 0; k < N_SRC_CFG && rc == LENS_OK; ++k) {
+    rc = launch_src_idx(ctx, c, d_params, P, 0, d_chi2, st, k);
+    for (int r = 0; r < 3 && rc == LENS_OK; ++r) {
+      cudaEventRecord(e0, st);
+      rc = launch_src_idx(ctx, c, d_params, P, 0, d_chi2, st, k);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(LENS_ECUDA, "autotune timing failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == LENS_OK && ms < best_t) {
+        best_t = ms;
+        best = k;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  c->tuned_cfg = best;
+  if (chosen) *chosen = SRC_CFG[best][0] * 100 + SRC_CFG[best][1];
+  if (best_ms) *best_ms = best_t;
   return LENS_OK;
 }
 

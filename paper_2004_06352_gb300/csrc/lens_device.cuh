@@ -169,34 +169,27 @@ __device__ __forceinline__ void fold(Acc<HESS, KP> &tot, Acc<HESS, KP> &cmp, Acc
   part.zero();
 }
 
-// atan(w)/w and atanh(w)/w as Maclaurin series in t = w^2,
-//   atan(w)/w  = sum_k (-1)^k t^k / (2k+1),   atanh(w)/w = sum_k t^k / (2k+1),
-// ten terms (Horner, FMA).  For t < T_SERIES = 0.16 the first dropped term is
-// below 0.16^10/21 = 5e-10, under half an FP32 ulp.
+// atan(w)/w and atanh(w)/w as degree-5 polynomials in t = w^2, valid for
+// t < T_SERIES = 0.16 (|w| < 0.4): Chebyshev interpolants of the exact
+// functions on [0, 0.16] (coefficients from csrc/fit_series.py); the
+// interpolation error is below 1.1e-9 relative, so FP32 rounding (~6e-8)
+// dominates.  Horner with FMA.
 constexpr float T_SERIES = 0.16f;
 __device__ __forceinline__ float atan_over_w(float t) {
-  float p = -1.f / 19.f;
-  p = fmaf(p, t, 1.f / 17.f);
-  p = fmaf(p, t, -1.f / 15.f);
-  p = fmaf(p, t, 1.f / 13.f);
-  p = fmaf(p, t, -1.f / 11.f);
-  p = fmaf(p, t, 1.f / 9.f);
-  p = fmaf(p, t, -1.f / 7.f);
-  p = fmaf(p, t, 1.f / 5.f);
-  p = fmaf(p, t, -1.f / 3.f);
-  return fmaf(p, t, 1.f);
+  float p = -6.186992596e-02f;
+  p = fmaf(p, t, 1.062997788e-01f);
+  p = fmaf(p, t, -1.424732623e-01f);
+  p = fmaf(p, t, 1.999858949e-01f);
+  p = fmaf(p, t, -3.333331418e-01f);
+  return fmaf(p, t, 9.999999996e-01f);
 }
 __device__ __forceinline__ float atanh_over_w(float t) {
-  float p = 1.f / 19.f;
-  p = fmaf(p, t, 1.f / 17.f);
-  p = fmaf(p, t, 1.f / 15.f);
-  p = fmaf(p, t, 1.f / 13.f);
-  p = fmaf(p, t, 1.f / 11.f);
-  p = fmaf(p, t, 1.f / 9.f);
-  p = fmaf(p, t, 1.f / 7.f);
-  p = fmaf(p, t, 1.f / 5.f);
-  p = fmaf(p, t, 1.f / 3.f);
-  return fmaf(p, t, 1.f);
+  float p = 1.399562492e-01f;
+  p = fmaf(p, t, 1.014973434e-01f);
+  p = fmaf(p, t, 1.436870917e-01f);
+  p = fmaf(p, t, 1.999682206e-01f);
+  p = fmaf(p, t, 3.333337736e-01f);
+  return fmaf(p, t, 9.999999990e-01f);
 }
 
 // One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the

@@ -12,14 +12,21 @@
 //                     barycentric weights with a small tolerance so that a
 //                     source on a shared edge is never lost), and every hit
 //                     is appended to the set's candidate buffer.
-//   3. k_img_newton   one warp per candidate: Newton on the lens equation with
-//                     the full model, FP32 potentials (lanes split the
-//                     potentials) plus FP64 cluster-scale and varying ones.
+//   3. k_img_newton   one warp per candidate: the hit triangle is subdivided
+//                     up to SUBDIV_LEVELS times (keeping the sub-triangle that
+//                     best contains the source; stopping early when none does),
+//                     then Newton on the lens equation, steps limited to one
+//                     cell, starts there; full model with the lanes splitting
+//                     the potentials (FP32, cluster-scale static ones in FP64);
+//                     a root further than LOCAL_CELLS cells from its triangle
+//                     is dropped.
 //   4. k_img_dedup    per set: candidates of the same source closer than
 //                     1e-3" are one image.
 //   5. k_img_polish   one warp per distinct image: Newton steps whose residual
 //                     uses the full model in FP64, until the step is < 1e-7".
-//   6. k_img_chi2     per set: each constraint takes the nearest image of its
+//   6. k_img_chi2     per set: polished images of one source closer than
+//                     1e-3" are merged again (as after the definition's FP64
+//                     Newton); each constraint takes the nearest image of its
 //                     own source (ties: lower y, then lower x); chi2 reduced in
 //                     a fixed order.
 // Candidate buffers live in scratch memory (IMG_CAP per set); an overflow
@@ -36,18 +43,22 @@ constexpr double DEDUP = 1e-3;      // images closer than this are one image (ar
 constexpr double NEWTON32_TOL = 1e-4;
 constexpr double POLISH_TOL = 1e-7;
 constexpr double ACCEPT_TOL = 1e-6;  // same criterion as the FP64 Newton of the definition
-constexpr int NEWTON_MAXIT = 20, POLISH_MAXIT = 6;
+constexpr int NEWTON_MAXIT = 40, POLISH_MAXIT = 6;
 constexpr float BARY_TOL = 1e-3f;
+constexpr int SUBDIV_LEVELS = 6;     // subdivisions of a hit triangle before Newton
+constexpr double SUBDIV_TOL = 1e-3;  // refinement stops when the source is this far outside every sub-triangle
+constexpr double LOCAL_CELLS = 2.0;  // a root must lie this many cell sizes from its triangle
 constexpr int CT_X = 32, CT_Y = 8, NX_T = CT_X + 1, NY_T = CT_Y + 1;
-constexpr int ST_PENDING = 0, ST_NEWTON = 1, ST_FINAL = 2, ST_FAILED = -1;
+// candidate status; the failures say which stage rejected it
+constexpr int ST_PENDING = 0, ST_NEWTON = 1, ST_FINAL = 2, ST_FAILED = -1, ST_FAR = -2, ST_NO_POLISH = -3;
 
 struct Hit {
   double tx, ty;       // image position
-  float sx, sy;        // seed from the triangle
+  float cx, cy;        // centroid of the hit triangle (image plane)
   float h11, h22, h12; // r H at the last FP32 Newton step
   int src;
   int status;
-  int pad;
+  int cell;            // 2 * (j * (nx-1) + i) + triangle of the hit
 };
 
 struct Layout {
@@ -143,7 +154,7 @@ struct SearchArgs {
 
 __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 tA, float2 tB, float2 tC,
                                          const float2 *s_src, const int32_t *__restrict__ gsrc, int g0, int g1,
-                                         float tiny, int *cnt, Hit *hits) {
+                                         float tiny, int *cnt, Hit *hits, int cell) {
   const float lox = fminf(A.x, fminf(Bv.x, Cv.x)), hix = fmaxf(A.x, fmaxf(Bv.x, Cv.x));
   const float loy = fminf(A.y, fminf(Bv.y, Cv.y)), hiy = fmaxf(A.y, fmaxf(Bv.y, Cv.y));
   const float padx = BARY_TOL * (hix - lox) + 1e-6f, pady = BARY_TOL * (hiy - loy) + 1e-6f;
@@ -162,8 +173,9 @@ __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 
     if (slot < IMG_CAP) {
       Hit *h = hits + slot;
       h->src = src;
-      h->sx = wa * tA.x + wb * tB.x + wc * tC.x;
-      h->sy = wa * tA.y + wb * tB.y + wc * tC.y;
+      h->cx = (tA.x + tB.x + tC.x) * (1.f / 3.f);
+      h->cy = (tA.y + tB.y + tC.y) * (1.f / 3.f);
+      h->cell = cell;
       h->status = ST_PENDING;
     }
   }
@@ -221,8 +233,9 @@ __global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const Searc
     const float2 b00 = make_float2(X0 - r * a00.x, Y0 - r * a00.y), b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
                  b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y), b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
     const int g0 = g.grp_off[q], g1 = g.grp_off[q + 1];
-    tri_test(b00, b10, b11, t00, t10, t11, s_src, g.grp_src, g0, g1, tiny, cnt, hits);
-    tri_test(b00, b11, b01, t00, t11, t01, s_src, g.grp_src, g0, g1, tiny, cnt, hits);
+    const int cell = 2 * (gj * (g.nx - 1) + gi);
+    tri_test(b00, b10, b11, t00, t10, t11, s_src, g.grp_src, g0, g1, tiny, cnt, hits, cell);
+    tri_test(b00, b11, b01, t00, t11, t01, s_src, g.grp_src, g0, g1, tiny, cnt, hits, cell + 1);
   }
 }
 
@@ -235,6 +248,8 @@ struct NewtonArgs {
   const double *all64;         // every static potential in FP64 (polish)
   int n_stat;
   const double *ratio;         // per source
+  double xmin, ymin, dx, dy;   // search grid
+  int nx;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -245,64 +260,189 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int NW_THREADS = 256, NW_WARPS = NW_THREADS / 32;
 
+// Per-warp copy of the varying potentials of the warp's parameter set: FP32
+// records and hi/lo centres (subdivision and FP32 Newton), FP64 records
+// (polish).
+struct __align__(16) VarRecs {
+  float r32[2][REC32];
+  float cen[2][4];
+  double r64[2][REC64];
+};
+
+__device__ __forceinline__ void load_var(const double *q, int type0, int type1, int lane, VarRecs &v) {
+  if (lane < 2) {
+    const double *w = q + 7 * lane;
+    const int type = lane == 0 ? type0 : type1;
+    make_rec32(type, w[3], w[2], w[4], w[5], w[6], v.r32[lane]);
+    const float xh = (float)w[0], yh = (float)w[1];
+    v.cen[lane][0] = xh;
+    v.cen[lane][1] = yh;
+    v.cen[lane][2] = (float)(w[0] - (double)xh);
+    v.cen[lane][3] = (float)(w[1] - (double)yh);
+    load_var_rec64(q, type0, type1, lane, &v.r64[0][0]);  // writes record `lane` of the array
+  }
+  __syncwarp();
+}
+
+// Full model at (tx, ty), D_ls/D_s = 1, summed over the warp (every lane gets
+// the same bits): FP32 for the static light potentials and the two varying
+// ones, FP64 for static cluster-scale ones.  v = {ax, ay, kappa, g1, g2}.
+template <bool HESS>
+__device__ __forceinline__ void warp_eval(const NewtonArgs &n, const VarRecs &vr, int lane, double tx, double ty,
+                                          double (&v)[5]) {
+  const float hx = (float)tx, hy = (float)ty;
+  const float lx = (float)(tx - (double)hx), ly = (float)(ty - (double)hy);
+  Acc<HESS, 1> part;
+  part.zero();
+  for (int j = lane; j < n.n_light + 2; j += 32) {
+    const float4 *r4;
+    float4 c;
+    if (j < n.n_light) {
+      c = reinterpret_cast<const float4 *>(n.cen32)[j];
+      r4 = reinterpret_cast<const float4 *>(n.rec32) + (size_t)j * (REC32 / 4);
+    } else {
+      const float *cc = vr.cen[j - n.n_light];
+      c = make_float4(cc[0], cc[1], cc[2], cc[3]);
+      r4 = reinterpret_cast<const float4 *>(vr.r32[j - n.n_light]);
+    }
+    const float dY[1] = {(hy - c.y) + (ly - c.w)};
+    eval32_any<HESS, 1>(r4, (hx - c.x) + (lx - c.z), dY, part);
+  }
+  v[0] = part.ax[0];
+  v[1] = part.ay[0];
+  v[2] = HESS ? part.k[0] : 0.0;
+  v[3] = HESS ? part.g1[0] : 0.0;
+  v[4] = HESS ? part.g2[0] : 0.0;
+  for (int j = lane; j < n.n_heavy; j += 32) {
+    double e0, e1, e2 = 0, e3 = 0, e4 = 0;
+    eval64<HESS>(n.heavy + (size_t)j * REC64, tx, ty, e0, e1, e2, e3, e4);
+    v[0] += e0;
+    v[1] += e1;
+    v[2] += e2;
+    v[3] += e3;
+    v[4] += e4;
+  }
+#pragma unroll
+  for (int c = 0; c < (HESS ? 5 : 2); ++c) v[c] = warp_sum(v[c]);
+}
+
+// Barycentric weights of p in (a, b, c); false when degenerate.
+__device__ __forceinline__ bool bary_w(const double *a, const double *b, const double *c, const double *p,
+                                       double tiny, double w[3]) {
+  const double area2 = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]);
+  if (!(fabs(area2) > tiny)) return false;
+  w[0] = ((b[0] - p[0]) * (c[1] - p[1]) - (b[1] - p[1]) * (c[0] - p[0])) / area2;
+  w[1] = ((c[0] - p[0]) * (a[1] - p[1]) - (c[1] - p[1]) * (a[0] - p[0])) / area2;
+  w[2] = 1.0 - w[0] - w[1];
+  return true;
+}
+
 __global__ void __launch_bounds__(NW_THREADS) k_img_newton(const SetArgs a, const NewtonArgs n) {
-  __shared__ double s_var[NW_WARPS][2 * REC64];
+  __shared__ VarRecs s_var[NW_WARPS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * NW_WARPS;
+  const double cell_tiny = 1e-14 * n.dx * n.dy;  // degenerate-triangle bound, as in the definition
+  const double step_max = fmax(n.dx, n.dy);
   for (long long task = (long long)blockIdx.x * NW_WARPS + w; task < (long long)a.B * IMG_CAP; task += nwarps) {
     const int b = (int)(task / IMG_CAP), k = (int)(task % IMG_CAP);
     if (!a.s.valid[b] || k >= min(a.s.cnt[b], IMG_CAP)) continue;
     Hit *h = a.s.hits + (size_t)b * IMG_CAP + k;
-    const double *q = a.params + (size_t)(a.p0 + b) * 14;
-    if (lane < 2) load_var_rec64(q, a.type0, a.type1, lane, s_var[w]);
-    __syncwarp();
+    load_var(a.params + (size_t)(a.p0 + b) * 14, a.type0, a.type1, lane, s_var[w]);
+    const VarRecs &vr = s_var[w];
     const int src = h->src;
     const double r = n.ratio[src];
-    const double bx = a.s.bary[((size_t)b * a.nsrc + src) * 2], by = a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1];
-    double tx = h->sx, ty = h->sy;
+    const double P[2] = {a.s.bary[((size_t)b * a.nsrc + src) * 2], a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1]};
+    // the hit triangle, mapped with the full model
+    const int cell = h->cell, tri = cell & 1, ci = (cell >> 1) % (n.nx - 1), cj = (cell >> 1) / (n.nx - 1);
+    // triangle 0: (i,j),(i+1,j),(i+1,j+1); triangle 1: (i,j),(i+1,j+1),(i,j+1)
+    double th[3][2], be[3][2];
+    const int oi[2][3] = {{ci, ci + 1, ci + 1}, {ci, ci + 1, ci}}, oj[2][3] = {{cj, cj, cj + 1}, {cj, cj + 1, cj + 1}};
+    for (int q = 0; q < 3; ++q) {
+      th[q][0] = n.xmin + oi[tri][q] * n.dx;
+      th[q][1] = n.ymin + oj[tri][q] * n.dy;
+      double v[5];
+      warp_eval<false>(n, vr, lane, th[q][0], th[q][1], v);
+      be[q][0] = th[q][0] - r * v[0];
+      be[q][1] = th[q][1] - r * v[1];
+    }
+    // subdivision: keep the sub-triangle that best contains the source
+    double tiny = cell_tiny, wgt[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+    for (int lev = 0; lev <= SUBDIV_LEVELS; ++lev) {
+      if (lev == SUBDIV_LEVELS) {
+        if (!bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
+        break;
+      }
+      double t6[6][2], b6[6][2];
+      for (int q = 0; q < 3; ++q) {
+        t6[q][0] = th[q][0];
+        t6[q][1] = th[q][1];
+        b6[q][0] = be[q][0];
+        b6[q][1] = be[q][1];
+        const int q1 = q == 2 ? 0 : q + 1;
+        t6[3 + q][0] = 0.5 * (th[q][0] + th[q1][0]);
+        t6[3 + q][1] = 0.5 * (th[q][1] + th[q1][1]);
+        double v[5];
+        warp_eval<false>(n, vr, lane, t6[3 + q][0], t6[3 + q][1], v);
+        b6[3 + q][0] = t6[3 + q][0] - r * v[0];
+        b6[3 + q][1] = t6[3 + q][1] - r * v[1];
+      }
+      const double tiny_sub = 0.25 * tiny;
+      const int sub[4][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}, {3, 4, 5}};
+      int best = -1;
+      double best_score = -INFINITY;
+      for (int sb = 0; sb < 4; ++sb) {
+        double ww[3];
+        if (!bary_w(b6[sub[sb][0]], b6[sub[sb][1]], b6[sub[sb][2]], P, tiny_sub, ww)) continue;
+        const double score = fmin(ww[0], fmin(ww[1], ww[2]));
+        if (score > best_score) {
+          best_score = score;
+          best = sb;
+        }
+      }
+      if (best < 0 || best_score < -SUBDIV_TOL) {
+        // the map is far from linear on this triangle: stop refining here
+        if (!bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
+        break;
+      }
+      tiny = tiny_sub;
+      for (int q = 0; q < 3; ++q) {
+        th[q][0] = t6[sub[best][q]][0];
+        th[q][1] = t6[sub[best][q]][1];
+        be[q][0] = b6[sub[best][q]][0];
+        be[q][1] = b6[sub[best][q]][1];
+      }
+    }
+    double tx = wgt[0] * th[0][0] + wgt[1] * th[1][0] + wgt[2] * th[2][0];
+    double ty = wgt[0] * th[0][1] + wgt[1] * th[1][1] + wgt[2] * th[2][1];
     int status = ST_FAILED;
     float h11 = 0.f, h22 = 0.f, h12 = 0.f;
     for (int it = 0; it < NEWTON_MAXIT; ++it) {
-      const float hx = (float)tx, hy = (float)ty;
-      const float lx = (float)(tx - (double)hx), ly = (float)(ty - (double)hy);
-      Acc<true, 1> part;
-      part.zero();
-      for (int j = lane; j < n.n_light; j += 32) {
-        const float4 c = reinterpret_cast<const float4 *>(n.cen32)[j];
-        const float dY[1] = {(hy - c.y) + (ly - c.w)};
-        eval32_any<true, 1>(reinterpret_cast<const float4 *>(n.rec32) + (size_t)j * (REC32 / 4), (hx - c.x) + (lx - c.z),
-                            dY, part);
-      }
-      double v[5] = {part.ax[0], part.ay[0], part.k[0], part.g1[0], part.g2[0]};
-      for (int j = lane; j < n.n_heavy + 2; j += 32) {
-        const double *rec = j < n.n_heavy ? n.heavy + (size_t)j * REC64 : s_var[w] + (j - n.n_heavy) * REC64;
-        double e0, e1, e2, e3, e4;
-        eval64<true>(rec, tx, ty, e0, e1, e2, e3, e4);
-        v[0] += e0;
-        v[1] += e1;
-        v[2] += e2;
-        v[3] += e3;
-        v[4] += e4;
-      }
-#pragma unroll
-      for (int c = 0; c < 5; ++c) v[c] = warp_sum(v[c]);
-      const double fx = bx - (tx - r * v[0]), fy = by - (ty - r * v[1]);
+      double v[5];
+      warp_eval<true>(n, vr, lane, tx, ty, v);
+      const double fx = P[0] - (tx - r * v[0]), fy = P[1] - (ty - r * v[1]);
       const double m11 = r * (v[2] + v[3]), m22 = r * (v[2] - v[3]), m12 = r * v[4];
       const double a11 = 1.0 - m11, a22 = 1.0 - m22, a12 = -m12;
       const double det = a11 * a22 - a12 * a12;
       if (!(det != 0.0) || !isfinite(det)) break;
-      const double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+      double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+      const double len = sqrt(dx * dx + dy * dy);
+      if (len > step_max) {  // trust region: at most one cell per step
+        dx *= step_max / len;
+        dy *= step_max / len;
+      }
       tx += dx;
       ty += dy;
       h11 = (float)m11;
       h22 = (float)m22;
       h12 = (float)m12;
       if (!isfinite(tx) || !isfinite(ty)) break;
-      if (sqrt(dx * dx + dy * dy) < NEWTON32_TOL) {
+      if (len < NEWTON32_TOL) {
         status = ST_NEWTON;
         break;
       }
     }
+    // a root far from its triangle belongs to another triangle's search
+    if (status == ST_NEWTON && hypot(tx - h->cx, ty - h->cy) > LOCAL_CELLS * fmax(n.dx, n.dy)) status = ST_FAR;
     if (lane == 0) {
       h->tx = tx;
       h->ty = ty;
@@ -398,7 +538,7 @@ __global__ void __launch_bounds__(NW_THREADS) k_img_polish(const SetArgs a, cons
     if (lane == 0) {
       h->tx = tx;
       h->ty = ty;
-      h->status = (step < ACCEPT_TOL && isfinite(tx) && isfinite(ty)) ? ST_FINAL : ST_FAILED;
+      h->status = (step < ACCEPT_TOL && isfinite(tx) && isfinite(ty)) ? ST_FINAL : ST_NO_POLISH;
     }
     __syncwarp();
   }
@@ -411,12 +551,16 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ sigma,
                                                          const int32_t *__restrict__ src_of, double *chi2,
-                                                         int32_t *nfound, int *err) {
+                                                         int32_t *nfound, int *err, double *images, int img_max,
+                                                         int32_t *img_count) {
   __shared__ double s_red[C2_THREADS / 32];
   const int b = blockIdx.x, p = a.p0 + b;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   if (!a.s.valid[b]) {
-    if (threadIdx.x == 0) chi2[p] = nan;
+    if (threadIdx.x == 0) {
+      if (chi2) chi2[p] = nan;
+      if (img_count) img_count[p] = 0;
+    }
     if (nfound)
       for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) nfound[(size_t)p * a.nsrc + i] = 0;
     return;
@@ -425,13 +569,40 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
   const Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
   const int *uniq = a.s.uniq + (size_t)b * IMG_CAP;
   const int nu = a.s.nuniq[b];
+  // Final images: polished, and not within DEDUP of an earlier final image of
+  // the same source (candidates of one highly magnified image can end the
+  // FP32 Newton further apart than DEDUP and meet only after the polish).
+  __shared__ unsigned char s_use[IMG_CAP];
+  for (int u = threadIdx.x; u < nu; u += C2_THREADS) {
+    const Hit &h = hits[uniq[u]];
+    bool use = h.status == ST_FINAL;
+    for (int v = 0; v < u && use; ++v) {
+      const Hit &g = hits[uniq[v]];
+      const double ex = g.tx - h.tx, ey = g.ty - h.ty;
+      if (g.status == ST_FINAL && g.src == h.src && ex * ex + ey * ey < DEDUP * DEDUP) use = false;
+    }
+    s_use[u] = use;
+  }
+  __syncthreads();
+  if (images && threadIdx.x == 0) {  // predicted images, in candidate order
+    int c = 0;
+    for (int u = 0; u < nu; ++u) {
+      if (!s_use[u]) continue;
+      if (c < img_max) {
+        const Hit &h = hits[uniq[u]];
+        double *o = images + ((size_t)p * img_max + c) * 3;
+        o[0] = h.tx;
+        o[1] = h.ty;
+        o[2] = (double)h.src;
+      }
+      ++c;
+    }
+    img_count[p] = overflow ? -1 : c;
+  }
   if (nfound)
     for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) {
       int c = 0;
-      for (int u = 0; u < nu; ++u) {
-        const Hit &h = hits[uniq[u]];
-        c += (h.status == ST_FINAL && h.src == i);
-      }
+      for (int u = 0; u < nu; ++u) c += (s_use[u] && hits[uniq[u]].src == i);
       nfound[(size_t)p * a.nsrc + i] = overflow ? -1 : c;
     }
   double acc[1] = {0.0};
@@ -440,7 +611,7 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
     double best = INFINITY, bx = 0.0, by = 0.0;
     for (int u = 0; u < nu; ++u) {
       const Hit &h = hits[uniq[u]];
-      if (h.status != ST_FINAL || h.src != i) continue;
+      if (!s_use[u] || h.src != i) continue;
       const double ex = x[j] - h.tx, ey = y[j] - h.ty, d2 = ex * ex + ey * ey;
       if (d2 < best || (d2 == best && (h.ty < by || (h.ty == by && h.tx < bx)))) {
         best = d2;
@@ -452,7 +623,7 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
   }
   block_sum<1, C2_THREADS>(acc, s_red);
   if (threadIdx.x == 0) {
-    chi2[p] = (overflow || !isfinite(acc[0])) ? nan : acc[0];
+    if (chi2) chi2[p] = (overflow || !isfinite(acc[0])) ? nan : acc[0];
     if (overflow) atomicOr(err, ERRBIT_CAPACITY);
   }
 }
@@ -462,7 +633,8 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
 size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch) { return layout(batch, c->nsrc).total; }
 
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P, double *d_chi2,
-                   int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st) {
+                   int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st, double *d_images,
+                   int32_t img_max, int32_t *d_img_count) {
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   const Model *sm = c->stat_model;
@@ -475,6 +647,11 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   n.all64 = sm->all64;
   n.n_stat = sm->n;
   n.ratio = c->ratio;
+  n.xmin = gc->xmin;
+  n.ymin = gc->ymin;
+  n.dx = (gc->xmax - gc->xmin) / (gc->nx - 1);
+  n.dy = (gc->ymax - gc->ymin) / (gc->ny - 1);
+  n.nx = gc->nx;
   SearchArgs g;
   g.ax = gc->alpha32;
   g.ay = gc->alpha32 + (size_t)gc->nx * gc->ny;
@@ -510,7 +687,8 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
     k_img_newton<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
     k_img_dedup<<<a.B, DD_THREADS, 0, st>>>(a);
     k_img_polish<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
-    k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err);
+    k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err,
+                                           d_images, img_max, d_img_count);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LENS_ECUDA, "image-plane chi2 launch: %s", cudaGetErrorString(e));
   }
@@ -552,7 +730,8 @@ int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st
 }
 
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
-                      double *d_chi2, int32_t *d_nfound, cudaStream_t st) {
+                      double *d_chi2, int32_t *d_nfound, cudaStream_t st, double *d_images, int32_t img_max,
+                      int32_t *d_img_count) {
   (void)m;
   if (c->nsrc > MAX_SRC) return fail(LENS_EINVAL, "image-plane chi2 supports at most %d sources", MAX_SRC);
   const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
@@ -567,7 +746,8 @@ int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g
   const int32_t batch = std::min<int32_t>(IMG_BATCH, P);
   const int rc = ensure_scratch(ctx, chi2_image_scratch_bytes(c, batch));
   if (rc) return rc;
-  return run_chi2_image(ctx, c, gc, d_params, P, d_chi2, d_nfound, ctx->scratch, batch, st);
+  return run_chi2_image(ctx, c, gc, d_params, P, d_chi2, d_nfound, ctx->scratch, batch, st, d_images, img_max,
+                        d_img_count);
 }
 
 }  // namespace lens

@@ -183,6 +183,7 @@ struct CSet {
   double *var_base = nullptr;   // [2][16] FP64 records of the varying potentials' base types (type in D_KIND)
   int32_t var_type[2] = {0, 0};
   Model *stat_model = nullptr;  // every potential except the two varying ones
+  int32_t tuned_cfg = -1;       // launch shape of the source-plane chi2 picked by the autotuner
   int32_t ng = 0;               // distinct source distance ratios
   int32_t *grp_off = nullptr;   // [ng+1] sources of ratio group g: grp_src[grp_off[g] .. grp_off[g+1]-1]
   int32_t *grp_src = nullptr;   // [nsrc]
@@ -233,13 +234,17 @@ int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dl
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);
+int autotune_chi2_source(lens_ctx *ctx, CSet *c, const double *d_params, int32_t P, double *d_chi2, cudaStream_t st,
+                         int32_t *chosen, float *best_ms);
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
-                      double *d_chi2, int32_t *d_nfound, cudaStream_t st);
+                      double *d_chi2, int32_t *d_nfound, cudaStream_t st, double *d_images = nullptr,
+                      int32_t img_max = 0, int32_t *d_img_count = nullptr);
 size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch);
 const GridCache *find_grid_cache(const CSet *c, const lens_grid *g);
 int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st);
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P,
-                   double *d_chi2, int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st);
+                   double *d_chi2, int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st,
+                   double *d_images = nullptr, int32_t img_max = 0, int32_t *d_img_count = nullptr);
 
 // device error word bits (read and cleared by lens_wait)
 constexpr int ERRBIT_WAIT = 1;

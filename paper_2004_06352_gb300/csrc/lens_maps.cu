@@ -27,6 +27,18 @@
 namespace lens {
 namespace {
 
+// Launch shape (overridable at build time for tuning): CTAs per SM the
+// register budget targets, and points per thread of the Hessian and
+// deflection-only kernels.
+#ifndef LENS_MAP_MINB
+#define LENS_MAP_MINB 2
+#endif
+#ifndef LENS_KP_HESS
+#define LENS_KP_HESS 2
+#endif
+#ifndef LENS_KP_GRAD
+#define LENS_KP_GRAD 4
+#endif
 constexpr int MAP_THREADS = 256;
 constexpr int MAP_WARPS = MAP_THREADS / 32;
 constexpr int CH = 64;   // potentials per staged chunk (8 KB of records)
@@ -47,10 +59,12 @@ struct MapArgs {
 };
 
 template <bool HESS, int KP>
-__global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
+__global__ void __launch_bounds__(MAP_THREADS, LENS_MAP_MINB) k_map_mixed(const MapArgs a) {
   __shared__ __align__(128) float s_rec[2][CH * REC32];
   __shared__ float4 s_off[2][CH];  // hi.x, hi.y, lo.x, lo.y of (Tx - x0, Ty - y0)
   __shared__ __align__(8) uint64_t s_bar[2];
+  constexpr int NC = HESS ? 5 : 2;
+  __shared__ double s_hv[MAP_THREADS][KP][NC];  // FP64 potentials' sums per point
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * (MAP_WARPS * KP);
@@ -72,6 +86,35 @@ __global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
   tot.zero();
   cmp.zero();
   part.zero();
+
+  // FP64 potentials (cluster scale).  Half of the tiles evaluate them before
+  // the FP32 loop, half after, so the two CTAs sharing an SM rarely load the
+  // FP64 pipe at the same time.
+  auto heavy_pass = [&]() {
+    const double X = a.xmin + (i0 + lane) * a.dx;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const double Y = a.ymin + (j0 + warp * KP + k) * a.dy;
+      double v[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] = 0.0;
+      for (int h = 0; h < a.n_heavy; ++h) {
+        double ax, ay, kk = 0, q1 = 0, q2 = 0;
+        eval64<HESS>(a.heavy + (size_t)h * REC64, X, Y, ax, ay, kk, q1, q2);
+        v[0] += ax;
+        v[1] += ay;
+        if (HESS) {
+          v[NC > 2 ? 2 : 0] += kk;
+          v[NC > 3 ? 3 : 0] += q1;
+          v[NC > 4 ? 4 : 0] += q2;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s_hv[tid][k][c] = v[c];
+    }
+  };
+  const bool heavy_first = ((blockIdx.x + blockIdx.y) & 1) != 0;
+  if (heavy_first) heavy_pass();
 
   const int nch = (a.n_light + CH - 1) / CH;
   if (tid == 0) {
@@ -138,31 +181,20 @@ __global__ void __launch_bounds__(MAP_THREADS, 2) k_map_mixed(const MapArgs a) {
     }
   }
   fold(tot, cmp, part);
+  if (!heavy_first) heavy_pass();
 
-  // FP64 potentials and the per-point epilogue
+  // per-point epilogue: FP32 totals + FP64 sums, scaled, derived maps
   const int i = i0 + lane;
-  const double X = a.xmin + i * a.dx;
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     const int j = j0 + warp * KP + k;
-    const double Y = a.ymin + j * a.dy;
-    double AX = (double)tot.ax[k] - (double)cmp.ax[k], AY = (double)tot.ay[k] - (double)cmp.ay[k];
+    const double AX = (double)tot.ax[k] - (double)cmp.ax[k] + s_hv[tid][k][0];
+    const double AY = (double)tot.ay[k] - (double)cmp.ay[k] + s_hv[tid][k][1];
     double KA = 0, G1 = 0, G2 = 0;
     if (HESS) {
-      KA = (double)tot.k[k] - (double)cmp.k[k];
-      G1 = (double)tot.g1[k] - (double)cmp.g1[k];
-      G2 = (double)tot.g2[k] - (double)cmp.g2[k];
-    }
-    for (int h = 0; h < a.n_heavy; ++h) {
-      double ax, ay, kk = 0, q1 = 0, q2 = 0;
-      eval64<HESS>(a.heavy + (size_t)h * REC64, X, Y, ax, ay, kk, q1, q2);
-      AX += ax;
-      AY += ay;
-      if (HESS) {
-        KA += kk;
-        G1 += q1;
-        G2 += q2;
-      }
+      KA = (double)tot.k[k] - (double)cmp.k[k] + s_hv[tid][k][NC > 2 ? 2 : 0];
+      G1 = (double)tot.g1[k] - (double)cmp.g1[k] + s_hv[tid][k][NC > 3 ? 3 : 0];
+      G2 = (double)tot.g2[k] - (double)cmp.g2[k] + s_hv[tid][k][NC > 4 ? 4 : 0];
     }
     if (i < a.nx && j < a.ny) {
       const long long o = (long long)j * a.nx + i;
@@ -231,7 +263,7 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.out = (float *)out;
   a.plane = (long long)g->nx * g->ny;
   a.err = ctx->d_err;
-  constexpr int KPG = 4, KPH = 2;
+  constexpr int KPG = LENS_KP_GRAD, KPH = LENS_KP_HESS;
   if (hess) {
     dim3 grid((g->nx + 31) / 32, (g->ny + MAP_WARPS * KPH - 1) / (MAP_WARPS * KPH));
     k_map_mixed<true, KPH><<<grid, MAP_THREADS, 0, st>>>(a);

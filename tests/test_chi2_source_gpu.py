@@ -60,3 +60,46 @@ def test_chi2_source_invalid_sets_are_nan_and_base_set_matches(lens):
     assert abs(got[3] - ref) <= T.CHI2_REL * ref
     ref0 = oracle.chi2_source(oracle.apply_params(m, var, params[0]), cons, 0)
     assert abs(got[0] - ref0) <= T.CHI2_REL * ref0
+
+
+def test_chi2_source_autotune_and_graph_replay(lens):
+    """The autotuner keeps a launch shape whose results match the default one;
+    the batched chi2 captured once in a CUDA graph and replayed on new
+    parameter sets written into the same device buffer matches the oracle."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    P = 256
+    p1 = I.perturbed_params(m, var, P, seed=51)
+    p2 = I.perturbed_params(m, var, P, seed=52)
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        params = torch.tensor(p1, device=DEV)
+        ref = torch.empty(P, dtype=torch.float64, device=DEV)
+        ctx.chi2_source(cs, params, P, 0, ref)
+        out = torch.empty_like(ref)
+        cfg, ms = ctx.chi2_autotune(cs, params, P, out)
+        assert cfg // 100 in (64, 128, 256) and ms > 0
+        ctx.chi2_source(cs, params, P, 0, out)
+        ctx.wait()
+        assert torch.allclose(out, ref, rtol=1e-12, atol=0)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            ctx.chi2_source(cs, params, P, 0, out, stream=s)    # warm-up outside capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        gout = torch.empty_like(ref)
+        with torch.cuda.graph(g, stream=s):
+            ctx.chi2_source(cs, params, P, 0, gout, stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.allclose(gout, out, rtol=1e-12, atol=0)
+        params.copy_(torch.tensor(p2, device=DEV))
+        g.replay()
+        torch.cuda.synchronize()
+        got2 = gout.cpu().numpy()
+    ref2 = oracle.chi2_source_batch(m, cons, var, p2[:48], 0)
+    assert np.all(np.abs(got2[:48] - ref2) <= T.CHI2_REL * np.abs(ref2))
