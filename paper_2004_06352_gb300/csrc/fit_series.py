@@ -1,10 +1,12 @@
-"""Coefficients of the FP32 polynomials for atan(w)/w and atanh(w)/w in
-t = w^2 on [0, T] used by lens_device.cuh (atan_over_w / atanh_over_w).
+"""Coefficients of the polynomials for atan(w)/w and atanh(w)/w in t = w^2 on
+[0, T] used by lens_device.cuh: FP32 (atan_over_w / atanh_over_w, degree 5)
+and FP64 (atan_over_w64 / atanh_over_w64, degree 11).
 
-Chebyshev interpolation of the exact functions at the DEG+1 Chebyshev nodes
-of [0, T], converted to monomial coefficients in t; prints the coefficients
-and the worst relative error over a dense grid, exact (float64) and with the
-coefficients rounded to float32 and evaluated by FP32 Horner.
+Both interpolate the exact functions at the DEG+1 Chebyshev nodes of [0, T]:
+the FP32 set with numpy (Chebyshev fit converted to monomials), the FP64 set
+by solving the interpolation conditions in the monomial basis with 60-digit
+mpmath arithmetic (the float64 conversion would lose digits).  Prints the
+coefficients and the worst relative error on a dense grid.
 
   python paper_2004_06352_gb300/csrc/fit_series.py
 """
@@ -43,6 +45,20 @@ def fp32_horner(P, t):
     return acc
 
 
+def fit64(name, deg=11):
+    import mpmath as mp
+    mp.mp.dps = 60
+    T64 = mp.mpf(T)
+    f = {"atan": mp.atan, "atanh": mp.atanh}[name]
+    g = lambda t: mp.mpf(1) if t == 0 else f(mp.sqrt(t)) / mp.sqrt(t)
+    nodes = [T64 / 2 * (1 + mp.cos(mp.pi * (k + mp.mpf(1) / 2) / (deg + 1))) for k in range(deg + 1)]
+    A = mp.matrix([[t ** j for j in range(deg + 1)] for t in nodes])
+    c = mp.lu_solve(A, mp.matrix([g(t) for t in nodes]))
+    worst = max(abs(sum(c[j] * t ** j for j in range(deg + 1)) / g(t) - 1)
+                for t in (T64 * i / 2000 for i in range(2001)))
+    return [float(c[j]) for j in range(deg + 1)], float(worst)
+
+
 if __name__ == "__main__":
     tt = np.linspace(0, T, 200001)
     t32 = tt.astype(np.float32).astype(np.float64)
@@ -52,3 +68,7 @@ if __name__ == "__main__":
         e32 = np.max(np.abs(fp32_horner(P, t32) / f(t32) - 1))
         print(f"{name}: max rel err {e:.2e} (exact arithmetic), {e32:.2e} (FP32 Horner)")
         print("  " + ", ".join(f"{v:.9e}f" for v in P))
+    for name in ("atan", "atanh"):
+        c, worst = fit64(name)
+        print(f"{name} (FP64, degree 11): max rel interpolation error {worst:.2e}")
+        print("  " + ", ".join(f"{v:.17e}" for v in c))

@@ -95,6 +95,7 @@ void free_model(lens_ctx *ctx, Model *m) {
   dev_free(ctx, m->cen32, (size_t)m->n_light * 4 * sizeof(float));
   dev_free(ctx, m->heavy, (size_t)m->n_heavy * REC64 * sizeof(double));
   dev_free(ctx, m->all64, (size_t)m->n * REC64 * sizeof(double));
+  dev_free(ctx, m->recdf, (size_t)m->n * RECDF * sizeof(float));
   delete m;
 }
 
@@ -112,6 +113,7 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->n_heavy = (int32_t)heavy.size();
   std::vector<float> r32((size_t)m->n_light * REC32), c32((size_t)m->n_light * 4);
   std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
+  std::vector<float> adf((size_t)n * RECDF);
   for (int32_t k = 0; k < m->n_light; ++k) {
     const lens_halo &a = h[light[k]];
     make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, &r32[(size_t)k * REC32]);
@@ -133,23 +135,25 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   for (int32_t k = 0; k < n; ++k) {
     const lens_halo &a = h[k];
     make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
+    make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &adf[(size_t)k * RECDF]);
   }
   int rc = LENS_OK;
   size_t b32 = r32.size() * sizeof(float), bp = p64.size() * sizeof(double), bc = c32.size() * sizeof(float),
-         bh = hv.size() * sizeof(double), ba = a64.size() * sizeof(double);
+         bh = hv.size() * sizeof(double), ba = a64.size() * sizeof(double), bd = adf.size() * sizeof(float);
   if ((rc = dev_alloc(ctx, (void **)&m->rec32, b32)) || (rc = dev_alloc(ctx, (void **)&m->pos64, bp)) ||
       (rc = dev_alloc(ctx, (void **)&m->cen32, bc)) || (rc = dev_alloc(ctx, (void **)&m->heavy, bh)) ||
-      (rc = dev_alloc(ctx, (void **)&m->all64, ba))) {
+      (rc = dev_alloc(ctx, (void **)&m->all64, ba)) || (rc = dev_alloc(ctx, (void **)&m->recdf, bd))) {
     free_model(ctx, m);
     return rc;
   }
-  m->bytes = b32 + bp + bc + bh + ba;
+  m->bytes = b32 + bp + bc + bh + ba + bd;
   cudaError_t e = cudaSuccess;
   if (b32) e = cudaMemcpy(m->rec32, r32.data(), b32, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && bp) e = cudaMemcpy(m->pos64, p64.data(), bp, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && bc) e = cudaMemcpy(m->cen32, c32.data(), bc, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && bh) e = cudaMemcpy(m->heavy, hv.data(), bh, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && ba) e = cudaMemcpy(m->all64, a64.data(), ba, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bd) e = cudaMemcpy(m->recdf, adf.data(), bd, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_model(ctx, m);
     return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));

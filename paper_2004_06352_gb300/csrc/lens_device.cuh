@@ -57,6 +57,50 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
   return false;
 }
 
+// FP64 counterparts (degree 11, same interval): interpolants at the
+// Chebyshev nodes of [0, 0.16] computed in 60-digit arithmetic
+// (csrc/fit_series.py); interpolation error below 4e-18 relative.
+__device__ __forceinline__ double atan_over_w64(double t) {
+  double p = -1.88510462903004675e-02;
+  p = fma(p, t, 3.88765647477774812e-02);
+  p = fma(p, t, -5.06934062578019290e-02);
+  p = fma(p, t, 5.85413360654678111e-02);
+  p = fma(p, t, -6.66390440659186400e-02);
+  p = fma(p, t, 7.69212547783340445e-02);
+  p = fma(p, t, -9.09090112754652180e-02);
+  p = fma(p, t, 1.11111108895220217e-01);
+  p = fma(p, t, -1.42857142820646682e-01);
+  p = fma(p, t, 1.99999999999688677e-01);
+  p = fma(p, t, -3.33333333333332316e-01);
+  return fma(p, t, 1.0);
+}
+__device__ __forceinline__ double atanh_over_w64(double t) {
+  double p = 1.11279998802890107e-01;
+  p = fma(p, t, 1.42027510153455820e-02);
+  p = fma(p, t, 6.13504335260846093e-02);
+  p = fma(p, t, 5.74260884066186833e-02);
+  p = fma(p, t, 6.68122440454864269e-02);
+  p = fma(p, t, 7.69130553539208311e-02);
+  p = fma(p, t, 9.09095422594738550e-02);
+  p = fma(p, t, 1.11111098280666135e-01);
+  p = fma(p, t, 1.42857143071626003e-01);
+  p = fma(p, t, 1.99999999998152628e-01);
+  p = fma(p, t, 3.33333333333339532e-01);
+  return fma(p, t, 1.0);
+}
+constexpr double T_SERIES64 = 0.16;
+// The same coefficients as float pairs (hi, lo) for the double-float path.
+__device__ __constant__ const float C_ATAN_DF[12][2] = {
+    {1.000000000e+00f, 0.000000000e+00f}, {-3.333333433e-01f, 9.934108647e-09f}, {2.000000030e-01f, -2.980543590e-09f},
+    {-1.428571492e-01f, 6.422708143e-09f}, {1.111111119e-01f, -3.043733265e-09f}, {-9.090901166e-02f, 3.865411602e-10f},
+    {7.692125440e-02f, 3.818954597e-10f}, {-6.663904339e-02f, -6.751677550e-10f}, {5.854133517e-02f, 8.999671564e-10f},
+    {-5.069340765e-02f, 1.396960325e-09f}, {3.887656331e-02f, 1.437154284e-09f}, {-1.885104552e-02f, -7.711869476e-10f}};
+__device__ __constant__ const float C_ATANH_DF[12][2] = {
+    {1.000000000e+00f, 0.000000000e+00f}, {3.333333433e-01f, -9.934101541e-09f}, {2.000000030e-01f, -2.982079694e-09f},
+    {1.428571492e-01f, -6.171728906e-09f}, {1.111110970e-01f, 1.242873915e-09f}, {9.090954065e-02f, 1.606245137e-09f},
+    {7.691305876e-02f, -3.403861193e-09f}, {6.681224704e-02f, -2.992401216e-09f}, {5.742608756e-02f, 8.483491687e-10f},
+    {6.135043502e-02f, -1.492454826e-09f}, {1.420275122e-02f, -2.039270280e-10f}, {1.112800017e-01f, -2.897034390e-09f}};
+
 // ----------------------------------------------------------------- FP64 path
 // One potential in FP64 at sky position (X, Y), D_ls/D_s = 1.
 // Outputs in the sky frame: deflection (ax, ay) and, if HESS, kappa, gamma1,
@@ -116,8 +160,14 @@ __device__ __forceinline__ void eval64(const double *__restrict__ r, double X, d
     axp = bq * Zx * (1.0 - wx / 3.0 + wx * wx / 5.0);
     ayp = bq * Zy * (1.0 + wy / 3.0 + wy * wy / 5.0);
   } else {
-    axp = bq / u * atan(u * Zx);
-    ayp = bq / u * atanh(u * Zy);
+    const double wx = u * Zx, wy = u * Zy, tx = wx * wx, ty = wy * wy;
+    if (fmax(tx, ty) < T_SERIES64) {  // bq/u atan(u Z) = bq Z atan(w)/w
+      axp = bq * Zx * atan_over_w64(tx);
+      ayp = bq * Zy * atanh_over_w64(ty);
+    } else {
+      axp = bq / u * atan(wx);
+      ayp = bq / u * atanh(wy);
+    }
   }
   ax = c * axp - s * ayp;
   ay = s * axp + c * ayp;
@@ -300,6 +350,108 @@ __device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, float 
     circ32<HESS, KP, false>(r4, dX, dY, p);
   else
     circ32<HESS, KP, true>(r4, dX, dY, p);
+}
+
+
+// ------------------------------------------------------------ double-float
+// An unevaluated sum hi + lo of two floats (~48 significant bits) on the FP32
+// pipe, for the image polish: GB300's FP64 rate is 1/64 of its FP32 rate.
+// Error-free transformations: TwoSum (Knuth), FastTwoSum and the product
+// error by FMA; compound operations as in Dekker (1971).
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = df_sub(a, df_mulf(b, q1));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  r = df_sub(r, df_mulf(b, q2));
+  const float q3 = __fdiv_rn(r.hi, b.hi);
+  return df_add(fast_two_sum(q1, q2), df{q3, 0.f});
+}
+__device__ __forceinline__ df df_sqrt(df a) {
+  if (!(a.hi > 0.f)) return {0.f, 0.f};
+  const float s = __fsqrt_rn(a.hi);
+  const float p = s * s;
+  const float e = fmaf(s, s, -p);  // s*s = p + e exactly
+  const float c = __fdiv_rn(((a.hi - p) - e) + a.lo, 2.f * s);
+  return fast_two_sum(s, c);
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_from_double(double d) {
+  const float h = (float)d;
+  return {h, (float)(d - (double)h)};
+}
+
+// atan(w)/w, atanh(w)/w on t = w^2 < T_SERIES64 in double-float: the FP64
+// interpolants' terms t^7.. (below 5e-7 of the result) in FP32, the rest in
+// double-float Horner.
+__device__ __forceinline__ df df_poly(df t, const float (*c)[2]) {
+  float tail = c[11][0];
+#pragma unroll
+  for (int k = 10; k >= 7; --k) tail = fmaf(tail, t.hi, c[k][0]);
+  df p = df_add(df{c[6][0], c[6][1]}, df_mulf(t, tail));
+#pragma unroll
+  for (int k = 5; k >= 0; --k) p = df_add(df{c[k][0], c[k][1]}, df_mul(p, t));
+  return p;
+}
+
+// Deflection of one dPIE in double-float at (X, Y) given as pairs; false when
+// |w| is too large for the polynomial (the caller then uses FP64).
+__device__ __forceinline__ bool dpie_alpha_df(const float *__restrict__ r, df X, df Y, df &ax, df &ay) {
+  const df c = {r[2 * F_C], r[2 * F_C + 1]}, s = {r[2 * F_S], r[2 * F_S + 1]};
+  const df dX = df_sub(X, df{r[2 * F_X0], r[2 * F_X0 + 1]}), dY = df_sub(Y, df{r[2 * F_Y0], r[2 * F_Y0 + 1]});
+  const df x = df_add(df_mul(c, dX), df_mul(s, dY)), y = df_sub(df_mul(c, dY), df_mul(s, dX));
+  const df q2 = {r[2 * F_Q2], r[2 * F_Q2 + 1]}, u2 = {r[2 * F_U2], r[2 * F_U2 + 1]};
+  const df x2 = df_mul(x, x), y2 = df_mul(y, y);
+  const df R = df_add(df_mul(q2, x2), y2);
+  const df psc = df_sqrt(df_add(R, df{r[2 * F_KC], r[2 * F_KC + 1]}));
+  const df pst = df_sqrt(df_add(R, df{r[2 * F_KT], r[2 * F_KT + 1]}));
+  const df Sp = df_add(psc, pst);
+  const df Ec = df_add(psc, df{r[2 * F_SC], r[2 * F_SC + 1]}), Et = df_add(pst, df{r[2 * F_ST], r[2 * F_ST + 1]});
+  const df dS = df_sub(df{r[2 * F_ST], r[2 * F_ST + 1]}, df{r[2 * F_SC], r[2 * F_SC + 1]});
+  const df numx = df_mul(df_mul(x, dS), df_add(Sp, df{r[2 * F_Q2SS], r[2 * F_Q2SS + 1]}));
+  const df denx = df_mul(Sp, df_add(df_mul(Ec, Et), df_mul(u2, x2)));
+  const df Zx = df_div(numx, denx);
+  const df Fc = df_add(psc, df{r[2 * F_Q2SC], r[2 * F_Q2SC + 1]}), Ft = df_add(pst, df{r[2 * F_Q2ST], r[2 * F_Q2ST + 1]});
+  const df numy = df_mul(df_mul(y, df{r[2 * F_Q2DS], r[2 * F_Q2DS + 1]}), df_add(Sp, df{r[2 * F_SS], r[2 * F_SS + 1]}));
+  const df deny = df_mul(Sp, df_sub(df_mul(Fc, Ft), df_mul(u2, y2)));
+  const df Zy = df_div(numy, deny);
+  const df tx = df_mul(u2, df_mul(Zx, Zx)), ty = df_mul(u2, df_mul(Zy, Zy));
+  if (!(tx.hi < (float)T_SERIES64 && ty.hi < (float)T_SERIES64)) return false;  // also catches NaN
+  const df bq = {r[2 * F_BQ], r[2 * F_BQ + 1]};
+  const df axp = df_mul(df_mul(bq, Zx), df_poly(tx, C_ATAN_DF)), ayp = df_mul(df_mul(bq, Zy), df_poly(ty, C_ATANH_DF));
+  ax = df_sub(df_mul(c, axp), df_mul(s, ayp));
+  ay = df_add(df_mul(s, axp), df_mul(c, ayp));
+  return true;
 }
 
 // --------------------------------------------------------- constraint sets

@@ -7,11 +7,12 @@
 //   2. k_img_search   per (grid tile, set): deflection at the tile's nodes =
 //                     cached static part + the two varying potentials (FP32);
 //                     for each distance ratio the nodes are mapped to the
-//                     source plane, both triangles of every cell are tested
-//                     against that ratio's sources (bounding box, then
-//                     barycentric weights with a small tolerance so that a
-//                     source on a shared edge is never lost), and every hit
-//                     is appended to the set's candidate buffer.
+//                     source plane, the sources inside the tile's footprint
+//                     (bounding box of its mapped nodes) are listed, and both
+//                     triangles of every cell are tested against that list
+//                     (bounding box, then barycentric weights with a small
+//                     tolerance so that a source on a shared edge is never
+//                     lost); every hit is appended to the set's buffer.
 //   3. k_img_newton   one warp per candidate: the hit triangle is subdivided
 //                     up to SUBDIV_LEVELS times (keeping the sub-triangle that
 //                     best contains the source; stopping early when none does),
@@ -37,7 +38,7 @@ namespace lens {
 namespace {
 
 constexpr int IMG_CAP = 4096;       // candidate images per parameter set
-constexpr int IMG_BATCH = 64;       // parameter sets per batch
+constexpr int IMG_BATCH = 256;      // parameter sets per batch
 constexpr int MAX_SRC = 1024;
 constexpr double DEDUP = 1e-3;      // images closer than this are one image (arcsec)
 constexpr double NEWTON32_TOL = 1e-4;
@@ -61,8 +62,18 @@ struct Hit {
   int cell;            // 2 * (j * (nx-1) + i) + triangle of the hit
 };
 
+// Records of the two varying potentials of one parameter set, built once per
+// set by k_img_sources: FP32 records and hi/lo centres (search, subdivision,
+// FP32 Newton), double-float and FP64 records (polish).
+struct __align__(16) VarRecs {
+  float r32[2][REC32];
+  float cen[2][4];
+  float rdf[2][RECDF];
+  double r64[2][REC64];
+};
+
 struct Layout {
-  size_t cnt, valid, nuniq, bary, hits, uniq, total;
+  size_t cnt, valid, nuniq, bary, hits, uniq, var, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -82,6 +93,8 @@ __host__ __device__ inline Layout layout(int B, int nsrc) {
   o = align_up(o + (size_t)B * IMG_CAP * sizeof(Hit));
   L.uniq = o;
   o = align_up(o + (size_t)B * IMG_CAP * sizeof(int));
+  L.var = o;
+  o = align_up(o + (size_t)B * sizeof(VarRecs));
   L.total = o;
   return L;
 }
@@ -90,6 +103,7 @@ struct Bufs {
   int *cnt, *valid, *nuniq, *uniq;
   double *bary;
   Hit *hits;
+  VarRecs *var;
 };
 
 __host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc) {
@@ -102,6 +116,7 @@ __host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc) {
   r.bary = (double *)(b + L.bary);
   r.hits = (Hit *)(b + L.hits);
   r.uniq = (int *)(b + L.uniq);
+  r.var = (VarRecs *)(b + L.var);
   return r;
 }
 
@@ -130,7 +145,20 @@ __global__ void __launch_bounds__(SRC_THREADS) k_img_sources(const SetArgs a, co
   const double *q = a.params + (size_t)(a.p0 + b) * 14;
   if (threadIdx.x == 0) s_ok = 1;
   __syncthreads();
-  if (threadIdx.x < 2 && !load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
+  if (threadIdx.x < 2) {
+    if (!load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
+    // every later kernel of this set reads the varying potentials from here
+    VarRecs &v = a.s.var[b];
+    const double *w = q + 7 * threadIdx.x;
+    make_rec32(threadIdx.x == 0 ? a.type0 : a.type1, w[3], w[2], w[4], w[5], w[6], v.r32[threadIdx.x]);
+    const float xh = (float)w[0], yh = (float)w[1];
+    v.cen[threadIdx.x][0] = xh;
+    v.cen[threadIdx.x][1] = yh;
+    v.cen[threadIdx.x][2] = (float)(w[0] - (double)xh);
+    v.cen[threadIdx.x][3] = (float)(w[1] - (double)yh);
+    make_recdf(threadIdx.x == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6], v.rdf[threadIdx.x]);
+    for (int k = 0; k < REC64; ++k) v.r64[threadIdx.x][k] = s_rec[threadIdx.x * REC64 + k];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     a.s.valid[b] = s_ok;
@@ -153,8 +181,8 @@ struct SearchArgs {
 };
 
 __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 tA, float2 tB, float2 tC,
-                                         const float2 *s_src, const int32_t *__restrict__ gsrc, int g0, int g1,
-                                         float tiny, int *cnt, Hit *hits, int cell) {
+                                         const float2 *s_src, const int *list, int nlist, float tiny, int *cnt,
+                                         Hit *hits, int cell) {
   const float lox = fminf(A.x, fminf(Bv.x, Cv.x)), hix = fmaxf(A.x, fmaxf(Bv.x, Cv.x));
   const float loy = fminf(A.y, fminf(Bv.y, Cv.y)), hiy = fmaxf(A.y, fmaxf(Bv.y, Cv.y));
   const float padx = BARY_TOL * (hix - lox) + 1e-6f, pady = BARY_TOL * (hiy - loy) + 1e-6f;
@@ -162,8 +190,8 @@ __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 
   const float area2 = e1x * e2y - e1y * e2x;
   if (!(fabsf(area2) > tiny)) return;
   const float inv = 1.f / area2;
-  for (int k = g0; k < g1; ++k) {
-    const int src = gsrc[k];
+  for (int k = 0; k < nlist; ++k) {
+    const int src = list[k];
     const float2 P = s_src[src];
     if (P.x < lox - padx || P.x > hix + padx || P.y < loy - pady || P.y > hiy + pady) continue;
     const float px = P.x - A.x, py = P.y - A.y;
@@ -183,33 +211,36 @@ __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 
 
 __global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const SearchArgs g) {
   __shared__ __align__(16) float s_rec[2][REC32];
-  __shared__ double s_cen[2][2];
+  __shared__ float2 s_off[2];  // tile origin minus each varying potential's centre
   __shared__ float2 s_al[NX_T * NY_T];
   __shared__ float2 s_src[MAX_SRC];
   const int b = blockIdx.z;
   if (!a.s.valid[b]) return;
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * CT_X, j0 = blockIdx.y * CT_Y;
-  if (tid < 2) {
-    const double *w = a.params + (size_t)(a.p0 + b) * 14 + 7 * tid;
-    make_rec32(tid == 0 ? a.type0 : a.type1, w[3], w[2], w[4], w[5], w[6], s_rec[tid]);
-    s_cen[tid][0] = w[0];
-    s_cen[tid][1] = w[1];
-  }
+  // positions in FP32 relative to the tile origin (the search only decides
+  // which triangles seed a candidate; the refinement is exact)
+  const double Tx = g.xmin + i0 * g.dx, Ty = g.ymin + j0 * g.dy;
+  const float fdx = (float)g.dx, fdy = (float)g.dy, fTx = (float)Tx, fTy = (float)Ty;
+  const VarRecs &var = a.s.var[b];
+  if (tid < 2 * REC32) s_rec[tid / REC32][tid % REC32] = var.r32[tid / REC32][tid % REC32];
+  if (tid < 2) s_off[tid] = make_float2((float)(Tx - ((double)var.cen[tid][0] + (double)var.cen[tid][2])),
+                                        (float)(Ty - ((double)var.cen[tid][1] + (double)var.cen[tid][3])));
   const double *bary = a.s.bary + (size_t)b * a.nsrc * 2;
   for (int i = tid; i < a.nsrc; i += 256) s_src[i] = make_float2((float)bary[2 * i], (float)bary[2 * i + 1]);
   __syncthreads();
   for (int n = tid; n < NX_T * NY_T; n += 256) {
-    const int ii = min(i0 + n % NX_T, g.nx - 1), jj = min(j0 + n / NX_T, g.ny - 1);
+    const int li = n % NX_T, lj = n / NX_T;
+    const int ii = min(i0 + li, g.nx - 1), jj = min(j0 + lj, g.ny - 1);
     const size_t o = (size_t)jj * g.nx + ii;
-    const double X = g.xmin + ii * g.dx, Y = g.ymin + jj * g.dy;
     float tx = g.ax[o], ty = g.ay[o];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
       Acc<false, 1> acc;
       acc.zero();
-      const float dY[1] = {(float)(Y - s_cen[v][1])};
-      eval32_any<false, 1>(reinterpret_cast<const float4 *>(s_rec[v]), (float)(X - s_cen[v][0]), dY, acc);
+      const float dY[1] = {fmaf((float)(jj - j0), fdy, s_off[v].y)};
+      eval32_any<false, 1>(reinterpret_cast<const float4 *>(s_rec[v]), fmaf((float)(ii - i0), fdx, s_off[v].x), dY,
+                           acc);
       tx += acc.ax[0];
       ty += acc.ay[0];
     }
@@ -218,9 +249,10 @@ __global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const Searc
   __syncthreads();
   const int ci = tid % CT_X, cj = tid / CT_X;
   const int gi = i0 + ci, gj = j0 + cj;
-  if (gi >= g.nx - 1 || gj >= g.ny - 1) return;
-  const float X0 = (float)(g.xmin + gi * g.dx), X1 = (float)(g.xmin + (gi + 1) * g.dx);
-  const float Y0 = (float)(g.ymin + gj * g.dy), Y1 = (float)(g.ymin + (gj + 1) * g.dy);
+  const bool live = gi < g.nx - 1 && gj < g.ny - 1;
+  const int lane = tid & 31, warp = tid >> 5;
+  const float X0 = fmaf((float)ci, fdx, fTx), X1 = fmaf((float)(ci + 1), fdx, fTx);
+  const float Y0 = fmaf((float)cj, fdy, fTy), Y1 = fmaf((float)(cj + 1), fdy, fTy);
   const int n00 = cj * NX_T + ci;
   const float2 a00 = s_al[n00], a10 = s_al[n00 + 1], a01 = s_al[n00 + NX_T], a11 = s_al[n00 + NX_T + 1];
   const float tiny = (float)(1e-10 * g.dx * g.dy);
@@ -228,14 +260,74 @@ __global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const Searc
   Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
   const float2 t00 = make_float2(X0, Y0), t10 = make_float2(X1, Y0), t11 = make_float2(X1, Y1),
                t01 = make_float2(X0, Y1);
+  const int cell = 2 * (gj * (g.nx - 1) + gi);
+  __shared__ float s_box[4][8];
+  __shared__ int s_list[MAX_SRC];
+  __shared__ int s_nlist;
   for (int q = 0; q < g.ng; ++q) {
     const float r = (float)g.grp_ratio[q];
-    const float2 b00 = make_float2(X0 - r * a00.x, Y0 - r * a00.y), b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
-                 b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y), b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
-    const int g0 = g.grp_off[q], g1 = g.grp_off[q + 1];
-    const int cell = 2 * (gj * (g.nx - 1) + gi);
-    tri_test(b00, b10, b11, t00, t10, t11, s_src, g.grp_src, g0, g1, tiny, cnt, hits, cell);
-    tri_test(b00, b11, b01, t00, t11, t01, s_src, g.grp_src, g0, g1, tiny, cnt, hits, cell + 1);
+    // the tile's footprint in this ratio's source plane (bounding box of its nodes)
+    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY;
+    for (int n = tid; n < NX_T * NY_T; n += 256) {
+      const int ii = i0 + n % NX_T, jj = j0 + n / NX_T;
+      if (ii >= g.nx || jj >= g.ny) continue;
+      const float bx = fmaf((float)(n % NX_T), fdx, fTx) - r * s_al[n].x;
+      const float by = fmaf((float)(n / NX_T), fdy, fTy) - r * s_al[n].y;
+      lox = fminf(lox, bx);
+      hix = fmaxf(hix, bx);
+      loy = fminf(loy, by);
+      hiy = fmaxf(hiy, by);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+      hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+      loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+      hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+    }
+    if (lane == 0) {
+      s_box[0][warp] = lox;
+      s_box[1][warp] = hix;
+      s_box[2][warp] = loy;
+      s_box[3][warp] = hiy;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // the sources of this ratio inside the footprint (+ the test's tolerance)
+      float L = INFINITY, H = -INFINITY, Ly = INFINITY, Hy = -INFINITY;
+      for (int w = 0; w < 8; ++w) {
+        L = fminf(L, s_box[0][w]);
+        H = fmaxf(H, s_box[1][w]);
+        Ly = fminf(Ly, s_box[2][w]);
+        Hy = fmaxf(Hy, s_box[3][w]);
+      }
+      const float px = BARY_TOL * (H - L) + 1e-5f, py = BARY_TOL * (Hy - Ly) + 1e-5f;
+      const int g0 = g.grp_off[q], g1 = g.grp_off[q + 1];
+      int base = 0;
+      for (int k0 = g0; k0 < g1; k0 += 32) {
+        const int k = k0 + lane;
+        bool in = false;
+        int src = 0;
+        if (k < g1) {
+          src = g.grp_src[k];
+          const float2 P = s_src[src];
+          in = P.x >= L - px && P.x <= H + px && P.y >= Ly - py && P.y <= Hy + py;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (in) s_list[base + __popc(m & ((1u << lane) - 1u))] = src;
+        base += __popc(m);
+      }
+      if (lane == 0) s_nlist = base;
+    }
+    __syncthreads();
+    const int nlist = s_nlist;
+    if (live && nlist > 0) {
+      const float2 b00 = make_float2(X0 - r * a00.x, Y0 - r * a00.y), b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
+                   b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y), b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
+      tri_test(b00, b10, b11, t00, t10, t11, s_src, s_list, nlist, tiny, cnt, hits, cell);
+      tri_test(b00, b11, b01, t00, t11, t01, s_src, s_list, nlist, tiny, cnt, hits, cell + 1);
+    }
+    __syncthreads();
   }
 }
 
@@ -246,6 +338,7 @@ struct NewtonArgs {
   const double *heavy;         // static potentials on the FP64 path
   int n_heavy;
   const double *all64;         // every static potential in FP64 (polish)
+  const float *recdf;          // every static potential in double-float (polish)
   int n_stat;
   const double *ratio;         // per source
   double xmin, ymin, dx, dy;   // search grid
@@ -260,72 +353,6 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int NW_THREADS = 256, NW_WARPS = NW_THREADS / 32;
 
-// Per-warp copy of the varying potentials of the warp's parameter set: FP32
-// records and hi/lo centres (subdivision and FP32 Newton), FP64 records
-// (polish).
-struct __align__(16) VarRecs {
-  float r32[2][REC32];
-  float cen[2][4];
-  double r64[2][REC64];
-};
-
-__device__ __forceinline__ void load_var(const double *q, int type0, int type1, int lane, VarRecs &v) {
-  if (lane < 2) {
-    const double *w = q + 7 * lane;
-    const int type = lane == 0 ? type0 : type1;
-    make_rec32(type, w[3], w[2], w[4], w[5], w[6], v.r32[lane]);
-    const float xh = (float)w[0], yh = (float)w[1];
-    v.cen[lane][0] = xh;
-    v.cen[lane][1] = yh;
-    v.cen[lane][2] = (float)(w[0] - (double)xh);
-    v.cen[lane][3] = (float)(w[1] - (double)yh);
-    load_var_rec64(q, type0, type1, lane, &v.r64[0][0]);  // writes record `lane` of the array
-  }
-  __syncwarp();
-}
-
-// Full model at (tx, ty), D_ls/D_s = 1, summed over the warp (every lane gets
-// the same bits): FP32 for the static light potentials and the two varying
-// ones, FP64 for static cluster-scale ones.  v = {ax, ay, kappa, g1, g2}.
-template <bool HESS>
-__device__ __forceinline__ void warp_eval(const NewtonArgs &n, const VarRecs &vr, int lane, double tx, double ty,
-                                          double (&v)[5]) {
-  const float hx = (float)tx, hy = (float)ty;
-  const float lx = (float)(tx - (double)hx), ly = (float)(ty - (double)hy);
-  Acc<HESS, 1> part;
-  part.zero();
-  for (int j = lane; j < n.n_light + 2; j += 32) {
-    const float4 *r4;
-    float4 c;
-    if (j < n.n_light) {
-      c = reinterpret_cast<const float4 *>(n.cen32)[j];
-      r4 = reinterpret_cast<const float4 *>(n.rec32) + (size_t)j * (REC32 / 4);
-    } else {
-      const float *cc = vr.cen[j - n.n_light];
-      c = make_float4(cc[0], cc[1], cc[2], cc[3]);
-      r4 = reinterpret_cast<const float4 *>(vr.r32[j - n.n_light]);
-    }
-    const float dY[1] = {(hy - c.y) + (ly - c.w)};
-    eval32_any<HESS, 1>(r4, (hx - c.x) + (lx - c.z), dY, part);
-  }
-  v[0] = part.ax[0];
-  v[1] = part.ay[0];
-  v[2] = HESS ? part.k[0] : 0.0;
-  v[3] = HESS ? part.g1[0] : 0.0;
-  v[4] = HESS ? part.g2[0] : 0.0;
-  for (int j = lane; j < n.n_heavy; j += 32) {
-    double e0, e1, e2 = 0, e3 = 0, e4 = 0;
-    eval64<HESS>(n.heavy + (size_t)j * REC64, tx, ty, e0, e1, e2, e3, e4);
-    v[0] += e0;
-    v[1] += e1;
-    v[2] += e2;
-    v[3] += e3;
-    v[4] += e4;
-  }
-#pragma unroll
-  for (int c = 0; c < (HESS ? 5 : 2); ++c) v[c] = warp_sum(v[c]);
-}
-
 // Barycentric weights of p in (a, b, c); false when degenerate.
 __device__ __forceinline__ bool bary_w(const double *a, const double *b, const double *c, const double *p,
                                        double tiny, double w[3]) {
@@ -337,121 +364,219 @@ __device__ __forceinline__ bool bary_w(const double *a, const double *b, const d
   return true;
 }
 
-__global__ void __launch_bounds__(NW_THREADS) k_img_newton(const SetArgs a, const NewtonArgs n) {
-  __shared__ VarRecs s_var[NW_WARPS];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long nwarps = (long long)gridDim.x * NW_WARPS;
-  const double cell_tiny = 1e-14 * n.dx * n.dy;  // degenerate-triangle bound, as in the definition
-  const double step_max = fmax(n.dx, n.dy);
-  for (long long task = (long long)blockIdx.x * NW_WARPS + w; task < (long long)a.B * IMG_CAP; task += nwarps) {
-    const int b = (int)(task / IMG_CAP), k = (int)(task % IMG_CAP);
-    if (!a.s.valid[b] || k >= min(a.s.cnt[b], IMG_CAP)) continue;
-    Hit *h = a.s.hits + (size_t)b * IMG_CAP + k;
-    load_var(a.params + (size_t)(a.p0 + b) * 14, a.type0, a.type1, lane, s_var[w]);
-    const VarRecs &vr = s_var[w];
-    const int src = h->src;
-    const double r = n.ratio[src];
-    const double P[2] = {a.s.bary[((size_t)b * a.nsrc + src) * 2], a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1]};
-    // the hit triangle, mapped with the full model
-    const int cell = h->cell, tri = cell & 1, ci = (cell >> 1) % (n.nx - 1), cj = (cell >> 1) / (n.nx - 1);
-    // triangle 0: (i,j),(i+1,j),(i+1,j+1); triangle 1: (i,j),(i+1,j+1),(i,j+1)
-    double th[3][2], be[3][2];
-    const int oi[2][3] = {{ci, ci + 1, ci + 1}, {ci, ci + 1, ci}}, oj[2][3] = {{cj, cj, cj + 1}, {cj, cj + 1, cj + 1}};
+// One candidate per thread.  Every evaluation is a sweep of the CTA over all
+// static FP32 potentials, staged chunk by chunk in shared memory (all threads
+// read the same record: broadcast), with the compensated accumulation of the
+// map kernel, plus the two varying potentials (FP32) and static cluster-scale
+// ones (FP64).  Each thread evaluates NP points of its own per sweep.
+constexpr int RF_THREADS = 64, RF_CH = 64;
+
+template <int NP, bool HESS>
+__device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, float4 *s_rec, float4 *s_cen,
+                                      const double (&px)[NP], const double (&py)[NP], double (&out)[NP][5]) {
+  float hx[NP], lx[NP], hy[NP], ly[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    hx[k] = (float)px[k];
+    lx[k] = (float)(px[k] - (double)hx[k]);
+    hy[k] = (float)py[k];
+    ly[k] = (float)(py[k] - (double)hy[k]);
+  }
+  Acc<HESS, 1> tot[NP], cmp[NP], part[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    tot[k].zero();
+    cmp[k].zero();
+    part[k].zero();
+  }
+  int seen = 0;
+  const float4 *g_rec = reinterpret_cast<const float4 *>(n.rec32);
+  const float4 *g_cen = reinterpret_cast<const float4 *>(n.cen32);
+  for (int c0 = 0; c0 < n.n_light + 2; c0 += RF_CH) {
+    const int cnt = min(RF_CH, n.n_light + 2 - c0);
+    __syncthreads();  // the previous chunk has been used by every thread
+    for (int i = threadIdx.x; i < cnt * (REC32 / 4); i += RF_THREADS) {
+      const int hh = c0 + i / (REC32 / 4), q = i % (REC32 / 4);
+      s_rec[i] = hh < n.n_light ? g_rec[(size_t)hh * (REC32 / 4) + q]
+                                : reinterpret_cast<const float4 *>(var.r32[hh - n.n_light])[q];
+    }
+    for (int i = threadIdx.x; i < cnt; i += RF_THREADS) {
+      const int hh = c0 + i;
+      s_cen[i] = hh < n.n_light ? g_cen[hh]
+                                : make_float4(var.cen[hh - n.n_light][0], var.cen[hh - n.n_light][1],
+                                              var.cen[hh - n.n_light][2], var.cen[hh - n.n_light][3]);
+    }
+    __syncthreads();
+    for (int h = 0; h < cnt; ++h) {
+      const float4 *r4 = s_rec + h * (REC32 / 4);
+      const float4 c = s_cen[h];
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const float dY[1] = {(hy[k] - c.y) + (ly[k] - c.w)};
+        eval32_any<HESS, 1>(r4, (hx[k] - c.x) + (lx[k] - c.z), dY, part[k]);
+      }
+      if (++seen == 16) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) fold(tot[k], cmp[k], part[k]);
+        seen = 0;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    fold(tot[k], cmp[k], part[k]);
+    out[k][0] = (double)tot[k].ax[0] - (double)cmp[k].ax[0];
+    out[k][1] = (double)tot[k].ay[0] - (double)cmp[k].ay[0];
+    out[k][2] = HESS ? (double)tot[k].k[0] - (double)cmp[k].k[0] : 0.0;
+    out[k][3] = HESS ? (double)tot[k].g1[0] - (double)cmp[k].g1[0] : 0.0;
+    out[k][4] = HESS ? (double)tot[k].g2[0] - (double)cmp[k].g2[0] : 0.0;
+    for (int j = 0; j < n.n_heavy; ++j) {
+      double e0, e1, e2 = 0, e3 = 0, e4 = 0;
+      eval64<HESS>(n.heavy + (size_t)j * REC64, px[k], py[k], e0, e1, e2, e3, e4);
+      out[k][0] += e0;
+      out[k][1] += e1;
+      out[k][2] += e2;
+      out[k][3] += e3;
+      out[k][4] += e4;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, const NewtonArgs n) {
+  __shared__ float4 s_rec[RF_CH * (REC32 / 4)];
+  __shared__ float4 s_cen[RF_CH];
+  __shared__ VarRecs s_var;
+  const int b = blockIdx.y;
+  if (!a.s.valid[b]) return;
+  const int ncand = min(a.s.cnt[b], IMG_CAP);
+  if (blockIdx.x * RF_THREADS >= ncand) return;  // both exits are uniform over the CTA
+  {
+    const float *f = reinterpret_cast<const float *>(&a.s.var[b]);
+    float *d = reinterpret_cast<float *>(&s_var);
+    for (int i = threadIdx.x; i < (int)(sizeof(VarRecs) / sizeof(float)); i += RF_THREADS) d[i] = f[i];
+  }
+  const int k = blockIdx.x * RF_THREADS + threadIdx.x;
+  const bool mine = k < ncand;
+  Hit *h = a.s.hits + (size_t)b * IMG_CAP + (mine ? k : 0);
+  const int src = mine ? h->src : 0;
+  const double r = n.ratio[src];
+  const double P[2] = {a.s.bary[((size_t)b * a.nsrc + src) * 2], a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1]};
+  const int cell = mine ? h->cell : 0, tri = cell & 1, ci = (cell >> 1) % (n.nx - 1), cj = (cell >> 1) / (n.nx - 1);
+  // triangle 0: (i,j),(i+1,j),(i+1,j+1); triangle 1: (i,j),(i+1,j+1),(i,j+1)
+  const int oi[2][3] = {{ci, ci + 1, ci + 1}, {ci, ci + 1, ci}}, oj[2][3] = {{cj, cj, cj + 1}, {cj, cj + 1, cj + 1}};
+  double th[3][2], be[3][2];
+  {
+    double vx[3], vy[3], o[3][5];
     for (int q = 0; q < 3; ++q) {
-      th[q][0] = n.xmin + oi[tri][q] * n.dx;
-      th[q][1] = n.ymin + oj[tri][q] * n.dy;
-      double v[5];
-      warp_eval<false>(n, vr, lane, th[q][0], th[q][1], v);
-      be[q][0] = th[q][0] - r * v[0];
-      be[q][1] = th[q][1] - r * v[1];
+      th[q][0] = vx[q] = n.xmin + oi[tri][q] * n.dx;
+      th[q][1] = vy[q] = n.ymin + oj[tri][q] * n.dy;
     }
-    // subdivision: keep the sub-triangle that best contains the source
-    double tiny = cell_tiny, wgt[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3};
-    for (int lev = 0; lev <= SUBDIV_LEVELS; ++lev) {
-      if (lev == SUBDIV_LEVELS) {
-        if (!bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
-        break;
-      }
-      double t6[6][2], b6[6][2];
-      for (int q = 0; q < 3; ++q) {
-        t6[q][0] = th[q][0];
-        t6[q][1] = th[q][1];
-        b6[q][0] = be[q][0];
-        b6[q][1] = be[q][1];
-        const int q1 = q == 2 ? 0 : q + 1;
-        t6[3 + q][0] = 0.5 * (th[q][0] + th[q1][0]);
-        t6[3 + q][1] = 0.5 * (th[q][1] + th[q1][1]);
-        double v[5];
-        warp_eval<false>(n, vr, lane, t6[3 + q][0], t6[3 + q][1], v);
-        b6[3 + q][0] = t6[3 + q][0] - r * v[0];
-        b6[3 + q][1] = t6[3 + q][1] - r * v[1];
-      }
-      const double tiny_sub = 0.25 * tiny;
-      const int sub[4][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}, {3, 4, 5}};
-      int best = -1;
-      double best_score = -INFINITY;
-      for (int sb = 0; sb < 4; ++sb) {
-        double ww[3];
-        if (!bary_w(b6[sub[sb][0]], b6[sub[sb][1]], b6[sub[sb][2]], P, tiny_sub, ww)) continue;
-        const double score = fmin(ww[0], fmin(ww[1], ww[2]));
-        if (score > best_score) {
-          best_score = score;
-          best = sb;
-        }
-      }
-      if (best < 0 || best_score < -SUBDIV_TOL) {
-        // the map is far from linear on this triangle: stop refining here
-        if (!bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
-        break;
-      }
-      tiny = tiny_sub;
-      for (int q = 0; q < 3; ++q) {
-        th[q][0] = t6[sub[best][q]][0];
-        th[q][1] = t6[sub[best][q]][1];
-        be[q][0] = b6[sub[best][q]][0];
-        be[q][1] = b6[sub[best][q]][1];
+    __syncthreads();  // s_var complete
+    sweep<3, false>(n, s_var, s_rec, s_cen, vx, vy, o);
+    for (int q = 0; q < 3; ++q) {
+      be[q][0] = th[q][0] - r * o[q][0];
+      be[q][1] = th[q][1] - r * o[q][1];
+    }
+  }
+  // subdivision: keep the sub-triangle that best contains the source; stop
+  // when none does (map far from linear on this triangle)
+  double tiny = 1e-14 * n.dx * n.dy, wgt[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+  bool refining = mine;
+  for (int lev = 0; lev < SUBDIV_LEVELS; ++lev) {
+    if (!__syncthreads_or(refining)) break;
+    double t6[6][2], mx[3], my[3], o[3][5];
+    for (int q = 0; q < 3; ++q) {
+      const int q1 = q == 2 ? 0 : q + 1;
+      t6[q][0] = th[q][0];
+      t6[q][1] = th[q][1];
+      t6[3 + q][0] = mx[q] = 0.5 * (th[q][0] + th[q1][0]);
+      t6[3 + q][1] = my[q] = 0.5 * (th[q][1] + th[q1][1]);
+    }
+    sweep<3, false>(n, s_var, s_rec, s_cen, mx, my, o);
+    if (!refining) continue;
+    double b6[6][2];
+    for (int q = 0; q < 3; ++q) {
+      b6[q][0] = be[q][0];
+      b6[q][1] = be[q][1];
+      b6[3 + q][0] = t6[3 + q][0] - r * o[q][0];
+      b6[3 + q][1] = t6[3 + q][1] - r * o[q][1];
+    }
+    const double tiny_sub = 0.25 * tiny;
+    const int sub[4][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}, {3, 4, 5}};
+    int best = -1;
+    double best_score = -INFINITY;
+    for (int sb = 0; sb < 4; ++sb) {
+      double ww[3];
+      if (!bary_w(b6[sub[sb][0]], b6[sub[sb][1]], b6[sub[sb][2]], P, tiny_sub, ww)) continue;
+      const double score = fmin(ww[0], fmin(ww[1], ww[2]));
+      if (score > best_score) {
+        best_score = score;
+        best = sb;
       }
     }
-    double tx = wgt[0] * th[0][0] + wgt[1] * th[1][0] + wgt[2] * th[2][0];
-    double ty = wgt[0] * th[0][1] + wgt[1] * th[1][1] + wgt[2] * th[2][1];
-    int status = ST_FAILED;
-    float h11 = 0.f, h22 = 0.f, h12 = 0.f;
-    for (int it = 0; it < NEWTON_MAXIT; ++it) {
-      double v[5];
-      warp_eval<true>(n, vr, lane, tx, ty, v);
-      const double fx = P[0] - (tx - r * v[0]), fy = P[1] - (ty - r * v[1]);
-      const double m11 = r * (v[2] + v[3]), m22 = r * (v[2] - v[3]), m12 = r * v[4];
-      const double a11 = 1.0 - m11, a22 = 1.0 - m22, a12 = -m12;
-      const double det = a11 * a22 - a12 * a12;
-      if (!(det != 0.0) || !isfinite(det)) break;
-      double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
-      const double len = sqrt(dx * dx + dy * dy);
-      if (len > step_max) {  // trust region: at most one cell per step
-        dx *= step_max / len;
-        dy *= step_max / len;
-      }
-      tx += dx;
-      ty += dy;
-      h11 = (float)m11;
-      h22 = (float)m22;
-      h12 = (float)m12;
-      if (!isfinite(tx) || !isfinite(ty)) break;
-      if (len < NEWTON32_TOL) {
-        status = ST_NEWTON;
-        break;
-      }
+    if (best < 0 || best_score < -SUBDIV_TOL) {
+      if (!bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
+      refining = false;
+      continue;
     }
-    // a root far from its triangle belongs to another triangle's search
-    if (status == ST_NEWTON && hypot(tx - h->cx, ty - h->cy) > LOCAL_CELLS * fmax(n.dx, n.dy)) status = ST_FAR;
-    if (lane == 0) {
-      h->tx = tx;
-      h->ty = ty;
-      h->h11 = h11;
-      h->h22 = h22;
-      h->h12 = h12;
-      h->status = status;
+    tiny = tiny_sub;
+    for (int q = 0; q < 3; ++q) {
+      th[q][0] = t6[sub[best][q]][0];
+      th[q][1] = t6[sub[best][q]][1];
+      be[q][0] = b6[sub[best][q]][0];
+      be[q][1] = b6[sub[best][q]][1];
     }
-    __syncwarp();
+  }
+  if (refining && !bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
+  // FP32 Newton with steps limited to one cell
+  double tx = wgt[0] * th[0][0] + wgt[1] * th[1][0] + wgt[2] * th[2][0];
+  double ty = wgt[0] * th[0][1] + wgt[1] * th[1][1] + wgt[2] * th[2][1];
+  const double step_max = fmax(n.dx, n.dy);
+  int status = ST_FAILED;
+  float h11 = 0.f, h22 = 0.f, h12 = 0.f;
+  bool active = mine;
+  for (int it = 0; it < NEWTON_MAXIT; ++it) {
+    if (!__syncthreads_or(active)) break;
+    double px[1] = {tx}, py[1] = {ty}, o[1][5];
+    sweep<1, true>(n, s_var, s_rec, s_cen, px, py, o);
+    if (!active) continue;
+    const double fx = P[0] - (tx - r * o[0][0]), fy = P[1] - (ty - r * o[0][1]);
+    const double m11 = r * (o[0][2] + o[0][3]), m22 = r * (o[0][2] - o[0][3]), m12 = r * o[0][4];
+    const double a11 = 1.0 - m11, a22 = 1.0 - m22, a12 = -m12;
+    const double det = a11 * a22 - a12 * a12;
+    if (!(det != 0.0) || !isfinite(det)) {
+      active = false;
+      continue;
+    }
+    double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+    const double len = sqrt(dx * dx + dy * dy);
+    if (len > step_max) {
+      dx *= step_max / len;
+      dy *= step_max / len;
+    }
+    tx += dx;
+    ty += dy;
+    h11 = (float)m11;
+    h22 = (float)m22;
+    h12 = (float)m12;
+    if (!isfinite(tx) || !isfinite(ty)) {
+      active = false;
+      continue;
+    }
+    if (len < NEWTON32_TOL) {
+      status = ST_NEWTON;
+      active = false;
+    }
+  }
+  // a root far from its triangle belongs to another triangle's search
+  if (status == ST_NEWTON && hypot(tx - h->cx, ty - h->cy) > LOCAL_CELLS * fmax(n.dx, n.dy)) status = ST_FAR;
+  if (mine) {
+    h->tx = tx;
+    h->ty = ty;
+    h->h11 = h11;
+    h->h22 = h22;
+    h->h12 = h12;
+    h->status = status;
   }
 }
 
@@ -504,14 +629,17 @@ __global__ void __launch_bounds__(DD_THREADS) k_img_dedup(const SetArgs a) {
 // ----------------------------------------------------------------- 5. polish
 __global__ void __launch_bounds__(NW_THREADS) k_img_polish(const SetArgs a, const NewtonArgs n) {
   __shared__ double s_var[NW_WARPS][2 * REC64];
+  __shared__ float s_vdf[NW_WARPS][2 * RECDF];
+  __shared__ int s_q[NW_WARPS][64];  // potentials left to the FP64 evaluator
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * NW_WARPS;
+  const int ntot = n.n_stat + 2;
   for (long long task = (long long)blockIdx.x * NW_WARPS + w; task < (long long)a.B * IMG_CAP; task += nwarps) {
     const int b = (int)(task / IMG_CAP), u = (int)(task % IMG_CAP);
     if (!a.s.valid[b] || u >= a.s.nuniq[b]) continue;
     Hit *h = a.s.hits + (size_t)b * IMG_CAP + a.s.uniq[(size_t)b * IMG_CAP + u];
-    const double *q = a.params + (size_t)(a.p0 + b) * 14;
-    if (lane < 2) load_var_rec64(q, a.type0, a.type1, lane, s_var[w]);
+    if (lane < 2 * REC64) s_var[w][lane] = a.s.var[b].r64[lane / REC64][lane % REC64];
+    for (int i = lane; i < 2 * RECDF; i += 32) s_vdf[w][i] = a.s.var[b].rdf[i / RECDF][i % RECDF];
     __syncwarp();
     const int src = h->src;
     const double r = n.ratio[src];
@@ -520,17 +648,53 @@ __global__ void __launch_bounds__(NW_THREADS) k_img_polish(const SetArgs a, cons
     const double det = a11 * a22 - a12 * a12;
     double tx = h->tx, ty = h->ty, step = 1e30;
     for (int it = 0; it < POLISH_MAXIT && step >= POLISH_TOL; ++it) {
+      // alpha(tx, ty): dPIE terms inside the polynomial range in
+      // double-float; the rest (cores, SIS, point masses) queued and
+      // evaluated 32 at a time in FP64 so the warp stays converged.
+      const df X = df_from_double(tx), Y = df_from_double(ty);
+      df fx = {0.f, 0.f}, fy = {0.f, 0.f};
       double sx = 0.0, sy = 0.0, e2, e3, e4, ex, ey;
-      for (int j = lane; j < n.n_stat + 2; j += 32) {
-        const double *rec = j < n.n_stat ? n.all64 + (size_t)j * REC64 : s_var[w] + (j - n.n_stat) * REC64;
+      int nq = 0;
+      for (int base = 0; base < ntot; base += 32) {
+        const int j = base + lane;
+        bool need = false;
+        if (j < ntot) {
+          const float *rec = j < n.n_stat ? n.recdf + (size_t)j * RECDF : s_vdf[w] + (j - n.n_stat) * RECDF;
+          df gx, gy;
+          if (rec[2 * F_U2] >= 0.f && dpie_alpha_df(rec, X, Y, gx, gy)) {
+            fx = df_add(fx, gx);
+            fy = df_add(fy, gy);
+          } else {
+            need = true;
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) s_q[w][nq + __popc(m & ((1u << lane) - 1u))] = j;
+        nq += __popc(m);
+        if (nq >= 32) {
+          __syncwarp();
+          const int jj = s_q[w][nq - 32 + lane];
+          const double *rec = jj < n.n_stat ? n.all64 + (size_t)jj * REC64 : s_var[w] + (jj - n.n_stat) * REC64;
+          eval64<false>(rec, tx, ty, ex, ey, e2, e3, e4);
+          sx += ex;
+          sy += ey;
+          nq -= 32;
+          __syncwarp();
+        }
+      }
+      __syncwarp();
+      if (lane < nq) {
+        const int jj = s_q[w][lane];
+        const double *rec = jj < n.n_stat ? n.all64 + (size_t)jj * REC64 : s_var[w] + (jj - n.n_stat) * REC64;
         eval64<false>(rec, tx, ty, ex, ey, e2, e3, e4);
         sx += ex;
         sy += ey;
       }
-      sx = warp_sum(sx);
-      sy = warp_sum(sy);
-      const double fx = bx - (tx - r * sx), fy = by - (ty - r * sy);
-      const double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+      __syncwarp();
+      sx = warp_sum(sx + df_to_double(fx));
+      sy = warp_sum(sy + df_to_double(fy));
+      const double fxr = bx - (tx - r * sx), fyr = by - (ty - r * sy);
+      const double dx = (a22 * fxr - a12 * fyr) / det, dy = (a11 * fyr - a12 * fxr) / det;
       tx += dx;
       ty += dy;
       step = sqrt(dx * dx + dy * dy);
@@ -645,6 +809,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   n.heavy = sm->heavy;
   n.n_heavy = sm->n_heavy;
   n.all64 = sm->all64;
+  n.recdf = sm->recdf;
   n.n_stat = sm->n;
   n.ratio = c->ratio;
   n.xmin = gc->xmin;
@@ -684,7 +849,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
     k_img_sources<<<a.B, SRC_THREADS, src_smem, st>>>(a, c->stat, c->x, c->y, c->ratio, c->src_of, c->img_off);
     dim3 sg((gc->nx - 1 + CT_X - 1) / CT_X, (gc->ny - 1 + CT_Y - 1) / CT_Y, a.B);
     k_img_search<<<sg, 256, 0, st>>>(a, g);
-    k_img_newton<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
+    k_img_newton<<<dim3(IMG_CAP / RF_THREADS, a.B), RF_THREADS, 0, st>>>(a, n);
     k_img_dedup<<<a.B, DD_THREADS, 0, st>>>(a);
     k_img_polish<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
     k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err,

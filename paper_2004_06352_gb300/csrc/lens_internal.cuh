@@ -153,6 +153,49 @@ __host__ __device__ inline bool halo_params_ok(int type, double x0, double y0, d
 }
 
 // ---------------------------------------------------------------- objects
+// Double-float record of one potential (32 floats = 16 pairs).
+enum RecDF : int {
+  F_X0 = 0, F_Y0, F_C, F_S, F_Q2, F_U2, F_KC, F_KT, F_SC, F_ST, F_Q2SC, F_Q2ST, F_Q2SS, F_Q2DS, F_SS, F_BQ
+};
+constexpr int RECDF = 32;
+// SIS and point-mass records carry F_U2 = -1 (never negative for a dPIE) and
+// are left to the FP64 path.
+
+// Host + device: double-float record from user parameters.
+__host__ __device__ inline void make_recdf(int type, double x0, double y0, double theta, double eps, double rcore,
+                                           double rcut, double b0, float *r) {
+  double v[16];
+  for (int k = 0; k < 16; ++k) v[k] = 0.0;
+  v[F_X0] = x0;
+  v[F_Y0] = y0;
+  if (type == LENS_SIS || type == LENS_POINT) {
+    v[F_C] = 1.0;
+    v[F_U2] = -1.0;
+  } else {
+    const double q = (1.0 - eps) / (1.0 + eps), u = 2.0 * sqrt(eps) / (1.0 + eps);
+    const double q2 = q * q, sc = rcore * (1.0 + eps), st = rcut * (1.0 + eps);
+    v[F_C] = cos(theta);
+    v[F_S] = sin(theta);
+    v[F_Q2] = q2;
+    v[F_U2] = u * u;
+    v[F_KC] = q2 * sc * sc;
+    v[F_KT] = q2 * st * st;
+    v[F_SC] = sc;
+    v[F_ST] = st;
+    v[F_Q2SC] = q2 * sc;
+    v[F_Q2ST] = q2 * st;
+    v[F_Q2SS] = q2 * (st + sc);
+    v[F_Q2DS] = q2 * (st - sc);
+    v[F_SS] = st + sc;
+    v[F_BQ] = b0 * (1.0 + eps) * q;
+  }
+  for (int k = 0; k < 16; ++k) {
+    const float h = (float)v[k];
+    r[2 * k] = h;
+    r[2 * k + 1] = (float)(v[k] - (double)h);
+  }
+}
+
 struct Model {
   int32_t n = 0, n_light = 0, n_heavy = 0;
   float *rec32 = nullptr;
@@ -160,6 +203,7 @@ struct Model {
   float *cen32 = nullptr;   // [n_light][4]: x0, y0 as hi/lo float pairs (hi x, hi y, lo x, lo y)
   double *heavy = nullptr;
   double *all64 = nullptr;
+  float *recdf = nullptr;   // [n][RECDF] double-float records in upload order (image polish)
   std::vector<lens_halo> host;
   size_t bytes = 0;
 };
