@@ -1,6 +1,7 @@
 """Coefficients of the polynomials for atan(w)/w and atanh(w)/w in t = w^2 on
 [0, T] used by lens_device.cuh: FP32 (atan_over_w / atanh_over_w, degree 5)
-and FP64 (atan_over_w64 / atanh_over_w64, degree 11).
+and FP64 (atan_over_w64 / atanh_over_w64, degree 11; also split into float
+hi/lo pairs for the double-float evaluator).
 
 Both interpolate the exact functions at the DEG+1 Chebyshev nodes of [0, T]:
 the FP32 set with numpy (Chebyshev fit converted to monomials), the FP64 set
@@ -72,3 +73,7 @@ if __name__ == "__main__":
         c, worst = fit64(name)
         print(f"{name} (FP64, degree 11): max rel interpolation error {worst:.2e}")
         print("  " + ", ".join(f"{v:.17e}" for v in c))
+        # the double-float table: each coefficient split into float hi + float lo
+        hi = np.array(c).astype(np.float32)
+        lo = (np.array(c) - hi.astype(np.float64)).astype(np.float32)
+        print("  pairs: " + ", ".join(f"{{{h:.9e}f, {l:.9e}f}}" for h, l in zip(hi, lo)))

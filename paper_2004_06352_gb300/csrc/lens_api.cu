@@ -95,7 +95,7 @@ void free_model(lens_ctx *ctx, Model *m) {
   dev_free(ctx, m->cen32, (size_t)m->n_light * 4 * sizeof(float));
   dev_free(ctx, m->heavy, (size_t)m->n_heavy * REC64 * sizeof(double));
   dev_free(ctx, m->all64, (size_t)m->n * REC64 * sizeof(double));
-  dev_free(ctx, m->recdf, (size_t)m->n * RECDF * sizeof(float));
+  dev_free(ctx, m->recdf, (size_t)m->n * RECDF * sizeof(float2));
   delete m;
 }
 
@@ -113,7 +113,7 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->n_heavy = (int32_t)heavy.size();
   std::vector<float> r32((size_t)m->n_light * REC32), c32((size_t)m->n_light * 4);
   std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
-  std::vector<float> adf((size_t)n * RECDF);
+  std::vector<float2> adf((size_t)n * RECDF);
   for (int32_t k = 0; k < m->n_light; ++k) {
     const lens_halo &a = h[light[k]];
     make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, &r32[(size_t)k * REC32]);
@@ -135,11 +135,11 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   for (int32_t k = 0; k < n; ++k) {
     const lens_halo &a = h[k];
     make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
-    make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &adf[(size_t)k * RECDF]);
+    make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &adf[k], n);
   }
   int rc = LENS_OK;
   size_t b32 = r32.size() * sizeof(float), bp = p64.size() * sizeof(double), bc = c32.size() * sizeof(float),
-         bh = hv.size() * sizeof(double), ba = a64.size() * sizeof(double), bd = adf.size() * sizeof(float);
+         bh = hv.size() * sizeof(double), ba = a64.size() * sizeof(double), bd = adf.size() * sizeof(float2);
   if ((rc = dev_alloc(ctx, (void **)&m->rec32, b32)) || (rc = dev_alloc(ctx, (void **)&m->pos64, bp)) ||
       (rc = dev_alloc(ctx, (void **)&m->cen32, bc)) || (rc = dev_alloc(ctx, (void **)&m->heavy, bh)) ||
       (rc = dev_alloc(ctx, (void **)&m->all64, ba)) || (rc = dev_alloc(ctx, (void **)&m->recdf, bd))) {
@@ -174,6 +174,7 @@ static void free_cset(lens_ctx *ctx, CSet *c) {
   dev_free(ctx, c->grp_off, (c->ng + 1) * sizeof(int32_t));
   dev_free(ctx, c->grp_src, c->nsrc * sizeof(int32_t));
   dev_free(ctx, c->grp_ratio, c->ng * sizeof(double));
+  dev_free(ctx, c->grp_ratio32, c->ng * sizeof(float));
   for (auto &g : c->grids) dev_free(ctx, g.alpha32, g.bytes);
   if (c->stat_model) free_model(ctx, c->stat_model);
   delete c;
@@ -387,6 +388,7 @@ int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *
   if ((rc = dev_alloc(ctx, (void **)&s->grp_off, (s->ng + 1) * sizeof(int32_t))) ||
       (rc = dev_alloc(ctx, (void **)&s->grp_src, c->nsrc * sizeof(int32_t))) ||
       (rc = dev_alloc(ctx, (void **)&s->grp_ratio, s->ng * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->grp_ratio32, s->ng * sizeof(float))) ||
       (rc = build_model(ctx, stat_h.data(), (int32_t)stat_h.size(), &s->stat_model))) {
     free_cset(ctx, s);
     return rc;
@@ -394,6 +396,9 @@ int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *
   e = cudaMemcpy(s->grp_off, goff.data(), goff.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->grp_src, gsrc.data(), gsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->grp_ratio, ratios.data(), ratios.size() * sizeof(double), cudaMemcpyHostToDevice);
+  std::vector<float> ratios32(ratios.begin(), ratios.end());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(s->grp_ratio32, ratios32.data(), ratios32.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_cset(ctx, s);
     return fail(LENS_ECUDA, "constraint upload: %s", cudaGetErrorString(e));

@@ -425,29 +425,37 @@ __device__ __forceinline__ df df_poly(df t, const float (*c)[2]) {
 }
 
 // Deflection of one dPIE in double-float at (X, Y) given as pairs; false when
-// |w| is too large for the polynomial (the caller then uses FP64).
-__device__ __forceinline__ bool dpie_alpha_df(const float *__restrict__ r, df X, df Y, df &ax, df &ay) {
-  const df c = {r[2 * F_C], r[2 * F_C + 1]}, s = {r[2 * F_S], r[2 * F_S + 1]};
-  const df dX = df_sub(X, df{r[2 * F_X0], r[2 * F_X0 + 1]}), dY = df_sub(Y, df{r[2 * F_Y0], r[2 * F_Y0 + 1]});
+// |w| is too large for the polynomial (the caller then uses FP64).  Pair k of
+// the record is r[k * stride] (stride 1: one record; stride n: field-major
+// table of n records).
+__device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax,
+                                              df &ay) {
+  auto ld = [&](int k) {
+    const float2 v = r[k * stride];
+    return df{v.x, v.y};
+  };
+  const df c = ld(F_C), s = ld(F_S);
+  const df dX = df_sub(X, ld(F_X0)), dY = df_sub(Y, ld(F_Y0));
   const df x = df_add(df_mul(c, dX), df_mul(s, dY)), y = df_sub(df_mul(c, dY), df_mul(s, dX));
-  const df q2 = {r[2 * F_Q2], r[2 * F_Q2 + 1]}, u2 = {r[2 * F_U2], r[2 * F_U2 + 1]};
+  const df q2 = ld(F_Q2), u2 = ld(F_U2);
   const df x2 = df_mul(x, x), y2 = df_mul(y, y);
   const df R = df_add(df_mul(q2, x2), y2);
-  const df psc = df_sqrt(df_add(R, df{r[2 * F_KC], r[2 * F_KC + 1]}));
-  const df pst = df_sqrt(df_add(R, df{r[2 * F_KT], r[2 * F_KT + 1]}));
+  const df psc = df_sqrt(df_add(R, ld(F_KC)));
+  const df pst = df_sqrt(df_add(R, ld(F_KT)));
   const df Sp = df_add(psc, pst);
-  const df Ec = df_add(psc, df{r[2 * F_SC], r[2 * F_SC + 1]}), Et = df_add(pst, df{r[2 * F_ST], r[2 * F_ST + 1]});
-  const df dS = df_sub(df{r[2 * F_ST], r[2 * F_ST + 1]}, df{r[2 * F_SC], r[2 * F_SC + 1]});
-  const df numx = df_mul(df_mul(x, dS), df_add(Sp, df{r[2 * F_Q2SS], r[2 * F_Q2SS + 1]}));
+  const df sc = ld(F_SC), st = ld(F_ST);
+  const df Ec = df_add(psc, sc), Et = df_add(pst, st);
+  const df dS = df_sub(st, sc);
+  const df numx = df_mul(df_mul(x, dS), df_add(Sp, ld(F_Q2SS)));
   const df denx = df_mul(Sp, df_add(df_mul(Ec, Et), df_mul(u2, x2)));
   const df Zx = df_div(numx, denx);
-  const df Fc = df_add(psc, df{r[2 * F_Q2SC], r[2 * F_Q2SC + 1]}), Ft = df_add(pst, df{r[2 * F_Q2ST], r[2 * F_Q2ST + 1]});
-  const df numy = df_mul(df_mul(y, df{r[2 * F_Q2DS], r[2 * F_Q2DS + 1]}), df_add(Sp, df{r[2 * F_SS], r[2 * F_SS + 1]}));
+  const df Fc = df_add(psc, ld(F_Q2SC)), Ft = df_add(pst, ld(F_Q2ST));
+  const df numy = df_mul(df_mul(y, ld(F_Q2DS)), df_add(Sp, ld(F_SS)));
   const df deny = df_mul(Sp, df_sub(df_mul(Fc, Ft), df_mul(u2, y2)));
   const df Zy = df_div(numy, deny);
   const df tx = df_mul(u2, df_mul(Zx, Zx)), ty = df_mul(u2, df_mul(Zy, Zy));
   if (!(tx.hi < (float)T_SERIES64 && ty.hi < (float)T_SERIES64)) return false;  // also catches NaN
-  const df bq = {r[2 * F_BQ], r[2 * F_BQ + 1]};
+  const df bq = ld(F_BQ);
   const df axp = df_mul(df_mul(bq, Zx), df_poly(tx, C_ATAN_DF)), ayp = df_mul(df_mul(bq, Zy), df_poly(ty, C_ATANH_DF));
   ax = df_sub(df_mul(c, axp), df_mul(s, ayp));
   ay = df_add(df_mul(s, axp), df_mul(c, ayp));

@@ -49,7 +49,11 @@ constexpr float BARY_TOL = 1e-3f;
 constexpr int SUBDIV_LEVELS = 6;     // subdivisions of a hit triangle before Newton
 constexpr double SUBDIV_TOL = 1e-3;  // refinement stops when the source is this far outside every sub-triangle
 constexpr double LOCAL_CELLS = 2.0;  // a root must lie this many cell sizes from its triangle
-constexpr int CT_X = 32, CT_Y = 8, NX_T = CT_X + 1, NY_T = CT_Y + 1;
+// search tile: CT_X x CT_Y cells per CTA of SEARCH_THREADS threads, each
+// thread two cells of one column; ratio groups tested SEARCH_GCH at a time
+constexpr int CT_X = 32, CT_Y = 16, NX_T = CT_X + 1, NY_T = CT_Y + 1;
+constexpr int SEARCH_THREADS = 256, SEARCH_WARPS = SEARCH_THREADS / 32, SEARCH_GCH = SEARCH_WARPS;
+static_assert(CT_X * CT_Y == 2 * SEARCH_THREADS, "two cells per thread");
 // candidate status; the failures say which stage rejected it
 constexpr int ST_PENDING = 0, ST_NEWTON = 1, ST_FINAL = 2, ST_FAILED = -1, ST_FAR = -2, ST_NO_POLISH = -3;
 
@@ -68,12 +72,12 @@ struct Hit {
 struct __align__(16) VarRecs {
   float r32[2][REC32];
   float cen[2][4];
-  float rdf[2][RECDF];
+  float2 rdf[2][RECDF];
   double r64[2][REC64];
 };
 
 struct Layout {
-  size_t cnt, valid, nuniq, bary, hits, uniq, var, total;
+  size_t cnt, valid, nuniq, bary, src32, hits, uniq, var, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -89,6 +93,8 @@ __host__ __device__ inline Layout layout(int B, int nsrc) {
   o = align_up(o + (size_t)B * sizeof(int));
   L.bary = o;
   o = align_up(o + (size_t)B * nsrc * 2 * sizeof(double));
+  L.src32 = o;
+  o = align_up(o + (size_t)B * nsrc * sizeof(float2));
   L.hits = o;
   o = align_up(o + (size_t)B * IMG_CAP * sizeof(Hit));
   L.uniq = o;
@@ -102,6 +108,7 @@ __host__ __device__ inline Layout layout(int B, int nsrc) {
 struct Bufs {
   int *cnt, *valid, *nuniq, *uniq;
   double *bary;
+  float2 *src32;  // barycentres rounded to FP32 (search)
   Hit *hits;
   VarRecs *var;
 };
@@ -114,6 +121,7 @@ __host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc) {
   r.valid = (int *)(b + L.valid);
   r.nuniq = (int *)(b + L.nuniq);
   r.bary = (double *)(b + L.bary);
+  r.src32 = (float2 *)(b + L.src32);
   r.hits = (Hit *)(b + L.hits);
   r.uniq = (int *)(b + L.uniq);
   r.var = (VarRecs *)(b + L.var);
@@ -168,15 +176,18 @@ __global__ void __launch_bounds__(SRC_THREADS) k_img_sources(const SetArgs a, co
   if (!s_ok) return;
   backtrace_set<SRC_THREADS>(stat, x, y, ratio, src_of, img_off, a.nimg, a.nsrc, s_rec, s_beta, nullptr, s_bary);
   for (int i = threadIdx.x; i < 2 * a.nsrc; i += SRC_THREADS) a.s.bary[(size_t)b * a.nsrc * 2 + i] = s_bary[i];
+  for (int i = threadIdx.x; i < a.nsrc; i += SRC_THREADS)
+    a.s.src32[(size_t)b * a.nsrc + i] = make_float2((float)s_bary[2 * i], (float)s_bary[2 * i + 1]);
 }
 
 // ----------------------------------------------------------------- 2. search
 struct SearchArgs {
   const float *ax, *ay;  // static deflection planes [ny][nx]
   double xmin, ymin, dx, dy;
+  float fdx, fdy, tiny;  // FP32 cell sizes; degenerate-triangle threshold on the doubled area
   int nx, ny;
   const int32_t *grp_off, *grp_src;
-  const double *grp_ratio;
+  const float *grp_r32;  // ratio of each group, FP32
   int ng;
 };
 
@@ -209,27 +220,36 @@ __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 
   }
 }
 
-__global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const SearchArgs g) {
+__global__ void __launch_bounds__(SEARCH_THREADS) k_img_search(const SetArgs a, const SearchArgs g) {
   __shared__ __align__(16) float s_rec[2][REC32];
   __shared__ float2 s_off[2];  // tile origin minus each varying potential's centre
+  __shared__ float s_T[2];     // tile origin
   __shared__ float2 s_al[NX_T * NY_T];
   __shared__ float2 s_src[MAX_SRC];
+  __shared__ float s_box[SEARCH_GCH][4][SEARCH_WARPS];
+  __shared__ int s_list[MAX_SRC];  // group q's sources inside the footprint, from s_list[grp_off[q]]
+  __shared__ int s_nlist[SEARCH_GCH];
   const int b = blockIdx.z;
   if (!a.s.valid[b]) return;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * CT_X, j0 = blockIdx.y * CT_Y;
   // positions in FP32 relative to the tile origin (the search only decides
-  // which triangles seed a candidate; the refinement is exact)
-  const double Tx = g.xmin + i0 * g.dx, Ty = g.ymin + j0 * g.dy;
-  const float fdx = (float)g.dx, fdy = (float)g.dy, fTx = (float)Tx, fTy = (float)Ty;
+  // which triangles seed a candidate; the refinement is exact); the few FP64
+  // operations are done once per CTA
   const VarRecs &var = a.s.var[b];
+  if (tid < 2) {
+    const double T = tid == 0 ? g.xmin + i0 * g.dx : g.ymin + j0 * g.dy;
+    s_T[tid] = (float)T;
+    const double Tx = g.xmin + i0 * g.dx, Ty = g.ymin + j0 * g.dy;
+    s_off[tid] = make_float2((float)(Tx - ((double)var.cen[tid][0] + (double)var.cen[tid][2])),
+                             (float)(Ty - ((double)var.cen[tid][1] + (double)var.cen[tid][3])));
+  }
   if (tid < 2 * REC32) s_rec[tid / REC32][tid % REC32] = var.r32[tid / REC32][tid % REC32];
-  if (tid < 2) s_off[tid] = make_float2((float)(Tx - ((double)var.cen[tid][0] + (double)var.cen[tid][2])),
-                                        (float)(Ty - ((double)var.cen[tid][1] + (double)var.cen[tid][3])));
-  const double *bary = a.s.bary + (size_t)b * a.nsrc * 2;
-  for (int i = tid; i < a.nsrc; i += 256) s_src[i] = make_float2((float)bary[2 * i], (float)bary[2 * i + 1]);
+  const float2 *src32 = a.s.src32 + (size_t)b * a.nsrc;
+  for (int i = tid; i < a.nsrc; i += SEARCH_THREADS) s_src[i] = src32[i];
   __syncthreads();
-  for (int n = tid; n < NX_T * NY_T; n += 256) {
+  const float fdx = g.fdx, fdy = g.fdy, fTx = s_T[0], fTy = s_T[1];
+  for (int n = tid; n < NX_T * NY_T; n += SEARCH_THREADS) {
     const int li = n % NX_T, lj = n / NX_T;
     const int ii = min(i0 + li, g.nx - 1), jj = min(j0 + lj, g.ny - 1);
     const size_t o = (size_t)jj * g.nx + ii;
@@ -247,62 +267,53 @@ __global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const Searc
     s_al[n] = make_float2(tx, ty);
   }
   __syncthreads();
-  const int ci = tid % CT_X, cj = tid / CT_X;
-  const int gi = i0 + ci, gj = j0 + cj;
-  const bool live = gi < g.nx - 1 && gj < g.ny - 1;
-  const int lane = tid & 31, warp = tid >> 5;
-  const float X0 = fmaf((float)ci, fdx, fTx), X1 = fmaf((float)(ci + 1), fdx, fTx);
-  const float Y0 = fmaf((float)cj, fdy, fTy), Y1 = fmaf((float)(cj + 1), fdy, fTy);
-  const int n00 = cj * NX_T + ci;
-  const float2 a00 = s_al[n00], a10 = s_al[n00 + 1], a01 = s_al[n00 + NX_T], a11 = s_al[n00 + NX_T + 1];
-  const float tiny = (float)(1e-10 * g.dx * g.dy);
+  // this thread's cells: column ci, rows cj and cj + CT_Y / 2
+  const int ci = tid % CT_X, cj0 = tid / CT_X;
+  const float tiny = g.tiny;
   int *cnt = a.s.cnt + b;
   Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
-  const float2 t00 = make_float2(X0, Y0), t10 = make_float2(X1, Y0), t11 = make_float2(X1, Y1),
-               t01 = make_float2(X0, Y1);
-  const int cell = 2 * (gj * (g.nx - 1) + gi);
-  __shared__ float s_box[4][8];
-  __shared__ int s_list[MAX_SRC];
-  __shared__ int s_nlist;
-  for (int q = 0; q < g.ng; ++q) {
-    const float r = (float)g.grp_ratio[q];
-    // the tile's footprint in this ratio's source plane (bounding box of its nodes)
-    float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY;
-    for (int n = tid; n < NX_T * NY_T; n += 256) {
-      const int ii = i0 + n % NX_T, jj = j0 + n / NX_T;
-      if (ii >= g.nx || jj >= g.ny) continue;
-      const float bx = fmaf((float)(n % NX_T), fdx, fTx) - r * s_al[n].x;
-      const float by = fmaf((float)(n / NX_T), fdy, fTy) - r * s_al[n].y;
-      lox = fminf(lox, bx);
-      hix = fmaxf(hix, bx);
-      loy = fminf(loy, by);
-      hiy = fmaxf(hiy, by);
-    }
+  for (int q0 = 0; q0 < g.ng; q0 += SEARCH_GCH) {
+    const int nq = min(SEARCH_GCH, g.ng - q0);
+    // the tile's footprint in each ratio's source plane (bounding box of its nodes)
+    for (int qq = 0; qq < nq; ++qq) {
+      const float r = g.grp_r32[q0 + qq];
+      float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY;
+      for (int n = tid; n < NX_T * NY_T; n += SEARCH_THREADS) {
+        const int ii = i0 + n % NX_T, jj = j0 + n / NX_T;
+        if (ii >= g.nx || jj >= g.ny) continue;
+        const float bx = fmaf((float)(n % NX_T), fdx, fTx) - r * s_al[n].x;
+        const float by = fmaf((float)(n / NX_T), fdy, fTy) - r * s_al[n].y;
+        lox = fminf(lox, bx);
+        hix = fmaxf(hix, bx);
+        loy = fminf(loy, by);
+        hiy = fmaxf(hiy, by);
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
-      hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
-      loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
-      hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
-    }
-    if (lane == 0) {
-      s_box[0][warp] = lox;
-      s_box[1][warp] = hix;
-      s_box[2][warp] = loy;
-      s_box[3][warp] = hiy;
+      for (int o = 16; o > 0; o >>= 1) {
+        lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+        hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+        loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+        hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+      }
+      if (lane == 0) {
+        s_box[qq][0][warp] = lox;
+        s_box[qq][1][warp] = hix;
+        s_box[qq][2][warp] = loy;
+        s_box[qq][3][warp] = hiy;
+      }
     }
     __syncthreads();
-    if (warp == 0) {
-      // the sources of this ratio inside the footprint (+ the test's tolerance)
+    if (warp < nq) {
+      // warp w: the sources of group q0 + w inside the footprint (+ the test's tolerance)
       float L = INFINITY, H = -INFINITY, Ly = INFINITY, Hy = -INFINITY;
-      for (int w = 0; w < 8; ++w) {
-        L = fminf(L, s_box[0][w]);
-        H = fmaxf(H, s_box[1][w]);
-        Ly = fminf(Ly, s_box[2][w]);
-        Hy = fmaxf(Hy, s_box[3][w]);
+      for (int w = 0; w < SEARCH_WARPS; ++w) {
+        L = fminf(L, s_box[warp][0][w]);
+        H = fmaxf(H, s_box[warp][1][w]);
+        Ly = fminf(Ly, s_box[warp][2][w]);
+        Hy = fmaxf(Hy, s_box[warp][3][w]);
       }
       const float px = BARY_TOL * (H - L) + 1e-5f, py = BARY_TOL * (Hy - Ly) + 1e-5f;
-      const int g0 = g.grp_off[q], g1 = g.grp_off[q + 1];
+      const int g0 = g.grp_off[q0 + warp], g1 = g.grp_off[q0 + warp + 1];
       int base = 0;
       for (int k0 = g0; k0 < g1; k0 += 32) {
         const int k = k0 + lane;
@@ -314,20 +325,38 @@ __global__ void __launch_bounds__(256) k_img_search(const SetArgs a, const Searc
           in = P.x >= L - px && P.x <= H + px && P.y >= Ly - py && P.y <= Hy + py;
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (in) s_list[base + __popc(m & ((1u << lane) - 1u))] = src;
+        if (in) s_list[g0 + base + __popc(m & ((1u << lane) - 1u))] = src;
         base += __popc(m);
       }
-      if (lane == 0) s_nlist = base;
+      if (lane == 0) s_nlist[warp] = base;
     }
     __syncthreads();
-    const int nlist = s_nlist;
-    if (live && nlist > 0) {
-      const float2 b00 = make_float2(X0 - r * a00.x, Y0 - r * a00.y), b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
-                   b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y), b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
-      tri_test(b00, b10, b11, t00, t10, t11, s_src, s_list, nlist, tiny, cnt, hits, cell);
-      tri_test(b00, b11, b01, t00, t11, t01, s_src, s_list, nlist, tiny, cnt, hits, cell + 1);
+    for (int qq = 0; qq < nq; ++qq) {
+      const int nlist = s_nlist[qq];
+      if (nlist == 0) continue;
+      const float r = g.grp_r32[q0 + qq];
+      const int *list = s_list + g.grp_off[q0 + qq];
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int cj = cj0 + half * (CT_Y / 2);
+        const int gi = i0 + ci, gj = j0 + cj;
+        if (gi >= g.nx - 1 || gj >= g.ny - 1) continue;
+        const float X0 = fmaf((float)ci, fdx, fTx), X1 = fmaf((float)(ci + 1), fdx, fTx);
+        const float Y0 = fmaf((float)cj, fdy, fTy), Y1 = fmaf((float)(cj + 1), fdy, fTy);
+        const int n00 = cj * NX_T + ci;
+        const float2 a00 = s_al[n00], a10 = s_al[n00 + 1], a01 = s_al[n00 + NX_T], a11 = s_al[n00 + NX_T + 1];
+        const float2 t00 = make_float2(X0, Y0), t10 = make_float2(X1, Y0), t11 = make_float2(X1, Y1),
+                     t01 = make_float2(X0, Y1);
+        const float2 b00 = make_float2(X0 - r * a00.x, Y0 - r * a00.y),
+                     b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
+                     b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y),
+                     b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
+        const int cell = 2 * (gj * (g.nx - 1) + gi);
+        tri_test(b00, b10, b11, t00, t10, t11, s_src, list, nlist, tiny, cnt, hits, cell);
+        tri_test(b00, b11, b01, t00, t11, t01, s_src, list, nlist, tiny, cnt, hits, cell + 1);
+      }
     }
-    __syncthreads();
+    __syncthreads();  // s_box, s_list and s_nlist are rewritten by the next chunk
   }
 }
 
@@ -338,7 +367,7 @@ struct NewtonArgs {
   const double *heavy;         // static potentials on the FP64 path
   int n_heavy;
   const double *all64;         // every static potential in FP64 (polish)
-  const float *recdf;          // every static potential in double-float (polish)
+  const float2 *recdf;         // every static potential in double-float, field-major [RECDF][n_stat] (polish)
   int n_stat;
   const double *ratio;         // per source
   double xmin, ymin, dx, dy;   // search grid
@@ -364,16 +393,29 @@ __device__ __forceinline__ bool bary_w(const double *a, const double *b, const d
   return true;
 }
 
-// One candidate per thread.  Every evaluation is a sweep of the CTA over all
-// static FP32 potentials, staged chunk by chunk in shared memory (all threads
-// read the same record: broadcast), with the compensated accumulation of the
-// map kernel, plus the two varying potentials (FP32) and static cluster-scale
-// ones (FP64).  Each thread evaluates NP points of its own per sweep.
-constexpr int RF_THREADS = 64, RF_CH = 64;
+// One candidate per group of RF_G threads.  Every evaluation is a sweep of
+// the CTA over all static FP32 potentials, staged chunk by chunk in shared
+// memory, each thread of a group taking every RF_G-th potential of a chunk
+// with the compensated accumulation of the map kernel, plus the two varying
+// potentials (FP32) and static cluster-scale ones (FP64, spread over the
+// group); the group's partial sums are then combined by an xor butterfly,
+// which gives every thread of the group the same bits (each level adds the
+// same two values, and FP addition commutes).  Each thread evaluates NP
+// points of its candidate per sweep.
+#ifndef LENS_RF_THREADS
+#define LENS_RF_THREADS 128
+#endif
+#ifndef LENS_RF_G
+#define LENS_RF_G 8
+#endif
+constexpr int RF_THREADS = LENS_RF_THREADS, RF_CH = 64, RF_G = LENS_RF_G, RF_CAND = RF_THREADS / RF_G;
+constexpr int RF_STRIDE4 = REC32 / 4 + 1;  // float4 slots per staged record: the pad spreads a group's 8 records over all banks
+static_assert(32 % RF_G == 0, "groups never straddle a warp");
 
 template <int NP, bool HESS>
 __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, float4 *s_rec, float4 *s_cen,
                                       const double (&px)[NP], const double (&py)[NP], double (&out)[NP][5]) {
+  const int gl = threadIdx.x % RF_G;
   float hx[NP], lx[NP], hy[NP], ly[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
@@ -396,9 +438,9 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     const int cnt = min(RF_CH, n.n_light + 2 - c0);
     __syncthreads();  // the previous chunk has been used by every thread
     for (int i = threadIdx.x; i < cnt * (REC32 / 4); i += RF_THREADS) {
-      const int hh = c0 + i / (REC32 / 4), q = i % (REC32 / 4);
-      s_rec[i] = hh < n.n_light ? g_rec[(size_t)hh * (REC32 / 4) + q]
-                                : reinterpret_cast<const float4 *>(var.r32[hh - n.n_light])[q];
+      const int hl = i / (REC32 / 4), hh = c0 + hl, q = i % (REC32 / 4);
+      s_rec[hl * RF_STRIDE4 + q] = hh < n.n_light ? g_rec[(size_t)hh * (REC32 / 4) + q]
+                                                  : reinterpret_cast<const float4 *>(var.r32[hh - n.n_light])[q];
     }
     for (int i = threadIdx.x; i < cnt; i += RF_THREADS) {
       const int hh = c0 + i;
@@ -407,8 +449,8 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
                                               var.cen[hh - n.n_light][2], var.cen[hh - n.n_light][3]);
     }
     __syncthreads();
-    for (int h = 0; h < cnt; ++h) {
-      const float4 *r4 = s_rec + h * (REC32 / 4);
+    for (int h = gl; h < cnt; h += RF_G) {
+      const float4 *r4 = s_rec + h * RF_STRIDE4;
       const float4 c = s_cen[h];
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
@@ -430,7 +472,7 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     out[k][2] = HESS ? (double)tot[k].k[0] - (double)cmp[k].k[0] : 0.0;
     out[k][3] = HESS ? (double)tot[k].g1[0] - (double)cmp[k].g1[0] : 0.0;
     out[k][4] = HESS ? (double)tot[k].g2[0] - (double)cmp[k].g2[0] : 0.0;
-    for (int j = 0; j < n.n_heavy; ++j) {
+    for (int j = gl; j < n.n_heavy; j += RF_G) {
       double e0, e1, e2 = 0, e3 = 0, e4 = 0;
       eval64<HESS>(n.heavy + (size_t)j * REC64, px[k], py[k], e0, e1, e2, e3, e4);
       out[k][0] += e0;
@@ -439,24 +481,28 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
       out[k][3] += e3;
       out[k][4] += e4;
     }
+#pragma unroll
+    for (int o = 1; o < RF_G; o <<= 1)
+#pragma unroll
+      for (int q = 0; q < (HESS ? 5 : 2); ++q) out[k][q] += __shfl_xor_sync(0xffffffffu, out[k][q], o);
   }
 }
 
 __global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, const NewtonArgs n) {
-  __shared__ float4 s_rec[RF_CH * (REC32 / 4)];
+  __shared__ float4 s_rec[RF_CH * RF_STRIDE4];
   __shared__ float4 s_cen[RF_CH];
   __shared__ VarRecs s_var;
   const int b = blockIdx.y;
   if (!a.s.valid[b]) return;
   const int ncand = min(a.s.cnt[b], IMG_CAP);
-  if (blockIdx.x * RF_THREADS >= ncand) return;  // both exits are uniform over the CTA
+  if (blockIdx.x * RF_CAND >= ncand) return;  // both exits are uniform over the CTA
   {
     const float *f = reinterpret_cast<const float *>(&a.s.var[b]);
     float *d = reinterpret_cast<float *>(&s_var);
     for (int i = threadIdx.x; i < (int)(sizeof(VarRecs) / sizeof(float)); i += RF_THREADS) d[i] = f[i];
   }
-  const int k = blockIdx.x * RF_THREADS + threadIdx.x;
-  const bool mine = k < ncand;
+  const int k = blockIdx.x * RF_CAND + threadIdx.x / RF_G;  // the group's candidate
+  const bool mine = k < ncand, lead = threadIdx.x % RF_G == 0;
   Hit *h = a.s.hits + (size_t)b * IMG_CAP + (mine ? k : 0);
   const int src = mine ? h->src : 0;
   const double r = n.ratio[src];
@@ -570,7 +616,7 @@ __global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, cons
   }
   // a root far from its triangle belongs to another triangle's search
   if (status == ST_NEWTON && hypot(tx - h->cx, ty - h->cy) > LOCAL_CELLS * fmax(n.dx, n.dy)) status = ST_FAR;
-  if (mine) {
+  if (mine && lead) {
     h->tx = tx;
     h->ty = ty;
     h->h11 = h11;
@@ -627,9 +673,12 @@ __global__ void __launch_bounds__(DD_THREADS) k_img_dedup(const SetArgs a) {
 }
 
 // ----------------------------------------------------------------- 5. polish
-__global__ void __launch_bounds__(NW_THREADS) k_img_polish(const SetArgs a, const NewtonArgs n) {
+#ifndef LENS_POLISH_MINB
+#define LENS_POLISH_MINB 2  // resident CTAs per SM the polish is compiled for (3: same speed, spills)
+#endif
+__global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(const SetArgs a, const NewtonArgs n) {
   __shared__ double s_var[NW_WARPS][2 * REC64];
-  __shared__ float s_vdf[NW_WARPS][2 * RECDF];
+  __shared__ float2 s_vdf[NW_WARPS][2 * RECDF];
   __shared__ int s_q[NW_WARPS][64];  // potentials left to the FP64 evaluator
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nwarps = (long long)gridDim.x * NW_WARPS;
@@ -659,9 +708,11 @@ __global__ void __launch_bounds__(NW_THREADS) k_img_polish(const SetArgs a, cons
         const int j = base + lane;
         bool need = false;
         if (j < ntot) {
-          const float *rec = j < n.n_stat ? n.recdf + (size_t)j * RECDF : s_vdf[w] + (j - n.n_stat) * RECDF;
+          const bool st = j < n.n_stat;
+          const float2 *rec = st ? n.recdf + j : s_vdf[w] + (j - n.n_stat) * RECDF;
+          const int stride = st ? n.n_stat : 1;
           df gx, gy;
-          if (rec[2 * F_U2] >= 0.f && dpie_alpha_df(rec, X, Y, gx, gy)) {
+          if (rec[F_U2 * stride].x >= 0.f && dpie_alpha_df(rec, stride, X, Y, gx, gy)) {
             fx = df_add(fx, gx);
             fy = df_add(fy, gy);
           } else {
@@ -828,14 +879,13 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   g.ny = gc->ny;
   g.grp_off = c->grp_off;
   g.grp_src = c->grp_src;
-  g.grp_ratio = c->grp_ratio;
+  g.grp_r32 = c->grp_ratio32;
   g.ng = c->ng;
+  g.fdx = (float)g.dx;
+  g.fdy = (float)g.dy;
+  g.tiny = (float)(1e-10 * g.dx * g.dy);
   const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_img_sources, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  cudaFuncSetAttribute(k_img_sources, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   for (int32_t p0 = 0; p0 < P; p0 += batch) {
     SetArgs a;
     a.params = d_params;
@@ -848,8 +898,8 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
     a.s = bufs(scratch, batch, c->nsrc);
     k_img_sources<<<a.B, SRC_THREADS, src_smem, st>>>(a, c->stat, c->x, c->y, c->ratio, c->src_of, c->img_off);
     dim3 sg((gc->nx - 1 + CT_X - 1) / CT_X, (gc->ny - 1 + CT_Y - 1) / CT_Y, a.B);
-    k_img_search<<<sg, 256, 0, st>>>(a, g);
-    k_img_newton<<<dim3(IMG_CAP / RF_THREADS, a.B), RF_THREADS, 0, st>>>(a, n);
+    k_img_search<<<sg, SEARCH_THREADS, 0, st>>>(a, g);
+    k_img_newton<<<dim3(IMG_CAP / RF_CAND, a.B), RF_THREADS, 0, st>>>(a, n);
     k_img_dedup<<<a.B, DD_THREADS, 0, st>>>(a);
     k_img_polish<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
     k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err,

@@ -153,19 +153,20 @@ __host__ __device__ inline bool halo_params_ok(int type, double x0, double y0, d
 }
 
 // ---------------------------------------------------------------- objects
-// Double-float record of one potential (32 floats = 16 pairs).
+// Double-float record of one potential: 16 (hi, lo) float pairs.
 enum RecDF : int {
   F_X0 = 0, F_Y0, F_C, F_S, F_Q2, F_U2, F_KC, F_KT, F_SC, F_ST, F_Q2SC, F_Q2ST, F_Q2SS, F_Q2DS, F_SS, F_BQ
 };
-constexpr int RECDF = 32;
+constexpr int RECDF = 16;
 // SIS and point-mass records carry F_U2 = -1 (never negative for a dPIE) and
 // are left to the FP64 path.
 
-// Host + device: double-float record from user parameters.
+// Host + device: double-float record from user parameters; pair k goes to
+// r[k * stride].
 __host__ __device__ inline void make_recdf(int type, double x0, double y0, double theta, double eps, double rcore,
-                                           double rcut, double b0, float *r) {
-  double v[16];
-  for (int k = 0; k < 16; ++k) v[k] = 0.0;
+                                           double rcut, double b0, float2 *r, int stride = 1) {
+  double v[RECDF];
+  for (int k = 0; k < RECDF; ++k) v[k] = 0.0;
   v[F_X0] = x0;
   v[F_Y0] = y0;
   if (type == LENS_SIS || type == LENS_POINT) {
@@ -189,10 +190,9 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
     v[F_SS] = st + sc;
     v[F_BQ] = b0 * (1.0 + eps) * q;
   }
-  for (int k = 0; k < 16; ++k) {
+  for (int k = 0; k < RECDF; ++k) {
     const float h = (float)v[k];
-    r[2 * k] = h;
-    r[2 * k + 1] = (float)(v[k] - (double)h);
+    r[(size_t)k * stride] = make_float2(h, (float)(v[k] - (double)h));
   }
 }
 
@@ -203,7 +203,7 @@ struct Model {
   float *cen32 = nullptr;   // [n_light][4]: x0, y0 as hi/lo float pairs (hi x, hi y, lo x, lo y)
   double *heavy = nullptr;
   double *all64 = nullptr;
-  float *recdf = nullptr;   // [n][RECDF] double-float records in upload order (image polish)
+  float2 *recdf = nullptr;  // [RECDF][n] double-float records, field-major, upload order (image polish)
   std::vector<lens_halo> host;
   size_t bytes = 0;
 };
@@ -232,6 +232,7 @@ struct CSet {
   int32_t *grp_off = nullptr;   // [ng+1] sources of ratio group g: grp_src[grp_off[g] .. grp_off[g+1]-1]
   int32_t *grp_src = nullptr;   // [nsrc]
   double *grp_ratio = nullptr;  // [ng]
+  float *grp_ratio32 = nullptr; // [ng] the same rounded to FP32 (image search)
   std::vector<GridCache> grids;
   size_t bytes = 0;
 };
