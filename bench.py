@@ -33,7 +33,11 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
 # map_hessian_mixed_2048x1000.md); the compensated-fold overhead (~1 op per
 # pair) is included.
 FP32_OPS_PER_PAIR = 78.2
-MUFU_OPS_PER_PAIR = None
+MUFU_OPS_PER_PAIR = 6.03
+# DRAM bytes (read + write) of one launch of that kernel on that workload,
+# from the same ncu capture; the 100.7 MB of output are partly still in L2
+# when the kernel ends
+MAP_TRAFFIC_BYTES = 855296 + 40353792
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 
 
@@ -250,7 +254,7 @@ def main():
         ctx.close()
         return
     f_max = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
-    roof = {"bound": "alu", "unit": "Top/s", "traffic": None}
+    roof = {"bound": "alu", "unit": "Top/s", "traffic": MAP_TRAFFIC_BYTES}
     if FP32_OPS_PER_PAIR:
         ach = FP32_OPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12
         peak = SMS * FP32_LANES * f_max / 1e12
@@ -327,6 +331,14 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P,
                          "ms_default_shape": t_default, "autotuned_shape": cfg, "graph_replay": True,
                          "workload": "source-plane chi2, 4096 parameter sets, 1000 potentials"}
+    # the same without the static cache: every potential at every image for
+    # every set (FP64), the per-model cost when any potential may vary
+    t = timed(lambda: ctx.chi2_source_nocache(cs, params, P, 0, chi2, stream), 1)
+    nimg = int(cons["img_off"][-1])
+    ex["chi2_source_nocache"] = {"ms": t, "models_per_s": P / (t * 1e-3), "P": P,
+                                 "pair_per_s": nimg * (N_HALO - 2) * P / (t * 1e-3),
+                                 "workload": "source-plane chi2 without the static cache, 4096 sets x 372 images "
+                                             "x 1000 potentials, FP64 with Hessian"}
     Pi = 256
     gi = I.grid(1024)
     chi2i = torch.empty(Pi, dtype=torch.float64, device=dev)
@@ -346,7 +358,37 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     except Exception as e:  # the benchmark line still prints without it
         ex["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                               "sample": f"failed: {e}"}
+    try:
+        ex["cpu_oracle_other"] = oracle_other_legs(m, g, cons, params.cpu().numpy())
+    except Exception as e:
+        ex["cpu_oracle_other"] = {"error": str(e)}
     return ex
+
+
+def oracle_other_legs(m, g, cons, params):
+    """The oracle on the host cores for the other workloads (bounded samples):
+    the Hessian map on one core, source-plane chi2 on 64 sets, image-plane
+    chi2 on one set of the 1024^2 grid."""
+    import oracle
+    from paper_2004_06352_gb300 import inputs as I
+    out = {}
+    thr = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        rate, rows, _ = oracle_map_sample(m, g, 3.0)
+    finally:
+        oracle.set_threads(thr)
+    out["hessian_map_1core"] = {"pair_per_s": rate, "cores": 1, "sample": f"{rows} rows x 2048 x 1000"}
+    n = 64
+    t0 = time.perf_counter()
+    oracle.chi2_source_batch(m, cons, (0, 1), params[:n], 0)
+    dt = time.perf_counter() - t0
+    out["chi2_source"] = {"models_per_s": n / dt, "cores": thr, "sample": f"{n} parameter sets"}
+    t0 = time.perf_counter()
+    oracle.chi2_image_batch(m, cons, I.grid(1024), (0, 1), params[:1])
+    dt = time.perf_counter() - t0
+    out["chi2_image"] = {"models_per_s": 1.0 / dt, "cores": thr, "sample": "1 parameter set, 1024^2 grid"}
+    return out
 
 
 def profile_leg(args):
@@ -393,7 +435,7 @@ def serving_leg(ctx, api, torch):
     srv = api.Server(ctx, slots=4, pool_bytes=12 << 30)
     pool = S.PinnedPool()
     for side in S.MAP_SIDES:   # page-lock the result buffers before timing
-        for _ in range(4 if side == 8192 else 6):
+        for _ in range(6 if side == 8192 else 12):
             pool.give(torch.empty((6, side, side), dtype=torch.float32, pin_memory=True))
     warm = S.mixed_requests(8, seed=12, n_models=8, sides=(512, 1024))
     S.run_stream(srv, sess, warm, pool=pool, max_outstanding=8, keep_results=False)
@@ -405,9 +447,11 @@ def serving_leg(ctx, api, torch):
     out["closed_loop"] = S.percentiles(lat)
     for frac in (0.5, 0.8, 0.95):
         arr = S.poisson_arrivals(len(reqs), frac * cap, seed=int(1000 * frac))
+        miss0 = pool.misses
         lat, wall, _, _ = S.run_stream(srv, sess, reqs, arr, pool=pool, keep_results=False)
         out[f"load_{int(100 * frac)}"] = dict(S.percentiles(lat), offered_req_per_s=frac * cap,
-                                               served_req_per_s=len(reqs) / wall, n=len(reqs))
+                                               served_req_per_s=len(reqs) / wall, n=len(reqs),
+                                               pinned_on_demand=pool.misses - miss0)
     srv.close()
     # same small-map requests through the mixed and the plain FP64 forms
     small = S.mixed_requests(24, seed=14, n_models=8, sides=(512, 1024, 2048))

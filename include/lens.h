@@ -174,6 +174,16 @@ int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
 int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                      double *d_chi2, void *stream);
 
+/* lens_chi2_source without the static cache: the FP64 deflection and
+ * Hessian of every static potential at every image are recomputed for every
+ * parameter set (batches of 512 sets in the context's scratch memory), as in
+ * the paper's fit, which evaluates every potential for every model (Sec. 2.2,
+ * Sec. 4.2).  Same arguments, results and errors as lens_chi2_source; the
+ * per-set cost is N potentials x images instead of 2 x images.  Grows the
+ * context's scratch to 512 x images x 40 bytes (LENS_ENOMEM over budget). */
+int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
+                             double *d_chi2, void *stream);
+
 /* Autotuner of lens_chi2_source's launch shape (threads per CTA x CTAs per
  * SM, 8 candidates) for this constraint set: runs each candidate on d_params
  * (DEVICE [P][14]) into d_chi2 (DEVICE [P]) on `stream`, times it (best of

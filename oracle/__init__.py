@@ -70,6 +70,7 @@ def _load():
         hp, cp, gp = C.POINTER(Halo), C.POINTER(Constraints), C.POINTER(Grid)
         sig = {
             "or_num_threads": (C.c_int, []),
+            "or_set_threads": (None, [C.c_int]),
             "or_halo_eval": (None, [hp, C.c_double, C.c_double, dp]),
             "or_halo_potential": (C.c_double, [hp, C.c_double, C.c_double]),
             "or_halo_kappa": (C.c_double, [hp, C.c_double, C.c_double]),
@@ -161,6 +162,11 @@ def _grid(g):
 
 def num_threads():
     return int(_load().or_num_threads())
+
+
+def set_threads(n):
+    """OpenMP threads of later calls (e.g. 1 to time a single core)."""
+    _load().or_set_threads(int(n))
 
 
 # ------------------------------------------------------------------ evaluation

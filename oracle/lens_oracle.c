@@ -87,6 +87,15 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads used by later calls (timing a single core); n < 1 is ignored. */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* atan(u t)/u and atanh(u t)/u; for tiny u the quotient is 0/0 in floating
  * point, so use the Taylor series (|u t| < u < 1e-4: the first dropped term is
  * below 1e-24 relative). */

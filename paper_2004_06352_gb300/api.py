@@ -24,7 +24,8 @@ LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_cset_create", "lens_cset_release",
-           "lens_chi2_source", "lens_chi2_autotune", "lens_chi2_image", "lens_find_images", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
+           "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_autotune", "lens_chi2_image",
+           "lens_find_images", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
            "lens_server_progress", "lens_server_cancel", "lens_server_stats")
 LENS_REQ_MAP, LENS_REQ_CHI2_SOURCE, LENS_REQ_CHI2_IMAGE = 0, 1, 2
@@ -85,6 +86,7 @@ def load_library(path=LIB_PATH):
         "lens_cset_create": (C.c_int, [vp, i64, C.POINTER(lens_constraints), C.POINTER(C.c_int32), C.POINTER(i64)]),
         "lens_cset_release": (C.c_int, [vp, i64]),
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
+        "lens_chi2_source_nocache": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_autotune": (C.c_int, [vp, i64, vp, C.c_int32, vp, vp, C.POINTER(C.c_int32),
                                          C.POINTER(C.c_float)]),
         "lens_chi2_image": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
@@ -211,6 +213,11 @@ class Context:
     def chi2_source(self, cset, params, P, variant, chi2, stream=None):
         _check(_lib.lens_chi2_source(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(chi2),
                                      _stream(stream)), "lens_chi2_source")
+        return chi2
+
+    def chi2_source_nocache(self, cset, params, P, variant, chi2, stream=None):
+        _check(_lib.lens_chi2_source_nocache(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(chi2),
+                                             _stream(stream)), "lens_chi2_source_nocache")
         return chi2
 
     def chi2_autotune(self, cset, params, P, chi2, stream=None):

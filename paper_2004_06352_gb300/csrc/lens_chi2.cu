@@ -10,18 +10,26 @@
 // CTA rebuilds the two varying potentials, back-traces every image
 // (beta = theta - r alpha, Sec. 2.1 Eq. 1), forms each source's barycentre
 // and reduces the chi2 with warp shuffles in a fixed order.
+//
+// No-cache form: the static sum is recomputed for every parameter set (a
+// batch of sets at a time, into scratch memory) before the same source-plane
+// kernel runs; this is the per-set cost when any potential may vary, as in
+// the paper's fit, where every potential is evaluated for every model.
 #include "lens_device.cuh"
 
 namespace lens {
 namespace {
 
 constexpr int CACHE_THREADS = 128;
+constexpr int NOCACHE_BATCH = 512;  // parameter sets per batch of the no-cache form
 
+// grid (nimg, copies): copy c of the sums goes to stat + c * nimg * 5
 __global__ void __launch_bounds__(CACHE_THREADS) k_static_cache(const double *__restrict__ all64, int n, int v0,
                                                                 int v1, const double *__restrict__ x,
                                                                 const double *__restrict__ y, double *stat) {
   __shared__ double s_red[(CACHE_THREADS / 32) * 5];
   const int img = blockIdx.x;
+  stat += (size_t)blockIdx.y * gridDim.x * 5;
   const double X = x[img], Y = y[img];
   double v[5] = {0, 0, 0, 0, 0};
   for (int h = threadIdx.x; h < n; h += CACHE_THREADS) {
@@ -41,6 +49,7 @@ __global__ void __launch_bounds__(CACHE_THREADS) k_static_cache(const double *__
 
 struct Chi2SrcArgs {
   const double *stat, *x, *y, *sigma, *ratio, *params;
+  long long stat_stride;  // doubles between the static sums of consecutive sets (0: one shared cache)
   const int32_t *img_off, *src_of;
   int nsrc, nimg, P, variant;
   int type0, type1;
@@ -67,7 +76,8 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
       __syncthreads();
       continue;
     }
-    backtrace_set<THREADS>(a.stat, a.x, a.y, a.ratio, a.src_of, a.img_off, a.nimg, a.nsrc, s_rec, s_beta,
+    backtrace_set<THREADS>(a.stat + p * a.stat_stride, a.x, a.y, a.ratio, a.src_of, a.img_off, a.nimg, a.nsrc,
+                           s_rec, s_beta,
                            a.variant == LENS_CHI2_SRC_PLAIN ? nullptr : s_m, s_bary);
     double acc[1] = {0.0};
     for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
@@ -106,14 +116,11 @@ int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c) {
 
 template <int T>
 static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, int32_t P, int32_t variant,
-                          double *d_chi2, cudaStream_t st, int blocks_per_sm) {
+                          double *d_chi2, cudaStream_t st, int blocks_per_sm, const double *stat = nullptr,
+                          long long stat_stride = 0) {
   const size_t smem = sizeof(double) * (2 * REC64 + 5 * (size_t)c->nimg + 2 * (size_t)c->nsrc + T / 32);
   if (smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_chi2_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  cudaFuncSetAttribute(k_chi2_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int per_sm = 0, nsm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chi2_source<T>, T, smem);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
@@ -121,7 +128,8 @@ static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, 
   if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
   const int blocks = std::max(1, std::min(P, per_sm * nsm));
   Chi2SrcArgs a;
-  a.stat = c->stat;
+  a.stat = stat ? stat : c->stat;
+  a.stat_stride = stat_stride;
   a.x = c->x;
   a.y = c->y;
   a.sigma = c->sigma;
@@ -160,6 +168,24 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
   (void)m;
   const int idx = (c->tuned_cfg >= 0 && c->tuned_cfg < N_SRC_CFG) ? c->tuned_cfg : 2;
   return launch_src_idx(ctx, c, d_params, P, variant, d_chi2, st, idx);
+}
+
+size_t chi2_nocache_scratch_bytes(const CSet *c) { return (size_t)NOCACHE_BATCH * c->nimg * 5 * sizeof(double); }
+
+int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                               int32_t variant, double *d_chi2, cudaStream_t st) {
+  double *stat = (double *)ctx->scratch;
+  for (int32_t p0 = 0; p0 < P; p0 += NOCACHE_BATCH) {
+    const int B = std::min(NOCACHE_BATCH, P - p0);
+    k_static_cache<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->all64, m->n, c->var[0], c->var[1], c->x, c->y,
+                                                                stat);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LENS_ECUDA, "static sums launch: %s", cudaGetErrorString(e));
+    const int rc = launch_src_cfg<128>(ctx, c, d_params + (size_t)p0 * 14, B, variant, d_chi2 + p0, st, 0, stat,
+                                       (long long)c->nimg * 5);
+    if (rc) return rc;
+  }
+  return LENS_OK;
 }
 
 // Time every launch shape on this constraint set and P (each once to warm

@@ -13,18 +13,20 @@
 //                     (bounding box, then barycentric weights with a small
 //                     tolerance so that a source on a shared edge is never
 //                     lost); every hit is appended to the set's buffer.
-//   3. k_img_newton   one warp per candidate: the hit triangle is subdivided
-//                     up to SUBDIV_LEVELS times (keeping the sub-triangle that
-//                     best contains the source; stopping early when none does),
-//                     then Newton on the lens equation, steps limited to one
-//                     cell, starts there; full model with the lanes splitting
-//                     the potentials (FP32, cluster-scale static ones in FP64);
-//                     a root further than LOCAL_CELLS cells from its triangle
-//                     is dropped.
+//   3. k_img_newton   one group of RF_G threads per candidate: the hit
+//                     triangle is subdivided up to SUBDIV_LEVELS times
+//                     (keeping the sub-triangle that best contains the source;
+//                     stopping early when none does), then Newton on the lens
+//                     equation, steps limited to one cell, starts there; full
+//                     model with the group splitting the potentials (FP32,
+//                     cluster-scale static ones in FP64); a root further than
+//                     LOCAL_CELLS cells from its triangle is dropped.
 //   4. k_img_dedup    per set: candidates of the same source closer than
 //                     1e-3" are one image.
 //   5. k_img_polish   one warp per distinct image: Newton steps whose residual
-//                     uses the full model in FP64, until the step is < 1e-7".
+//                     uses the full model in double-float (FP64 for cores,
+//                     SIS and point masses) until the step is < 1e-6", the
+//                     stopping rule of the definition's FP64 Newton.
 //   6. k_img_chi2     per set: polished images of one source closer than
 //                     1e-3" are merged again (as after the definition's FP64
 //                     Newton); each constraint takes the nearest image of its
@@ -42,8 +44,8 @@ constexpr int IMG_BATCH = 256;      // parameter sets per batch
 constexpr int MAX_SRC = 1024;
 constexpr double DEDUP = 1e-3;      // images closer than this are one image (arcsec)
 constexpr double NEWTON32_TOL = 1e-4;
-constexpr double POLISH_TOL = 1e-7;
-constexpr double ACCEPT_TOL = 1e-6;  // same criterion as the FP64 Newton of the definition
+constexpr double POLISH_TOL = 1e-6;  // same stopping rule as the FP64 Newton of the definition
+constexpr double ACCEPT_TOL = 1e-6;
 constexpr int NEWTON_MAXIT = 40, POLISH_MAXIT = 6;
 constexpr float BARY_TOL = 1e-3f;
 constexpr int SUBDIV_LEVELS = 6;     // subdivisions of a hit triangle before Newton
@@ -382,15 +384,32 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 constexpr int NW_THREADS = 256, NW_WARPS = NW_THREADS / 32;
 
-// Barycentric weights of p in (a, b, c); false when degenerate.
+// Barycentric weights of p in (a, b, c); false when degenerate.  The vertex
+// offsets from p are formed in FP64 and the rest in FP32: the mapped vertices
+// carry the FP32 sweep's error (~1e-7 of alpha), far above FP32 rounding of
+// offsets of a (sub-)cell, and FP64 division is slow on this GPU.
 __device__ __forceinline__ bool bary_w(const double *a, const double *b, const double *c, const double *p,
                                        double tiny, double w[3]) {
-  const double area2 = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]);
-  if (!(fabs(area2) > tiny)) return false;
-  w[0] = ((b[0] - p[0]) * (c[1] - p[1]) - (b[1] - p[1]) * (c[0] - p[0])) / area2;
-  w[1] = ((c[0] - p[0]) * (a[1] - p[1]) - (c[1] - p[1]) * (a[0] - p[0])) / area2;
-  w[2] = 1.0 - w[0] - w[1];
+  const float ax = (float)(a[0] - p[0]), ay = (float)(a[1] - p[1]);
+  const float bx = (float)(b[0] - p[0]), by = (float)(b[1] - p[1]);
+  const float cx = (float)(c[0] - p[0]), cy = (float)(c[1] - p[1]);
+  const float area2 = (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+  if (!(fabs((double)area2) > tiny)) return false;
+  const float inv = 1.f / area2;
+  const float w0 = (bx * cy - by * cx) * inv, w1 = (cx * ay - cy * ax) * inv;
+  w[0] = w0;
+  w[1] = w1;
+  w[2] = 1.0 - (double)w0 - (double)w1;
   return true;
+}
+
+// Vertex k of sub-triangle sb of a triangle (0, 1, 2) whose edge midpoints
+// are 3 = (0,1), 4 = (1,2), 5 = (2,0): three corner triangles, then the middle.
+__host__ __device__ constexpr int sub_vertex(int sb, int k) {
+  return sb == 0   ? (k == 0 ? 0 : k == 1 ? 3 : 5)
+         : sb == 1 ? (k == 0 ? 3 : k == 1 ? 1 : 4)
+         : sb == 2 ? (k == 0 ? 5 : k == 1 ? 4 : 2)
+                   : (k == 0 ? 3 : k == 1 ? 4 : 5);
 }
 
 // One candidate per group of RF_G threads.  Every evaluation is a sweep of
@@ -548,12 +567,14 @@ __global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, cons
       b6[3 + q][1] = t6[3 + q][1] - r * o[q][1];
     }
     const double tiny_sub = 0.25 * tiny;
-    const int sub[4][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}, {3, 4, 5}};
     int best = -1;
     double best_score = -INFINITY;
+    // (every loop over sub-triangles is unrolled so the vertex tables index
+    // registers with constants)
+#pragma unroll
     for (int sb = 0; sb < 4; ++sb) {
       double ww[3];
-      if (!bary_w(b6[sub[sb][0]], b6[sub[sb][1]], b6[sub[sb][2]], P, tiny_sub, ww)) continue;
+      if (!bary_w(b6[sub_vertex(sb, 0)], b6[sub_vertex(sb, 1)], b6[sub_vertex(sb, 2)], P, tiny_sub, ww)) continue;
       const double score = fmin(ww[0], fmin(ww[1], ww[2]));
       if (score > best_score) {
         best_score = score;
@@ -566,12 +587,16 @@ __global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, cons
       continue;
     }
     tiny = tiny_sub;
-    for (int q = 0; q < 3; ++q) {
-      th[q][0] = t6[sub[best][q]][0];
-      th[q][1] = t6[sub[best][q]][1];
-      be[q][0] = b6[sub[best][q]][0];
-      be[q][1] = b6[sub[best][q]][1];
-    }
+#pragma unroll
+    for (int sb = 0; sb < 4; ++sb)
+      if (sb == best)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          th[q][0] = t6[sub_vertex(sb, q)][0];
+          th[q][1] = t6[sub_vertex(sb, q)][1];
+          be[q][0] = b6[sub_vertex(sb, q)][0];
+          be[q][1] = b6[sub_vertex(sb, q)][1];
+        }
   }
   if (refining && !bary_w(be[0], be[1], be[2], P, tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
   // FP32 Newton with steps limited to one cell

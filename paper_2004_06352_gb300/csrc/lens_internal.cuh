@@ -279,6 +279,9 @@ int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dl
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);
+size_t chi2_nocache_scratch_bytes(const CSet *c);
+int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                               int32_t variant, double *d_chi2, cudaStream_t st);
 int autotune_chi2_source(lens_ctx *ctx, CSet *c, const double *d_params, int32_t P, double *d_chi2, cudaStream_t st,
                          int32_t *chosen, float *best_ms);
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,

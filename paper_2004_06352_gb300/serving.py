@@ -62,10 +62,13 @@ def percentiles(lat_ms):
 
 
 class PinnedPool:
-    """Reusable page-locked host buffers keyed by (shape, dtype)."""
+    """Reusable page-locked host buffers keyed by (shape, dtype).  `misses`
+    counts buffers that had to be page-locked on demand (slow: the call
+    blocks the submitting thread)."""
 
     def __init__(self):
         self.free = {}
+        self.misses = 0
 
     def take(self, shape, dtype):
         import torch
@@ -73,6 +76,7 @@ class PinnedPool:
         lst = self.free.get(key)
         if lst:
             return lst.pop()
+        self.misses += 1
         return torch.empty(shape, dtype=dtype, pin_memory=True)
 
     def give(self, t):

@@ -103,3 +103,33 @@ def test_chi2_source_autotune_and_graph_replay(lens):
         got2 = gout.cpu().numpy()
     ref2 = oracle.chi2_source_batch(m, cons, var, p2[:48], 0)
     assert np.all(np.abs(got2[:48] - ref2) <= T.CHI2_REL * np.abs(ref2))
+
+
+def test_chi2_source_nocache_matches_cache_and_oracle(lens):
+    """Recomputing every static potential for every set (no static cache)
+    gives the cached result up to summation order, and the oracle's; P spans
+    two no-cache batches plus a ragged tail."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    P = 1100
+    params = I.perturbed_params(m, var, P, seed=61)
+    params[7, 2] = 1.3  # eps >= 1: NaN in both forms
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        for variant in (0, 2):
+            a = torch.empty(P, dtype=torch.float64, device=DEV)
+            b = torch.empty(P, dtype=torch.float64, device=DEV)
+            ctx.chi2_source(cs, p, P, variant, a)
+            ctx.chi2_source_nocache(cs, p, P, variant, b)
+            ctx.wait()
+            a, b = a.cpu().numpy(), b.cpu().numpy()
+            assert np.isnan(a[7]) and np.isnan(b[7])
+            ok = np.isfinite(a)
+            assert np.all(np.abs(a[ok] - b[ok]) <= 1e-12 * np.abs(a[ok]))
+            sample = [0, 1, 513, 1099]
+            ref = oracle.chi2_source_batch(m, cons, var, params[sample], variant)
+            assert np.all(np.abs(b[sample] - ref) <= T.CHI2_REL * np.abs(ref))
