@@ -1,7 +1,8 @@
 """Coefficients of the polynomials for atan(w)/w and atanh(w)/w in t = w^2 on
 [0, T] used by lens_device.cuh: FP32 (atan_over_w / atanh_over_w, degree 5)
 and FP64 (atan_over_w64 / atanh_over_w64, degree 11; also split into float
-hi/lo pairs for the double-float evaluator).
+hi/lo pairs for the double-float evaluator), and the tables of the FP64
+atan/atanh argument reduction (atan64 / atanh64).
 
 Both interpolate the exact functions at the DEG+1 Chebyshev nodes of [0, T]:
 the FP32 set with numpy (Chebyshev fit converted to monomials), the FP64 set
@@ -60,6 +61,18 @@ def fit64(name, deg=11):
     return [float(c[j]) for j in range(deg + 1)], float(worst)
 
 
+def reduction_tables(step="0.8", kmax=22):
+    """Centres of the FP64 atanh argument reduction: c_k = tanh(step k)
+    rounded to double and the 60-digit atanh of that double; atan(11/16) and
+    pi/2 as hi + lo."""
+    import mpmath as mp
+    mp.mp.dps = 60
+    c = [float(mp.tanh(mp.mpf(step) * k)) for k in range(kmax + 1)]
+    a = [float(mp.atanh(mp.mpf(v))) for v in c]
+    pi2 = mp.pi / 2
+    return c, a, float(mp.atan(mp.mpf(11) / 16)), float(pi2), float(pi2 - mp.mpf(float(pi2)))
+
+
 if __name__ == "__main__":
     tt = np.linspace(0, T, 200001)
     t32 = tt.astype(np.float32).astype(np.float64)
@@ -77,3 +90,7 @@ if __name__ == "__main__":
         hi = np.array(c).astype(np.float32)
         lo = (np.array(c) - hi.astype(np.float64)).astype(np.float32)
         print("  pairs: " + ", ".join(f"{{{h:.9e}f, {l:.9e}f}}" for h, l in zip(hi, lo)))
+    c, a, at, ph, pl = reduction_tables()
+    print("ATANH_C:", ", ".join(repr(v) for v in c))
+    print("ATANH_A:", ", ".join(repr(v) for v in a))
+    print("ATAN_11_16:", repr(at), " PI_2_HI, PI_2_LO:", repr(ph), repr(pl))

@@ -89,6 +89,59 @@ __device__ __forceinline__ double atanh_over_w64(double t) {
   return fma(p, t, 1.0);
 }
 constexpr double T_SERIES64 = 0.16;
+
+// FP64 atan and atanh for every argument, by argument reduction into the
+// interval of the degree-11 interpolants (|v| <= 0.4) with the addition
+// formulas (table-based reduction, as in Muller, "Elementary Functions",
+// ch. 6): atan folds |w| > 1 to pi/2 - atan(1/|w|) and shifts [0.4, 1] about
+// c = 11/16; atanh shifts about the nearest c_k = tanh(0.8 k) (rounded to
+// double; ATANH_A[k] = atanh of that double, 60-digit value), k from a
+// single-precision estimate of atanh.  Reduced arguments stay within
+// |v| < 0.4; the only FP64 divisions are the one of the shift and, for
+// |w| > 1, the reciprocal.  Tables: csrc/fit_series.py.
+constexpr double ATAN_11_16 = 0.6022873461349642;  // atan(11/16)
+constexpr double PI_2_HI = 1.5707963267948966, PI_2_LO = 6.123233995736766e-17;
+constexpr int ATANH_K = 22;
+__device__ __constant__ const double ATANH_C[23] = {
+    0.0, 0.664036770267849, 0.9216685544064713, 0.9836748576936802,
+    0.9966823978396512, 0.999329299739067, 0.9998645517007605, 0.9999726519818308,
+    0.9999944784700996, 0.9999988852198828, 0.9999997749296758, 0.9999999545590812,
+    0.9999999908256365, 0.999999998147728, 0.9999999996260327, 0.9999999999244973,
+    0.9999999999847563, 0.9999999999969224, 0.9999999999993786, 0.9999999999998745,
+    0.9999999999999747, 0.9999999999999949, 0.999999999999999};
+__device__ __constant__ const double ATANH_A[23] = {
+    0.0, 0.8, 1.6000000000000003, 2.400000000000001,
+    3.2000000000000037, 3.999999999999993, 4.800000000000132, 5.60000000000052,
+    6.399999999997866, 7.199999999979319, 7.999999999898783, 8.800000000192549,
+    9.599999997824579, 10.400000010784895, 11.199999965832989, 11.999999839023337,
+    12.800001154374243, 13.60000111127314, 14.399980865672688, 15.199987419265298,
+    16.000301060641295, 16.800653176873976, 17.616361586450413};
+
+__device__ __forceinline__ double atan64(double w) {
+  const double a = fabs(w);
+  const bool inv = a > 1.0;
+  double v = inv ? 1.0 / a : a, base = 0.0;
+  if (v > 0.4) {
+    v = (v - 0.6875) / fma(v, 0.6875, 1.0);
+    base = ATAN_11_16;
+  }
+  double r = fma(v, atan_over_w64(v * v), base);
+  if (inv) r = (PI_2_HI - r) + PI_2_LO;
+  return copysign(r, w);
+}
+
+__device__ __forceinline__ double atanh64(double w) {
+  const double a = fabs(w);
+  if (a <= 0.4) return w * atanh_over_w64(w * w);
+  // hyperbolic angle estimate 0.5 ln((1+a)/(1-a)); 1-a is exact for a >= 0.5
+  const float est = 0.5f * (__logf((float)(1.0 + a)) - __logf((float)(1.0 - a)));
+  const int k = __float2int_rn(est * 1.25f);
+  if (!(a < 1.0) || k > ATANH_K) return atanh(w);  // |w| >= 1 or within 1e-15 of it
+  const int kk = k < 1 ? 1 : k;
+  const double c = ATANH_C[kk];
+  const double v = (a - c) / fma(-a, c, 1.0);
+  return copysign(fma(v, atanh_over_w64(v * v), ATANH_A[kk]), w);
+}
 // The same coefficients as float pairs (hi, lo) for the double-float path.
 __device__ __constant__ const float C_ATAN_DF[12][2] = {
     {1.000000000e+00f, 0.000000000e+00f}, {-3.333333433e-01f, 9.934108647e-09f}, {2.000000030e-01f, -2.980543590e-09f},
@@ -165,8 +218,8 @@ __device__ __forceinline__ void eval64(const double *__restrict__ r, double X, d
       axp = bq * Zx * atan_over_w64(tx);
       ayp = bq * Zy * atanh_over_w64(ty);
     } else {
-      axp = bq / u * atan(wx);
-      ayp = bq / u * atanh(wy);
+      axp = bq / u * atan64(wx);
+      ayp = bq / u * atanh64(wy);
     }
   }
   ax = c * axp - s * ayp;

@@ -222,6 +222,14 @@ __device__ __forceinline__ void tri_test(float2 A, float2 Bv, float2 Cv, float2 
   }
 }
 
+// Order-preserving map of floats to signed ints (and back: it is its own
+// inverse), so that integer warp min/max reductions apply to floats.
+__device__ __forceinline__ int f2ord(float f) {
+  const int i = __float_as_int(f);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i ^ ((i >> 31) & 0x7fffffff)); }
+
 __global__ void __launch_bounds__(SEARCH_THREADS) k_img_search(const SetArgs a, const SearchArgs g) {
   __shared__ __align__(16) float s_rec[2][REC32];
   __shared__ float2 s_off[2];  // tile origin minus each varying potential's centre
@@ -276,32 +284,38 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_img_search(const SetArgs a, 
   Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
   for (int q0 = 0; q0 < g.ng; q0 += SEARCH_GCH) {
     const int nq = min(SEARCH_GCH, g.ng - q0);
-    // the tile's footprint in each ratio's source plane (bounding box of its nodes)
-    for (int qq = 0; qq < nq; ++qq) {
-      const float r = g.grp_r32[q0 + qq];
-      float lox = INFINITY, hix = -INFINITY, loy = INFINITY, hiy = -INFINITY;
-      for (int n = tid; n < NX_T * NY_T; n += SEARCH_THREADS) {
-        const int ii = i0 + n % NX_T, jj = j0 + n / NX_T;
-        if (ii >= g.nx || jj >= g.ny) continue;
-        const float bx = fmaf((float)(n % NX_T), fdx, fTx) - r * s_al[n].x;
-        const float by = fmaf((float)(n / NX_T), fdy, fTy) - r * s_al[n].y;
-        lox = fminf(lox, bx);
-        hix = fmaxf(hix, bx);
-        loy = fminf(loy, by);
-        hiy = fmaxf(hiy, by);
-      }
+    // the tile's footprint in each ratio's source plane (bounding box of its
+    // nodes): one pass over this thread's nodes for all groups of the chunk,
+    // then one integer min/max reduction per warp and bound
+    float lo[SEARCH_GCH][2], hi[SEARCH_GCH][2];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lox = fminf(lox, __shfl_xor_sync(0xffffffffu, lox, o));
-        hix = fmaxf(hix, __shfl_xor_sync(0xffffffffu, hix, o));
-        loy = fminf(loy, __shfl_xor_sync(0xffffffffu, loy, o));
-        hiy = fmaxf(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+    for (int qq = 0; qq < SEARCH_GCH; ++qq) lo[qq][0] = lo[qq][1] = INFINITY, hi[qq][0] = hi[qq][1] = -INFINITY;
+    for (int n = tid; n < NX_T * NY_T; n += SEARCH_THREADS) {
+      const int li = n % NX_T, lj = n / NX_T;
+      if (i0 + li >= g.nx || j0 + lj >= g.ny) continue;
+      const float X = fmaf((float)li, fdx, fTx), Y = fmaf((float)lj, fdy, fTy);
+      const float2 al = s_al[n];
+#pragma unroll
+      for (int qq = 0; qq < SEARCH_GCH; ++qq) {
+        if (qq >= nq) break;
+        const float r = g.grp_r32[q0 + qq];
+        const float bx = X - r * al.x, by = Y - r * al.y;
+        lo[qq][0] = fminf(lo[qq][0], bx);
+        hi[qq][0] = fmaxf(hi[qq][0], bx);
+        lo[qq][1] = fminf(lo[qq][1], by);
+        hi[qq][1] = fmaxf(hi[qq][1], by);
       }
+    }
+#pragma unroll
+    for (int qq = 0; qq < SEARCH_GCH; ++qq) {
+      if (qq >= nq) break;
+      const int lx = __reduce_min_sync(0xffffffffu, f2ord(lo[qq][0])), hx = __reduce_max_sync(0xffffffffu, f2ord(hi[qq][0]));
+      const int ly = __reduce_min_sync(0xffffffffu, f2ord(lo[qq][1])), hy = __reduce_max_sync(0xffffffffu, f2ord(hi[qq][1]));
       if (lane == 0) {
-        s_box[qq][0][warp] = lox;
-        s_box[qq][1][warp] = hix;
-        s_box[qq][2][warp] = loy;
-        s_box[qq][3][warp] = hiy;
+        s_box[qq][0][warp] = ord2f(lx);
+        s_box[qq][1][warp] = ord2f(hx);
+        s_box[qq][2][warp] = ord2f(ly);
+        s_box[qq][3][warp] = ord2f(hy);
       }
     }
     __syncthreads();
@@ -353,6 +367,18 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_img_search(const SetArgs a, 
                      b10 = make_float2(X1 - r * a10.x, Y0 - r * a10.y),
                      b11 = make_float2(X1 - r * a11.x, Y1 - r * a11.y),
                      b01 = make_float2(X0 - r * a01.x, Y1 - r * a01.y);
+        // the cell's padded bounding box contains both triangles' padded boxes
+        const float qlx = fminf(fminf(b00.x, b10.x), fminf(b11.x, b01.x)),
+                    qhx = fmaxf(fmaxf(b00.x, b10.x), fmaxf(b11.x, b01.x));
+        const float qly = fminf(fminf(b00.y, b10.y), fminf(b11.y, b01.y)),
+                    qhy = fmaxf(fmaxf(b00.y, b10.y), fmaxf(b11.y, b01.y));
+        const float qpx = BARY_TOL * (qhx - qlx) + 1e-6f, qpy = BARY_TOL * (qhy - qly) + 1e-6f;
+        bool any = false;
+        for (int k = 0; k < nlist && !any; ++k) {
+          const float2 P = s_src[list[k]];
+          any = P.x >= qlx - qpx && P.x <= qhx + qpx && P.y >= qly - qpy && P.y <= qhy + qpy;
+        }
+        if (!any) continue;
         const int cell = 2 * (gj * (g.nx - 1) + gi);
         tri_test(b00, b10, b11, t00, t10, t11, s_src, list, nlist, tiny, cnt, hits, cell);
         tri_test(b00, b11, b01, t00, t11, t01, s_src, list, nlist, tiny, cnt, hits, cell + 1);
@@ -374,6 +400,7 @@ struct NewtonArgs {
   const double *ratio;         // per source
   double xmin, ymin, dx, dy;   // search grid
   int nx;
+  const float *gax, *gay;      // static deflection at the grid nodes [ny][nx] (D_ls/D_s = 1)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -530,18 +557,27 @@ __global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, cons
   // triangle 0: (i,j),(i+1,j),(i+1,j+1); triangle 1: (i,j),(i+1,j+1),(i,j+1)
   const int oi[2][3] = {{ci, ci + 1, ci + 1}, {ci, ci + 1, ci}}, oj[2][3] = {{cj, cj, cj + 1}, {cj, cj + 1, cj + 1}};
   double th[3][2], be[3][2];
-  {
-    double vx[3], vy[3], o[3][5];
-    for (int q = 0; q < 3; ++q) {
-      th[q][0] = vx[q] = n.xmin + oi[tri][q] * n.dx;
-      th[q][1] = vy[q] = n.ymin + oj[tri][q] * n.dy;
+  __syncthreads();  // s_var complete
+  // the vertices are grid nodes: static deflection from the grid cache (the
+  // search's values), the two varying potentials in FP32
+  for (int q = 0; q < 3; ++q) {
+    const int ii = oi[tri][q], jj = oj[tri][q];
+    th[q][0] = n.xmin + ii * n.dx;
+    th[q][1] = n.ymin + jj * n.dy;
+    const size_t o = (size_t)jj * n.nx + ii;
+    float ax = n.gax[o], ay = n.gay[o];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      Acc<false, 1> acc;
+      acc.zero();
+      const float dY[1] = {(float)(th[q][1] - ((double)s_var.cen[v][1] + (double)s_var.cen[v][3]))};
+      eval32_any<false, 1>(reinterpret_cast<const float4 *>(s_var.r32[v]),
+                           (float)(th[q][0] - ((double)s_var.cen[v][0] + (double)s_var.cen[v][2])), dY, acc);
+      ax += acc.ax[0];
+      ay += acc.ay[0];
     }
-    __syncthreads();  // s_var complete
-    sweep<3, false>(n, s_var, s_rec, s_cen, vx, vy, o);
-    for (int q = 0; q < 3; ++q) {
-      be[q][0] = th[q][0] - r * o[q][0];
-      be[q][1] = th[q][1] - r * o[q][1];
-    }
+    be[q][0] = th[q][0] - r * ax;
+    be[q][1] = th[q][1] - r * ay;
   }
   // subdivision: keep the sub-triangle that best contains the source; stop
   // when none does (map far from linear on this triangle)
@@ -893,6 +929,8 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   n.dx = (gc->xmax - gc->xmin) / (gc->nx - 1);
   n.dy = (gc->ymax - gc->ymin) / (gc->ny - 1);
   n.nx = gc->nx;
+  n.gax = gc->alpha32;
+  n.gay = gc->alpha32 + (size_t)gc->nx * gc->ny;
   SearchArgs g;
   g.ax = gc->alpha32;
   g.ay = gc->alpha32 + (size_t)gc->nx * gc->ny;
