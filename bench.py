@@ -439,14 +439,16 @@ def serving_leg(ctx, api, torch):
             pool.give(torch.empty((6, side, side), dtype=torch.float32, pin_memory=True))
     warm = S.mixed_requests(8, seed=12, n_models=8, sides=(512, 1024))
     S.run_stream(srv, sess, warm, pool=pool, max_outstanding=8, keep_results=False)
-    # one request list (200 requests) for the capacity and every load level
-    reqs = S.mixed_requests(200, seed=13, n_models=8)
+    # one request list (400 requests) for the capacity and every load level;
+    # the load levels share one Poisson draw, scaled to each rate, so they
+    # differ only in rate and not in the shape of their bursts
+    reqs = S.mixed_requests(400, seed=13, n_models=8)
     lat, wall, _, _ = S.run_stream(srv, sess, reqs, pool=pool, max_outstanding=8, keep_results=False)
     cap = len(reqs) / wall
     out["capacity_req_per_s"] = cap
     out["closed_loop"] = S.percentiles(lat)
     for frac in (0.5, 0.8, 0.95):
-        arr = S.poisson_arrivals(len(reqs), frac * cap, seed=int(1000 * frac))
+        arr = S.poisson_arrivals(len(reqs), frac * cap, seed=15)
         miss0 = pool.misses
         lat, wall, _, _ = S.run_stream(srv, sess, reqs, arr, pool=pool, keep_results=False)
         out[f"load_{int(100 * frac)}"] = dict(S.percentiles(lat), offered_req_per_s=frac * cap,

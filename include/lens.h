@@ -200,9 +200,11 @@ int lens_chi2_autotune(lens_ctx *ctx, lens_cset_t cset, const double *d_params, 
  * solutions closer than 1e-3 arcsec merge, and each constraint is matched to
  * the nearest predicted image of its source.  d_chi2: DEVICE double [P];
  * d_nimg_found: DEVICE int32 [P][nsrc] (may be NULL) receives the number of
- * distinct images found per source.  A source without images, or a buffer
- * overflow, makes that set's chi2 NaN (the call then returns
- * LENS_ECAPACITY after synchronising the stream on overflow). */
+ * distinct images found per source (-1 for every source of a set whose
+ * candidate buffer, 4096 candidates, overflowed).  A source without images,
+ * or an overflow, makes that set's chi2 NaN; an overflow also sets the
+ * context's error flag, which the next lens_wait reports as LENS_ECAPACITY
+ * (and clears). */
 int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
                     double *d_chi2, int32_t *d_nimg_found, void *stream);
 

@@ -442,21 +442,31 @@ __device__ __forceinline__ df df_mulf(df a, float b) {
   const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
   return fast_two_sum(p, e);
 }
-__device__ __forceinline__ df df_div(df a, df b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
-  df r = df_sub(a, df_mulf(b, q1));
-  const float q2 = __fdiv_rn(r.hi, b.hi);
-  r = df_sub(r, df_mulf(b, q2));
-  const float q3 = __fdiv_rn(r.hi, b.hi);
-  return df_add(fast_two_sum(q1, q2), df{q3, 0.f});
+// a + b for operands of one sign (or without severe cancellation): one
+// TwoSum on the high parts, error within 2^-47 (|a| + |b|) (Dekker's add).
+__device__ __forceinline__ df df_add_ss(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
+// a / b: MUFU reciprocal of b.hi, then two exact remainders a - b q
+// correct the quotient (its first term may be off by a few 2^-24).
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float ib = rcp_a(b.hi);
+  const float q1 = a.hi * ib;
+  df r = df_sub(a, df_mulf(b, q1));
+  const float q2 = r.hi * ib;
+  r = df_sub(r, df_mulf(b, q2));
+  const float q3 = r.hi * ib;
+  return df_add_ss(fast_two_sum(q1, q2), df{q3, 0.f});
+}
+// sqrt(a): MUFU reciprocal square root y of a.hi, s = a.hi y, one Newton
+// correction (a - s^2) y / 2 with the residual from an FMA.
 __device__ __forceinline__ df df_sqrt(df a) {
   if (!(a.hi > 0.f)) return {0.f, 0.f};
-  const float s = __fsqrt_rn(a.hi);
-  const float p = s * s;
-  const float e = fmaf(s, s, -p);  // s*s = p + e exactly
-  const float c = __fdiv_rn(((a.hi - p) - e) + a.lo, 2.f * s);
-  return fast_two_sum(s, c);
+  const float y = rsqrt_a(a.hi);
+  const float s = a.hi * y;
+  const float e = fmaf(-s, s, a.hi) + a.lo;
+  return fast_two_sum(s, e * (0.5f * y));
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ df df_from_double(double d) {
@@ -471,9 +481,9 @@ __device__ __forceinline__ df df_poly(df t, const float (*c)[2]) {
   float tail = c[11][0];
 #pragma unroll
   for (int k = 10; k >= 7; --k) tail = fmaf(tail, t.hi, c[k][0]);
-  df p = df_add(df{c[6][0], c[6][1]}, df_mulf(t, tail));
+  df p = df_add_ss(df{c[6][0], c[6][1]}, df_mulf(t, tail));
 #pragma unroll
-  for (int k = 5; k >= 0; --k) p = df_add(df{c[k][0], c[k][1]}, df_mul(p, t));
+  for (int k = 5; k >= 0; --k) p = df_add_ss(df{c[k][0], c[k][1]}, df_mul(p, t));  // |p t| < 0.16 |p|: no cancellation
   return p;
 }
 
@@ -492,18 +502,19 @@ __device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int 
   const df x = df_add(df_mul(c, dX), df_mul(s, dY)), y = df_sub(df_mul(c, dY), df_mul(s, dX));
   const df q2 = ld(F_Q2), u2 = ld(F_U2);
   const df x2 = df_mul(x, x), y2 = df_mul(y, y);
-  const df R = df_add(df_mul(q2, x2), y2);
-  const df psc = df_sqrt(df_add(R, ld(F_KC)));
-  const df pst = df_sqrt(df_add(R, ld(F_KT)));
-  const df Sp = df_add(psc, pst);
+  // every sum below adds non-negative terms except dS and the y denominator
+  const df R = df_add_ss(df_mul(q2, x2), y2);
+  const df psc = df_sqrt(df_add_ss(R, ld(F_KC)));
+  const df pst = df_sqrt(df_add_ss(R, ld(F_KT)));
+  const df Sp = df_add_ss(psc, pst);
   const df sc = ld(F_SC), st = ld(F_ST);
-  const df Ec = df_add(psc, sc), Et = df_add(pst, st);
+  const df Ec = df_add_ss(psc, sc), Et = df_add_ss(pst, st);
   const df dS = df_sub(st, sc);
-  const df numx = df_mul(df_mul(x, dS), df_add(Sp, ld(F_Q2SS)));
-  const df denx = df_mul(Sp, df_add(df_mul(Ec, Et), df_mul(u2, x2)));
+  const df numx = df_mul(df_mul(x, dS), df_add_ss(Sp, ld(F_Q2SS)));
+  const df denx = df_mul(Sp, df_add_ss(df_mul(Ec, Et), df_mul(u2, x2)));
   const df Zx = df_div(numx, denx);
-  const df Fc = df_add(psc, ld(F_Q2SC)), Ft = df_add(pst, ld(F_Q2ST));
-  const df numy = df_mul(df_mul(y, ld(F_Q2DS)), df_add(Sp, ld(F_SS)));
+  const df Fc = df_add_ss(psc, ld(F_Q2SC)), Ft = df_add_ss(pst, ld(F_Q2ST));
+  const df numy = df_mul(df_mul(y, ld(F_Q2DS)), df_add_ss(Sp, ld(F_SS)));
   const df deny = df_mul(Sp, df_sub(df_mul(Fc, Ft), df_mul(u2, y2)));
   const df Zy = df_div(numy, deny);
   const df tx = df_mul(u2, df_mul(Zx, Zx)), ty = df_mul(u2, df_mul(Zy, Zy));

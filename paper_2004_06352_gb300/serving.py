@@ -114,8 +114,10 @@ def run_stream(server, session, reqs, arrivals=None, pool=None, timeout_s=600.0,
                keep_results=True):
     """Submit reqs at their arrival times (as fast as allowed if arrivals is
     None: at most max_outstanding submitted and not yet completed), poll
-    until every ticket completes.  Returns (latencies_ms, wall_s,
-    completions, buffers by ticket)."""
+    until every ticket completes.  Latency runs from the request's arrival
+    (its submission when arrivals is None) to its completion: the library's
+    submit-to-completion time plus how late this loop submitted it.  Returns
+    (latencies_ms, wall_s, completions, buffers by ticket)."""
     pool = pool or PinnedPool()
     t0 = time.perf_counter()
     pending, bufs, done = {}, {}, []
@@ -125,14 +127,16 @@ def run_stream(server, session, reqs, arrivals=None, pool=None, timeout_s=600.0,
         now = time.perf_counter() - t0
         while k < n and (arrivals is None or arrivals[k] <= now) and (
                 max_outstanding is None or len(pending) < max_outstanding):
+            late_ms = 0.0 if arrivals is None else 1e3 * max(0.0, time.perf_counter() - t0 - arrivals[k])
             t, buf = session.submit(server, reqs[k], pool)
-            pending[t] = buf
+            pending[t] = (buf, late_ms)
             k += 1
         for (ticket, status, qms, lms) in server.progress():
             if status != api.LENS_OK:
                 raise RuntimeError(f"request {ticket} failed: {api.strerror(status)}")
-            bufs[ticket] = pending.pop(ticket)
-            done.append((ticket, qms, lms))
+            buf, late_ms = pending.pop(ticket)
+            bufs[ticket] = buf
+            done.append((ticket, qms, lms + late_ms))
             if keep_results is False:
                 pool.give(bufs.pop(ticket))
         if now > timeout_s:

@@ -148,3 +148,83 @@ def test_chi2_image_invalid_set_is_nan(lens):
     ok = np.isfinite(ref)
     assert np.array_equal(np.isfinite(got[[0, 2]]), ok)
     assert np.all(np.abs(got[[0, 2]][ok] - ref[ok]) <= T.CHI2_REL * np.abs(ref[ok]))
+
+
+def test_chi2_image_batched_sets_match_single_calls(lens):
+    """P = 260 spans a full 256-set batch and a ragged one; every set's chi2
+    and image counts equal those of the same set evaluated alone."""
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    g = I.grid(256)
+    P = 260
+    params = I.perturbed_params(m, var, P, seed=71)
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        allc = torch.empty(P, dtype=torch.float64, device=DEV)
+        alln = torch.empty((P, len(cons["img_off"]) - 1), dtype=torch.int32, device=DEV)
+        ctx.chi2_image(cs, g, p, P, allc, alln)
+        ctx.wait()
+        for k in (0, 1, 255, 256, 259):
+            one = torch.empty(1, dtype=torch.float64, device=DEV)
+            onen = torch.empty((1, alln.shape[1]), dtype=torch.int32, device=DEV)
+            ctx.chi2_image(cs, g, p[k:k + 1], 1, one, onen)
+            ctx.wait()
+            assert torch.equal(onen[0], alln[k]), k
+            a, b = float(allc[k]), float(one[0])
+            assert (np.isnan(a) and np.isnan(b)) or abs(a - b) <= T.CHI2_REL * abs(b), (k, a, b)
+
+
+def test_chi2_image_candidate_overflow_is_nan_and_reported(lens):
+    """1024 sources (the maximum) at one position inside a five-image caustic
+    produce more than the 4096 candidates a set can hold: the set's chi2 is
+    NaN, every count is -1, lens_wait reports LENS_ECAPACITY once, and the
+    context keeps working."""
+    m = np.vstack([I.halo_row(I.DPIE, 0.0, 0.0, 0.3, 0.3, 0.5, 200.0, 20.0),
+                   I.halo_row(I.DPIE, 35.0, 30.0, 0.0, 0.1, 0.2, 20.0, 1.0)])
+    g = I.grid(128, field=(-50, 50, -50, 50))
+    n = 1024
+    cons = I.constraints_dict(np.arange(n + 1), np.full(n, 0.05), np.full(n, 0.03), np.full(n, 0.1),
+                              np.full(n, 0.9))
+    params = I.var_params_of(m, (0, 1))[None]
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, (0, 1))
+        p = torch.tensor(params, device=DEV)
+        out = torch.zeros(1, dtype=torch.float64, device=DEV)
+        nf = torch.zeros((1, n), dtype=torch.int32, device=DEV)
+        ctx.chi2_image(cs, g, p, 1, out, nf)
+        with pytest.raises(lens.LensError) as e:
+            ctx.wait()
+        assert e.value.code == lens.LENS_ECAPACITY
+        assert np.isnan(float(out[0])) and bool(torch.all(nf == -1))
+        ctx.wait()  # the flag was cleared
+        small = I.constraints_dict(np.arange(5), np.full(4, 0.05), np.full(4, 0.03), np.full(4, 0.1),
+                                   np.full(4, 0.9))
+        cs2 = ctx.cset_create(mid, small, (0, 1))
+        nf2 = torch.zeros((1, 4), dtype=torch.int32, device=DEV)
+        ctx.chi2_image(cs2, g, p, 1, out, nf2)
+        ctx.wait()
+        assert bool(torch.all(nf2 == 5)) and np.isfinite(float(out[0]))
+
+
+def test_chi2_image_source_without_images_is_nan(lens):
+    """A source far outside the lensed field has no image on the grid: its
+    count is 0 and the set's chi2 is NaN (no finite Eq. 6 without a match);
+    the other sources still get their images."""
+    m = np.vstack([I.halo_row(I.DPIE, 0.0, 0.0, 0.3, 0.3, 0.5, 200.0, 20.0),
+                   I.halo_row(I.DPIE, 35.0, 30.0, 0.0, 0.1, 0.2, 20.0, 1.0)])
+    g = I.grid(96, field=(-40, 40, -30, 30), ny=72)   # nx != ny
+    # source 0: one image at (0.3, 0.1) (inside the caustic); source 1: a
+    # constraint at the field's edge whose back-traced source maps nowhere
+    # on the grid (its images would lie outside it)
+    cons = I.constraints_dict([0, 1, 2], [0.3, 1.0e3], [0.1, 1.0e3], [0.1, 0.1], [0.9, 0.9])
+    params = I.var_params_of(m, (0, 1))[None]
+    ref, nf_ref = oracle.chi2_image_batch(m, cons, g, (0, 1), params)
+    with lens.Context(0) as ctx:
+        got, nf = gpu_chi2_image(lens, m, cons, (0, 1), g, params, ctx=ctx)
+    assert np.isnan(ref[0]) and np.isnan(got[0])
+    assert nf_ref[0, 1] == 0 and nf[0, 1] == 0
+    assert nf[0, 0] == nf_ref[0, 0] == 5
