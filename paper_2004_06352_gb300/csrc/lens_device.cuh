@@ -487,10 +487,71 @@ __device__ __forceinline__ df df_poly(df t, const float (*c)[2]) {
   return p;
 }
 
-// Deflection of one dPIE in double-float at (X, Y) given as pairs; false when
-// |w| is too large for the polynomial (the caller then uses FP64).  Pair k of
-// the record is r[k * stride] (stride 1: one record; stride n: field-major
-// table of n records).
+// Double-float tables of the same reductions: centre k is the pair's exact
+// value c_k ~ tanh(0.8 k), and ATANH_A_DF[k] = atanh(c_k) (60 digits).
+__device__ __constant__ const float ATANH_C_DF[23][2] = {
+    {0.000000000e+00f, 0.000000000e+00f}, {6.640367508e-01f, 1.947439188e-08f}, {9.216685295e-01f, 2.489597328e-08f},
+    {9.836748838e-01f, -2.614878802e-08f}, {9.966824055e-01f, -7.632150911e-09f}, {9.993293285e-01f, -2.879792049e-08f},
+    {9.998645782e-01f, -2.654631004e-08f}, {9.999726415e-01f, 1.051378273e-08f}, {9.999944568e-01f, 2.170206415e-08f},
+    {9.999988675e-01f, 1.770813363e-08f}, {9.999997616e-01f, 1.334825495e-08f}, {9.999999404e-01f, 1.416372619e-08f},
+    {1.000000000e+00f, -9.174363491e-09f}, {1.000000000e+00f, -1.852272002e-09f}, {1.000000000e+00f, -3.739672738e-10f},
+    {1.000000000e+00f, -7.550268744e-11f}, {1.000000000e+00f, -1.524372989e-11f}, {1.000000000e+00f, -3.077656185e-12f},
+    {1.000000000e+00f, -6.213680286e-13f}, {1.000000000e+00f, -1.254520440e-13f}, {1.000000000e+00f, -2.532833155e-14f},
+    {1.000000000e+00f, -5.113701803e-15f}, {1.000000000e+00f, -1.032438613e-15f}};
+__device__ __constant__ const float ATANH_A_DF[23][2] = {
+    {0.000000000e+00f, 0.000000000e+00f}, {8.000000119e-01f, -1.192092913e-08f}, {1.600000024e+00f, -2.384185827e-08f},
+    {2.400000095e+00f, -9.536743306e-08f}, {3.200000048e+00f, -4.768376272e-08f}, {4.000000000e+00f, -1.728711168e-13f},
+    {4.800000191e+00f, -1.907355482e-07f}, {5.599999905e+00f, 9.536795176e-08f}, {6.400000095e+00f, -9.532934797e-08f},
+    {7.199999809e+00f, 1.907639842e-07f}, {8.000000000e+00f, -1.012165907e-10f}, {8.800000191e+00f, -1.880990936e-07f},
+    {9.600000381e+00f, -3.836451583e-07f}, {1.039999962e+01f, 3.922546341e-07f}, {1.119999981e+01f, 1.936774794e-07f},
+    {1.200000000e+01f, 2.282851952e-08f}, {1.280000019e+01f, -1.743534028e-07f}, {1.360000038e+01f, -3.974995195e-07f},
+    {1.439999962e+01f, 3.966487157e-07f}, {1.519999981e+01f, 1.952836897e-07f}, {1.600000000e+01f, -9.008017443e-09f},
+    {1.679999924e+01f, 7.680131375e-07f}, {1.760000038e+01f, -3.882470310e-07f}};
+__device__ __constant__ const float ATAN_11_16_DF[2] = {6.022873521e-01f, -5.950149262e-09f};
+__device__ __constant__ const float PI_2_DF[2] = {1.570796371e+00f, -4.371138829e-08f};
+
+// atan(w) and atanh(w) in double-float for any argument (|w| < 1 for
+// atanh), by the reductions of atan64 / atanh64 (pairs instead of doubles);
+// atanh returns NaN beyond the table (|w| within ~1e-15 of 1).
+__device__ __forceinline__ df df_atan(df w) {
+  const bool neg = w.hi < 0.f;
+  const df a = neg ? df_neg(w) : w;
+  const bool inv = a.hi > 1.f;
+  df v = inv ? df_div(df{1.f, 0.f}, a) : a;
+  df base = {0.f, 0.f};
+  if (v.hi > 0.4f) {
+    v = df_div(df_sub(v, df{0.6875f, 0.f}), df_add_ss(df{1.f, 0.f}, df_mulf(v, 0.6875f)));
+    base = df{ATAN_11_16_DF[0], ATAN_11_16_DF[1]};
+  }
+  df r = df_add(base, df_mul(v, df_poly(df_mul(v, v), C_ATAN_DF)));
+  if (inv) r = df_sub(df{PI_2_DF[0], PI_2_DF[1]}, r);
+  return neg ? df_neg(r) : r;
+}
+__device__ __forceinline__ df df_atanh(df w) {
+  const bool neg = w.hi < 0.f;
+  const df a = neg ? df_neg(w) : w;
+  df r;
+  if (a.hi <= 0.4f) {
+    r = df_mul(a, df_poly(df_mul(a, a), C_ATANH_DF));
+  } else {
+    const df om = df_sub(df{1.f, 0.f}, a);  // 1 - a, exact enough to pick the centre
+    const float est = 0.5f * (__logf(1.f + a.hi) - __logf(om.hi));
+    const int k = __float2int_rn(est * 1.25f);
+    if (!(om.hi > 0.f) || k > 22) return df{__int_as_float(0x7fc00000), 0.f};
+    const int kk = k < 1 ? 1 : k;
+    const df c = {ATANH_C_DF[kk][0], ATANH_C_DF[kk][1]};
+    const df v = df_div(df_sub(a, c), df_sub(df{1.f, 0.f}, df_mul(a, c)));
+    r = df_add(df{ATANH_A_DF[kk][0], ATANH_A_DF[kk][1]}, df_mul(v, df_poly(df_mul(v, v), C_ATANH_DF)));
+  }
+  return neg ? df_neg(r) : r;
+}
+
+// Deflection of one dPIE in double-float at (X, Y) given as pairs.  ANY =
+// false: false when |w|^2 >= 0.16 for either term (polynomial only, the
+// common case); ANY = true: such terms through df_atan / df_atanh, false only
+// for a non-finite result.  Pair k of the record is r[k * stride] (stride 1:
+// one record; stride n: field-major table of n records).
+template <bool ANY>
 __device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax,
                                               df &ay) {
   auto ld = [&](int k) {
@@ -499,7 +560,8 @@ __device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int 
   };
   const df c = ld(F_C), s = ld(F_S);
   const df dX = df_sub(X, ld(F_X0)), dY = df_sub(Y, ld(F_Y0));
-  const df x = df_add(df_mul(c, dX), df_mul(s, dY)), y = df_sub(df_mul(c, dY), df_mul(s, dX));
+  // rotations: the one-TwoSum add's error is bounded by 2^-47 |(dX, dY)|
+  const df x = df_add_ss(df_mul(c, dX), df_mul(s, dY)), y = df_add_ss(df_mul(c, dY), df_neg(df_mul(s, dX)));
   const df q2 = ld(F_Q2), u2 = ld(F_U2);
   const df x2 = df_mul(x, x), y2 = df_mul(y, y);
   // every sum below adds non-negative terms except dS and the y denominator
@@ -509,7 +571,7 @@ __device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int 
   const df Sp = df_add_ss(psc, pst);
   const df sc = ld(F_SC), st = ld(F_ST);
   const df Ec = df_add_ss(psc, sc), Et = df_add_ss(pst, st);
-  const df dS = df_sub(st, sc);
+  const df dS = df_add_ss(st, df_neg(sc));  // st > sc > 0: error 2^-47 (st + sc) < 2^-46 dS
   const df numx = df_mul(df_mul(x, dS), df_add_ss(Sp, ld(F_Q2SS)));
   const df denx = df_mul(Sp, df_add_ss(df_mul(Ec, Et), df_mul(u2, x2)));
   const df Zx = df_div(numx, denx);
@@ -518,12 +580,37 @@ __device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int 
   const df deny = df_mul(Sp, df_sub(df_mul(Fc, Ft), df_mul(u2, y2)));
   const df Zy = df_div(numy, deny);
   const df tx = df_mul(u2, df_mul(Zx, Zx)), ty = df_mul(u2, df_mul(Zy, Zy));
-  if (!(tx.hi < (float)T_SERIES64 && ty.hi < (float)T_SERIES64)) return false;  // also catches NaN
   const df bq = ld(F_BQ);
-  const df axp = df_mul(df_mul(bq, Zx), df_poly(tx, C_ATAN_DF)), ayp = df_mul(df_mul(bq, Zy), df_poly(ty, C_ATANH_DF));
-  ax = df_sub(df_mul(c, axp), df_mul(s, ayp));
-  ay = df_add(df_mul(s, axp), df_mul(c, ayp));
+  df axp, ayp;
+  if (tx.hi < (float)T_SERIES64 && ty.hi < (float)T_SERIES64) {  // bq Z atan(w)/w, w = u Z
+    axp = df_mul(df_mul(bq, Zx), df_poly(tx, C_ATAN_DF));
+    ayp = df_mul(df_mul(bq, Zy), df_poly(ty, C_ATANH_DF));
+  } else {
+    if (!ANY) return false;  // (also for NaN)
+    const df u = df_sqrt(u2), bu = df_div(bq, u);  // (bq / u) atan(u Z)
+    axp = df_mul(bu, df_atan(df_mul(u, Zx)));
+    ayp = df_mul(bu, df_atanh(df_mul(u, Zy)));
+    if (!(fabsf(axp.hi) < INFINITY && fabsf(ayp.hi) < INFINITY)) return false;
+  }
+  ax = df_add_ss(df_mul(c, axp), df_neg(df_mul(s, ayp)));  // rotation back: error 2^-47 |(axp, ayp)|
+  ay = df_add_ss(df_mul(s, axp), df_mul(c, ayp));
   return true;
+}
+
+// SIS (F_U2 = -1, b = F_BQ) or point mass (F_U2 = -2, b = theta_E^2 in
+// F_BQ) in double-float; zero at the centre.
+__device__ __forceinline__ void circ_alpha_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax,
+                                              df &ay) {
+  const float2 x0 = r[F_X0 * stride], y0 = r[F_Y0 * stride], b = r[F_BQ * stride];
+  const df dX = df_sub(X, df{x0.x, x0.y}), dY = df_sub(Y, df{y0.x, y0.y});
+  const df r2 = df_add_ss(df_mul(dX, dX), df_mul(dY, dY));
+  if (!(r2.hi > 0.f)) {
+    ax = ay = df{0.f, 0.f};
+    return;
+  }
+  const df f = r[F_U2 * stride].x < -1.5f ? df_div(df{b.x, b.y}, r2) : df_div(df{b.x, b.y}, df_sqrt(r2));
+  ax = df_mul(f, dX);
+  ay = df_mul(f, dY);
 }
 
 // --------------------------------------------------------- constraint sets

@@ -510,31 +510,53 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
       }
     }
   }
+  constexpr int NC = HESS ? 5 : 2;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     fold(tot[k], cmp[k], part[k]);
-    out[k][0] = (double)tot[k].ax[0] - (double)cmp[k].ax[0];
-    out[k][1] = (double)tot[k].ay[0] - (double)cmp[k].ay[0];
-    out[k][2] = HESS ? (double)tot[k].k[0] - (double)cmp[k].k[0] : 0.0;
-    out[k][3] = HESS ? (double)tot[k].g1[0] - (double)cmp[k].g1[0] : 0.0;
-    out[k][4] = HESS ? (double)tot[k].g2[0] - (double)cmp[k].g2[0] : 0.0;
-    for (int j = gl; j < n.n_heavy; j += RF_G) {
-      double e0, e1, e2 = 0, e3 = 0, e4 = 0;
-      eval64<HESS>(n.heavy + (size_t)j * REC64, px[k], py[k], e0, e1, e2, e3, e4);
-      out[k][0] += e0;
-      out[k][1] += e1;
-      out[k][2] += e2;
-      out[k][3] += e3;
-      out[k][4] += e4;
-    }
+    // each thread's compensated sum tot - cmp as a float pair, combined over
+    // the group in double-float (TwoSum gives both partners the same bits)
+    float hi[5] = {tot[k].ax[0], tot[k].ay[0], HESS ? tot[k].k[0] : 0.f, HESS ? tot[k].g1[0] : 0.f,
+                   HESS ? tot[k].g2[0] : 0.f};
+    float lo[5] = {-cmp[k].ax[0], -cmp[k].ay[0], HESS ? -cmp[k].k[0] : 0.f, HESS ? -cmp[k].g1[0] : 0.f,
+                   HESS ? -cmp[k].g2[0] : 0.f};
 #pragma unroll
     for (int o = 1; o < RF_G; o <<= 1)
 #pragma unroll
-      for (int q = 0; q < (HESS ? 5 : 2); ++q) out[k][q] += __shfl_xor_sync(0xffffffffu, out[k][q], o);
+      for (int q = 0; q < NC; ++q) {
+        const float ph = __shfl_xor_sync(0xffffffffu, hi[q], o), pl = __shfl_xor_sync(0xffffffffu, lo[q], o);
+        const df t = two_sum(hi[q], ph);
+        const df u = fast_two_sum(t.hi, t.lo + (lo[q] + pl));
+        hi[q] = u.hi;
+        lo[q] = u.lo;
+      }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) out[k][q] = q < NC ? (double)hi[q] + (double)lo[q] : 0.0;
+    if (n.n_heavy > 0) {  // static cluster-scale potentials: FP64, spread over the group
+      double hv[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int j = gl; j < n.n_heavy; j += RF_G) {
+        double e0, e1, e2 = 0, e3 = 0, e4 = 0;
+        eval64<HESS>(n.heavy + (size_t)j * REC64, px[k], py[k], e0, e1, e2, e3, e4);
+        hv[0] += e0;
+        hv[1] += e1;
+        hv[2] += e2;
+        hv[3] += e3;
+        hv[4] += e4;
+      }
+#pragma unroll
+      for (int o = 1; o < RF_G; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) hv[q] += __shfl_xor_sync(0xffffffffu, hv[q], o);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) out[k][q] += hv[q];
+    }
   }
 }
 
-__global__ void __launch_bounds__(RF_THREADS) k_img_newton(const SetArgs a, const NewtonArgs n) {
+#ifndef LENS_NEWTON_MINB
+#define LENS_NEWTON_MINB 4  // resident CTAs per SM the Newton kernel is compiled for
+#endif
+__global__ void __launch_bounds__(RF_THREADS, LENS_NEWTON_MINB) k_img_newton(const SetArgs a, const NewtonArgs n) {
   __shared__ float4 s_rec[RF_CH * RF_STRIDE4];
   __shared__ float4 s_cen[RF_CH];
   __shared__ VarRecs s_var;
@@ -759,12 +781,31 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
     double tx = h->tx, ty = h->ty, step = 1e30;
     for (int it = 0; it < POLISH_MAXIT && step >= POLISH_TOL; ++it) {
       // alpha(tx, ty): dPIE terms inside the polynomial range in
-      // double-float; the rest (cores, SIS, point masses) queued and
-      // evaluated 32 at a time in FP64 so the warp stays converged.
+      // double-float; the rest (cores: |w|^2 >= 0.16, SIS, point masses)
+      // queued and evaluated 32 at a time, so the warp stays converged, by
+      // the double-float reductions of atan/atanh (FP64 only if those fail)
       const df X = df_from_double(tx), Y = df_from_double(ty);
       df fx = {0.f, 0.f}, fy = {0.f, 0.f};
-      double sx = 0.0, sy = 0.0, e2, e3, e4, ex, ey;
+      double sx = 0.0, sy = 0.0;
       int nq = 0;
+      auto queued = [&](int jj) {
+        const bool stq = jj < n.n_stat;
+        const float2 *rec = stq ? n.recdf + jj : s_vdf[w] + (jj - n.n_stat) * RECDF;
+        const int stride = stq ? n.n_stat : 1;
+        df gx, gy;
+        if (rec[F_U2 * stride].x < 0.f) {
+          circ_alpha_df(rec, stride, X, Y, gx, gy);
+        } else if (!dpie_alpha_df<true>(rec, stride, X, Y, gx, gy)) {
+          const double *r64 = stq ? n.all64 + (size_t)jj * REC64 : s_var[w] + (jj - n.n_stat) * REC64;
+          double ex, ey, e2, e3, e4;
+          eval64<false>(r64, tx, ty, ex, ey, e2, e3, e4);
+          sx += ex;
+          sy += ey;
+          return;
+        }
+        fx = df_add(fx, gx);
+        fy = df_add(fy, gy);
+      };
       for (int base = 0; base < ntot; base += 32) {
         const int j = base + lane;
         bool need = false;
@@ -773,9 +814,11 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
           const float2 *rec = st ? n.recdf + j : s_vdf[w] + (j - n.n_stat) * RECDF;
           const int stride = st ? n.n_stat : 1;
           df gx, gy;
-          if (rec[F_U2 * stride].x >= 0.f && dpie_alpha_df(rec, stride, X, Y, gx, gy)) {
-            fx = df_add(fx, gx);
-            fy = df_add(fy, gy);
+          if (rec[F_U2 * stride].x >= 0.f && dpie_alpha_df<false>(rec, stride, X, Y, gx, gy)) {
+            // one-TwoSum accumulation: absolute error 2^-47 sum |alpha_i|,
+            // a few 1e-13 arcsec over a cluster
+            fx = df_add_ss(fx, gx);
+            fy = df_add_ss(fy, gy);
           } else {
             need = true;
           }
@@ -785,23 +828,13 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
         nq += __popc(m);
         if (nq >= 32) {
           __syncwarp();
-          const int jj = s_q[w][nq - 32 + lane];
-          const double *rec = jj < n.n_stat ? n.all64 + (size_t)jj * REC64 : s_var[w] + (jj - n.n_stat) * REC64;
-          eval64<false>(rec, tx, ty, ex, ey, e2, e3, e4);
-          sx += ex;
-          sy += ey;
+          queued(s_q[w][nq - 32 + lane]);
           nq -= 32;
           __syncwarp();
         }
       }
       __syncwarp();
-      if (lane < nq) {
-        const int jj = s_q[w][lane];
-        const double *rec = jj < n.n_stat ? n.all64 + (size_t)jj * REC64 : s_var[w] + (jj - n.n_stat) * REC64;
-        eval64<false>(rec, tx, ty, ex, ey, e2, e3, e4);
-        sx += ex;
-        sy += ey;
-      }
+      if (lane < nq) queued(s_q[w][lane]);
       __syncwarp();
       sx = warp_sum(sx + df_to_double(fx));
       sy = warp_sum(sy + df_to_double(fy));

@@ -158,8 +158,8 @@ enum RecDF : int {
   F_X0 = 0, F_Y0, F_C, F_S, F_Q2, F_U2, F_KC, F_KT, F_SC, F_ST, F_Q2SC, F_Q2ST, F_Q2SS, F_Q2DS, F_SS, F_BQ
 };
 constexpr int RECDF = 16;
-// SIS and point-mass records carry F_U2 = -1 (never negative for a dPIE) and
-// are left to the FP64 path.
+// SIS and point-mass records carry F_U2 = -1 and -2 (never negative for a
+// dPIE) and b, theta_E^2 in F_BQ.
 
 // Host + device: double-float record from user parameters; pair k goes to
 // r[k * stride].
@@ -171,7 +171,8 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
   v[F_Y0] = y0;
   if (type == LENS_SIS || type == LENS_POINT) {
     v[F_C] = 1.0;
-    v[F_U2] = -1.0;
+    v[F_U2] = type == LENS_SIS ? -1.0 : -2.0;
+    v[F_BQ] = type == LENS_SIS ? b0 : b0 * b0;
   } else {
     const double q = (1.0 - eps) / (1.0 + eps), u = 2.0 * sqrt(eps) / (1.0 + eps);
     const double q2 = q * q, sc = rcore * (1.0 + eps), st = rcut * (1.0 + eps);

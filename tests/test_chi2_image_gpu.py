@@ -228,3 +228,28 @@ def test_chi2_image_source_without_images_is_nan(lens):
     assert np.isnan(ref[0]) and np.isnan(got[0])
     assert nf_ref[0, 1] == 0 and nf[0, 1] == 0
     assert nf[0, 0] == nf_ref[0, 0] == 5
+
+
+def test_chi2_image_static_sis_and_point_mass(lens):
+    """Static SIS and point-mass potentials beside the varying dPIEs (their
+    polish terms take the double-float circular path): constraints placed
+    on the oracle's images give chi2 ~ 0 and the oracle's image counts."""
+    m = np.vstack([I.halo_row(I.DPIE, 0.3, -0.2, 0.5, 0.3, 1.5, 300.0, 12.0),
+                   I.halo_row(I.DPIE, -2.0, 1.0, 1.1, 0.2, 0.8, 150.0, 6.0),
+                   I.halo_row(I.SIS, 6.0, -4.0, 0.0, 0.0, 0.0, 0.0, 1.2),
+                   I.halo_row(I.POINT, -7.0, 5.0, 0.0, 0.0, 0.0, 0.0, 0.9),
+                   I.member_model(12, seed=45, field=30)])
+    g = I.grid(161, field=(-40, 40, -40, 40))
+    xs, ys, off, rs = [], [], [0], []
+    for bs, r in (((0.4, 0.3), 0.7), ((-0.6, 0.2), 0.9), ((1.5, -1.0), 0.8)):
+        img, nfound = oracle.find_images(m, g, r, bs)
+        assert nfound >= 1
+        xs += list(img[:, 0])
+        ys += list(img[:, 1])
+        off.append(len(xs))
+        rs.append(r)
+    cons = I.constraints_dict(off, xs, ys, np.full(len(xs), 0.05), rs)
+    params = I.var_params_of(m, (0, 1))[None]
+    got, nf = gpu_chi2_image(lens, m, cons, (0, 1), g, params)
+    assert got[0] < 1e-12, got
+    assert list(nf[0]) == [off[i + 1] - off[i] for i in range(3)]
