@@ -111,6 +111,12 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
                    [&](int32_t a, int32_t b) { return kind_order(h[a]) < kind_order(h[b]); });
   m->n_light = (int32_t)light.size();
   m->n_heavy = (int32_t)heavy.size();
+  for (int k = 0; k < 4; ++k) {
+    int32_t c = 0;
+    for (int32_t i : light) c += kind_order(h[i]) < k ? 1 : 0;
+    m->koff[k] = c;
+  }
+  m->koff[4] = m->n_light;
   std::vector<float> r32((size_t)m->n_light * REC32), c32((size_t)m->n_light * 4);
   std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
   std::vector<float2> adf((size_t)n * RECDF);

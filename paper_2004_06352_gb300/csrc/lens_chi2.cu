@@ -12,9 +12,14 @@
 // and reduces the chi2 with warp shuffles in a fixed order.
 //
 // No-cache form: the static sum is recomputed for every parameter set (a
-// batch of sets at a time, into scratch memory) before the same source-plane
-// kernel runs; this is the per-set cost when any potential may vary, as in
-// the paper's fit, where every potential is evaluated for every model.
+// batch of sets at a time, into scratch memory, in double-float) before the
+// same source-plane kernel runs; this is the per-set cost when any potential
+// may vary, as in the paper's fit, where every potential is evaluated for
+// every model.
+//
+// The two varying potentials are evaluated in double-float (FP32 pipe,
+// ~1e-13 relative), FP64 only where that fails; the static cache itself is
+// FP64.
 #include "lens_device.cuh"
 
 namespace lens {
@@ -65,11 +70,17 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
   double *s_bary = s_m + 3 * a.nimg;     // [nsrc][2]
   double *s_red = s_bary + 2 * a.nsrc;   // [THREADS/32]
   __shared__ int s_ok;
+  __shared__ float2 s_rdf[2 * RECDF];  // the varying potentials in double-float
   for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
     const double *q = a.params + (size_t)p * 14;
     if (threadIdx.x == 0) s_ok = 1;
     __syncthreads();
-    if (threadIdx.x < 2 && !load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
+    if (threadIdx.x < 2) {
+      if (!load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
+      const double *w = q + 7 * threadIdx.x;  // x0, y0, eps, theta, rcore, rcut, b0
+      make_recdf(threadIdx.x == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6],
+                 s_rdf + threadIdx.x * RECDF);
+    }
     __syncthreads();
     if (!s_ok) {
       if (threadIdx.x == 0) a.chi2[p] = __longlong_as_double(0x7ff8000000000000ll);
@@ -77,8 +88,7 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
       continue;
     }
     backtrace_set<THREADS>(a.stat + p * a.stat_stride, a.x, a.y, a.ratio, a.src_of, a.img_off, a.nimg, a.nsrc,
-                           s_rec, s_beta,
-                           a.variant == LENS_CHI2_SRC_PLAIN ? nullptr : s_m, s_bary);
+                           s_rec, s_rdf, s_beta, a.variant == LENS_CHI2_SRC_PLAIN ? nullptr : s_m, s_bary);
     double acc[1] = {0.0};
     for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
       const int i = a.src_of[j];
@@ -170,6 +180,27 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
   return launch_src_idx(ctx, c, d_params, P, variant, d_chi2, st, idx);
 }
 
+// Static sums of the no-cache form, grid (nimg, sets): every static potential
+// at the image in double-float (FP64 where that fails), per-thread sums in
+// FP64, deterministic CTA reduction; copy c goes to stat + c * nimg * 5.
+__global__ void __launch_bounds__(CACHE_THREADS) k_static_df(const float2 *__restrict__ recdf,
+                                                             const double *__restrict__ all64, int n, int v0, int v1,
+                                                             const double *__restrict__ x,
+                                                             const double *__restrict__ y, double *stat) {
+  __shared__ double s_red[(CACHE_THREADS / 32) * 5];
+  const int img = blockIdx.x;
+  stat += (size_t)blockIdx.y * gridDim.x * 5;
+  const double X = x[img], Y = y[img];
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int h = threadIdx.x; h < n; h += CACHE_THREADS) {
+    if (h == v0 || h == v1) continue;
+    add_potential_df<true>(recdf + h, n, all64 + (size_t)h * REC64, X, Y, v);
+  }
+  block_sum<5, CACHE_THREADS>(v, s_red);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) stat[(size_t)img * 5 + k] = v[k];
+}
+
 size_t chi2_nocache_scratch_bytes(const CSet *c) { return (size_t)NOCACHE_BATCH * c->nimg * 5 * sizeof(double); }
 
 int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
@@ -177,8 +208,8 @@ int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, con
   double *stat = (double *)ctx->scratch;
   for (int32_t p0 = 0; p0 < P; p0 += NOCACHE_BATCH) {
     const int B = std::min(NOCACHE_BATCH, P - p0);
-    k_static_cache<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->all64, m->n, c->var[0], c->var[1], c->x, c->y,
-                                                                stat);
+    k_static_df<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1], c->x,
+                                                             c->y, stat);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LENS_ECUDA, "static sums launch: %s", cudaGetErrorString(e));
     const int rc = launch_src_cfg<128>(ctx, c, d_params + (size_t)p0 * 14, B, variant, d_chi2 + p0, st, 0, stat,

@@ -298,7 +298,24 @@ __device__ __forceinline__ float atanh_over_w(float t) {
 // One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the
 // potential's centre are formed by the caller from hi/lo float pairs, then
 //   x = c dX + s dY,  y = c dY - s dX   (halo frame).
-template <bool HESS, int KP, bool SERIES>
+// Decision-grade atan for the image search: the reduction of atan64 in FP32
+// (fold |w| > 1, shift [0.4, 1] about 11/16) into the degree-5 interpolant,
+// branch-free so that lanes do not diverge.
+__device__ __forceinline__ float atan_fast(float w) {
+  const float a = fabsf(w);
+  const bool inv = a > 1.f;
+  float v = inv ? rcp_a(a) : a;
+  const bool sh = v > 0.4f;
+  v = sh ? (v - 0.6875f) * rcp_a(fmaf(v, 0.6875f, 1.f)) : v;
+  float r = v * atan_over_w(v * v) + (sh ? 0.602287352f : 0.f);
+  r = inv ? 1.57079637f - r : r;
+  return copysignf(r, w);
+}
+
+// FAST: outside the polynomial range, atan by atan_fast and
+// 2 atanh(w) = ln((1+w)/(1-w)) by the MUFU log2 (absolute error ~1e-7; the
+// image search only decides which triangles seed a candidate).
+template <bool HESS, int KP, bool SERIES, bool FAST = false>
 __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
                                        Acc<HESS, KP> &p) {
   const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4], F = r4[5], G = r4[6];
@@ -334,6 +351,9 @@ __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, 
         const float bq = 2.f * F.z;  // (bq/u) atan(u Z) = bq Z atan(w)/w
         axp = bq * Zx * atan_over_w(tx);
         ayp = bq * Zy * atanh_over_w(ty);
+      } else if (FAST) {
+        axp = axs * atan_fast(wx);
+        ayp = ays * (0.693147181f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
       } else {
         axp = axs * atanf(wx);
         ayp = ays * log1pf((wy + wy) * rcp_a(1.f - wy));
@@ -391,12 +411,12 @@ __device__ __forceinline__ void circ32(const float4 *__restrict__ r4, float x, c
 
 // Any FP32 potential at KP points sharing dX (kind is warp-uniform in the
 // map kernel; per-lane in the image kernels).
-template <bool HESS, int KP>
+template <bool HESS, int KP, bool FAST = false>
 __device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
                                            Acc<HESS, KP> &p) {
   const int kind = __float_as_int(r4[7].x);
   if (kind == K32_DPIE)
-    dpie32<HESS, KP, false>(r4, dX, dY, p);
+    dpie32<HESS, KP, false, FAST>(r4, dX, dY, p);
   else if (kind == K32_DPIE_SERIES)
     dpie32<HESS, KP, true>(r4, dX, dY, p);
   else if (kind == K32_SIS)
@@ -546,14 +566,17 @@ __device__ __forceinline__ df df_atanh(df w) {
   return neg ? df_neg(r) : r;
 }
 
-// Deflection of one dPIE in double-float at (X, Y) given as pairs.  ANY =
-// false: false when |w|^2 >= 0.16 for either term (polynomial only, the
-// common case); ANY = true: such terms through df_atan / df_atanh, false only
-// for a non-finite result.  Pair k of the record is r[k * stride] (stride 1:
-// one record; stride n: field-major table of n records).
-template <bool ANY>
-__device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax,
-                                              df &ay) {
+// One dPIE in double-float at (X, Y) given as pairs: deflection and, if HESS,
+// kappa, gamma1, gamma2 into h[0..2] (the forms of eval64; kappa's core-minus-
+// cut difference 1/psc - 1/pst as q^2 (st^2 - sc^2) / ((psc + pst) psc pst),
+// free of cancellation).  ANY = false: false when |w|^2 >= 0.16 for either
+// deflection term (polynomial only, the common case); ANY = true: such terms
+// through df_atan / df_atanh, false only for a non-finite result.  Pair k of
+// the record is r[k * stride] (stride 1: one record; stride n: field-major
+// table of n records).
+template <bool ANY, bool HESS = false>
+__device__ __forceinline__ bool dpie_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax, df &ay,
+                                        df *h = nullptr) {
   auto ld = [&](int k) {
     const float2 v = r[k * stride];
     return df{v.x, v.y};
@@ -594,62 +617,131 @@ __device__ __forceinline__ bool dpie_alpha_df(const float2 *__restrict__ r, int 
   }
   ax = df_add_ss(df_mul(c, axp), df_neg(df_mul(s, ayp)));  // rotation back: error 2^-47 |(axp, ayp)|
   ay = df_add_ss(df_mul(s, axp), df_mul(c, ayp));
+  if (HESS) {
+    const df r2 = df_add_ss(x2, y2), ymx = df_sub(y2, x2);
+    const df Dc = df_add_ss(df_add_ss(ld(F_DC0), df_mul(df_mulf(sc, 2.f), psc)), r2);
+    const df Dt = df_add_ss(df_add_ss(ld(F_DT0), df_mul(df_mulf(st, 2.f), pst)), r2);
+    const df fc = df_div(df{1.f, 0.f}, df_mul(psc, Dc)), ft = df_div(df{1.f, 0.f}, df_mul(pst, Dt));
+    const df hb = ld(F_HB);
+    const df g1p = df_mul(hb, df_sub(df_mul(fc, df_sub(ymx, ld(F_U2SC2))), df_mul(ft, df_sub(ymx, ld(F_U2ST2)))));
+    const df g2p = df_neg(df_mul(df_mul(bq, df_sub(fc, ft)), df_mul(x, y)));
+    h[0] = df_div(df_mul(hb, ld(F_KTC)), df_mul(df_mul(Sp, psc), pst));
+    const df c2 = ld(F_C2), s2 = ld(F_S2);
+    h[1] = df_sub(df_mul(c2, g1p), df_mul(s2, g2p));
+    h[2] = df_add(df_mul(s2, g1p), df_mul(c2, g2p));
+  }
   return true;
 }
 
 // SIS (F_U2 = -1, b = F_BQ) or point mass (F_U2 = -2, b = theta_E^2 in
-// F_BQ) in double-float; zero at the centre.
-__device__ __forceinline__ void circ_alpha_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax,
-                                              df &ay) {
-  const float2 x0 = r[F_X0 * stride], y0 = r[F_Y0 * stride], b = r[F_BQ * stride];
+// F_BQ) in double-float; zero at the centre.  HESS: kappa, gamma1, gamma2
+// into h[0..2].
+template <bool HESS = false>
+__device__ __forceinline__ void circ_df(const float2 *__restrict__ r, int stride, df X, df Y, df &ax, df &ay,
+                                        df *h = nullptr) {
+  const float2 x0 = r[F_X0 * stride], y0 = r[F_Y0 * stride], b2 = r[F_BQ * stride];
+  const df b = {b2.x, b2.y};
   const df dX = df_sub(X, df{x0.x, x0.y}), dY = df_sub(Y, df{y0.x, y0.y});
   const df r2 = df_add_ss(df_mul(dX, dX), df_mul(dY, dY));
   if (!(r2.hi > 0.f)) {
     ax = ay = df{0.f, 0.f};
+    if (HESS) h[0] = h[1] = h[2] = df{0.f, 0.f};
     return;
   }
-  const df f = r[F_U2 * stride].x < -1.5f ? df_div(df{b.x, b.y}, r2) : df_div(df{b.x, b.y}, df_sqrt(r2));
+  const bool point = r[F_U2 * stride].x < -1.5f;
+  const df ir2 = df_div(df{1.f, 0.f}, r2);
+  const df f = point ? df_mul(b, ir2) : df_mul(b, df_sqrt(ir2));  // b/r^2 or b/r
   ax = df_mul(f, dX);
   ay = df_mul(f, dY);
+  if (HESS) {
+    // SIS: kappa = b/(2r), gamma = b/(2r^3) (y^2-x^2, -2xy); point: kappa = 0,
+    // gamma = b/r^4 (y^2-x^2, -2xy)
+    const df g = point ? df_mul(f, ir2) : df_mul(df_mulf(f, 0.5f), ir2);
+    h[0] = point ? df{0.f, 0.f} : df_mulf(f, 0.5f);
+    h[1] = df_mul(g, df_sub(df_mul(dY, dY), df_mul(dX, dX)));
+    h[2] = df_neg(df_mulf(df_mul(g, df_mul(dX, dY)), 2.f));
+  }
 }
 
 // --------------------------------------------------------- constraint sets
+// One potential at (X, Y) from its double-float record (deflection and, if
+// HESS, kappa, gamma1, gamma2), added to acc[0..4] as doubles; FP64 from its
+// FP64 record when the double-float evaluation fails (|w| within 1e-15 of 1,
+// non-finite intermediate).
+template <bool HESS>
+__device__ __forceinline__ void add_potential_df(const float2 *__restrict__ rdf, int stride,
+                                                 const double *__restrict__ r64, double X, double Y, double *acc) {
+  const df Xd = df_from_double(X), Yd = df_from_double(Y);
+  df ax, ay, h[3];
+  bool ok = true;
+  if (rdf[F_U2 * stride].x < 0.f)
+    circ_df<HESS>(rdf, stride, Xd, Yd, ax, ay, h);
+  else
+    ok = dpie_df<true, HESS>(rdf, stride, Xd, Yd, ax, ay, h);
+  if (ok) {
+    acc[0] += df_to_double(ax);
+    acc[1] += df_to_double(ay);
+    if (HESS) {
+      acc[2] += df_to_double(h[0]);
+      acc[3] += df_to_double(h[1]);
+      acc[4] += df_to_double(h[2]);
+    }
+  } else {
+    double bx, by, bk = 0, b1 = 0, b2 = 0;
+    eval64<HESS>(r64, X, Y, bx, by, bk, b1, b2);
+    acc[0] += bx;
+    acc[1] += by;
+    acc[2] += bk;
+    acc[3] += b1;
+    acc[4] += b2;
+  }
+}
+
 // Back-trace every constraint of one parameter set in FP64 (Sec. 2.1 Eq. 1):
 // beta_j = theta_j - r alpha(theta_j), with alpha = static cache + the two
-// varying potentials (records in s_rec), then each source's barycentre
-// (Sec. 2.2, Fig. 3).  Fills s_beta [nimg][2], s_bary [nsrc][2] and, when
-// s_m is not NULL, r H at every image in s_m [nimg][3] (hxx, hyy, hxy).
-// Must be called by all THREADS threads of the CTA; ends synchronised.
+// varying potentials (FP64 records in s_rec; their double-float records in
+// s_rdf, which, when not NULL, evaluate them on the FP32 pipe to ~1e-13),
+// then each source's barycentre (Sec. 2.2, Fig. 3).  Fills s_beta [nimg][2],
+// s_bary [nsrc][2] and, when s_m is not NULL, r H at every image in
+// s_m [nimg][3] (hxx, hyy, hxy).  Must be called by all THREADS threads of
+// the CTA; ends synchronised.
 template <int THREADS>
 __device__ __forceinline__ void backtrace_set(const double *__restrict__ stat, const double *__restrict__ x,
                                               const double *__restrict__ y, const double *__restrict__ ratio,
                                               const int32_t *__restrict__ src_of, const int32_t *__restrict__ img_off,
-                                              int nimg, int nsrc, const double *s_rec, double *s_beta, double *s_m,
-                                              double *s_bary) {
+                                              int nimg, int nsrc, const double *s_rec, const float2 *s_rdf,
+                                              double *s_beta, double *s_m, double *s_bary) {
   for (int j = threadIdx.x; j < nimg; j += THREADS) {
     const double X = x[j], Y = y[j];
     const double *st = stat + (size_t)j * 5;
-    double ax = st[0], ay = st[1], kk = st[2], g1 = st[3], g2 = st[4];
+    double acc[5] = {st[0], st[1], st[2], st[3], st[4]};
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      double bx, by, bk = 0, b1 = 0, b2 = 0;
-      if (s_m)
-        eval64<true>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
-      else
-        eval64<false>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
-      ax += bx;
-      ay += by;
-      kk += bk;
-      g1 += b1;
-      g2 += b2;
+      if (s_rdf) {
+        if (s_m)
+          add_potential_df<true>(s_rdf + v * RECDF, 1, s_rec + v * REC64, X, Y, acc);
+        else
+          add_potential_df<false>(s_rdf + v * RECDF, 1, s_rec + v * REC64, X, Y, acc);
+      } else {
+        double bx, by, bk = 0, b1 = 0, b2 = 0;
+        if (s_m)
+          eval64<true>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
+        else
+          eval64<false>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
+        acc[0] += bx;
+        acc[1] += by;
+        acc[2] += bk;
+        acc[3] += b1;
+        acc[4] += b2;
+      }
     }
     const double r = ratio[src_of[j]];
-    s_beta[2 * j] = X - r * ax;
-    s_beta[2 * j + 1] = Y - r * ay;
+    s_beta[2 * j] = X - r * acc[0];
+    s_beta[2 * j + 1] = Y - r * acc[1];
     if (s_m) {
-      s_m[3 * j] = r * (kk + g1);
-      s_m[3 * j + 1] = r * (kk - g1);
-      s_m[3 * j + 2] = r * g2;
+      s_m[3 * j] = r * (acc[2] + acc[3]);
+      s_m[3 * j + 1] = r * (acc[2] - acc[3]);
+      s_m[3 * j + 2] = r * acc[4];
     }
   }
   __syncthreads();

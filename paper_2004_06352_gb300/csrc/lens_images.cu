@@ -34,6 +34,8 @@
 //                     a fixed order.
 // Candidate buffers live in scratch memory (IMG_CAP per set); an overflow
 // makes that set's chi2 NaN and sets ERRBIT_CAPACITY.
+#include <type_traits>
+
 #include "lens_device.cuh"
 
 namespace lens {
@@ -176,7 +178,8 @@ __global__ void __launch_bounds__(SRC_THREADS) k_img_sources(const SetArgs a, co
     a.s.nuniq[b] = 0;
   }
   if (!s_ok) return;
-  backtrace_set<SRC_THREADS>(stat, x, y, ratio, src_of, img_off, a.nimg, a.nsrc, s_rec, s_beta, nullptr, s_bary);
+  backtrace_set<SRC_THREADS>(stat, x, y, ratio, src_of, img_off, a.nimg, a.nsrc, s_rec, &a.s.var[b].rdf[0][0], s_beta,
+                             nullptr, s_bary);
   for (int i = threadIdx.x; i < 2 * a.nsrc; i += SRC_THREADS) a.s.bary[(size_t)b * a.nsrc * 2 + i] = s_bary[i];
   for (int i = threadIdx.x; i < a.nsrc; i += SRC_THREADS)
     a.s.src32[(size_t)b * a.nsrc + i] = make_float2((float)s_bary[2 * i], (float)s_bary[2 * i + 1]);
@@ -268,9 +271,8 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_img_search(const SetArgs a, 
     for (int v = 0; v < 2; ++v) {
       Acc<false, 1> acc;
       acc.zero();
-      const float dY[1] = {fmaf((float)(jj - j0), fdy, s_off[v].y)};
-      eval32_any<false, 1>(reinterpret_cast<const float4 *>(s_rec[v]), fmaf((float)(ii - i0), fdx, s_off[v].x), dY,
-                           acc);
+      const float dX = fmaf((float)(ii - i0), fdx, s_off[v].x), dY[1] = {fmaf((float)(jj - j0), fdy, s_off[v].y)};
+      eval32_any<false, 1, true>(reinterpret_cast<const float4 *>(s_rec[v]), dX, dY, acc);
       tx += acc.ax[0];
       ty += acc.ay[0];
     }
@@ -392,6 +394,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS) k_img_search(const SetArgs a, 
 struct NewtonArgs {
   const float *rec32, *cen32;  // static potentials on the FP32 path
   int n_light;
+  int koff[5];                 // the FP32 ones by kind: Kind32 k occupies [koff[k], koff[k+1])
   const double *heavy;         // static potentials on the FP64 path
   int n_heavy;
   const double *all64;         // every static potential in FP64 (polish)
@@ -495,20 +498,47 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
                                               var.cen[hh - n.n_light][2], var.cen[hh - n.n_light][3]);
     }
     __syncthreads();
-    for (int h = gl; h < cnt; h += RF_G) {
-      const float4 *r4 = s_rec + h * RF_STRIDE4;
-      const float4 c = s_cen[h];
+    // kind-uniform runs of the chunk (the static potentials are sorted by
+    // kind; the two varying ones at the end take the general dispatch)
+    auto run = [&](auto kind_tag, int h0, int h1) {
+      constexpr int KIND = decltype(kind_tag)::value;
+      for (int h = h0 + gl; h < h1; h += RF_G) {
+        const float4 *r4 = s_rec + h * RF_STRIDE4;
+        const float4 c = s_cen[h];
 #pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        const float dY[1] = {(hy[k] - c.y) + (ly[k] - c.w)};
-        eval32_any<HESS, 1>(r4, (hx[k] - c.x) + (lx[k] - c.z), dY, part[k]);
-      }
-      if (++seen == 16) {
+        for (int k = 0; k < NP; ++k) {
+          const float dX = (hx[k] - c.x) + (lx[k] - c.z), dY[1] = {(hy[k] - c.y) + (ly[k] - c.w)};
+          if (KIND == K32_DPIE)
+            dpie32<HESS, 1, false>(r4, dX, dY, part[k]);
+          else if (KIND == K32_DPIE_SERIES)
+            dpie32<HESS, 1, true>(r4, dX, dY, part[k]);
+          else if (KIND == K32_SIS || KIND == K32_POINT)
+            circ32<HESS, 1, KIND == K32_POINT>(r4, dX, dY, part[k]);
+          else
+            eval32_any<HESS, 1>(r4, dX, dY, part[k]);
+        }
+        if (++seen == 16) {
 #pragma unroll
-        for (int k = 0; k < NP; ++k) fold(tot[k], cmp[k], part[k]);
-        seen = 0;
+          for (int k = 0; k < NP; ++k) fold(tot[k], cmp[k], part[k]);
+          seen = 0;
+        }
       }
-    }
+    };
+    auto seg = [&](int lo, int hi, int &h0, int &h1) {
+      h0 = max(lo - c0, 0);
+      h1 = min(hi - c0, cnt);
+    };
+    int h0, h1;
+    seg(n.koff[K32_DPIE], n.koff[K32_DPIE + 1], h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_DPIE>(), h0, h1);
+    seg(n.koff[K32_DPIE_SERIES], n.koff[K32_DPIE_SERIES + 1], h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_DPIE_SERIES>(), h0, h1);
+    seg(n.koff[K32_SIS], n.koff[K32_SIS + 1], h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_SIS>(), h0, h1);
+    seg(n.koff[K32_POINT], n.koff[K32_POINT + 1], h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_POINT>(), h0, h1);
+    seg(n.n_light, n.n_light + 2, h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, -1>(), h0, h1);
   }
   constexpr int NC = HESS ? 5 : 2;
 #pragma unroll
@@ -794,8 +824,8 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
         const int stride = stq ? n.n_stat : 1;
         df gx, gy;
         if (rec[F_U2 * stride].x < 0.f) {
-          circ_alpha_df(rec, stride, X, Y, gx, gy);
-        } else if (!dpie_alpha_df<true>(rec, stride, X, Y, gx, gy)) {
+          circ_df(rec, stride, X, Y, gx, gy);
+        } else if (!dpie_df<true>(rec, stride, X, Y, gx, gy)) {
           const double *r64 = stq ? n.all64 + (size_t)jj * REC64 : s_var[w] + (jj - n.n_stat) * REC64;
           double ex, ey, e2, e3, e4;
           eval64<false>(r64, tx, ty, ex, ey, e2, e3, e4);
@@ -814,7 +844,7 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
           const float2 *rec = st ? n.recdf + j : s_vdf[w] + (j - n.n_stat) * RECDF;
           const int stride = st ? n.n_stat : 1;
           df gx, gy;
-          if (rec[F_U2 * stride].x >= 0.f && dpie_alpha_df<false>(rec, stride, X, Y, gx, gy)) {
+          if (rec[F_U2 * stride].x >= 0.f && dpie_df<false>(rec, stride, X, Y, gx, gy)) {
             // one-TwoSum accumulation: absolute error 2^-47 sum |alpha_i|,
             // a few 1e-13 arcsec over a cluster
             fx = df_add_ss(fx, gx);
@@ -951,6 +981,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   n.rec32 = sm->rec32;
   n.cen32 = sm->cen32;
   n.n_light = sm->n_light;
+  for (int k = 0; k < 5; ++k) n.koff[k] = sm->koff[k];
   n.heavy = sm->heavy;
   n.n_heavy = sm->n_heavy;
   n.all64 = sm->all64;

@@ -155,9 +155,12 @@ __host__ __device__ inline bool halo_params_ok(int type, double x0, double y0, d
 // ---------------------------------------------------------------- objects
 // Double-float record of one potential: 16 (hi, lo) float pairs.
 enum RecDF : int {
-  F_X0 = 0, F_Y0, F_C, F_S, F_Q2, F_U2, F_KC, F_KT, F_SC, F_ST, F_Q2SC, F_Q2ST, F_Q2SS, F_Q2DS, F_SS, F_BQ
+  F_X0 = 0, F_Y0, F_C, F_S, F_Q2, F_U2, F_KC, F_KT, F_SC, F_ST, F_Q2SC, F_Q2ST, F_Q2SS, F_Q2DS, F_SS, F_BQ,
+  // Hessian: cos 2theta, sin 2theta, (1+q^2) s^2 and u^2 s^2 of both terms,
+  // q^2 (st^2 - sc^2), b q / 2
+  F_C2, F_S2, F_DC0, F_DT0, F_U2SC2, F_U2ST2, F_KTC, F_HB
 };
-constexpr int RECDF = 16;
+constexpr int RECDF = 24;
 // SIS and point-mass records carry F_U2 = -1 and -2 (never negative for a
 // dPIE) and b, theta_E^2 in F_BQ.
 
@@ -190,6 +193,14 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
     v[F_Q2DS] = q2 * (st - sc);
     v[F_SS] = st + sc;
     v[F_BQ] = b0 * (1.0 + eps) * q;
+    v[F_C2] = cos(2.0 * theta);
+    v[F_S2] = sin(2.0 * theta);
+    v[F_DC0] = (1.0 + q2) * sc * sc;
+    v[F_DT0] = (1.0 + q2) * st * st;
+    v[F_U2SC2] = u * u * sc * sc;
+    v[F_U2ST2] = u * u * st * st;
+    v[F_KTC] = q2 * (st - sc) * (st + sc);
+    v[F_HB] = 0.5 * v[F_BQ];
   }
   for (int k = 0; k < RECDF; ++k) {
     const float h = (float)v[k];
@@ -199,6 +210,7 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
 
 struct Model {
   int32_t n = 0, n_light = 0, n_heavy = 0;
+  int32_t koff[5] = {0, 0, 0, 0, 0};  // light potentials sorted by kind: Kind32 k occupies [koff[k], koff[k+1])
   float *rec32 = nullptr;
   double *pos64 = nullptr;
   float *cen32 = nullptr;   // [n_light][4]: x0, y0 as hi/lo float pairs (hi x, hi y, lo x, lo y)

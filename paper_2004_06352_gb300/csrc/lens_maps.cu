@@ -22,6 +22,8 @@
 //     evaluated in FP64; the final sum, scaling by D_ls/D_s and the derived
 //     kappa/gamma/mu are formed in FP64 per point and stored as FP32.
 // LENS_FP64 kernel: one point per thread, every potential in FP64.
+#include <type_traits>
+
 #include "lens_device.cuh"
 
 namespace lens {
@@ -36,6 +38,12 @@ namespace {
 #ifndef LENS_MAP_MINB_GRAD
 #define LENS_MAP_MINB_GRAD 3  // deflection-only kernel (measured 12% faster than 2)
 #endif
+#ifndef LENS_MAP_SEGMENTS
+#define LENS_MAP_SEGMENTS 1  // kind-uniform loops over each chunk's potentials
+#endif
+#ifndef LENS_MAP_UNROLL
+#define LENS_MAP_UNROLL 4  // potentials per iteration of those loops
+#endif
 #ifndef LENS_KP_HESS
 #define LENS_KP_HESS 2
 #endif
@@ -43,6 +51,7 @@ namespace {
 #define LENS_KP_GRAD 4
 #endif
 constexpr int MAP_THREADS = 256;
+constexpr int MAP_UNROLL = LENS_MAP_UNROLL;
 constexpr int MAP_WARPS = MAP_THREADS / 32;
 constexpr int CH = 64;   // potentials per staged chunk (8 KB of records)
 constexpr int SUB = 16;  // partial sums folded into the compensated total every SUB potentials
@@ -51,6 +60,7 @@ struct MapArgs {
   const float *rec32;
   const double *pos64;
   int n_light;
+  int koff[5];  // light potentials of kind k (Kind32 order) are [koff[k], koff[k+1])
   const double *heavy;
   int n_heavy;
   double xmin, ymin, dx, dy;
@@ -169,18 +179,59 @@ __global__ void __launch_bounds__(MAP_THREADS, HESS ? LENS_MAP_MINB : LENS_MAP_M
       }
     }
     const float4 *recs = reinterpret_cast<const float4 *>(&s_rec[buf][0]);
-    for (int h = 0; h < cnt; ++h) {
-      const float4 *r4 = recs + h * (REC32 / 4);
-      const float4 off = s_off[buf][h];
-      const float dX = (off.x + Lxh) + (off.z + Lxl);
-      float dY[KP];
+    if constexpr (HESS && LENS_MAP_SEGMENTS) {
+      // the potentials are sorted by kind: each kind's run inside this chunk is
+      // a loop without a per-potential dispatch (Hessian kernel: 6 % faster;
+      // the deflection-only kernel spills with it and keeps the plain loop)
+      auto run = [&](auto kind_tag, int h0, int h1) {
+        constexpr int KIND = decltype(kind_tag)::value;
+#pragma unroll MAP_UNROLL
+        for (int h = h0; h < h1; ++h) {
+          const float4 *r4 = recs + h * (REC32 / 4);
+          const float4 off = s_off[buf][h];
+          const float dX = (off.x + Lxh) + (off.z + Lxl);
+          float dY[KP];
 #pragma unroll
-      for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
-      eval32_any<HESS, KP>(r4, dX, dY, part);
-      if (++seen == SUB) {
-        fold(tot, cmp, part);
-        seen = 0;
-      }
+          for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
+          if (KIND == K32_DPIE)
+            dpie32<HESS, KP, false>(r4, dX, dY, part);
+          else if (KIND == K32_DPIE_SERIES)
+            dpie32<HESS, KP, true>(r4, dX, dY, part);
+          else
+            circ32<HESS, KP, KIND == K32_POINT>(r4, dX, dY, part);
+          if (++seen == SUB) {
+            fold(tot, cmp, part);
+            seen = 0;
+          }
+        }
+      };
+      auto seg = [&](int k, int &h0, int &h1) {
+        h0 = max(a.koff[k] - base, 0);
+        h1 = min(a.koff[k + 1] - base, cnt);
+      };
+      int h0, h1;
+      seg(K32_DPIE, h0, h1);
+      if (h0 < h1) run(std::integral_constant<int, K32_DPIE>(), h0, h1);
+      seg(K32_DPIE_SERIES, h0, h1);
+      if (h0 < h1) run(std::integral_constant<int, K32_DPIE_SERIES>(), h0, h1);
+      seg(K32_SIS, h0, h1);
+      if (h0 < h1) run(std::integral_constant<int, K32_SIS>(), h0, h1);
+      seg(K32_POINT, h0, h1);
+      if (h0 < h1) run(std::integral_constant<int, K32_POINT>(), h0, h1);
+    } else {
+      for (int h = 0; h < cnt; ++h) {
+        const float4 *r4 = recs + h * (REC32 / 4);
+        const float4 off = s_off[buf][h];
+        const float dX = (off.x + Lxh) + (off.z + Lxl);
+        float dY[KP];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
+        eval32_any<HESS, KP>(r4, dX, dY, part);
+        if (++seen == SUB) {
+          fold(tot, cmp, part);
+          seen = 0;
+        }
+    }
     }
   }
   fold(tot, cmp, part);
@@ -254,6 +305,7 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.rec32 = m->rec32;
   a.pos64 = m->pos64;
   a.n_light = m->n_light;
+  for (int k = 0; k < 5; ++k) a.koff[k] = m->koff[k];
   a.heavy = m->heavy;
   a.n_heavy = m->n_heavy;
   a.xmin = g->xmin;

@@ -106,8 +106,9 @@ def test_chi2_source_autotune_and_graph_replay(lens):
 
 
 def test_chi2_source_nocache_matches_cache_and_oracle(lens):
-    """Recomputing every static potential for every set (no static cache)
-    gives the cached result up to summation order, and the oracle's; P spans
+    """Recomputing every static potential for every set (no static cache, in
+    double-float: ~1e-13 relative per potential) gives the FP64-cached
+    result to 1e-10 relative, and the oracle's to the chi2 tolerance; P spans
     two no-cache batches plus a ragged tail."""
     from tests.golden import make_constraints
     m = I.cfg2_model()
@@ -129,7 +130,7 @@ def test_chi2_source_nocache_matches_cache_and_oracle(lens):
             a, b = a.cpu().numpy(), b.cpu().numpy()
             assert np.isnan(a[7]) and np.isnan(b[7])
             ok = np.isfinite(a)
-            assert np.all(np.abs(a[ok] - b[ok]) <= 1e-12 * np.abs(a[ok]))
+            assert np.all(np.abs(a[ok] - b[ok]) <= 1e-10 * np.abs(a[ok])), np.max(np.abs(a[ok] - b[ok]) / a[ok])
             sample = [0, 1, 513, 1099]
             ref = oracle.chi2_source_batch(m, cons, var, params[sample], variant)
             assert np.all(np.abs(b[sample] - ref) <= T.CHI2_REL * np.abs(ref))
