@@ -332,13 +332,13 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
                          "ms_default_shape": t_default, "autotuned_shape": cfg, "graph_replay": True,
                          "workload": "source-plane chi2, 4096 parameter sets, 1000 potentials"}
     # the same without the static cache: every potential at every image for
-    # every set (FP64), the per-model cost when any potential may vary
+    # every set (double-float), the per-model cost when any potential may vary
     t = timed(lambda: ctx.chi2_source_nocache(cs, params, P, 0, chi2, stream), 1)
     nimg = int(cons["img_off"][-1])
     ex["chi2_source_nocache"] = {"ms": t, "models_per_s": P / (t * 1e-3), "P": P,
                                  "pair_per_s": nimg * (N_HALO - 2) * P / (t * 1e-3),
                                  "workload": "source-plane chi2 without the static cache, 4096 sets x 372 images "
-                                             "x 1000 potentials, FP64 with Hessian"}
+                                             "x 1000 potentials, double-float with Hessian"}
     Pi = 256
     gi = I.grid(1024)
     chi2i = torch.empty(Pi, dtype=torch.float64, device=dev)

@@ -41,6 +41,9 @@ namespace {
 #ifndef LENS_MAP_SEGMENTS
 #define LENS_MAP_SEGMENTS 1  // kind-uniform loops over each chunk's potentials
 #endif
+#ifndef LENS_MAP_SEGMENTS_GRAD
+#define LENS_MAP_SEGMENTS_GRAD 0  // the same in the deflection-only kernel (spills at 3 CTAs/SM)
+#endif
 #ifndef LENS_MAP_UNROLL
 #define LENS_MAP_UNROLL 4  // potentials per iteration of those loops
 #endif
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(MAP_THREADS, HESS ? LENS_MAP_MINB : LENS_MAP_M
       }
     }
     const float4 *recs = reinterpret_cast<const float4 *>(&s_rec[buf][0]);
-    if constexpr (HESS && LENS_MAP_SEGMENTS) {
+    if constexpr (HESS ? LENS_MAP_SEGMENTS : LENS_MAP_SEGMENTS_GRAD) {
       // the potentials are sorted by kind: each kind's run inside this chunk is
       // a loop without a per-potential dispatch (Hessian kernel: 6 % faster;
       // the deflection-only kernel spills with it and keeps the plain loop)
