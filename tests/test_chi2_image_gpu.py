@@ -253,3 +253,28 @@ def test_chi2_image_static_sis_and_point_mass(lens):
     got, nf = gpu_chi2_image(lens, m, cons, (0, 1), g, params)
     assert got[0] < 1e-12, got
     assert list(nf[0]) == [off[i + 1] - off[i] for i in range(3)]
+
+
+def test_find_images_truncates_to_capacity(lens):
+    """d_count holds every set's number of images; only the first max_per_set
+    are written, and they are among the images of an uncapped call."""
+    m = np.vstack([I.halo_row(I.DPIE, 0.3, -0.2, 0.5, 0.3, 1.5, 300.0, 12.0),
+                   I.halo_row(I.DPIE, -2.0, 1.0, 1.1, 0.2, 0.8, 150.0, 6.0),
+                   I.member_model(8, seed=46, field=30)])
+    g = I.grid(121, field=(-40, 40, -40, 40))
+    cons = I.constraints_dict([0, 1, 2, 3], [0.4, -0.6, 1.2], [0.3, 0.2, -0.9], [0.1, 0.1, 0.1], [0.7, 0.9, 0.8])
+    params = I.perturbed_params(m, (0, 1), 3, seed=47)
+    with lens.Context(0) as ctx:
+        cs = ctx.cset_create(ctx.model_upload(m), cons, (0, 1))
+        full = gpu_images(ctx, cs, g, params, max_per_set=64)
+        P = len(params)
+        imgs = torch.full((P, 3, 3), -9.0, dtype=torch.float64, device=DEV)
+        cnt = torch.empty(P, dtype=torch.int32, device=DEV)
+        ctx.find_images(cs, g, torch.tensor(params, device=DEV), P, imgs, cnt)
+        ctx.wait()
+        imgs, cnt = imgs.cpu().numpy(), cnt.cpu().numpy()
+    for p in range(P):
+        assert cnt[p] == len(full[p]) > 3
+        for row in imgs[p]:
+            same_src = full[p][full[p][:, 2] == row[2]]
+            assert len(same_src) and np.min(np.hypot(same_src[:, 0] - row[0], same_src[:, 1] - row[1])) < 1e-9, (p, row)
