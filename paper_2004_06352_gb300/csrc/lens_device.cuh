@@ -428,7 +428,8 @@ __device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, float 
 
 // ------------------------------------------------------------ double-float
 // An unevaluated sum hi + lo of two floats (~48 significant bits) on the FP32
-// pipe, for the image polish: GB300's FP64 rate is 1/64 of its FP32 rate.
+// pipe, for the image polish and the chi2 potentials: GB300's FP64 rate is
+// 1/64 of its FP32 rate.
 // Error-free transformations: TwoSum (Knuth), FastTwoSum and the product
 // error by FMA; compound operations as in Dekker (1971).
 struct df {
