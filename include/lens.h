@@ -152,6 +152,20 @@ int lens_grad_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, doub
 int lens_hessian_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
                      void *d_out, void *stream);
 
+/* The same maps written to page-locked HOST memory h_out ([2 or 6][ny][nx],
+ * float for LENS_MIXED, double for LENS_FP64, from cudaHostAlloc or
+ * cudaHostRegister; LENS_EINVAL otherwise).  The grid is computed in about 8
+ * row bands on two streams of the context and each band is copied to the
+ * host as soon as it is done, so the copy overlaps the rest of the map; the
+ * values equal those of lens_grad_map / lens_hessian_map.  Asynchronous:
+ * h_out is complete when `stream` reaches this point.  Uses two device band
+ * buffers owned by the context (counted in lens_mem_used); calls on streams
+ * that are not ordered with each other must not overlap. */
+int lens_grad_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                       void *h_out, void *stream);
+int lens_hessian_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds,
+                          int32_t precision, void *h_out, void *stream);
+
 /* ----------------------------------------------------------- chi2 batches */
 
 /* Bind a constraint table to a model for batched chi2 evaluation.

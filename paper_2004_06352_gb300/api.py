@@ -23,7 +23,8 @@ LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
-           "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_cset_create", "lens_cset_release",
+           "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_grad_map_host", "lens_hessian_map_host",
+           "lens_cset_create", "lens_cset_release",
            "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_autotune", "lens_chi2_image",
            "lens_find_images", "lens_chi2_image_noalloc", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
@@ -83,6 +84,8 @@ def load_library(path=LIB_PATH):
         "lens_model_release": (C.c_int, [vp, i64]),
         "lens_grad_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
         "lens_hessian_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
+        "lens_grad_map_host": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
+        "lens_hessian_map_host": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
         "lens_cset_create": (C.c_int, [vp, i64, C.POINTER(lens_constraints), C.POINTER(C.c_int32), C.POINTER(i64)]),
         "lens_cset_release": (C.c_int, [vp, i64]),
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
@@ -135,11 +138,21 @@ def make_grid(g):
     return lens_grid(g["xmin"], g["xmax"], g["ymin"], g["ymax"], g["nx"], g["ny"])
 
 
+# lens_halo as a numpy record: int32 type, 4 bytes of padding, 7 doubles
+_HALO_DTYPE = np.dtype({"names": ["type", "x0", "y0", "theta", "eps", "rcore", "rcut", "b0"],
+                        "formats": ["<i4"] + ["<f8"] * 7,
+                        "offsets": [0, 8, 16, 24, 32, 40, 48, 56], "itemsize": 64})
+assert _HALO_DTYPE.itemsize == C.sizeof(lens_halo)
+
+
 def halos_from_table(table):
+    """Halo table rows (type, x0, y0, theta, eps, rcore, rcut, b0) as a
+    contiguous lens_halo array (numpy record array with the C layout)."""
     t = np.asarray(table, dtype=np.float64).reshape(-1, 8)
-    arr = (lens_halo * len(t))()
-    for k, r in enumerate(t):
-        arr[k] = lens_halo(int(r[0]), *map(float, r[1:]))
+    arr = np.zeros(len(t), dtype=_HALO_DTYPE)
+    arr["type"] = t[:, 0].astype(np.int32)
+    for k, name in enumerate(_HALO_DTYPE.names[1:], start=1):
+        arr[name] = t[:, k]
     return arr
 
 
@@ -176,7 +189,8 @@ class Context:
     def model_upload(self, table):
         arr = halos_from_table(table)
         out = C.c_int64()
-        _check(_lib.lens_model_upload(self.h, arr, len(arr), C.byref(out)), "lens_model_upload")
+        _check(_lib.lens_model_upload(self.h, arr.ctypes.data_as(C.POINTER(lens_halo)), len(arr), C.byref(out)),
+               "lens_model_upload")
         return out.value
 
     def model_release(self, model):
@@ -192,6 +206,21 @@ class Context:
         g = make_grid(grid)
         _check(_lib.lens_hessian_map(self.h, int(model), C.byref(g), float(dls_ds), int(precision), _ptr(out),
                                      _stream(stream)), "lens_hessian_map")
+        return out
+
+    def grad_map_host(self, model, grid, dls_ds, precision, out, stream=None):
+        """Deflection map into page-locked host memory `out` (e.g. a torch
+        tensor with pin_memory=True), band by band as the GPU finishes."""
+        g = make_grid(grid)
+        _check(_lib.lens_grad_map_host(self.h, int(model), C.byref(g), float(dls_ds), int(precision), _ptr(out),
+                                       _stream(stream)), "lens_grad_map_host")
+        return out
+
+    def hessian_map_host(self, model, grid, dls_ds, precision, out, stream=None):
+        """Six-plane Hessian map into page-locked host memory `out`."""
+        g = make_grid(grid)
+        _check(_lib.lens_hessian_map_host(self.h, int(model), C.byref(g), float(dls_ds), int(precision),
+                                          _ptr(out), _stream(stream)), "lens_hessian_map_host")
         return out
 
     def cset_create(self, model, cons, var_halo):

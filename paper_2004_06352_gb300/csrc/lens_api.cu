@@ -90,12 +90,7 @@ static int kind_order(const lens_halo &h) {
 }
 
 void free_model(lens_ctx *ctx, Model *m) {
-  dev_free(ctx, m->rec32, (size_t)m->n_light * REC32 * sizeof(float));
-  dev_free(ctx, m->pos64, (size_t)m->n_light * 4 * sizeof(double));
-  dev_free(ctx, m->cen32, (size_t)m->n_light * 4 * sizeof(float));
-  dev_free(ctx, m->heavy, (size_t)m->n_heavy * REC64 * sizeof(double));
-  dev_free(ctx, m->all64, (size_t)m->n * REC64 * sizeof(double));
-  dev_free(ctx, m->recdf, (size_t)m->n * RECDF * sizeof(float2));
+  dev_free(ctx, m->block, m->bytes);
   delete m;
 }
 
@@ -143,23 +138,33 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
     make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
     make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &adf[k], n);
   }
-  int rc = LENS_OK;
-  size_t b32 = r32.size() * sizeof(float), bp = p64.size() * sizeof(double), bc = c32.size() * sizeof(float),
-         bh = hv.size() * sizeof(double), ba = a64.size() * sizeof(double), bd = adf.size() * sizeof(float2);
-  if ((rc = dev_alloc(ctx, (void **)&m->rec32, b32)) || (rc = dev_alloc(ctx, (void **)&m->pos64, bp)) ||
-      (rc = dev_alloc(ctx, (void **)&m->cen32, bc)) || (rc = dev_alloc(ctx, (void **)&m->heavy, bh)) ||
-      (rc = dev_alloc(ctx, (void **)&m->all64, ba)) || (rc = dev_alloc(ctx, (void **)&m->recdf, bd))) {
-    free_model(ctx, m);
+  // one device block (one allocation, one copy) holding every array at
+  // 256-byte aligned offsets
+  const size_t sizes[6] = {r32.size() * sizeof(float), p64.size() * sizeof(double), c32.size() * sizeof(float),
+                           hv.size() * sizeof(double), a64.size() * sizeof(double), adf.size() * sizeof(float2)};
+  const void *srcs[6] = {r32.data(), p64.data(), c32.data(), hv.data(), a64.data(), adf.data()};
+  size_t offs[6], total = 0;
+  for (int k = 0; k < 6; ++k) {
+    offs[k] = total;
+    total += (sizes[k] + 255) & ~(size_t)255;
+  }
+  std::vector<unsigned char> img(total, 0);
+  for (int k = 0; k < 6; ++k)
+    if (sizes[k]) std::memcpy(img.data() + offs[k], srcs[k], sizes[k]);
+  int rc = dev_alloc(ctx, &m->block, total);
+  if (rc) {
+    delete m;
     return rc;
   }
-  m->bytes = b32 + bp + bc + bh + ba + bd;
-  cudaError_t e = cudaSuccess;
-  if (b32) e = cudaMemcpy(m->rec32, r32.data(), b32, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bp) e = cudaMemcpy(m->pos64, p64.data(), bp, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bc) e = cudaMemcpy(m->cen32, c32.data(), bc, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bh) e = cudaMemcpy(m->heavy, hv.data(), bh, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && ba) e = cudaMemcpy(m->all64, a64.data(), ba, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bd) e = cudaMemcpy(m->recdf, adf.data(), bd, cudaMemcpyHostToDevice);
+  m->bytes = total;
+  char *base = (char *)m->block;
+  m->rec32 = (float *)(base + offs[0]);
+  m->pos64 = (double *)(base + offs[1]);
+  m->cen32 = (float *)(base + offs[2]);
+  m->heavy = (double *)(base + offs[3]);
+  m->all64 = (double *)(base + offs[4]);
+  m->recdf = (float2 *)(base + offs[5]);
+  const cudaError_t e = total ? cudaMemcpy(m->block, img.data(), total, cudaMemcpyHostToDevice) : cudaSuccess;
   if (e != cudaSuccess) {
     free_model(ctx, m);
     return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));
@@ -234,7 +239,15 @@ int lens_destroy(lens_ctx *ctx) {
   for (auto &p : ctx->csets) free_cset(ctx, p.second);
   for (auto &p : ctx->models) free_model(ctx, p.second);
   dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
+  dev_free(ctx, ctx->band, ctx->band_bytes);
   dev_free(ctx, ctx->d_err, sizeof(int));
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->pipe_cs[k]) cudaStreamDestroy(ctx->pipe_cs[k]);
+    if (ctx->pipe_done[k]) cudaEventDestroy(ctx->pipe_done[k]);
+    if (ctx->pipe_copied[k]) cudaEventDestroy(ctx->pipe_copied[k]);
+  }
+  if (ctx->pipe_cp) cudaStreamDestroy(ctx->pipe_cp);
+  if (ctx->pipe_start) cudaEventDestroy(ctx->pipe_start);
   delete ctx;
   return LENS_OK;
 }
@@ -306,6 +319,90 @@ static int map_common(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, 
   if (precision == LENS_MIXED) return launch_map_mixed(ctx, m, grid, dls_ds, hess, d_out, st);
   if (precision == LENS_FP64) return launch_map_fp64(ctx, m, grid, dls_ds, hess, d_out, st);
   return fail(LENS_EINVAL, "precision must be LENS_FP64 or LENS_MIXED");
+}
+
+// Map straight to page-locked host memory: the grid in row bands computed
+// on two streams of the context (so one band's tail overlaps the next band)
+// into two device buffers, each band copied to the host on a third stream as
+// soon as it is done; `stream` waits for the last copies.  The bands are
+// whole multiples of the kernel's tile height, so every value is the one
+// lens_*_map would give.
+static int map_host_common(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds,
+                           int32_t precision, void *h_out, void *stream, bool hess) {
+  if (!ctx || !h_out) return fail(LENS_EINVAL, "NULL argument");
+  Model *m = find_model(ctx, model);
+  if (!m) return fail(LENS_ENOTFOUND, "model %lld not found", (long long)model);
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (!(std::isfinite(dls_ds) && dls_ds > 0.0)) return fail(LENS_EINVAL, "dls_ds must be finite and > 0");
+  if (precision != LENS_MIXED && precision != LENS_FP64)
+    return fail(LENS_EINVAL, "precision must be LENS_FP64 or LENS_MIXED");
+  cudaSetDevice(ctx->device);
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, h_out) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return fail(LENS_EINVAL, "h_out must be page-locked host memory (cudaHostAlloc or cudaHostRegister)");
+  }
+  const size_t esize = precision == LENS_FP64 ? 8 : 4;
+  if ((uintptr_t)h_out % esize) return fail(LENS_EINVAL, "h_out must be aligned to its element size");
+  const int planes = hess ? 6 : 2, nx = grid->nx, ny = grid->ny;
+  // about 8 bands, each a whole number of tiles
+  const int tile = map_tile_rows(hess);
+  int rows = (ny + 7) / 8;
+  rows = std::max(tile, (rows + tile - 1) / tile * tile);
+  const size_t band_bytes = (size_t)rows * nx * planes * esize;
+  if (ctx->band_bytes < 2 * band_bytes) {
+    if (ctx->band) {
+      cudaDeviceSynchronize();
+      dev_free(ctx, ctx->band, ctx->band_bytes);
+      ctx->band = nullptr;
+      ctx->band_bytes = 0;
+    }
+    if ((rc = dev_alloc(ctx, &ctx->band, 2 * band_bytes))) return rc;
+    ctx->band_bytes = 2 * band_bytes;
+  }
+  if (!ctx->pipe_cp) {
+    for (int k = 0; k < 2; ++k) {
+      LENS_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->pipe_cs[k], cudaStreamNonBlocking));
+      LENS_CUDA_TRY(cudaEventCreateWithFlags(&ctx->pipe_done[k], cudaEventDisableTiming));
+      LENS_CUDA_TRY(cudaEventCreateWithFlags(&ctx->pipe_copied[k], cudaEventDisableTiming));
+    }
+    LENS_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->pipe_cp, cudaStreamNonBlocking));
+    LENS_CUDA_TRY(cudaEventCreateWithFlags(&ctx->pipe_start, cudaEventDisableTiming));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  LENS_CUDA_TRY(cudaEventRecord(ctx->pipe_start, st));
+  for (int k = 0; k < 2; ++k) LENS_CUDA_TRY(cudaStreamWaitEvent(ctx->pipe_cs[k], ctx->pipe_start, 0));
+  char *host = (char *)h_out;
+  const size_t host_plane = (size_t)nx * ny * esize;
+  for (int row0 = 0, b = 0; row0 < ny; row0 += rows, ++b) {
+    const int r = std::min(rows, ny - row0), k = b & 1;
+    char *buf = (char *)ctx->band + k * band_bytes;
+    cudaStream_t cs = ctx->pipe_cs[k];
+    // the buffer's previous band (this call's or an earlier call's) has left
+    LENS_CUDA_TRY(cudaStreamWaitEvent(cs, ctx->pipe_copied[k], 0));
+    rc = precision == LENS_MIXED ? launch_map_mixed(ctx, m, grid, dls_ds, hess, buf, cs, row0, r)
+                                 : launch_map_fp64(ctx, m, grid, dls_ds, hess, buf, cs, row0, r);
+    if (rc) return rc;
+    LENS_CUDA_TRY(cudaEventRecord(ctx->pipe_done[k], cs));
+    LENS_CUDA_TRY(cudaStreamWaitEvent(ctx->pipe_cp, ctx->pipe_done[k], 0));
+    // band [planes][r][nx] -> host [planes][ny][nx] at row row0
+    LENS_CUDA_TRY(cudaMemcpy2DAsync(host + (size_t)row0 * nx * esize, host_plane, buf, (size_t)r * nx * esize,
+                                    (size_t)r * nx * esize, planes, cudaMemcpyDeviceToHost, ctx->pipe_cp));
+    LENS_CUDA_TRY(cudaEventRecord(ctx->pipe_copied[k], ctx->pipe_cp));
+  }
+  for (int k = 0; k < 2; ++k) LENS_CUDA_TRY(cudaStreamWaitEvent(st, ctx->pipe_copied[k], 0));
+  return LENS_OK;
+}
+
+int lens_grad_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                       void *h_out, void *stream) {
+  return map_host_common(ctx, model, grid, dls_ds, precision, h_out, stream, false);
+}
+
+int lens_hessian_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds,
+                          int32_t precision, void *h_out, void *stream) {
+  return map_host_common(ctx, model, grid, dls_ds, precision, h_out, stream, true);
 }
 
 int lens_grad_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,

@@ -209,6 +209,7 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
 }
 
 struct Model {
+  void *block = nullptr;    // one device allocation holding every array below
   int32_t n = 0, n_light = 0, n_heavy = 0;
   int32_t koff[5] = {0, 0, 0, 0, 0};  // light potentials sorted by kind: Kind32 k occupies [koff[k], koff[k+1])
   float *rec32 = nullptr;
@@ -262,6 +263,12 @@ struct lens_ctx {
   int *d_err = nullptr;          // device-side error word (bounded waits)
   void *scratch = nullptr;       // growable scratch for chi2 image search
   size_t scratch_bytes = 0;
+  // maps streamed to host memory: two device row-band buffers, two compute
+  // streams and a copy stream (created on first use)
+  void *band = nullptr;
+  size_t band_bytes = 0;
+  cudaStream_t pipe_cs[2] = {nullptr, nullptr}, pipe_cp = nullptr;
+  cudaEvent_t pipe_start = nullptr, pipe_done[2] = {nullptr, nullptr}, pipe_copied[2] = {nullptr, nullptr};
 };
 
 namespace lens {
@@ -285,10 +292,13 @@ void free_model(lens_ctx *ctx, Model *m);
 int check_grid(const lens_grid *g);
 
 // Kernel launchers (lens_maps.cu / lens_chi2.cu).
+// Maps of grid rows [row0, row0 + rows) (rows < 0: to the last row) into
+// out[planes][rows][nx]; the positions are those of the full grid.
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                     cudaStream_t st);
+                     cudaStream_t st, int row0 = 0, int rows = -1);
 int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                    cudaStream_t st);
+                    cudaStream_t st, int row0 = 0, int rows = -1);
+int map_tile_rows(bool hess);  // rows per CTA tile of the mixed map kernel
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);

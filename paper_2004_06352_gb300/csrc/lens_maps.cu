@@ -67,9 +67,10 @@ struct MapArgs {
   const double *heavy;
   int n_heavy;
   double xmin, ymin, dx, dy;
-  int nx, ny;
+  int nx, ny;   // ny: rows computed by this launch
+  int row0;     // grid row of the launch's first row (row bands of one grid)
   double dls;
-  float *out;
+  float *out;   // [planes][ny][nx] for the launch's rows
   long long plane;
   int *err;
 };
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(MAP_THREADS, HESS ? LENS_MAP_MINB : LENS_MAP_M
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * (MAP_WARPS * KP);
-  const double Tx = a.xmin + i0 * a.dx, Ty = a.ymin + j0 * a.dy;
+  const double Tx = a.xmin + i0 * a.dx, Ty = a.ymin + (a.row0 + j0) * a.dy;
   // the point's offset inside the tile as a hi/lo float pair: (hi_off + hi_L)
   // is exact when the point is near the potential's centre (Sterbenz), so
   // dX, dY keep full relative precision where the profile is steepest
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(MAP_THREADS, HESS ? LENS_MAP_MINB : LENS_MAP_M
     const double X = a.xmin + (i0 + lane) * a.dx;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
-      const double Y = a.ymin + (j0 + warp * KP + k) * a.dy;
+      const double Y = a.ymin + (a.row0 + j0 + warp * KP + k) * a.dy;
       double v[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) v[c] = 0.0;
@@ -271,12 +272,12 @@ __global__ void __launch_bounds__(MAP_THREADS, HESS ? LENS_MAP_MINB : LENS_MAP_M
 
 template <bool HESS>
 __global__ void __launch_bounds__(256) k_map_fp64(const double *__restrict__ all64, int n, double xmin, double ymin,
-                                                  double dx, double dy, int nx, int ny, double dls,
+                                                  double dx, double dy, int nx, int row0, double dls,
                                                   double *__restrict__ out, long long plane) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= plane) return;
   const int i = (int)(p % nx), j = (int)(p / nx);
-  const double X = xmin + i * dx, Y = ymin + j * dy;
+  const double X = xmin + i * dx, Y = ymin + (row0 + j) * dy;
   double AX = 0, AY = 0, KA = 0, G1 = 0, G2 = 0;
   for (int h = 0; h < n; ++h) {
     double ax, ay, kk = 0, q1 = 0, q2 = 0;
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(256) k_map_fp64(const double *__restrict__ all
 }  // namespace
 
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                     cudaStream_t st) {
+                     cudaStream_t st, int row0, int rows) {
+  if (rows < 0) rows = g->ny - row0;
   MapArgs a;
   a.rec32 = m->rec32;
   a.pos64 = m->pos64;
@@ -316,17 +318,18 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.dx = (g->xmax - g->xmin) / (g->nx - 1);
   a.dy = (g->ymax - g->ymin) / (g->ny - 1);
   a.nx = g->nx;
-  a.ny = g->ny;
+  a.ny = rows;
+  a.row0 = row0;
   a.dls = dls;
   a.out = (float *)out;
-  a.plane = (long long)g->nx * g->ny;
+  a.plane = (long long)g->nx * rows;
   a.err = ctx->d_err;
   constexpr int KPG = LENS_KP_GRAD, KPH = LENS_KP_HESS;
   if (hess) {
-    dim3 grid((g->nx + 31) / 32, (g->ny + MAP_WARPS * KPH - 1) / (MAP_WARPS * KPH));
+    dim3 grid((g->nx + 31) / 32, (rows + MAP_WARPS * KPH - 1) / (MAP_WARPS * KPH));
     k_map_mixed<true, KPH><<<grid, MAP_THREADS, 0, st>>>(a);
   } else {
-    dim3 grid((g->nx + 31) / 32, (g->ny + MAP_WARPS * KPG - 1) / (MAP_WARPS * KPG));
+    dim3 grid((g->nx + 31) / 32, (rows + MAP_WARPS * KPG - 1) / (MAP_WARPS * KPG));
     k_map_mixed<false, KPG><<<grid, MAP_THREADS, 0, st>>>(a);
   }
   cudaError_t e = cudaGetLastError();
@@ -334,20 +337,23 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   return LENS_OK;
 }
 
+int map_tile_rows(bool hess) { return MAP_WARPS * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
+
 int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                    cudaStream_t st) {
+                    cudaStream_t st, int row0, int rows) {
   (void)ctx;
-  const long long plane = (long long)g->nx * g->ny;
+  if (rows < 0) rows = g->ny - row0;
+  const long long plane = (long long)g->nx * rows;
   const double dx = (g->xmax - g->xmin) / (g->nx - 1), dy = (g->ymax - g->ymin) / (g->ny - 1);
   const unsigned blocks = (unsigned)((plane + 255) / 256);
   if (hess)
-    k_map_fp64<true><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, g->ny, dls,
+    k_map_fp64<true><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, row0, dls,
                                               (double *)out, plane);
   else
-    k_map_fp64<false><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, g->ny, dls,
+    k_map_fp64<false><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, row0, dls,
                                                (double *)out, plane);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(LENS_ECUDA, "map kernel launch: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "FP64 map kernel launch: %s", cudaGetErrorString(e));
   return LENS_OK;
 }
 

@@ -157,3 +157,27 @@ def test_memory_budget_admission(lens):
         with pytest.raises(lens.LensError) as e:
             ctx.model_upload(I.random_model(2000, seed=3))
         assert e.value.code == lens.LENS_ENOMEM
+
+
+@pytest.mark.parametrize("hess", [True, False])
+def test_map_to_host_equals_device_map(lens, hess):
+    """lens_*_map_host (row bands streamed to pinned host memory) gives the
+    device map's values bit for bit, on a grid whose rows are not a multiple
+    of the band, in both precisions; pageable memory is rejected."""
+    m = I.random_model(40, seed=81, types=(I.DPIE, I.DPIE, I.SIS, I.POINT))
+    m[0, 7] = 20.0  # one potential on the FP64 path
+    g = I.grid(97, field=(-60, 60, -50, 50), ny=203)
+    planes = 6 if hess else 2
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        for prec, dt in ((lens.LENS_MIXED, torch.float32), (lens.LENS_FP64, torch.float64)):
+            dev = torch.empty((planes, g["ny"], g["nx"]), dtype=dt, device=DEV)
+            host = torch.full((planes, g["ny"], g["nx"]), float("nan"), dtype=dt, pin_memory=True)
+            (ctx.hessian_map if hess else ctx.grad_map)(mid, g, 0.9, prec, dev)
+            (ctx.hessian_map_host if hess else ctx.grad_map_host)(mid, g, 0.9, prec, host)
+            ctx.wait()
+            assert torch.equal(host, dev.cpu())
+        pageable = torch.empty((planes, g["ny"], g["nx"]), dtype=torch.float32)
+        with pytest.raises(lens.LensError) as e:
+            (ctx.hessian_map_host if hess else ctx.grad_map_host)(mid, g, 0.9, lens.LENS_MIXED, pageable)
+        assert e.value.code == lens.LENS_EINVAL
