@@ -183,18 +183,21 @@ int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
  * then var_halo[1] -- d_params is DEVICE double [P][14].  For every image
  * beta = theta - r alpha(theta) (Sec. 2.1, Eq. 1), the source estimate is the
  * barycentre of its images, and d_chi2[p] (DEVICE double [P]) receives the
- * variant's sum.  All arithmetic in FP64.  A parameter set outside the dPIE
- * domain yields NaN. */
+ * variant's sum.  The static potentials' cache is FP64; the two varying
+ * potentials are evaluated in double-float (pairs of floats, ~1e-13 relative;
+ * FP64 where that fails); the back-trace, barycentres and sums are FP64.  A
+ * parameter set outside the dPIE domain yields NaN. */
 int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                      double *d_chi2, void *stream);
 
-/* lens_chi2_source without the static cache: the FP64 deflection and
- * Hessian of every static potential at every image are recomputed for every
- * parameter set (batches of 512 sets in the context's scratch memory), as in
- * the paper's fit, which evaluates every potential for every model (Sec. 2.2,
- * Sec. 4.2).  Same arguments, results and errors as lens_chi2_source; the
- * per-set cost is N potentials x images instead of 2 x images.  Grows the
- * context's scratch to 512 x images x 40 bytes (LENS_ENOMEM over budget). */
+/* lens_chi2_source without the static cache: the deflection and Hessian of
+ * every static potential at every image are recomputed for every parameter
+ * set (double-float, summed in FP64; batches of 512 sets in the context's
+ * scratch memory), as in the paper's fit, which evaluates every potential for
+ * every model (Sec. 2.2, Sec. 4.2).  Same arguments, results (to ~1e-10
+ * relative) and errors as lens_chi2_source; the per-set cost is N potentials
+ * x images instead of 2 x images.  Grows the context's scratch to 512 x
+ * images x 40 bytes (LENS_ENOMEM over budget). */
 int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                              double *d_chi2, void *stream);
 
