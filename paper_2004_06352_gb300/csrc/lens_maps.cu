@@ -33,16 +33,16 @@ namespace {
 // register budget targets, and points per thread of the Hessian and
 // deflection-only kernels.
 #ifndef LENS_MAP_MINB
-#define LENS_MAP_MINB 2     // Hessian kernel
+#define LENS_MAP_MINB 4     // Hessian kernel (128-thread CTAs)
 #endif
 #ifndef LENS_MAP_MINB_GRAD
-#define LENS_MAP_MINB_GRAD 3  // deflection-only kernel (measured 12% faster than 2)
+#define LENS_MAP_MINB_GRAD 6  // deflection-only kernel (128-thread CTAs)
 #endif
 #ifndef LENS_MAP_SEGMENTS
 #define LENS_MAP_SEGMENTS 1  // kind-uniform loops over each chunk's potentials
 #endif
 #ifndef LENS_MAP_SEGMENTS_GRAD
-#define LENS_MAP_SEGMENTS_GRAD 0  // the same in the deflection-only kernel (spills at 3 CTAs/SM)
+#define LENS_MAP_SEGMENTS_GRAD 0  // the same in the deflection-only kernel (measured slower: it spills)
 #endif
 #ifndef LENS_MAP_UNROLL
 #define LENS_MAP_UNROLL 4  // potentials per iteration of those loops
@@ -53,9 +53,19 @@ namespace {
 #ifndef LENS_KP_GRAD
 #define LENS_KP_GRAD 4
 #endif
-constexpr int MAP_THREADS = 256;
+// threads per CTA, one warp per KP rows of the tile (128 measured 3 % faster
+// than 256 for both kernels at the same warps per SM, 64 slower)
+#ifndef LENS_MAP_THREADS_HESS
+#define LENS_MAP_THREADS_HESS 128
+#endif
+#ifndef LENS_MAP_THREADS_GRAD
+#define LENS_MAP_THREADS_GRAD 128
+#endif
+__host__ __device__ constexpr int map_threads(bool hess) { return hess ? LENS_MAP_THREADS_HESS : LENS_MAP_THREADS_GRAD; }
+static_assert(map_threads(true) >= 64 && map_threads(false) >= 64 && map_threads(true) % 32 == 0 &&
+                  map_threads(false) % 32 == 0,
+              "the chunk staging uses 64 threads");
 constexpr int MAP_UNROLL = LENS_MAP_UNROLL;
-constexpr int MAP_WARPS = MAP_THREADS / 32;
 constexpr int CH = 64;   // potentials per staged chunk (8 KB of records)
 constexpr int SUB = 16;  // partial sums folded into the compensated total every SUB potentials
 
@@ -76,7 +86,9 @@ struct MapArgs {
 };
 
 template <bool HESS, int KP>
-__global__ void __launch_bounds__(MAP_THREADS, HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD) k_map_mixed(const MapArgs a) {
+__global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD)
+    k_map_mixed(const MapArgs a) {
+  constexpr int MAP_THREADS = map_threads(HESS), MAP_WARPS = MAP_THREADS / 32;
   __shared__ __align__(128) float s_rec[2][CH * REC32];
   __shared__ float4 s_off[2][CH];  // hi.x, hi.y, lo.x, lo.y of (Tx - x0, Ty - y0)
   __shared__ __align__(8) uint64_t s_bar[2];
@@ -303,6 +315,8 @@ __global__ void __launch_bounds__(256) k_map_fp64(const double *__restrict__ all
 
 }  // namespace
 
+int map_tile_rows(bool hess) { return map_threads(hess) / 32 * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
+
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
                      cudaStream_t st, int row0, int rows) {
   if (rows < 0) rows = g->ny - row0;
@@ -326,18 +340,19 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.err = ctx->d_err;
   constexpr int KPG = LENS_KP_GRAD, KPH = LENS_KP_HESS;
   if (hess) {
-    dim3 grid((g->nx + 31) / 32, (rows + MAP_WARPS * KPH - 1) / (MAP_WARPS * KPH));
-    k_map_mixed<true, KPH><<<grid, MAP_THREADS, 0, st>>>(a);
+    const int th = map_tile_rows(true);
+    dim3 grid((g->nx + 31) / 32, (rows + th - 1) / th);
+    k_map_mixed<true, KPH><<<grid, map_threads(true), 0, st>>>(a);
   } else {
-    dim3 grid((g->nx + 31) / 32, (rows + MAP_WARPS * KPG - 1) / (MAP_WARPS * KPG));
-    k_map_mixed<false, KPG><<<grid, MAP_THREADS, 0, st>>>(a);
+    const int th = map_tile_rows(false);
+    dim3 grid((g->nx + 31) / 32, (rows + th - 1) / th);
+    k_map_mixed<false, KPG><<<grid, map_threads(false), 0, st>>>(a);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "map kernel launch: %s", cudaGetErrorString(e));
   return LENS_OK;
 }
 
-int map_tile_rows(bool hess) { return MAP_WARPS * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
 
 int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
                     cudaStream_t st, int row0, int rows) {
