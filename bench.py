@@ -37,7 +37,7 @@ MUFU_OPS_PER_PAIR = 6.03
 # DRAM bytes (read + write) of one launch of that kernel on that workload,
 # from the same ncu capture; the 100.7 MB of output are partly still in L2
 # when the kernel ends
-MAP_TRAFFIC_BYTES = 523520 + 40169728
+MAP_TRAFFIC_BYTES = 880128 + 40267264
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 
 
