@@ -45,7 +45,7 @@ namespace {
 #define LENS_MAP_SEGMENTS_GRAD 0  // the same in the deflection-only kernel (measured slower: it spills)
 #endif
 #ifndef LENS_MAP_UNROLL
-#define LENS_MAP_UNROLL 4  // potentials per iteration of those loops
+#define LENS_MAP_UNROLL 2  // potentials per iteration of those loops (2: 0.6 % faster than 4 at 128 threads)
 #endif
 #ifndef LENS_KP_HESS
 #define LENS_KP_HESS 2
