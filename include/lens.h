@@ -315,6 +315,14 @@ int lens_server_stats(const lens_server *s, lens_server_info *info);
 
 /* --------------------------------------------------------------- control */
 
+/* Exercises the device-side failure path (no counterpart in the paper): a
+ * one-thread kernel waits on an mbarrier that nothing completes, gives up
+ * after `polls` (1..2^20) tries as every bounded wait of the library does,
+ * and sets the context's error flag, so the next lens_wait returns
+ * LENS_ETIMEOUT (and clears it).  Asynchronous on `stream`; nothing faults
+ * and the context stays usable. */
+int lens_selftest_wait(lens_ctx *ctx, int32_t polls, void *stream);
+
 /* Wait until all work enqueued on `stream` has finished, polling without
  * blocking the thread for more than timeout_ms (>= 0) milliseconds.
  * LENS_ETIMEOUT if it has not finished by then (the work keeps running). */

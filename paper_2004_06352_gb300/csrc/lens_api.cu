@@ -596,6 +596,13 @@ int lens_find_images(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, con
                            max_per_set, d_count);
 }
 
+int lens_selftest_wait(lens_ctx *ctx, int32_t polls, void *stream) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  if (polls < 1 || polls > (1 << 20)) return fail(LENS_EINVAL, "polls must be in 1..2^20");
+  cudaSetDevice(ctx->device);
+  return launch_wait_selftest(ctx, (unsigned)polls, (cudaStream_t)stream);
+}
+
 int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms) {
   if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
   if (timeout_ms < 0) return fail(LENS_EINVAL, "timeout_ms must be >= 0");

@@ -313,7 +313,26 @@ __global__ void __launch_bounds__(256) k_map_fp64(const double *__restrict__ all
   }
 }
 
+// The bounded-wait failure path on its own: one thread waits on an mbarrier
+// that nothing completes, gives up after `polls` tries, and reports it the way
+// the map kernel would (ERRBIT_WAIT in the context's error word).
+__global__ void k_wait_selftest(int *err, unsigned polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait_bounded(&bar, 0, polls)) atomicOr(err, ERRBIT_WAIT);
+  }
+}
+
 }  // namespace
+
+int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(ctx->d_err, polls);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "self-test launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
 
 int map_tile_rows(bool hess) { return map_threads(hess) / 32 * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
 
