@@ -257,11 +257,12 @@ int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const lens_grid *gr
 
 /* ---------------------------------------------------------- request loop */
 /* A server runs map and chi2 requests of uneven sizes on `slots` CUDA
- * streams of its own, admitting queued requests (in arrival order; a request
- * that does not fit may be overtaken by smaller ones until it has waited 64
- * rounds) whenever a slot is free and its device buffers fit in the server's
- * pool -- one allocation of pool_bytes made at creation and counted against
- * the context budget.  Work of different slots overlaps on the device; each
+ * streams of its own, admitting queued requests whenever a slot is free and
+ * their device buffers fit in the server's pool -- one allocation of
+ * pool_bytes made at creation and counted against the context budget.  The
+ * order is shortest expected GPU time first, less the time already waited (a
+ * large request waits at most about its own run time); a request that does
+ * not fit may be overtaken until it has been passed over 64 times.  Work of different slots overlaps on the device; each
  * request runs the same kernels as the direct calls on its own buffers, so
  * its result does not depend on what else is in flight.  Models and
  * constraint sets stay resident in the context.  Not part of the paper's
