@@ -152,3 +152,31 @@ def test_poisson_stream_driver(lens):
         for t, b in bufs.items():
             assert np.all(np.isfinite(b.numpy()))
         srv.close()
+
+
+def test_short_requests_go_first(lens):
+    """With one slot and everything queued before the first progress call,
+    requests run shortest expected work first: a 2048^2 x 300-potential map
+    submitted first finishes after the small chi2 batches queued behind it."""
+    with lens.Context(0) as ctx:
+        m = I.cfg2_model(seed=9, n_members=298)
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, I.random_constraints(10, seed=10, field=40), (0, 1))
+        srv = lens.Server(ctx, slots=1, pool_bytes=256 << 20)
+        big = pinned((6, 2048, 2048), torch.float32)
+        t_big = srv.submit_map(mid, I.grid(2048), 1.0, lens.LENS_MIXED, True, big)
+        small = []
+        for k in range(3):
+            buf = pinned((32,), torch.float64)
+            small.append((srv.submit_chi2_source(cs, I.perturbed_params(m, (0, 1), 32, seed=11 + k), 0, buf), buf))
+        order = []
+        for _ in range(200000):
+            for t, st, q, l in srv.progress():
+                assert st == 0
+                order.append(t)
+            if len(order) == 4:
+                break
+        assert order[-1] == t_big, order
+        assert sorted(order[:3]) == sorted(t for t, _ in small)
+        assert np.all(np.isfinite(big.numpy()[:5]))
+        srv.close()
