@@ -122,8 +122,13 @@ int lens_destroy(lens_ctx *ctx);
  * maps (default 5 arcsec).  Applies to models uploaded afterwards. */
 int lens_set_fp64_threshold(lens_ctx *ctx, double threshold_b0);
 
-/* Device bytes currently held by the context. */
+/* Device bytes currently held by the context (including released model
+ * blocks kept for reuse by later uploads; those are freed first when an
+ * allocation would exceed the budget). */
 size_t lens_mem_used(const lens_ctx *ctx);
+/* Bytes of device records of an uploaded model (what lens_model_upload
+ * copied to the device); 0 for an unknown model. */
+size_t lens_model_bytes(lens_ctx *ctx, lens_model_t model);
 
 /* ------------------------------------------------------------------ models */
 

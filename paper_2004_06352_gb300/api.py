@@ -22,7 +22,8 @@ LENS_FP64, LENS_MIXED = 0, 1
 LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test suite).
-EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_upload",
+EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_bytes",
+           "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
            "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_autotune", "lens_chi2_image",
@@ -80,6 +81,7 @@ def load_library(path=LIB_PATH):
         "lens_destroy": (C.c_int, [vp]),
         "lens_set_fp64_threshold": (C.c_int, [vp, C.c_double]),
         "lens_mem_used": (C.c_size_t, [vp]),
+        "lens_model_bytes": (C.c_size_t, [vp, i64]),
         "lens_model_upload": (C.c_int, [vp, C.POINTER(lens_halo), C.c_int32, C.POINTER(i64)]),
         "lens_model_release": (C.c_int, [vp, i64]),
         "lens_grad_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
@@ -186,6 +188,9 @@ class Context:
 
     def mem_used(self):
         return int(_lib.lens_mem_used(self.h))
+
+    def model_bytes(self, model):
+        return int(_lib.lens_model_bytes(self.h, int(model)))
 
     def model_upload(self, table):
         arr = halos_from_table(table)

@@ -42,6 +42,15 @@ CSet *find_cset(lens_ctx *ctx, lens_cset_t id) {
 int dev_alloc(lens_ctx *ctx, void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return LENS_OK;
+  if (ctx->budget && ctx->used + bytes > ctx->budget && !ctx->block_cache.empty()) {
+    // cached model blocks go first
+    for (auto &b : ctx->block_cache) {
+      cudaFree(b.first);
+      ctx->used -= std::min(ctx->used, b.second);
+    }
+    ctx->block_cache.clear();
+    ctx->cached_bytes = 0;
+  }
   if (ctx->budget && ctx->used + bytes > ctx->budget)
     return fail(LENS_ENOMEM, "device memory budget exceeded: %zu used + %zu requested > %zu", ctx->used, bytes,
                 ctx->budget);
@@ -89,12 +98,50 @@ static int kind_order(const lens_halo &h) {
   return u < U_SERIES32 ? 1 : 0;
 }
 
+// Released model blocks are kept (up to BLOCK_CACHE_MAX bytes) and reused by
+// later uploads of similar size: repeated upload/release then costs no
+// cudaMalloc/cudaFree.  They stay counted in the context's memory use and are
+// freed when an allocation would exceed the budget.
+static constexpr size_t BLOCK_CACHE_MAX = 64u << 20;
+
+static void flush_block_cache(lens_ctx *ctx) {
+  for (auto &b : ctx->block_cache) dev_free(ctx, b.first, b.second);
+  ctx->block_cache.clear();
+  ctx->cached_bytes = 0;
+}
+
 void free_model(lens_ctx *ctx, Model *m) {
-  dev_free(ctx, m->block, m->bytes);
+  if (m->block && ctx->cached_bytes + m->bytes <= BLOCK_CACHE_MAX) {
+    ctx->block_cache.push_back({m->block, m->bytes});
+    ctx->cached_bytes += m->bytes;
+  } else {
+    dev_free(ctx, m->block, m->bytes);
+  }
   delete m;
 }
 
-// Device store of n (already validated) potentials; n may be 0.
+// A device block of at least `bytes`: the smallest cached one that is not
+// more than twice as large, else a new allocation.
+static int model_block(lens_ctx *ctx, size_t bytes, void **p, size_t *got) {
+  int best = -1;
+  for (int k = 0; k < (int)ctx->block_cache.size(); ++k) {
+    const size_t b = ctx->block_cache[k].second;
+    if (b >= bytes && b <= 2 * bytes && (best < 0 || b < ctx->block_cache[best].second)) best = k;
+  }
+  if (best >= 0) {
+    *p = ctx->block_cache[best].first;
+    *got = ctx->block_cache[best].second;
+    ctx->cached_bytes -= *got;
+    ctx->block_cache.erase(ctx->block_cache.begin() + best);
+    return LENS_OK;
+  }
+  *got = bytes;
+  return dev_alloc(ctx, p, bytes);
+}
+
+// Device store of n (already validated) potentials; n may be 0.  The record
+// arrays are built in one page-locked host image (256-byte aligned offsets)
+// and copied into one device block with one copy.
 int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   Model *m = new Model();
   m->n = n;
@@ -112,9 +159,41 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
     m->koff[k] = c;
   }
   m->koff[4] = m->n_light;
-  std::vector<float> r32((size_t)m->n_light * REC32), c32((size_t)m->n_light * 4);
-  std::vector<double> p64((size_t)m->n_light * 4), hv((size_t)m->n_heavy * REC64), a64((size_t)n * REC64);
-  std::vector<float2> adf((size_t)n * RECDF);
+  const size_t nl = (size_t)m->n_light, nh = (size_t)m->n_heavy, na = (size_t)n;
+  const size_t sizes[6] = {nl * REC32 * sizeof(float), nl * 4 * sizeof(double), nl * 4 * sizeof(float),
+                           nh * REC64 * sizeof(double), na * REC64 * sizeof(double), na * RECDF * sizeof(float2)};
+  size_t offs[6], total = 0;
+  for (int k = 0; k < 6; ++k) {
+    offs[k] = total;
+    total += (sizes[k] + 255) & ~(size_t)255;
+  }
+  // host image: the context's page-locked staging buffer (pageable if that
+  // cannot be had)
+  std::vector<unsigned char> pageable;
+  unsigned char *img = nullptr;
+  if (ctx->h_stage_bytes < total) {
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    ctx->h_stage = nullptr;
+    ctx->h_stage_bytes = 0;
+    if (cudaHostAlloc(&ctx->h_stage, total, cudaHostAllocDefault) == cudaSuccess) {
+      ctx->h_stage_bytes = total;
+    } else {
+      cudaGetLastError();
+      ctx->h_stage = nullptr;
+    }
+  }
+  if (ctx->h_stage) {
+    img = (unsigned char *)ctx->h_stage;
+  } else {
+    pageable.resize(total);
+    img = pageable.data();
+  }
+  std::memset(img, 0, total);
+  float *r32 = (float *)(img + offs[0]);
+  double *p64 = (double *)(img + offs[1]);
+  float *c32 = (float *)(img + offs[2]);
+  double *hv = (double *)(img + offs[3]), *a64 = (double *)(img + offs[4]);
+  float2 *adf = (float2 *)(img + offs[5]);
   for (int32_t k = 0; k < m->n_light; ++k) {
     const lens_halo &a = h[light[k]];
     make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, &r32[(size_t)k * REC32]);
@@ -138,25 +217,16 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
     make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
     make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &adf[k], n);
   }
-  // one device block (one allocation, one copy) holding every array at
-  // 256-byte aligned offsets
-  const size_t sizes[6] = {r32.size() * sizeof(float), p64.size() * sizeof(double), c32.size() * sizeof(float),
-                           hv.size() * sizeof(double), a64.size() * sizeof(double), adf.size() * sizeof(float2)};
-  const void *srcs[6] = {r32.data(), p64.data(), c32.data(), hv.data(), a64.data(), adf.data()};
-  size_t offs[6], total = 0;
-  for (int k = 0; k < 6; ++k) {
-    offs[k] = total;
-    total += (sizes[k] + 255) & ~(size_t)255;
+  int rc = total ? model_block(ctx, total, &m->block, &m->bytes) : LENS_OK;
+  if (rc == LENS_ENOMEM && !ctx->block_cache.empty()) {
+    flush_block_cache(ctx);
+    rc = model_block(ctx, total, &m->block, &m->bytes);
   }
-  std::vector<unsigned char> img(total, 0);
-  for (int k = 0; k < 6; ++k)
-    if (sizes[k]) std::memcpy(img.data() + offs[k], srcs[k], sizes[k]);
-  int rc = dev_alloc(ctx, &m->block, total);
   if (rc) {
     delete m;
     return rc;
   }
-  m->bytes = total;
+  m->payload = total;
   char *base = (char *)m->block;
   m->rec32 = (float *)(base + offs[0]);
   m->pos64 = (double *)(base + offs[1]);
@@ -164,7 +234,7 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->heavy = (double *)(base + offs[3]);
   m->all64 = (double *)(base + offs[4]);
   m->recdf = (float2 *)(base + offs[5]);
-  const cudaError_t e = total ? cudaMemcpy(m->block, img.data(), total, cudaMemcpyHostToDevice) : cudaSuccess;
+  const cudaError_t e = total ? cudaMemcpy(m->block, img, total, cudaMemcpyHostToDevice) : cudaSuccess;
   if (e != cudaSuccess) {
     free_model(ctx, m);
     return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));
@@ -238,6 +308,8 @@ int lens_destroy(lens_ctx *ctx) {
   cudaDeviceSynchronize();
   for (auto &p : ctx->csets) free_cset(ctx, p.second);
   for (auto &p : ctx->models) free_model(ctx, p.second);
+  flush_block_cache(ctx);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
   dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
   dev_free(ctx, ctx->band, ctx->band_bytes);
   dev_free(ctx, ctx->d_err, sizeof(int));
@@ -260,6 +332,11 @@ int lens_set_fp64_threshold(lens_ctx *ctx, double t) {
 }
 
 size_t lens_mem_used(const lens_ctx *ctx) { return ctx ? ctx->used : 0; }
+
+size_t lens_model_bytes(lens_ctx *ctx, lens_model_t model) {
+  const Model *m = ctx ? find_model(ctx, model) : nullptr;
+  return m ? m->payload : 0;
+}
 
 int lens_model_upload(lens_ctx *ctx, const lens_halo *h, int32_t n, lens_model_t *out) {
   if (!ctx || !h || !out) return fail(LENS_EINVAL, "NULL argument");
@@ -627,7 +704,11 @@ int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms) {
       cudaEventDestroy(ev);
       return fail(LENS_ETIMEOUT, "stream work not finished after %lld ms", (long long)timeout_ms);
     }
-    std::this_thread::sleep_for(std::chrono::microseconds(50));
+    // short polls first (most waits end within a kernel's tail), then back off
+    if (ms < 2)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(ms < 50 ? 10 : 100));
   }
   cudaEventDestroy(ev);
   int flag = 0;

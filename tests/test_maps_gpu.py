@@ -181,3 +181,32 @@ def test_map_to_host_equals_device_map(lens, hess):
         with pytest.raises(lens.LensError) as e:
             (ctx.hessian_map_host if hess else ctx.grad_map_host)(mid, g, 0.9, lens.LENS_MIXED, pageable)
         assert e.value.code == lens.LENS_EINVAL
+
+
+def test_model_blocks_are_reused_and_yield_to_the_budget(lens):
+    """A released model's device block serves the next upload of similar
+    size (no growth of the context's memory, same maps as a fresh context);
+    kept blocks are freed when an upload would exceed the budget."""
+    a, b = I.random_model(300, seed=12), I.random_model(290, seed=13)  # b fits in a's block
+    g = I.grid(40, field=(-60, 60, -60, 60))
+    with lens.Context(0) as ctx:
+        ma = ctx.model_upload(a)
+        nbytes = ctx.model_bytes(ma)
+        assert nbytes > 300 * 400
+        used = ctx.mem_used()
+        ctx.model_release(ma)
+        mb = ctx.model_upload(b)
+        assert ctx.mem_used() == used
+        out = torch.empty((6, 40, 40), device=DEV)
+        ctx.hessian_map(mb, g, 1.0, lens.LENS_MIXED, out)
+        ctx.wait()
+    with lens.Context(0) as fresh:
+        ref = torch.empty((6, 40, 40), device=DEV)
+        fresh.hessian_map(fresh.model_upload(b), g, 1.0, lens.LENS_MIXED, ref)
+        fresh.wait()
+    assert torch.equal(out, ref)
+    with lens.Context(0, mem_budget_bytes=3 * nbytes // 2) as ctx:
+        ctx.model_release(ctx.model_upload(a))      # kept for reuse
+        big = I.random_model(420, seed=14)          # too big to reuse, fits once the kept block goes
+        mid = ctx.model_upload(big)
+        assert ctx.model_bytes(mid) > nbytes
