@@ -1,5 +1,6 @@
 """Coefficients of the polynomials for atan(w)/w and atanh(w)/w in t = w^2 on
-[0, T] used by lens_device.cuh: FP32 (atan_over_w / atanh_over_w, degree 5)
+[0, T] used by lens_device.cuh: FP32 (atan_over_w / atanh_over_w, degree 4
+by default, 5 as a build option)
 and FP64 (atan_over_w64 / atanh_over_w64, degree 11; also split into float
 hi/lo pairs for the double-float evaluator), and the tables of the FP64
 atan/atanh argument reduction (atan64 / atanh64).
@@ -10,13 +11,13 @@ by solving the interpolation conditions in the monomial basis with 60-digit
 mpmath arithmetic (the float64 conversion would lose digits).  Prints the
 coefficients and the worst relative error on a dense grid.
 
-  python paper_2004_06352_gb300/csrc/fit_series.py
+  python paper_2004_06352_gb300/csrc/fit_series.py [FP32 degree]
 """
 import numpy as np
 from numpy.polynomial import chebyshev as Ch
 from numpy.polynomial import polynomial as Pn
 
-T, DEG = 0.16, 5
+T, DEG = 0.16, 4
 
 
 def f_atan(t):
@@ -74,6 +75,9 @@ def reduction_tables(step="0.8", kmax=22):
 
 
 if __name__ == "__main__":
+    import sys
+    if len(sys.argv) > 1:
+        DEG = int(sys.argv[1])
     tt = np.linspace(0, T, 200001)
     t32 = tt.astype(np.float32).astype(np.float64)
     for name, f in (("atan", f_atan), ("atanh", f_atanh)):

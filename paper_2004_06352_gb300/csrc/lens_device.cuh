@@ -272,27 +272,48 @@ __device__ __forceinline__ void fold(Acc<HESS, KP> &tot, Acc<HESS, KP> &cmp, Acc
   part.zero();
 }
 
-// atan(w)/w and atanh(w)/w as degree-5 polynomials in t = w^2, valid for
+// atan(w)/w and atanh(w)/w as polynomials in t = w^2, valid for
 // t < T_SERIES = 0.16 (|w| < 0.4): Chebyshev interpolants of the exact
-// functions on [0, 0.16] (coefficients from csrc/fit_series.py); the
-// interpolation error is below 1.1e-9 relative, so FP32 rounding (~6e-8)
-// dominates.  Horner with FMA.
+// functions on [0, 0.16] (coefficients from csrc/fit_series.py), Horner with
+// FMA.  Degree 4 (default): interpolation error 1.4e-8 / 2.9e-8 relative,
+// 5.8e-8 / 1.1e-7 with the FP32 rounding of the evaluation; degree 5:
+// 4e-10 / 1.1e-9, 3.5e-8 / 6.1e-8.  The argument Z itself carries several
+// FP32 roundings, so degree 4 leaves the per-term error about where it was.
+#ifndef LENS_SERIES_DEG
+#define LENS_SERIES_DEG 4
+#endif
 constexpr float T_SERIES = 0.16f;
 __device__ __forceinline__ float atan_over_w(float t) {
+#if LENS_SERIES_DEG == 5
   float p = -6.186992596e-02f;
   p = fmaf(p, t, 1.062997788e-01f);
   p = fmaf(p, t, -1.424732623e-01f);
   p = fmaf(p, t, 1.999858949e-01f);
   p = fmaf(p, t, -3.333331418e-01f);
   return fmaf(p, t, 9.999999996e-01f);
+#else
+  float p = 8.147408669e-02f;
+  p = fmaf(p, t, -1.389835755e-01f);
+  p = fmaf(p, t, 1.997853999e-01f);
+  p = fmaf(p, t, -3.333291011e-01f);
+  return fmaf(p, t, 9.999999865e-01f);
+#endif
 }
 __device__ __forceinline__ float atanh_over_w(float t) {
+#if LENS_SERIES_DEG == 5
   float p = 1.399562492e-01f;
   p = fmaf(p, t, 1.014973434e-01f);
   p = fmaf(p, t, 1.436870917e-01f);
   p = fmaf(p, t, 1.999682206e-01f);
   p = fmaf(p, t, 3.333337736e-01f);
   return fmaf(p, t, 9.999999990e-01f);
+#else
+  float p = 1.572736881e-01f;
+  p = fmaf(p, t, 1.359152003e-01f);
+  p = fmaf(p, t, 2.004095578e-01f);
+  p = fmaf(p, t, 3.333250231e-01f);
+  return fmaf(p, t, 1.000000027e+00f);
+#endif
 }
 
 // One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the
@@ -315,60 +336,74 @@ __device__ __forceinline__ float atan_fast(float w) {
 // FAST: outside the polynomial range, atan by atan_fast and
 // 2 atanh(w) = ln((1+w)/(1-w)) by the MUFU log2 (absolute error ~1e-7; the
 // image search only decides which triangles seed a candidate).
+//
+// Per term (core s = sc, cut s = st) with psi^2 = q^2 (s^2 + x^2) + y^2:
+//   alpha_x' = (b q/u) atan(u x/(psi + s)),  alpha_y' = (b q/u) atanh(u y/(psi + q^2 s)),
+// and the core-cut differences as single atan / atanh of the arguments
+//   Zx = x (dS Sp + dK) / (Sp (Ec Et + u^2 x^2)),
+//   Zy = y (q^2 dS Sp + dK) / (Sp (Fc Ft - u^2 y^2))           (times u),
+// Sp = psi_c + psi_t, E = psi + s, F = psi + q^2 s, dS = st - sc,
+// dK = q^2 (st^2 - sc^2) = psi_t^2 - psi_c^2 (no cancellation in FP32).
+// Hessian: D = (1 + q^2) s^2 + 2 psi s + x^2 + y^2 = E^2 + u^2 x^2, and
+//   psi_xx' + psi_yy' = b q (1/psi_c - 1/psi_t),
+//   psi_yy' - psi_xx' = b q ((y^2 - x^2)(fc - ft) - u^2 (sc^2 fc - st^2 ft)),
+//   psi_xy' = -b q xy (fc - ft),  f = 1/(psi D),
+// rotated by 2 theta.  The factor b q rides on the rotation constants.
 template <bool HESS, int KP, bool SERIES, bool FAST = false>
 __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
                                        Acc<HESS, KP> &p) {
-  const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4], F = r4[5], G = r4[6];
+  const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
   const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
   const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
-  const float q2sS = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
-  const float sS = D.x, q2dS = D.y;
-  const float axs = F.x, ays = F.y;
+  const float dK = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
+  const float q2dS = D.y;
+  const float cb = E.x, sb = E.y;
   const float cdX = c * dX, sdX = s * dX;
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     const float x = fmaf(s, dY[k], cdX), y = fmaf(c, dY[k], -sdX);
-    const float x2 = x * x, y2 = y * y;
+    const float x2 = x * x, y2 = y * y, u2x2 = u2 * x2;
     const float R = fmaf(q2, x2, y2);
     const float pc2 = R + Kc, pt2 = R + Kt;
     const float ic = rsqrt_a(pc2), it = rsqrt_a(pt2);
     const float psc = pc2 * ic, pst = pt2 * it;
     const float Sp = psc + pst;
     const float Ec = psc + sc, Et = pst + st;
-    const float Zx = (x * dS) * (Sp + q2sS) * rcp_a(Sp * fmaf(u2, x2, Ec * Et));
+    const float Zx = x * fmaf(dS, Sp, dK) * rcp_a(Sp * fmaf(Ec, Et, u2x2));
     const float Fc = psc + q2sc, Ft = pst + q2st;
-    const float Zy = (y * q2dS) * (Sp + sS) * rcp_a(Sp * fmaf(-u2, y2, Fc * Ft));
-    float axp, ayp;
+    const float Zy = y * fmaf(q2dS, Sp, dK) * rcp_a(Sp * fmaf(-u2, y2, Fc * Ft));
+    const float tx = u2 * (Zx * Zx), ty = u2 * (Zy * Zy);
+    float axp, ayp;  // halo-frame deflection over b q
     if (SERIES) {
       // u < 0.12: t = w^2 < 0.0144 always
-      axp = axs * Zx * atan_over_w(u2 * Zx * Zx);
-      ayp = ays * Zy * atanh_over_w(u2 * Zy * Zy);
+      axp = Zx * atan_over_w(tx);
+      ayp = Zy * atanh_over_w(ty);
+    } else if (fmaxf(tx, ty) < T_SERIES) {
+      axp = Zx * atan_over_w(tx);
+      ayp = Zy * atanh_over_w(ty);
     } else {
-      const float u = F.w;
+      const float u = r4[6].x, iu = E.w;
       const float wx = u * Zx, wy = u * Zy;
-      const float tx = wx * wx, ty = wy * wy;
-      if (fmaxf(tx, ty) < T_SERIES) {
-        const float bq = 2.f * F.z;  // (bq/u) atan(u Z) = bq Z atan(w)/w
-        axp = bq * Zx * atan_over_w(tx);
-        ayp = bq * Zy * atanh_over_w(ty);
-      } else if (FAST) {
-        axp = axs * atan_fast(wx);
-        ayp = ays * (0.693147181f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
+      if (FAST) {
+        axp = iu * atan_fast(wx);
+        ayp = iu * (0.346573590f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
       } else {
-        axp = axs * atanf(wx);
-        ayp = ays * log1pf((wy + wy) * rcp_a(1.f - wy));
+        axp = iu * atanf(wx);
+        ayp = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
       }
     }
-    p.ax[k] = fmaf(c, axp, fmaf(-s, ayp, p.ax[k]));
-    p.ay[k] = fmaf(s, axp, fmaf(c, ayp, p.ay[k]));
+    p.ax[k] = fmaf(cb, axp, fmaf(-sb, ayp, p.ax[k]));
+    p.ay[k] = fmaf(sb, axp, fmaf(cb, ayp, p.ay[k]));
     if (HESS) {
-      const float KDc = D.z, KDt = D.w, s2c = E.x, s2t = E.y, u2sc2 = E.z, u2st2 = E.w;
-      const float r2 = x2 + y2, ymx = y2 - x2;
-      const float Dc = fmaf(s2c, psc, r2 + KDc), Dt = fmaf(s2t, pst, r2 + KDt);
+      const float4 G = r4[5];
+      const float u2sc2 = D.z, u2st2 = D.w;
+      const float ymx = y2 - x2;
+      const float Dc = fmaf(Ec, Ec, u2x2), Dt = fmaf(Et, Et, u2x2);
       const float fc = rcp_a(psc * Dc), ft = rcp_a(pst * Dt);
-      const float g1d = fmaf(fc, ymx - u2sc2, -ft * (ymx - u2st2));
-      const float g2d = (fc - ft) * (x * y);
-      p.k[k] = fmaf(F.z, ic - it, p.k[k]);
+      const float fd = fc - ft;
+      const float g1d = fmaf(ymx, fd, -fmaf(u2sc2, fc, -u2st2 * ft));
+      const float g2d = fd * (x * y);
+      p.k[k] = fmaf(E.z, ic - it, p.k[k]);
       p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
       p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
     }

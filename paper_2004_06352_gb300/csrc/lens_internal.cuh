@@ -32,12 +32,12 @@ enum Kind32 : int { K32_DPIE = 0, K32_DPIE_SERIES = 1, K32_SIS = 2, K32_POINT = 
 enum Rec32 : int {
   R_C = 0, R_S, R_Q2, R_U2,          // rotation, q^2, u^2
   R_KC, R_KT, R_SC, R_ST,            // q^2 sc^2, q^2 st^2, sc, st
-  R_Q2SS, R_DS, R_Q2SC, R_Q2ST,      // q^2 (st+sc), st-sc, q^2 sc, q^2 st
-  R_SS, R_Q2DS, R_KDC, R_KDT,        // st+sc, q^2 (st-sc), (1+q^2) sc^2, (1+q^2) st^2
-  R_2SC, R_2ST, R_U2SC2, R_U2ST2,    // 2 sc, 2 st, u^2 sc^2, u^2 st^2
-  R_AXS, R_AYS, R_KAPS, R_U,         // alpha_x scale, alpha_y scale, kappa scale, u
+  R_DK, R_DS, R_Q2SC, R_Q2ST,       // q^2 (st^2 - sc^2), st-sc, q^2 sc, q^2 st
+  R_PAD0, R_Q2DS, R_U2SC2, R_U2ST2,  // -, q^2 (st-sc), u^2 sc^2, u^2 st^2
+  R_CB, R_SB, R_KAPS, R_IU,          // rotation times b q, kappa scale b q / 2, 1/u
   R_C1, R_C2, R_C3, R_C4,            // shear rotation by 2 theta with the scale folded in
-  R_KIND, R_B, R_PAD0, R_PAD1        // kind, SIS b / point-mass b^2
+  R_U, R_PAD1, R_PAD2, R_PAD3,       // u
+  R_KIND, R_B, R_PAD4, R_PAD5        // kind, SIS b / point-mass b^2
 };
 constexpr int REC32 = 32;
 
@@ -111,21 +111,17 @@ __host__ __device__ inline void make_rec32(int type, double theta, double eps, d
     r[R_KT] = (float)(q2 * st * st);
     r[R_SC] = (float)sc;
     r[R_ST] = (float)st;
-    r[R_Q2SS] = (float)(q2 * (st + sc));
+    r[R_DK] = (float)(q2 * (st - sc) * (st + sc));
     r[R_DS] = (float)(st - sc);
     r[R_Q2SC] = (float)(q2 * sc);
     r[R_Q2ST] = (float)(q2 * st);
-    r[R_SS] = (float)(st + sc);
     r[R_Q2DS] = (float)(q2 * (st - sc));
-    r[R_KDC] = (float)((1.0 + q2) * sc * sc);
-    r[R_KDT] = (float)((1.0 + q2) * st * st);
-    r[R_2SC] = (float)(2.0 * sc);
-    r[R_2ST] = (float)(2.0 * st);
     r[R_U2SC2] = (float)(u2 * sc * sc);
     r[R_U2ST2] = (float)(u2 * st * st);
-    r[R_AXS] = (float)(series ? bq : bq / u);
-    r[R_AYS] = (float)(series ? bq : bq / (2.0 * u));
+    r[R_CB] = (float)(cos(theta) * bq);
+    r[R_SB] = (float)(sin(theta) * bq);
     r[R_KAPS] = (float)(0.5 * bq);
+    r[R_IU] = (float)(series ? 0.0 : 1.0 / u);
     r[R_U] = (float)u;
     r[R_C1] = (float)(c2 * 0.5 * bq);
     r[R_C2] = (float)(s2 * bq);

@@ -3,7 +3,7 @@
 // grid with inclusive corners.
 //
 // LENS_MIXED kernel (the hot path):
-//   - CTA = 256 threads = 8 warps over a 32 x (8 KP) point tile; lane l owns
+//   - CTA = 128 threads = 4 warps over a 32 x (4 KP) point tile; lane l owns
 //     column i0 + l, warp w owns rows j0 + w KP .. + KP-1, so every store of
 //     one row is 32 consecutive elements (one 128-byte segment per warp).
 //   - Potentials evaluated in FP32 are streamed through shared memory in
@@ -11,11 +11,12 @@
 //     cp.async.bulk + mbarrier), double-buffered: the copy of chunk c+1 is in
 //     flight while chunk c is evaluated.  Every thread reads the same record
 //     at the same time (shared-memory broadcast).
-//   - Point positions relative to each potential: the tile origin minus the
-//     potential's centre is formed in FP64 once per (tile, potential) and
-//     kept as a hi/lo float pair; adding the thread's in-tile offset (also a
-//     hi/lo pair) reproduces dX, dY to FP32 relative precision even next to
-//     a potential's centre, before rotating into its frame.
+//   - Point positions relative to each potential: per (tile, potential), the
+//     tile origin's X - x0 and Y - y0 in FP64, kept as hi/lo float pairs; a
+//     lane adds its column offset (also a hi/lo pair) to the first, and the
+//     staging adds each row's offset to the second, so (hi + offset) is
+//     exact next to a potential's centre (Sterbenz) and dX, dY keep FP32
+//     relative precision there, before rotating into its frame.
 //   - FP32 contributions go into naive partial sums that are folded every
 //     SUB potentials into a Kahan-compensated total.
 //   - Potentials at or above the FP64 threshold (cluster-scale halos) are
@@ -90,7 +91,17 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
     k_map_mixed(const MapArgs a) {
   constexpr int MAP_THREADS = map_threads(HESS), MAP_WARPS = MAP_THREADS / 32;
   __shared__ __align__(128) float s_rec[2][CH * REC32];
-  __shared__ float4 s_off[2][CH];  // hi.x, hi.y, lo.x, lo.y of (Tx - x0, Ty - y0)
+  // Offsets of the tile from each staged potential's centre: X - x0 at the
+  // tile's first column as a hi/lo float pair (a lane adds its column
+  // offset), Y - y0 of every row of the tile rounded to float (rows are
+  // per warp, so no per-thread work).  KP = 2: one float4 per (warp,
+  // potential) = (x hi, x lo, y row 0, y row 1); KP = 4: the x pair per
+  // potential and one float4 of rows per (warp, potential).
+  static_assert(KP == 2 || KP == 4, "offset staging layout");
+  constexpr int ROWS = MAP_WARPS * KP;
+  __shared__ __align__(16) float4 s_offy[2][MAP_WARPS][CH];
+  __shared__ __align__(8) float2 s_offx[2][KP == 2 ? 1 : CH];
+  __shared__ float2 s_ly[ROWS];  // row r's offset r dy inside the tile, hi/lo
   __shared__ __align__(8) uint64_t s_bar[2];
   constexpr int NC = HESS ? 5 : 2;
   __shared__ double s_hv[MAP_THREADS][KP][NC];  // FP64 potentials' sums per point
@@ -103,12 +114,10 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
   // dX, dY keep full relative precision where the profile is steepest
   const double lx = lane * a.dx;
   const float Lxh = (float)lx, Lxl = (float)(lx - (double)Lxh);
-  float Lyh[KP], Lyl[KP];
-#pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    const double ly = (warp * KP + k) * a.dy;
-    Lyh[k] = (float)ly;
-    Lyl[k] = (float)(ly - (double)Lyh[k]);
+  if (tid < ROWS) {
+    const double ly = tid * a.dy;
+    const float h = (float)ly;
+    s_ly[tid] = make_float2(h, (float)(ly - (double)h));
   }
 
   Acc<HESS, KP> tot, cmp, part;
@@ -157,22 +166,62 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
     mbar_expect_tx(&s_bar[0], cnt * REC32 * 4);
     bulk_g2s(&s_rec[0][0], a.rec32, cnt * REC32 * 4, &s_bar[0]);
   }
-  // FP64 position data of the next chunk, prefetched into registers
-  double2 pxy = make_double2(0, 0), pcs = make_double2(1, 0);
-  if (tid < CH && tid < a.n_light) {
-    pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * tid];
-    pcs = reinterpret_cast<const double2 *>(a.pos64)[2 * tid + 1];
-  }
+  // FP64 centre of the potential this thread stages in the next chunk,
+  // prefetched into registers (threads hs and hs + CH stage the same one)
+  const int hs = tid % CH, spart = tid / CH;
+  constexpr int PARTS = MAP_THREADS / CH;
+  static_assert(MAP_THREADS % CH == 0 && PARTS >= 2, "staging threads");
+  double2 pxy = make_double2(0, 0);
+  if (hs < a.n_light) pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * hs];
+
+  // (X - x0, Y - y0) of this thread's KP points: the column offset added to
+  // the staged hi/lo pair ((hi + Lxh) is exact next to the centre, by
+  // Sterbenz), the rows as staged
+  auto tile_offsets = [&](int buf, int h, float &dX, float (&dY)[KP]) {
+    const float4 oy = s_offy[buf][warp][h];
+    if constexpr (KP == 2) {
+      dX = (oy.x + Lxh) + (oy.y + Lxl);
+      dY[0] = oy.z;
+      dY[1] = oy.w;
+    } else {
+      const float2 ox = s_offx[buf][KP == 2 ? 0 : h];
+      dX = (ox.x + Lxh) + (ox.y + Lxl);
+      dY[0] = oy.x;
+      dY[1] = oy.y;
+      dY[2] = oy.z;
+      dY[3] = oy.w;
+    }
+  };
 
   int seen = 0;
   for (int ch = 0; ch < nch; ++ch) {
     const int buf = ch & 1;
     const int base = ch * CH, cnt = min(CH, a.n_light - base);
-    if (tid < cnt) {
-      // tile origin rotated into the potential's frame, in FP64
-      const double dX = Tx - pxy.x, dY = Ty - pxy.y;
-      const float hx = (float)dX, hy = (float)dY;
-      s_off[buf][tid] = make_float4(hx, hy, (float)(dX - (double)hx), (float)(dY - (double)hy));
+    if (hs < cnt) {
+      // offsets from the potential's centre: one staging thread forms X - x0,
+      // the other Y - y0 (FP64, kept as hi/lo float pairs), from which it
+      // adds each row's offset inside the tile as a hi/lo pair too
+      if (spart == 0) {
+        const double dX = Tx - pxy.x;
+        const float hx = (float)dX, lx = (float)(dX - (double)hx);
+        if constexpr (KP == 2) {
+#pragma unroll
+          for (int w = 0; w < MAP_WARPS; ++w) {
+            s_offy[buf][w][hs].x = hx;
+            s_offy[buf][w][hs].y = lx;
+          }
+        } else {
+          s_offx[buf][KP == 2 ? 0 : hs] = make_float2(hx, lx);
+        }
+      } else if (spart == 1) {
+        const double dY = Ty - pxy.y;
+        const float hy = (float)dY, ly = (float)(dY - (double)hy);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+          const float2 L = s_ly[r];
+          reinterpret_cast<float *>(&s_offy[buf][r / KP][hs])[(KP == 2 ? 2 : 0) + r % KP] = (hy + L.x) + (ly + L.y);
+        }
+      }
     }
     const bool ok = mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);
     if (!__syncthreads_and(ok)) {
@@ -189,10 +238,7 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
         mbar_expect_tx(&s_bar[buf ^ 1], ncnt * REC32 * 4);
         bulk_g2s(&s_rec[buf ^ 1][0], a.rec32 + (size_t)(base + CH) * REC32, ncnt * REC32 * 4, &s_bar[buf ^ 1]);
       }
-      if (tid < CH && base + CH + tid < a.n_light) {
-        pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * (base + CH + tid)];
-        pcs = reinterpret_cast<const double2 *>(a.pos64)[2 * (base + CH + tid) + 1];
-      }
+      if (base + CH + hs < a.n_light) pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * (base + CH + hs)];
     }
     const float4 *recs = reinterpret_cast<const float4 *>(&s_rec[buf][0]);
     if constexpr (HESS ? LENS_MAP_SEGMENTS : LENS_MAP_SEGMENTS_GRAD) {
@@ -204,11 +250,8 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
 #pragma unroll MAP_UNROLL
         for (int h = h0; h < h1; ++h) {
           const float4 *r4 = recs + h * (REC32 / 4);
-          const float4 off = s_off[buf][h];
-          const float dX = (off.x + Lxh) + (off.z + Lxl);
-          float dY[KP];
-#pragma unroll
-          for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
+          float dX, dY[KP];
+          tile_offsets(buf, h, dX, dY);
           if (KIND == K32_DPIE)
             dpie32<HESS, KP, false>(r4, dX, dY, part);
           else if (KIND == K32_DPIE_SERIES)
@@ -237,11 +280,8 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
     } else {
       for (int h = 0; h < cnt; ++h) {
         const float4 *r4 = recs + h * (REC32 / 4);
-        const float4 off = s_off[buf][h];
-        const float dX = (off.x + Lxh) + (off.z + Lxl);
-        float dY[KP];
-#pragma unroll
-        for (int k = 0; k < KP; ++k) dY[k] = (off.y + Lyh[k]) + (off.w + Lyl[k]);
+        float dX, dY[KP];
+        tile_offsets(buf, h, dX, dY);
         eval32_any<HESS, KP>(r4, dX, dY, part);
         if (++seen == SUB) {
           fold(tot, cmp, part);
