@@ -329,6 +329,13 @@ int lens_server_stats(const lens_server *s, lens_server_info *info);
  * and the context stays usable. */
 int lens_selftest_wait(lens_ctx *ctx, int32_t polls, void *stream);
 
+/* The FP64 reciprocal and reciprocal square root the FP64 evaluators use
+ * (MUFU approximation + two Newton-Raphson steps) next to CUDA's division
+ * and rsqrt, for testing: for each of the n doubles at d_x (device, positive
+ * normal values), d_out (device, [4][n]) receives rcp, 1/x, rsqrt, CUDA
+ * rsqrt.  Asynchronous on `stream`. */
+int lens_selftest_math(lens_ctx *ctx, const double *d_x, int32_t n, double *d_out, void *stream);
+
 /* Wait until all work enqueued on `stream` has finished, polling without
  * blocking the thread for more than timeout_ms (>= 0) milliseconds.
  * LENS_ETIMEOUT if it has not finished by then (the work keeps running). */

@@ -27,7 +27,7 @@ EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_u
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
            "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_autotune", "lens_chi2_image",
-           "lens_find_images", "lens_chi2_image_noalloc", "lens_selftest_wait", "lens_wait", "lens_strerror",
+           "lens_find_images", "lens_chi2_image_noalloc", "lens_selftest_wait", "lens_selftest_math", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
            "lens_server_progress", "lens_server_cancel", "lens_server_stats")
 LENS_REQ_MAP, LENS_REQ_CHI2_SOURCE, LENS_REQ_CHI2_IMAGE = 0, 1, 2
@@ -98,6 +98,7 @@ def load_library(path=LIB_PATH):
         "lens_find_images": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, C.c_int32, vp, vp]),
         "lens_chi2_image_noalloc": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
         "lens_selftest_wait": (C.c_int, [vp, C.c_int32, vp]),
+        "lens_selftest_math": (C.c_int, [vp, vp, C.c_int32, vp, vp]),
         "lens_wait": (C.c_int, [vp, vp, i64]),
         "lens_server_create": (C.c_int, [vp, C.c_int32, C.c_size_t, C.POINTER(vp)]),
         "lens_server_destroy": (C.c_int, [vp]),
@@ -294,6 +295,11 @@ class Context:
     def selftest_wait(self, polls=64, stream=None):
         """Run the bounded-wait failure path once (see lens.h)."""
         _check(_lib.lens_selftest_wait(self.h, int(polls), _stream(stream)), "lens_selftest_wait")
+
+    def selftest_math(self, x, out, stream=None):
+        """rcp, 1/x, rsqrt, CUDA rsqrt of the device doubles x into out [4][n] (see lens.h)."""
+        _check(_lib.lens_selftest_math(self.h, _ptr(x), int(x.numel()), _ptr(out), _stream(stream)),
+               "lens_selftest_math")
 
     def wait(self, stream=None, timeout_ms=60000):
         return _check(_lib.lens_wait(self.h, _stream(stream), int(timeout_ms)), "lens_wait")

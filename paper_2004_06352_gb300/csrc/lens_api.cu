@@ -680,6 +680,13 @@ int lens_selftest_wait(lens_ctx *ctx, int32_t polls, void *stream) {
   return launch_wait_selftest(ctx, (unsigned)polls, (cudaStream_t)stream);
 }
 
+int lens_selftest_math(lens_ctx *ctx, const double *d_x, int32_t n, double *d_out, void *stream) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!d_x || !d_out))) return fail(LENS_EINVAL, "bad self-test arguments");
+  cudaSetDevice(ctx->device);
+  return launch_math_selftest(d_x, n, d_out, (cudaStream_t)stream);
+}
+
 int lens_wait(lens_ctx *ctx, void *stream, int64_t timeout_ms) {
   if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
   if (timeout_ms < 0) return fail(LENS_EINVAL, "timeout_ms must be >= 0");

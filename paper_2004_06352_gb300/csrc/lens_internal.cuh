@@ -303,6 +303,7 @@ int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dl
                     cudaStream_t st, int row0 = 0, int rows = -1);
 int map_tile_rows(bool hess);  // rows per CTA tile of the mixed map kernel
 int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st);
+int launch_math_selftest(const double *x, int n, double *out, cudaStream_t st);
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);

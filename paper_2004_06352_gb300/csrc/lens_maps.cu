@@ -247,18 +247,23 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
       // the deflection-only kernel spills with it and keeps the plain loop)
       auto run = [&](auto kind_tag, int h0, int h1) {
         constexpr int KIND = decltype(kind_tag)::value;
+        for (int h = h0; h < h1;) {
+          // up to the next fold: no per-potential counter in the inner loop
+          const int he = min(h + (SUB - seen), h1);
+          seen += he - h;
 #pragma unroll MAP_UNROLL
-        for (int h = h0; h < h1; ++h) {
-          const float4 *r4 = recs + h * (REC32 / 4);
-          float dX, dY[KP];
-          tile_offsets(buf, h, dX, dY);
-          if (KIND == K32_DPIE)
-            dpie32<HESS, KP, false>(r4, dX, dY, part);
-          else if (KIND == K32_DPIE_SERIES)
-            dpie32<HESS, KP, true>(r4, dX, dY, part);
-          else
-            circ32<HESS, KP, KIND == K32_POINT>(r4, dX, dY, part);
-          if (++seen == SUB) {
+          for (; h < he; ++h) {
+            const float4 *r4 = recs + h * (REC32 / 4);
+            float dX, dY[KP];
+            tile_offsets(buf, h, dX, dY);
+            if (KIND == K32_DPIE)
+              dpie32<HESS, KP, false>(r4, dX, dY, part);
+            else if (KIND == K32_DPIE_SERIES)
+              dpie32<HESS, KP, true>(r4, dX, dY, part);
+            else
+              circ32<HESS, KP, KIND == K32_POINT>(r4, dX, dY, part);
+          }
+          if (seen == SUB) {
             fold(tot, cmp, part);
             seen = 0;
           }
@@ -278,16 +283,20 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
       seg(K32_POINT, h0, h1);
       if (h0 < h1) run(std::integral_constant<int, K32_POINT>(), h0, h1);
     } else {
-      for (int h = 0; h < cnt; ++h) {
-        const float4 *r4 = recs + h * (REC32 / 4);
-        float dX, dY[KP];
-        tile_offsets(buf, h, dX, dY);
-        eval32_any<HESS, KP>(r4, dX, dY, part);
-        if (++seen == SUB) {
+      for (int h = 0; h < cnt;) {
+        const int he = min(h + (SUB - seen), cnt);
+        seen += he - h;
+        for (; h < he; ++h) {
+          const float4 *r4 = recs + h * (REC32 / 4);
+          float dX, dY[KP];
+          tile_offsets(buf, h, dX, dY);
+          eval32_any<HESS, KP>(r4, dX, dY, part);
+        }
+        if (seen == SUB) {
           fold(tot, cmp, part);
           seen = 0;
         }
-    }
+      }
     }
   }
   fold(tot, cmp, part);
@@ -365,7 +374,26 @@ __global__ void k_wait_selftest(int *err, unsigned polls) {
   }
 }
 
+// The FP64 reciprocal and reciprocal square root of the evaluators next to
+// CUDA's division and rsqrt: out[0..3][i] = rcp64, 1/x, rsqrt64, rsqrt.
+__global__ void k_math_selftest(const double *__restrict__ x, int n, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  out[i] = rcp64(v);
+  out[n + i] = 1.0 / v;
+  out[2 * n + i] = rsqrt64(v);
+  out[3 * n + i] = rsqrt(v);
+}
+
 }  // namespace
+
+int launch_math_selftest(const double *x, int n, double *out, cudaStream_t st) {
+  if (n > 0) k_math_selftest<<<(n + 255) / 256, 256, 0, st>>>(x, n, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "self-test launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
 
 int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st) {
   k_wait_selftest<<<1, 32, 0, st>>>(ctx->d_err, polls);
