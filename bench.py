@@ -29,15 +29,15 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
 
 # FP32-pipe thread instructions (FFMA + FADD + FMUL) and MUFU (XU pipe)
 # instructions per point-halo pair of the LENS_MIXED Hessian map kernel,
-# measured with ncu on the 2048^2 x 1000 workload (profiles/
-# map_hessian_mixed_2048x1000.md); the compensated-fold overhead (~1 op per
-# pair) is included.
-FP32_OPS_PER_PAIR = 78.2
+# measured with ncu on the 2048^2 x 1000 workload (the counter group of the
+# map kernel's summary under profiles/); the compensated-fold overhead
+# (~1 op per pair) is included.
+FP32_OPS_PER_PAIR = 64.9
 MUFU_OPS_PER_PAIR = 6.03
 # DRAM bytes (read + write) of one launch of that kernel on that workload,
 # from the same ncu capture; the 100.7 MB of output are partly still in L2
 # when the kernel ends
-MAP_TRAFFIC_BYTES = 880128 + 40267264
+MAP_TRAFFIC_BYTES = 482816 + 39919616
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 
 

@@ -385,51 +385,80 @@ __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, 
   const float q2dS = D.y;
   const float cb = E.x, sb = E.y;
   const float cdX = c * dX, sdX = s * dX;
+  float x[KP], y[KP], x2[KP], y2[KP], u2x2[KP], ic[KP], it[KP], psc[KP], pst[KP], Ec[KP], Et[KP];
+  float Zx[KP], Zy[KP], tx[KP], ty[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
-    const float x = fmaf(s, dY[k], cdX), y = fmaf(c, dY[k], -sdX);
-    const float x2 = x * x, y2 = y * y, u2x2 = u2 * x2;
-    const float R = fmaf(q2, x2, y2);
+    x[k] = fmaf(s, dY[k], cdX);
+    y[k] = fmaf(c, dY[k], -sdX);
+    x2[k] = x[k] * x[k];
+    y2[k] = y[k] * y[k];
+    u2x2[k] = u2 * x2[k];
+    const float R = fmaf(q2, x2[k], y2[k]);
     const float pc2 = R + Kc, pt2 = R + Kt;
-    const float ic = rsqrt_a(pc2), it = rsqrt_a(pt2);
-    const float psc = pc2 * ic, pst = pt2 * it;
-    const float Sp = psc + pst;
-    const float Ec = psc + sc, Et = pst + st;
-    const float Zx = x * fmaf(dS, Sp, dK) * rcp_a(Sp * fmaf(Ec, Et, u2x2));
-    const float Fc = psc + q2sc, Ft = pst + q2st;
-    const float Zy = y * fmaf(q2dS, Sp, dK) * rcp_a(Sp * fmaf(-u2, y2, Fc * Ft));
-    const float tx = u2 * (Zx * Zx), ty = u2 * (Zy * Zy);
-    float axp, ayp;  // halo-frame deflection over b q
-    if (SERIES) {
-      // u < 0.12: t = w^2 < 0.0144 always
-      axp = Zx * atan_over_w(tx);
-      ayp = Zy * atanh_over_w(ty);
-    } else if (fmaxf(tx, ty) < T_SERIES) {
-      axp = Zx * atan_over_w(tx);
-      ayp = Zy * atanh_over_w(ty);
-    } else {
-      const float u = r4[6].x, iu = E.w;
-      const float wx = u * Zx, wy = u * Zy;
-      if (FAST) {
-        axp = iu * atan_fast(wx);
-        ayp = iu * (0.346573590f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
+    ic[k] = rsqrt_a(pc2);
+    it[k] = rsqrt_a(pt2);
+    psc[k] = pc2 * ic[k];
+    pst[k] = pt2 * it[k];
+    const float Sp = psc[k] + pst[k];
+    Ec[k] = psc[k] + sc;
+    Et[k] = pst[k] + st;
+    Zx[k] = x[k] * fmaf(dS, Sp, dK) * rcp_a(Sp * fmaf(Ec[k], Et[k], u2x2[k]));
+    const float Fc = psc[k] + q2sc, Ft = pst[k] + q2st;
+    Zy[k] = y[k] * fmaf(q2dS, Sp, dK) * rcp_a(Sp * fmaf(-u2, y2[k], Fc * Ft));
+    tx[k] = u2 * (Zx[k] * Zx[k]);
+    ty[k] = u2 * (Zy[k] * Zy[k]);
+  }
+  // halo-frame deflection over b q: the interpolants where every point's
+  // |w|^2 < T_SERIES (always for the SERIES kind, u < 0.12: t < 0.0144),
+  // one branch for all KP points
+  float axp[KP], ayp[KP];
+  bool poly = SERIES;
+  if (!SERIES) {
+    float t = fmaxf(tx[0], ty[0]);
+#pragma unroll
+    for (int k = 1; k < KP; ++k) t = fmaxf(t, fmaxf(tx[k], ty[k]));
+    poly = t < T_SERIES;
+  }
+  if (poly) {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      axp[k] = Zx[k] * atan_over_w(tx[k]);
+      ayp[k] = Zy[k] * atanh_over_w(ty[k]);
+    }
+  } else {
+    const float u = r4[6].x, iu = E.w;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      if (fmaxf(tx[k], ty[k]) < T_SERIES) {
+        axp[k] = Zx[k] * atan_over_w(tx[k]);
+        ayp[k] = Zy[k] * atanh_over_w(ty[k]);
       } else {
-        axp = iu * atanf(wx);
-        ayp = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
+        const float wx = u * Zx[k], wy = u * Zy[k];
+        if (FAST) {
+          axp[k] = iu * atan_fast(wx);
+          ayp[k] = iu * (0.346573590f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
+        } else {
+          axp[k] = iu * atanf(wx);
+          ayp[k] = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
+        }
       }
     }
-    p.ax[k] = fmaf(cb, axp, fmaf(-sb, ayp, p.ax[k]));
-    p.ay[k] = fmaf(sb, axp, fmaf(cb, ayp, p.ay[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    p.ax[k] = fmaf(cb, axp[k], fmaf(-sb, ayp[k], p.ax[k]));
+    p.ay[k] = fmaf(sb, axp[k], fmaf(cb, ayp[k], p.ay[k]));
     if (HESS) {
       const float4 G = r4[5];
       const float u2sc2 = D.z, u2st2 = D.w;
-      const float ymx = y2 - x2;
-      const float Dc = fmaf(Ec, Ec, u2x2), Dt = fmaf(Et, Et, u2x2);
-      const float fc = rcp_a(psc * Dc), ft = rcp_a(pst * Dt);
+      const float ymx = y2[k] - x2[k];
+      const float Dc = fmaf(Ec[k], Ec[k], u2x2[k]), Dt = fmaf(Et[k], Et[k], u2x2[k]);
+      const float fc = rcp_a(psc[k] * Dc), ft = rcp_a(pst[k] * Dt);
       const float fd = fc - ft;
       const float g1d = fmaf(ymx, fd, -fmaf(u2sc2, fc, -u2st2 * ft));
-      const float g2d = fd * (x * y);
-      p.k[k] = fmaf(E.z, ic - it, p.k[k]);
+      const float g2d = fd * (x[k] * y[k]);
+      p.k[k] = fmaf(E.z, ic[k] - it[k], p.k[k]);
       p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
       p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
     }
