@@ -61,55 +61,68 @@ struct Chi2SrcArgs {
   double *chi2;
 };
 
+// Parameter sets whose varying potentials' records one warp builds at a
+// time (one thread per record: the FP64 record arithmetic runs 32 lanes wide
+// instead of on two threads per set).
+constexpr int SRC_BATCH = 16;
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
+  static_assert(THREADS >= 2 * SRC_BATCH, "one thread per record of a batch");
   extern __shared__ double sm[];
-  double *s_rec = sm;                    // [2][REC64]
-  double *s_beta = s_rec + 2 * REC64;    // [nimg][2]
+  double *s_beta = sm;                   // [nimg][2]
   double *s_m = s_beta + 2 * a.nimg;     // [nimg][3]: r hxx, r hyy, r hxy
   double *s_bary = s_m + 3 * a.nimg;     // [nsrc][2]
   double *s_red = s_bary + 2 * a.nsrc;   // [THREADS/32]
-  __shared__ int s_ok;
-  __shared__ float2 s_rdf[2 * RECDF];  // the varying potentials in double-float
-  for (int p = blockIdx.x; p < a.P; p += gridDim.x) {
-    const double *q = a.params + (size_t)p * 14;
-    if (threadIdx.x == 0) s_ok = 1;
-    __syncthreads();
-    if (threadIdx.x < 2) {
-      if (!load_var_rec64(q, a.type0, a.type1, threadIdx.x, s_rec)) atomicAnd(&s_ok, 0);
-      const double *w = q + 7 * threadIdx.x;  // x0, y0, eps, theta, rcore, rcut, b0
-      make_recdf(threadIdx.x == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6],
-                 s_rdf + threadIdx.x * RECDF);
-    }
-    __syncthreads();
-    if (!s_ok) {
-      if (threadIdx.x == 0) a.chi2[p] = __longlong_as_double(0x7ff8000000000000ll);
-      __syncthreads();
-      continue;
-    }
-    backtrace_set<THREADS>(a.stat + p * a.stat_stride, a.x, a.y, a.ratio, a.src_of, a.img_off, a.nimg, a.nsrc,
-                           s_rec, s_rdf, s_beta, a.variant == LENS_CHI2_SRC_PLAIN ? nullptr : s_m, s_bary);
-    double acc[1] = {0.0};
-    for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
-      const int i = a.src_of[j];
-      const double dbx = s_bary[2 * i] - s_beta[2 * j], dby = s_bary[2 * i + 1] - s_beta[2 * j + 1];
-      const double s2 = a.sigma[j] * a.sigma[j];
-      if (a.variant == LENS_CHI2_SRC_PLAIN) {
-        acc[0] += (dbx * dbx + dby * dby) / s2;
-      } else {
-        // A^-1 = I - r H (Sec. 2.1 Eq. 4)
-        const double a11 = 1.0 - s_m[3 * j], a22 = 1.0 - s_m[3 * j + 1], a12 = -s_m[3 * j + 2];
-        const double det = a11 * a22 - a12 * a12;
-        if (a.variant == LENS_CHI2_SRC_MU) {
-          acc[0] += (dbx * dbx + dby * dby) * fabs(1.0 / det) / s2;
-        } else {
-          const double rx = (a22 * dbx - a12 * dby) / det, ry = (a11 * dby - a12 * dbx) / det;
-          acc[0] += (rx * rx + ry * ry) / s2;
-        }
+  __shared__ double s_rec[SRC_BATCH][2 * REC64];   // FP64 records of the batch's varying potentials
+  __shared__ float2 s_rdf[SRC_BATCH][2 * RECDF];   // the same in double-float
+  __shared__ int s_ok[SRC_BATCH][2];
+  // this CTA's sets are p = blockIdx.x + j gridDim.x, taken SRC_BATCH at a time
+  for (long long p0 = blockIdx.x; p0 < a.P; p0 += (long long)gridDim.x * SRC_BATCH) {
+    __syncthreads();  // the previous batch's records are no longer read
+    if (threadIdx.x < 2 * SRC_BATCH) {
+      const int k = threadIdx.x >> 1, v = threadIdx.x & 1;
+      const long long p = p0 + (long long)k * gridDim.x;
+      if (p < a.P) {
+        const double *q = a.params + p * 14;
+        const double *w = q + 7 * v;  // x0, y0, eps, theta, rcore, rcut, b0
+        s_ok[k][v] = load_var_rec64(q, a.type0, a.type1, v, s_rec[k]);
+        make_recdf(v == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rdf[k] + v * RECDF);
       }
     }
-    block_sum<1, THREADS>(acc, s_red);
-    if (threadIdx.x == 0) a.chi2[p] = acc[0];
+    __syncthreads();
+    for (int k = 0; k < SRC_BATCH; ++k) {
+      const long long p = p0 + (long long)k * gridDim.x;
+      if (p >= a.P) break;  // uniform over the CTA
+      if (!(s_ok[k][0] && s_ok[k][1])) {
+        if (threadIdx.x == 0) a.chi2[p] = __longlong_as_double(0x7ff8000000000000ll);
+        continue;
+      }
+      backtrace_set<THREADS>(a.stat + p * a.stat_stride, a.x, a.y, a.ratio, a.src_of, a.img_off, a.nimg, a.nsrc,
+                             s_rec[k], s_rdf[k], s_beta, a.variant == LENS_CHI2_SRC_PLAIN ? nullptr : s_m, s_bary);
+      double acc[1] = {0.0};
+      for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
+        const int i = a.src_of[j];
+        const double dbx = s_bary[2 * i] - s_beta[2 * j], dby = s_bary[2 * i + 1] - s_beta[2 * j + 1];
+        const double is2 = rcp64(a.sigma[j] * a.sigma[j]);
+        if (a.variant == LENS_CHI2_SRC_PLAIN) {
+          acc[0] += (dbx * dbx + dby * dby) * is2;
+        } else {
+          // A^-1 = I - r H (Sec. 2.1 Eq. 4)
+          const double a11 = 1.0 - s_m[3 * j], a22 = 1.0 - s_m[3 * j + 1], a12 = -s_m[3 * j + 2];
+          const double det = a11 * a22 - a12 * a12;
+          const double id = 1.0 / det;
+          if (a.variant == LENS_CHI2_SRC_MU) {
+            acc[0] += (dbx * dbx + dby * dby) * fabs(id) * is2;
+          } else {
+            const double rx = (a22 * dbx - a12 * dby) * id, ry = (a11 * dby - a12 * dbx) * id;
+            acc[0] += (rx * rx + ry * ry) * is2;
+          }
+        }
+      }
+      block_sum<1, THREADS>(acc, s_red);
+      if (threadIdx.x == 0) a.chi2[p] = acc[0];
+    }
   }
 }
 
@@ -128,7 +141,7 @@ template <int T>
 static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, int32_t P, int32_t variant,
                           double *d_chi2, cudaStream_t st, int blocks_per_sm, const double *stat = nullptr,
                           long long stat_stride = 0) {
-  const size_t smem = sizeof(double) * (2 * REC64 + 5 * (size_t)c->nimg + 2 * (size_t)c->nsrc + T / 32);
+  const size_t smem = sizeof(double) * (5 * (size_t)c->nimg + 2 * (size_t)c->nsrc + T / 32);
   if (smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
   cudaFuncSetAttribute(k_chi2_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   int per_sm = 0, nsm = 0;
@@ -182,7 +195,8 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
 
 // Static sums of the no-cache form, grid (nimg, sets): every static potential
 // at the image in double-float (FP64 where that fails), per-thread sums in
-// FP64, deterministic CTA reduction; copy c goes to stat + c * nimg * 5.
+// double-float, deterministic CTA reduction in FP64; copy c goes to
+// stat + c * nimg * 5.
 __global__ void __launch_bounds__(CACHE_THREADS) k_static_df(const float2 *__restrict__ recdf,
                                                              const double *__restrict__ all64, int n, int v0, int v1,
                                                              const double *__restrict__ x,
@@ -191,11 +205,35 @@ __global__ void __launch_bounds__(CACHE_THREADS) k_static_df(const float2 *__res
   const int img = blockIdx.x;
   stat += (size_t)blockIdx.y * gridDim.x * 5;
   const double X = x[img], Y = y[img];
+  const df Xd = df_from_double(X), Yd = df_from_double(Y);
   double v[5] = {0, 0, 0, 0, 0};
+  // per-thread sums in double-float, converted once (FP64 only for the
+  // potentials whose double-float evaluation fails)
+  df sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int h = threadIdx.x; h < n; h += CACHE_THREADS) {
     if (h == v0 || h == v1) continue;
-    add_potential_df<true>(recdf + h, n, all64 + (size_t)h * REC64, X, Y, v);
+    const float2 *r = recdf + h;
+    df ax, ay, hh[3];
+    bool ok = true;
+    if (r[F_U2 * n].x < 0.f)
+      circ_df<true>(r, n, Xd, Yd, ax, ay, hh);
+    else
+      ok = dpie_df<true, true>(r, n, Xd, Yd, ax, ay, hh);
+    if (ok) {
+      sum[0] = df_add(sum[0], ax);
+      sum[1] = df_add(sum[1], ay);
+      sum[2] = df_add(sum[2], hh[0]);
+      sum[3] = df_add(sum[3], hh[1]);
+      sum[4] = df_add(sum[4], hh[2]);
+    } else {
+      double e[5] = {0, 0, 0, 0, 0};
+      eval64<true>(all64 + (size_t)h * REC64, X, Y, e[0], e[1], e[2], e[3], e[4]);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] += e[k];
+    }
   }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k] += df_to_double(sum[k]);
   block_sum<5, CACHE_THREADS>(v, s_red);
   if (threadIdx.x == 0)
     for (int k = 0; k < 5; ++k) stat[(size_t)img * 5 + k] = v[k];

@@ -788,6 +788,46 @@ __device__ __forceinline__ void add_potential_df(const float2 *__restrict__ rdf,
   }
 }
 
+// The two varying potentials of a parameter set at (X, Y): both in
+// double-float, summed in double-float and added to acc[0..4] with one
+// conversion each (the FP64 pipe runs at 1/64 of the FP32 rate); FP64 for a
+// potential whose double-float evaluation fails.
+template <bool HESS>
+__device__ __forceinline__ void add_varying_df(const float2 *__restrict__ rdf, const double *__restrict__ r64,
+                                               double X, double Y, double *acc) {
+  const df Xd = df_from_double(X), Yd = df_from_double(Y);
+  df sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const float2 *r = rdf + v * RECDF;
+    df ax, ay, h[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    bool ok = true;
+    if (r[F_U2].x < 0.f)
+      circ_df<HESS>(r, 1, Xd, Yd, ax, ay, h);
+    else
+      ok = dpie_df<true, HESS>(r, 1, Xd, Yd, ax, ay, h);
+    if (ok) {
+      sum[0] = df_add(sum[0], ax);
+      sum[1] = df_add(sum[1], ay);
+      if (HESS) {
+        sum[2] = df_add(sum[2], h[0]);
+        sum[3] = df_add(sum[3], h[1]);
+        sum[4] = df_add(sum[4], h[2]);
+      }
+    } else {
+      double bx, by, bk = 0, b1 = 0, b2 = 0;
+      eval64<HESS>(r64 + v * REC64, X, Y, bx, by, bk, b1, b2);
+      acc[0] += bx;
+      acc[1] += by;
+      acc[2] += bk;
+      acc[3] += b1;
+      acc[4] += b2;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < (HESS ? 5 : 2); ++q) acc[q] += df_to_double(sum[q]);
+}
+
 // Back-trace every constraint of one parameter set in FP64 (Sec. 2.1 Eq. 1):
 // beta_j = theta_j - r alpha(theta_j), with alpha = static cache + the two
 // varying potentials (FP64 records in s_rec; their double-float records in
@@ -806,14 +846,14 @@ __device__ __forceinline__ void backtrace_set(const double *__restrict__ stat, c
     const double X = x[j], Y = y[j];
     const double *st = stat + (size_t)j * 5;
     double acc[5] = {st[0], st[1], st[2], st[3], st[4]};
+    if (s_rdf) {
+      if (s_m)
+        add_varying_df<true>(s_rdf, s_rec, X, Y, acc);
+      else
+        add_varying_df<false>(s_rdf, s_rec, X, Y, acc);
+    } else {
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-      if (s_rdf) {
-        if (s_m)
-          add_potential_df<true>(s_rdf + v * RECDF, 1, s_rec + v * REC64, X, Y, acc);
-        else
-          add_potential_df<false>(s_rdf + v * RECDF, 1, s_rec + v * REC64, X, Y, acc);
-      } else {
+      for (int v = 0; v < 2; ++v) {
         double bx, by, bk = 0, b1 = 0, b2 = 0;
         if (s_m)
           eval64<true>(s_rec + v * REC64, X, Y, bx, by, bk, b1, b2);
@@ -843,9 +883,9 @@ __device__ __forceinline__ void backtrace_set(const double *__restrict__ stat, c
       sx += s_beta[2 * j];
       sy += s_beta[2 * j + 1];
     }
-    const int m = e - b;
-    s_bary[2 * i] = m > 0 ? sx / m : 0.0;
-    s_bary[2 * i + 1] = m > 0 ? sy / m : 0.0;
+    const double im = e > b ? 1.0 / (e - b) : 0.0;
+    s_bary[2 * i] = sx * im;
+    s_bary[2 * i + 1] = sy * im;
   }
   __syncthreads();
 }

@@ -70,8 +70,9 @@ __host__ __device__ inline void make_rec64(int type, double x0, double y0, doubl
   double u = 2.0 * sqrt(eps) / (1.0 + eps);
   double b = b0 * (1.0 + eps);
   double sc = rcore * (1.0 + eps), st = rcut * (1.0 + eps);
-  r[D_C] = cos(theta);
-  r[D_S] = sin(theta);
+  const double c = cos(theta), s = sin(theta);
+  r[D_C] = c;
+  r[D_S] = s;
   r[D_Q2] = q * q;
   r[D_U] = u;
   r[D_U2] = u * u;
@@ -80,8 +81,8 @@ __host__ __device__ inline void make_rec64(int type, double x0, double y0, doubl
   r[D_ST] = st;
   r[D_DS] = st - sc;
   r[D_SS] = st + sc;
-  r[D_C2T] = cos(2.0 * theta);
-  r[D_S2T] = sin(2.0 * theta);
+  r[D_C2T] = (c - s) * (c + s);  // double-angle formulas
+  r[D_S2T] = 2.0 * s * c;
   r[D_KIND] = u < U_SERIES64 ? K64_DPIE_SERIES : K64_DPIE;
 }
 
@@ -175,8 +176,9 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
   } else {
     const double q = (1.0 - eps) / (1.0 + eps), u = 2.0 * sqrt(eps) / (1.0 + eps);
     const double q2 = q * q, sc = rcore * (1.0 + eps), st = rcut * (1.0 + eps);
-    v[F_C] = cos(theta);
-    v[F_S] = sin(theta);
+    const double c = cos(theta), s = sin(theta);
+    v[F_C] = c;
+    v[F_S] = s;
     v[F_Q2] = q2;
     v[F_U2] = u * u;
     v[F_KC] = q2 * sc * sc;
@@ -189,8 +191,8 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
     v[F_Q2DS] = q2 * (st - sc);
     v[F_SS] = st + sc;
     v[F_BQ] = b0 * (1.0 + eps) * q;
-    v[F_C2] = cos(2.0 * theta);
-    v[F_S2] = sin(2.0 * theta);
+    v[F_C2] = (c - s) * (c + s);  // cos 2 theta, sin 2 theta by the double-angle formulas
+    v[F_S2] = 2.0 * s * c;
     v[F_DC0] = (1.0 + q2) * sc * sc;
     v[F_DT0] = (1.0 + q2) * st * st;
     v[F_U2SC2] = u * u * sc * sc;
