@@ -375,8 +375,14 @@ __device__ __forceinline__ float atan_fast(float w) {
 //   psi_yy' - psi_xx' = b q ((y^2 - x^2)(fc - ft) - u^2 (sc^2 fc - st^2 ft)),
 //   psi_xy' = -b q xy (fc - ft),  f = 1/(psi D),
 // rotated by 2 theta.  The factor b q rides on the rotation constants.
-template <bool HESS, int KP, bool SERIES, bool FAST = false>
-__device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
+// dX of point k: one value shared by the KP points (a map column) or one
+// per point.
+__device__ __forceinline__ float dx_of(float dX, int) { return dX; }
+template <int KP>
+__device__ __forceinline__ float dx_of(const float (&dX)[KP], int k) { return dX[k]; }
+
+template <bool HESS, int KP, bool SERIES, bool FAST = false, typename DX>
+__device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, const DX &dX, const float (&dY)[KP],
                                        Acc<HESS, KP> &p) {
   const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
   const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
@@ -384,11 +390,11 @@ __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, 
   const float dK = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
   const float q2dS = D.y;
   const float cb = E.x, sb = E.y;
-  const float cdX = c * dX, sdX = s * dX;
   float x[KP], y[KP], x2[KP], y2[KP], u2x2[KP], ic[KP], it[KP], psc[KP], pst[KP], Ec[KP], Et[KP];
   float Zx[KP], Zy[KP], tx[KP], ty[KP];
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
+    const float cdX = c * dx_of(dX, k), sdX = s * dx_of(dX, k);  // once when dX is shared
     x[k] = fmaf(s, dY[k], cdX);
     y[k] = fmaf(c, dY[k], -sdX);
     x2[k] = x[k] * x[k];
@@ -466,13 +472,13 @@ __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, float dX, 
 }
 
 // SIS / point mass (FP32): circular, evaluated directly on (dX, dY).
-template <bool HESS, int KP, bool POINT>
-__device__ __forceinline__ void circ32(const float4 *__restrict__ r4, float x, const float (&dY)[KP],
+template <bool HESS, int KP, bool POINT, typename DX>
+__device__ __forceinline__ void circ32(const float4 *__restrict__ r4, const DX &dX, const float (&dY)[KP],
                                        Acc<HESS, KP> &p) {
   const float b = r4[7].y;
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
-    const float y = dY[k];
+    const float x = dx_of(dX, k), y = dY[k];
     const float r2 = fmaf(x, x, y * y);
     if (POINT) {
       const float ir2 = r2 > 0.f ? rcp_a(r2) : 0.f;
@@ -499,10 +505,10 @@ __device__ __forceinline__ void circ32(const float4 *__restrict__ r4, float x, c
   }
 }
 
-// Any FP32 potential at KP points sharing dX (kind is warp-uniform in the
-// map kernel; per-lane in the image kernels).
-template <bool HESS, int KP, bool FAST = false>
-__device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, float dX, const float (&dY)[KP],
+// Any FP32 potential at KP points (kind is warp-uniform in the map kernel;
+// per-lane in the image kernels).
+template <bool HESS, int KP, bool FAST = false, typename DX>
+__device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, const DX &dX, const float (&dY)[KP],
                                            Acc<HESS, KP> &p) {
   const int kind = __float_as_int(r4[7].x);
   if (kind == K32_DPIE)

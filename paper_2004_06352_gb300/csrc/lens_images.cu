@@ -500,13 +500,10 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     hy[k] = (float)py[k];
     ly[k] = (float)(py[k] - (double)hy[k]);
   }
-  Acc<HESS, 1> tot[NP], cmp[NP], part[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    tot[k].zero();
-    cmp[k].zero();
-    part[k].zero();
-  }
+  Acc<HESS, NP> tot, cmp, part;  // the NP points side by side (one range branch per potential)
+  tot.zero();
+  cmp.zero();
+  part.zero();
   int seen = 0;
   const float4 *g_rec = reinterpret_cast<const float4 *>(n.rec32);
   const float4 *g_cen = reinterpret_cast<const float4 *>(n.cen32);
@@ -532,21 +529,22 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
       for (int h = h0 + gl; h < h1; h += RF_G) {
         const float4 *r4 = s_rec + h * RF_STRIDE4;
         const float4 c = s_cen[h];
+        float dX[NP], dY[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
-          const float dX = (hx[k] - c.x) + (lx[k] - c.z), dY[1] = {(hy[k] - c.y) + (ly[k] - c.w)};
-          if (KIND == K32_DPIE)
-            dpie32<HESS, 1, false>(r4, dX, dY, part[k]);
-          else if (KIND == K32_DPIE_SERIES)
-            dpie32<HESS, 1, true>(r4, dX, dY, part[k]);
-          else if (KIND == K32_SIS || KIND == K32_POINT)
-            circ32<HESS, 1, KIND == K32_POINT>(r4, dX, dY, part[k]);
-          else
-            eval32_any<HESS, 1>(r4, dX, dY, part[k]);
+          dX[k] = (hx[k] - c.x) + (lx[k] - c.z);
+          dY[k] = (hy[k] - c.y) + (ly[k] - c.w);
         }
+        if (KIND == K32_DPIE)
+          dpie32<HESS, NP, false>(r4, dX, dY, part);
+        else if (KIND == K32_DPIE_SERIES)
+          dpie32<HESS, NP, true>(r4, dX, dY, part);
+        else if (KIND == K32_SIS || KIND == K32_POINT)
+          circ32<HESS, NP, KIND == K32_POINT>(r4, dX, dY, part);
+        else
+          eval32_any<HESS, NP>(r4, dX, dY, part);
         if (++seen == 16) {
-#pragma unroll
-          for (int k = 0; k < NP; ++k) fold(tot[k], cmp[k], part[k]);
+          fold(tot, cmp, part);
           seen = 0;
         }
       }
@@ -570,15 +568,14 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     }
   }
   constexpr int NC = HESS ? 5 : 2;
+  fold(tot, cmp, part);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
-    fold(tot[k], cmp[k], part[k]);
     // each thread's compensated sum tot - cmp as a float pair, combined over
     // the group in double-float (TwoSum gives both partners the same bits)
-    float hi[5] = {tot[k].ax[0], tot[k].ay[0], HESS ? tot[k].k[0] : 0.f, HESS ? tot[k].g1[0] : 0.f,
-                   HESS ? tot[k].g2[0] : 0.f};
-    float lo[5] = {-cmp[k].ax[0], -cmp[k].ay[0], HESS ? -cmp[k].k[0] : 0.f, HESS ? -cmp[k].g1[0] : 0.f,
-                   HESS ? -cmp[k].g2[0] : 0.f};
+    float hi[5] = {tot.ax[k], tot.ay[k], HESS ? tot.k[k] : 0.f, HESS ? tot.g1[k] : 0.f, HESS ? tot.g2[k] : 0.f};
+    float lo[5] = {-cmp.ax[k], -cmp.ay[k], HESS ? -cmp.k[k] : 0.f, HESS ? -cmp.g1[k] : 0.f,
+                   HESS ? -cmp.g2[k] : 0.f};
 #pragma unroll
     for (int o = 1; o < RF_G; o <<= 1)
 #pragma unroll
