@@ -526,24 +526,29 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     // kind; the two varying ones at the end take the general dispatch)
     auto run = [&](auto kind_tag, int h0, int h1) {
       constexpr int KIND = decltype(kind_tag)::value;
-      for (int h = h0 + gl; h < h1; h += RF_G) {
-        const float4 *r4 = s_rec + h * RF_STRIDE4;
-        const float4 c = s_cen[h];
-        float dX[NP], dY[NP];
+      for (int h = h0 + gl; h < h1;) {
+        // this thread's potentials up to the next fold (every 16 of them)
+        const int hs = h, he = min(h1, h + (16 - seen) * RF_G);
+        for (; h < he; h += RF_G) {
+          const float4 *r4 = s_rec + h * RF_STRIDE4;
+          const float4 c = s_cen[h];
+          float dX[NP], dY[NP];
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          dX[k] = (hx[k] - c.x) + (lx[k] - c.z);
-          dY[k] = (hy[k] - c.y) + (ly[k] - c.w);
+          for (int k = 0; k < NP; ++k) {
+            dX[k] = (hx[k] - c.x) + (lx[k] - c.z);
+            dY[k] = (hy[k] - c.y) + (ly[k] - c.w);
+          }
+          if (KIND == K32_DPIE)
+            dpie32<HESS, NP, false>(r4, dX, dY, part);
+          else if (KIND == K32_DPIE_SERIES)
+            dpie32<HESS, NP, true>(r4, dX, dY, part);
+          else if (KIND == K32_SIS || KIND == K32_POINT)
+            circ32<HESS, NP, KIND == K32_POINT>(r4, dX, dY, part);
+          else
+            eval32_any<HESS, NP>(r4, dX, dY, part);
         }
-        if (KIND == K32_DPIE)
-          dpie32<HESS, NP, false>(r4, dX, dY, part);
-        else if (KIND == K32_DPIE_SERIES)
-          dpie32<HESS, NP, true>(r4, dX, dY, part);
-        else if (KIND == K32_SIS || KIND == K32_POINT)
-          circ32<HESS, NP, KIND == K32_POINT>(r4, dX, dY, part);
-        else
-          eval32_any<HESS, NP>(r4, dX, dY, part);
-        if (++seen == 16) {
+        seen += (h - hs) / RF_G;
+        if (seen == 16) {
           fold(tot, cmp, part);
           seen = 0;
         }
