@@ -239,7 +239,9 @@ def main():
         ctx.hessian_map_host(mid2, g, 1.0, api.LENS_MIXED, host, stream)
         ctx.wait(stream)
         dt = time.perf_counter() - t1
-        h2d_bytes = ctx.model_bytes(mid2)  # the model's device records, copied from the host
+        # what lens_model_upload copies: the halo table (64-byte records) and
+        # one int32 slot per potential; the records are built on the device
+        h2d_bytes = len(m) * (api.HALO_BYTES + 4)
         ctx.model_release(mid2)
         if k >= args.warmup:
             e2e_ms.append(dt * 1e3)

@@ -126,18 +126,19 @@ int lens_set_fp64_threshold(lens_ctx *ctx, double threshold_b0);
  * blocks kept for reuse by later uploads; those are freed first when an
  * allocation would exceed the budget). */
 size_t lens_mem_used(const lens_ctx *ctx);
-/* Bytes of device records of an uploaded model (what lens_model_upload
- * copied to the device); 0 for an unknown model. */
+/* Device bytes holding an uploaded model (its records and the staged halo
+ * table they were built from); 0 for an unknown model. */
 size_t lens_model_bytes(lens_ctx *ctx, lens_model_t model);
 
 /* ------------------------------------------------------------------ models */
 
 /* Upload n >= 1 potentials (host array, copied).  Validates every field
- * (LENS_EINVAL on the first bad one), precomputes the per-potential
- * constants on the host in double precision and stores them on the device
- * (Sec. 3.2 structure-of-arrays discussion; here a packed per-potential
- * record read by all threads at once).  Synchronous.  The model is immutable
- * and owned by the context until lens_model_release. */
+ * (LENS_EINVAL on the first bad one) and orders the potentials on the host,
+ * copies the table (n x 64 bytes) and one int32 slot per potential to the
+ * device, where one kernel precomputes every potential's constants in double
+ * precision into its records (Sec. 3.2 structure-of-arrays discussion; here
+ * a packed per-potential record read by all threads at once).  Synchronous.
+ * The model is immutable and owned by the context until lens_model_release. */
 int lens_model_upload(lens_ctx *ctx, const lens_halo *h, int32_t n, lens_model_t *out);
 int lens_model_release(lens_ctx *ctx, lens_model_t model);
 

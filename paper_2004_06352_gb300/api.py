@@ -45,6 +45,9 @@ class lens_halo(C.Structure):
                 ("eps", C.c_double), ("rcore", C.c_double), ("rcut", C.c_double), ("b0", C.c_double)]
 
 
+HALO_BYTES = C.sizeof(lens_halo)  # one row of the halo table
+
+
 class lens_grid(C.Structure):
     _fields_ = [("xmin", C.c_double), ("xmax", C.c_double), ("ymin", C.c_double), ("ymax", C.c_double),
                 ("nx", C.c_int32), ("ny", C.c_int32)]

@@ -139,44 +139,89 @@ static int model_block(lens_ctx *ctx, size_t bytes, void **p, size_t *got) {
   return dev_alloc(ctx, p, bytes);
 }
 
-// Device store of n (already validated) potentials; n may be 0.  The record
-// arrays are built in one page-locked host image (256-byte aligned offsets)
-// and copied into one device block with one copy.
+// The records of the potentials, built on the device from the halo table,
+// three threads per potential (the FP64 arithmetic runs at 1/64 of the FP32
+// rate, so the work is spread): part 0 the FP64 record (upload order) and,
+// for a heavy potential (slot = -1 - heavy index), its copy in the heavy
+// table; part 1 the double-float record; part 2, for a light potential
+// (slot >= 0, the kind-sorted order), the FP32 record and position data.
+__global__ void k_build_records(const lens_halo *__restrict__ h, const int32_t *__restrict__ slot, int n,
+                                float *rec32, double *pos64, float *cen32, double *heavy, double *all64,
+                                float2 *recdf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int k = t / 3, part = t % 3;
+  const lens_halo a = h[k];
+  const int s = slot[k];
+  if (part == 0) {
+    double r[REC64];
+    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, r);
+    for (int q = 0; q < REC64; ++q) all64[(size_t)k * REC64 + q] = r[q];
+    if (s < 0)
+      for (int q = 0; q < REC64; ++q) heavy[(size_t)(-1 - s) * REC64 + q] = r[q];
+  } else if (part == 1) {
+    make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, recdf + k, n);
+  } else if (s >= 0) {
+    make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, rec32 + (size_t)s * REC32);
+    const bool circ = a.type != LENS_DPIE;
+    pos64[4 * s + 0] = a.x0;
+    pos64[4 * s + 1] = a.y0;
+    pos64[4 * s + 2] = circ ? 1.0 : cos(a.theta);
+    pos64[4 * s + 3] = circ ? 0.0 : sin(a.theta);
+    const float xh = (float)a.x0, yh = (float)a.y0;
+    cen32[4 * s + 0] = xh;
+    cen32[4 * s + 1] = yh;
+    cen32[4 * s + 2] = (float)(a.x0 - (double)xh);
+    cen32[4 * s + 3] = (float)(a.y0 - (double)yh);
+  }
+}
+
+// Device store of n (already validated) potentials; n may be 0.  The host
+// only classifies and orders the potentials: the halo table and each
+// potential's slot go through the context's page-locked staging buffer into
+// one device block (one copy, 256-byte aligned sections), where one kernel
+// builds every record in parallel; the upload is complete on return.
 int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   Model *m = new Model();
   m->n = n;
   m->host.assign(h, h + n);
   // light potentials grouped by kind so each warp-uniform branch runs in one stretch
   std::vector<int32_t> light, heavy;
-  for (int32_t i = 0; i < n; ++i) (h[i].b0 >= ctx->fp64_threshold ? heavy : light).push_back(i);
-  std::stable_sort(light.begin(), light.end(),
-                   [&](int32_t a, int32_t b) { return kind_order(h[a]) < kind_order(h[b]); });
+  std::vector<int32_t> kind(n);
+  for (int32_t i = 0; i < n; ++i) {
+    kind[i] = kind_order(h[i]);
+    (h[i].b0 >= ctx->fp64_threshold ? heavy : light).push_back(i);
+  }
+  std::stable_sort(light.begin(), light.end(), [&](int32_t a, int32_t b) { return kind[a] < kind[b]; });
   m->n_light = (int32_t)light.size();
   m->n_heavy = (int32_t)heavy.size();
   for (int k = 0; k < 4; ++k) {
     int32_t c = 0;
-    for (int32_t i : light) c += kind_order(h[i]) < k ? 1 : 0;
+    for (int32_t i : light) c += kind[i] < k ? 1 : 0;
     m->koff[k] = c;
   }
   m->koff[4] = m->n_light;
   const size_t nl = (size_t)m->n_light, nh = (size_t)m->n_heavy, na = (size_t)n;
-  const size_t sizes[6] = {nl * REC32 * sizeof(float), nl * 4 * sizeof(double), nl * 4 * sizeof(float),
-                           nh * REC64 * sizeof(double), na * REC64 * sizeof(double), na * RECDF * sizeof(float2)};
-  size_t offs[6], total = 0;
-  for (int k = 0; k < 6; ++k) {
+  // records (built on the device), then the staged halo table and slots
+  const size_t sizes[8] = {nl * REC32 * sizeof(float),  nl * 4 * sizeof(double),     nl * 4 * sizeof(float),
+                           nh * REC64 * sizeof(double), na * REC64 * sizeof(double),   na * RECDF * sizeof(float2),
+                           na * sizeof(lens_halo),      na * sizeof(int32_t)};
+  size_t offs[8], total = 0;
+  for (int k = 0; k < 8; ++k) {
     offs[k] = total;
     total += (sizes[k] + 255) & ~(size_t)255;
   }
-  // host image: the context's page-locked staging buffer (pageable if that
-  // cannot be had)
+  const size_t staged = total - offs[6];
+  // host image of the staged part: the context's page-locked staging buffer
+  // (pageable if that cannot be had)
   std::vector<unsigned char> pageable;
   unsigned char *img = nullptr;
-  if (ctx->h_stage_bytes < total) {
+  if (ctx->h_stage_bytes < staged) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     ctx->h_stage = nullptr;
     ctx->h_stage_bytes = 0;
-    if (cudaHostAlloc(&ctx->h_stage, total, cudaHostAllocDefault) == cudaSuccess) {
-      ctx->h_stage_bytes = total;
+    if (cudaHostAlloc(&ctx->h_stage, staged, cudaHostAllocDefault) == cudaSuccess) {
+      ctx->h_stage_bytes = staged;
     } else {
       cudaGetLastError();
       ctx->h_stage = nullptr;
@@ -185,38 +230,13 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   if (ctx->h_stage) {
     img = (unsigned char *)ctx->h_stage;
   } else {
-    pageable.resize(total);
+    pageable.resize(staged);
     img = pageable.data();
   }
-  std::memset(img, 0, total);
-  float *r32 = (float *)(img + offs[0]);
-  double *p64 = (double *)(img + offs[1]);
-  float *c32 = (float *)(img + offs[2]);
-  double *hv = (double *)(img + offs[3]), *a64 = (double *)(img + offs[4]);
-  float2 *adf = (float2 *)(img + offs[5]);
-  for (int32_t k = 0; k < m->n_light; ++k) {
-    const lens_halo &a = h[light[k]];
-    make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, &r32[(size_t)k * REC32]);
-    bool circ = a.type != LENS_DPIE;
-    p64[4 * k + 0] = a.x0;
-    p64[4 * k + 1] = a.y0;
-    p64[4 * k + 2] = circ ? 1.0 : std::cos(a.theta);
-    p64[4 * k + 3] = circ ? 0.0 : std::sin(a.theta);
-    float xh = (float)a.x0, yh = (float)a.y0;
-    c32[4 * k + 0] = xh;
-    c32[4 * k + 1] = yh;
-    c32[4 * k + 2] = (float)(a.x0 - (double)xh);
-    c32[4 * k + 3] = (float)(a.y0 - (double)yh);
-  }
-  for (int32_t k = 0; k < m->n_heavy; ++k) {
-    const lens_halo &a = h[heavy[k]];
-    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &hv[(size_t)k * REC64]);
-  }
-  for (int32_t k = 0; k < n; ++k) {
-    const lens_halo &a = h[k];
-    make_rec64(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &a64[(size_t)k * REC64]);
-    make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, &adf[k], n);
-  }
+  if (n > 0) std::memcpy(img, h, na * sizeof(lens_halo));
+  int32_t *slot = (int32_t *)(img + (offs[7] - offs[6]));
+  for (int32_t k = 0; k < m->n_light; ++k) slot[light[k]] = k;
+  for (int32_t k = 0; k < m->n_heavy; ++k) slot[heavy[k]] = -1 - k;
   int rc = total ? model_block(ctx, total, &m->block, &m->bytes) : LENS_OK;
   if (rc == LENS_ENOMEM && !ctx->block_cache.empty()) {
     flush_block_cache(ctx);
@@ -234,10 +254,21 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->heavy = (double *)(base + offs[3]);
   m->all64 = (double *)(base + offs[4]);
   m->recdf = (float2 *)(base + offs[5]);
-  const cudaError_t e = total ? cudaMemcpy(m->block, img, total, cudaMemcpyHostToDevice) : cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (n > 0) {
+    if (!ctx->upload_st) e = cudaStreamCreateWithFlags(&ctx->upload_st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + offs[6], img, staged, cudaMemcpyHostToDevice, ctx->upload_st);
+    if (e == cudaSuccess) {
+      k_build_records<<<(3 * n + 63) / 64, 64, 0, ctx->upload_st>>>(
+          (const lens_halo *)(base + offs[6]), (const int32_t *)(base + offs[7]), n, m->rec32, m->pos64, m->cen32,
+          m->heavy, m->all64, m->recdf);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload_st);
+  }
   if (e != cudaSuccess) {
     free_model(ctx, m);
-    return fail(LENS_ECUDA, "model upload copy: %s", cudaGetErrorString(e));
+    return fail(LENS_ECUDA, "model upload: %s", cudaGetErrorString(e));
   }
   *out = m;
   return LENS_OK;
@@ -319,6 +350,7 @@ int lens_destroy(lens_ctx *ctx) {
     if (ctx->pipe_copied[k]) cudaEventDestroy(ctx->pipe_copied[k]);
   }
   if (ctx->pipe_cp) cudaStreamDestroy(ctx->pipe_cp);
+  if (ctx->upload_st) cudaStreamDestroy(ctx->upload_st);
   if (ctx->pipe_start) cudaEventDestroy(ctx->pipe_start);
   delete ctx;
   return LENS_OK;

@@ -803,8 +803,8 @@ __device__ __forceinline__ void add_varying_df(const float2 *__restrict__ rdf, c
                                                double X, double Y, double *acc) {
   const df Xd = df_from_double(X), Yd = df_from_double(Y);
   df sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll
-  for (int v = 0; v < 2; ++v) {
+#pragma unroll 1
+  for (int v = 0; v < 2; ++v) {  // not unrolled: one copy of the (large) evaluator in the code
     const float2 *r = rdf + v * RECDF;
     df ax, ay, h[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     bool ok = true;

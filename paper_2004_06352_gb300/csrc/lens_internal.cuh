@@ -208,7 +208,7 @@ __host__ __device__ inline void make_recdf(int type, double x0, double y0, doubl
 
 struct Model {
   void *block = nullptr;    // one device allocation holding every array below
-  size_t payload = 0;       // bytes of records copied into it (bytes: the block's size)
+  size_t payload = 0;       // bytes of the records and staged table in it (bytes: the block's size)
   int32_t n = 0, n_light = 0, n_heavy = 0;
   int32_t koff[5] = {0, 0, 0, 0, 0};  // light potentials sorted by kind: Kind32 k occupies [koff[k], koff[k+1])
   float *rec32 = nullptr;
@@ -272,6 +272,7 @@ struct lens_ctx {
   size_t cached_bytes = 0;
   void *h_stage = nullptr;
   size_t h_stage_bytes = 0;
+  cudaStream_t upload_st = nullptr;  // model uploads (record building on the device)
   cudaStream_t pipe_cs[2] = {nullptr, nullptr}, pipe_cp = nullptr;
   cudaEvent_t pipe_start = nullptr, pipe_done[2] = {nullptr, nullptr}, pipe_copied[2] = {nullptr, nullptr};
 };
