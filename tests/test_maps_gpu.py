@@ -124,6 +124,20 @@ def test_full_size_cfg2_sampled(lens):
     check_mixed(got, ref, True)
 
 
+def test_full_size_cfg2_sampled_deflection_only(lens):
+    """The deflection-only kernel (its own launch shape: 4 points per thread)
+    on the 2048^2 x 1000 workload; 12k sampled nodes against the oracle."""
+    m, g = I.cfg2_model(), I.grid(2048)
+    res = run_map(lens, m, g, 0.7, lens.LENS_MIXED, False)
+    rng = np.random.default_rng(25)
+    n = 12000
+    ii, jj = rng.integers(0, 2048, n), rng.integers(0, 2048, n)
+    ii[:4], jj[:4] = [0, 2047, 0, 2047], [0, 0, 2047, 2047]  # corners
+    dx = 200.0 / 2047
+    ev = oracle.model_eval(m, -100.0 + ii * dx, -100.0 + jj * dx, 0.7)
+    check_mixed(res[:, jj, ii], np.stack([ev[:, 0], ev[:, 1]]), False)
+
+
 def test_invalid_inputs_rejected(lens):
     with lens.Context(0) as ctx:
         bad = [I.halo_row(I.DPIE, 0, 0, 0, 1.0, 1, 10, 1),      # eps = 1
