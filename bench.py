@@ -34,11 +34,26 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
 # (~1 op per pair) is included.
 FP32_OPS_PER_PAIR = 64.9
 MUFU_OPS_PER_PAIR = 6.03
+# the same count for the potential-map kernel (ncu, same workload)
+POT_FP32_OPS_PER_PAIR = 48.9
 # DRAM bytes (read + write) of one launch of that kernel on that workload,
 # from the same ncu capture; the 100.7 MB of output are partly still in L2
 # when the kernel ends
 MAP_TRAFFIC_BYTES = 482816 + 39919616
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
+
+
+def hbm_peak_gbs():
+    """The measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json
+    beside this file), else the fallback figure; and which it is."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        if v > 0:
+            return v, "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        pass
+    return 6800.0, "fallback"
 
 
 def parse():
@@ -48,7 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the chi2 / FP64 comparison legs")
-    ap.add_argument("--profile-leg", default=None, choices=["map", "chi2_source", "chi2_image"],
+    ap.add_argument("--profile-leg", default=None, choices=["map", "potential", "chi2_source", "chi2_image"],
                     help="run only this workload `--steps` times (for ncu launch lists); prints nothing")
     return ap.parse_args()
 
@@ -269,6 +284,11 @@ def main():
                             "frac": mach / (SMS * MUFU_LANES * f_max / 1e12)}
     else:
         roof.update({"achieved": None, "peak": SMS * FP32_LANES * f_max / 1e12, "frac": None})
+    # the map's DRAM traffic against the measured copy bandwidth (the output
+    # planes are written once; the kernel is nowhere near this bound)
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    hbm_ach = MAP_TRAFFIC_BYTES / (ms * 1e-3) / 1e9
+    roof["hbm"] = {"achieved_gbs": hbm_ach, "peak_gbs": hbm_peak, "frac": hbm_ach / hbm_peak, "peak_source": hbm_src}
     cpu = extra.pop("cpu_baseline", None)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -304,6 +324,15 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     out2 = torch.empty((2, MAP_N, MAP_N), dtype=torch.float32, device=dev)
     t = timed(lambda: ctx.grad_map(mid, g, 1.0, api.LENS_MIXED, out2, stream), 5)
     ex["grad_map_mixed"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3)}
+    # potential + time-delay (Fermat) surface about a source position
+    outp = torch.empty((2, MAP_N, MAP_N), dtype=torch.float64, device=dev)
+    t = timed(lambda: ctx.potential_map(mid, g, 1.0, api.LENS_MIXED, outp, beta=(1.0, -2.0), stream=stream), 5)
+    ex["potential_map_mixed"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3),
+                                 "ops_per_pair": POT_FP32_OPS_PER_PAIR,
+                                 "fp32_frac": POT_FP32_OPS_PER_PAIR * pairs / (t * 1e-3)
+                                 / (SMS * FP32_LANES * 2.07e9) if POT_FP32_OPS_PER_PAIR else None,
+                                 "workload": "potential + Fermat surface, 2048^2 x 1000, LENS_MIXED"}
+    del outp
     out64 = torch.empty((6, MAP_N, MAP_N), dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.hessian_map(mid, g, 1.0, api.LENS_FP64, out64, stream), 1)
     ex["hessian_map_fp64_gpu"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3)}
@@ -409,6 +438,10 @@ def profile_leg(args):
         g = I.grid(MAP_N)
         out = torch.empty((6, MAP_N, MAP_N), dtype=torch.float32, device=dev)
         run = lambda: ctx.hessian_map(mid, g, 1.0, api.LENS_MIXED, out)
+    elif args.profile_leg == "potential":
+        g = I.grid(MAP_N)
+        out = torch.empty((2, MAP_N, MAP_N), dtype=torch.float64, device=dev)
+        run = lambda: ctx.potential_map(mid, g, 1.0, api.LENS_MIXED, out, beta=(1.0, -2.0))
     else:
         cons = I.load_constraints(os.path.join(ROOT, "tests", "golden", "cfg2_constraints.json"))
         cs = ctx.cset_create(mid, cons, (0, 1))

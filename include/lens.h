@@ -158,6 +158,23 @@ int lens_grad_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, doub
 int lens_hessian_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
                      void *d_out, void *stream);
 
+/* Lensing potential map (Sec. 2.4's list of map kinds; the potential of
+ * Sec. 2.1 Eq. 2): d_out holds phi [ny][nx], the summed potential times
+ * dls_ds, with each dPIE term x alpha_x' + y alpha_y' - b q s ln
+ * sqrt((psi+s)^2 + u^2 x^2) (core minus cut, halo frame), SIS b r and point
+ * mass theta_E^2 ln r (0 at the centre); phi is defined up to this constant.
+ * When beta (host, {x, y} in arcsec) is not NULL, a second plane follows:
+ * the time-delay (Fermat) surface tau = |theta - beta|^2 / 2 - phi in
+ * arcsec^2 (times (1+z_l) D_l D_s / (c D_ls) it is the delay; the distances
+ * are the caller's).  The planes are double for both precisions (phi
+ * carries an additive constant of order b0 r_cut ln r_cut that float would
+ * round to ~1e-2), 8-byte aligned; errors as for lens_grad_map, and
+ * LENS_EINVAL for a non-finite beta.  LENS_MIXED evaluates the potentials
+ * below the FP64 threshold in FP32 (logarithms by the MUFU log2), the rest in
+ * FP64; LENS_FP64 evaluates every potential in FP64. */
+int lens_potential_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                       const double *beta, void *d_out, void *stream);
+
 /* The same maps written to page-locked HOST memory h_out ([2 or 6][ny][nx],
  * float for LENS_MIXED, double for LENS_FP64, from cudaHostAlloc or
  * cudaHostRegister; LENS_EINVAL otherwise).  The grid is computed in about 8

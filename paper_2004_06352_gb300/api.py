@@ -24,7 +24,7 @@ LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_bytes",
            "lens_model_upload",
-           "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_grad_map_host", "lens_hessian_map_host",
+           "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_potential_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
            "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_autotune", "lens_chi2_image",
            "lens_find_images", "lens_chi2_image_noalloc", "lens_selftest_wait", "lens_selftest_math", "lens_wait", "lens_strerror",
@@ -89,6 +89,8 @@ def load_library(path=LIB_PATH):
         "lens_model_release": (C.c_int, [vp, i64]),
         "lens_grad_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
         "lens_hessian_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
+        "lens_potential_map": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32,
+                                         C.POINTER(C.c_double), vp, vp]),
         "lens_grad_map_host": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
         "lens_hessian_map_host": (C.c_int, [vp, i64, C.POINTER(lens_grid), C.c_double, C.c_int32, vp, vp]),
         "lens_cset_create": (C.c_int, [vp, i64, C.POINTER(lens_constraints), C.POINTER(C.c_int32), C.POINTER(i64)]),
@@ -216,6 +218,15 @@ class Context:
         g = make_grid(grid)
         _check(_lib.lens_hessian_map(self.h, int(model), C.byref(g), float(dls_ds), int(precision), _ptr(out),
                                      _stream(stream)), "lens_hessian_map")
+        return out
+
+    def potential_map(self, model, grid, dls_ds, precision, out, beta=None, stream=None):
+        """Lensing potential [ny][nx] into `out`, and with beta = (x, y) the
+        time-delay (Fermat) surface as a second plane ([2][ny][nx])."""
+        g = make_grid(grid)
+        b = None if beta is None else (C.c_double * 2)(float(beta[0]), float(beta[1]))
+        _check(_lib.lens_potential_map(self.h, int(model), C.byref(g), float(dls_ds), int(precision), b, _ptr(out),
+                                       _stream(stream)), "lens_potential_map")
         return out
 
     def grad_map_host(self, model, grid, dls_ds, precision, out, stream=None):

@@ -430,6 +430,22 @@ static int map_common(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, 
   return fail(LENS_EINVAL, "precision must be LENS_FP64 or LENS_MIXED");
 }
 
+int lens_potential_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
+                       const double *beta, void *d_out, void *stream) {
+  if (!ctx || !d_out) return fail(LENS_EINVAL, "NULL argument");
+  Model *m = find_model(ctx, model);
+  if (!m) return fail(LENS_ENOTFOUND, "model %lld not found", (long long)model);
+  int rc = check_grid(grid);
+  if (rc) return rc;
+  if (!(std::isfinite(dls_ds) && dls_ds > 0.0)) return fail(LENS_EINVAL, "dls_ds must be finite and > 0");
+  if (precision != LENS_MIXED && precision != LENS_FP64)
+    return fail(LENS_EINVAL, "precision must be LENS_FP64 or LENS_MIXED");
+  if (beta && !(std::isfinite(beta[0]) && std::isfinite(beta[1]))) return fail(LENS_EINVAL, "beta must be finite");
+  if ((uintptr_t)d_out % 8) return fail(LENS_EINVAL, "d_out must be 8-byte aligned (double planes)");
+  cudaSetDevice(ctx->device);
+  return launch_pot_map(ctx, m, grid, dls_ds, precision, beta, d_out, (cudaStream_t)stream);
+}
+
 // Map straight to page-locked host memory: the grid in row bands computed
 // on two streams of the context (so one band's tail overlaps the next band)
 // into two device buffers, each band copied to the host on a third stream as

@@ -265,6 +265,47 @@ __device__ __forceinline__ void eval64(const double *__restrict__ r, double X, d
 }
 
 
+// Lensing potential of one potential in FP64 at (X, Y), D_ls/D_s = 1, up to
+// the same constant as the definition: dPIE x alpha_x' + y alpha_y' minus
+// b q s ln sqrt((psi + s)^2 + u^2 x^2) of each term (core minus cut); SIS
+// b r; point mass theta_E^2 ln r (0 at the centre).
+__device__ __forceinline__ double pot64(const double *__restrict__ r, double X, double Y) {
+  const int kind = (int)r[D_KIND];
+  const double dX = X - r[D_X0], dY = Y - r[D_Y0];
+  const double r2 = dX * dX + dY * dY;
+  if (kind == K64_SIS) return r[D_B] * sqrt(r2);
+  if (kind == K64_POINT) return r2 > 0.0 ? 0.5 * r[D_B] * log(r2) : 0.0;
+  // the deflection's arguments as in eval64, then the two logarithms
+  const double c = r[D_C], s = r[D_S], q2 = r[D_Q2], u = r[D_U], u2 = r[D_U2], bq = r[D_BQ];
+  const double sc = r[D_SC], st = r[D_ST], dS = r[D_DS], sS = r[D_SS];
+  const double x = c * dX + s * dY, y = c * dY - s * dX;
+  const double x2 = x * x, y2 = y * y;
+  const double R = q2 * x2 + y2;
+  const double pc2 = R + q2 * sc * sc, pt2 = R + q2 * st * st;
+  const double psc = pc2 * rsqrt64(pc2), pst = pt2 * rsqrt64(pt2);
+  const double Sp = psc + pst, Ec = psc + sc, Et = pst + st, Fc = psc + q2 * sc, Ft = pst + q2 * st;
+  const double Zx = x * dS * (Sp + q2 * sS) * rcp64(Sp * (Ec * Et + u2 * x2));
+  const double Zy = y * q2 * dS * (Sp + sS) * rcp64(Sp * (Fc * Ft - u2 * y2));
+  double axp, ayp;  // halo-frame deflection
+  if (kind == K64_DPIE_SERIES) {
+    const double wx = u2 * Zx * Zx, wy = u2 * Zy * Zy;
+    axp = bq * Zx * (1.0 - wx / 3.0 + wx * wx / 5.0);
+    ayp = bq * Zy * (1.0 + wy / 3.0 + wy * wy / 5.0);
+  } else {
+    const double wx = u * Zx, wy = u * Zy, tx = wx * wx, ty = wy * wy;
+    if (fmax(tx, ty) < T_SERIES64) {
+      axp = bq * Zx * atan_over_w64(tx);
+      ayp = bq * Zy * atanh_over_w64(ty);
+    } else {
+      const double bu = bq * rcp64(u);
+      axp = bu * atan64(wx);
+      ayp = bu * atanh64(wy);
+    }
+  }
+  const double lc = log(Ec * Ec + u2 * x2), lt = log(Et * Et + u2 * x2);
+  return x * axp + y * ayp - 0.5 * bq * (sc * lc - st * lt);
+}
+
 // ----------------------------------------------------------------- FP32 path
 template <bool HESS, int KP>
 struct Acc {
@@ -381,9 +422,12 @@ __device__ __forceinline__ float dx_of(float dX, int) { return dX; }
 template <int KP>
 __device__ __forceinline__ float dx_of(const float (&dX)[KP], int k) { return dX[k]; }
 
-template <bool HESS, int KP, bool SERIES, bool FAST = false, typename DX>
+// POT: the lensing potential instead, into p.k (Acc<true, KP>; p.ax, p.ay,
+// p.g1, p.g2 untouched): per term x alpha_x' + y alpha_y' - b q s ln sqrt(D)
+// with D = (psi + s)^2 + u^2 x^2, the logarithms by the MUFU log2.
+template <bool HESS, int KP, bool SERIES, bool FAST = false, bool POT = false, typename DX>
 __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, const DX &dX, const float (&dY)[KP],
-                                       Acc<HESS, KP> &p) {
+                                       Acc<HESS || POT, KP> &p) {
   const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
   const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
   const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
@@ -451,35 +495,54 @@ __device__ __forceinline__ void dpie32(const float4 *__restrict__ r4, const DX &
       }
     }
   }
+  if constexpr (POT) {
+    const float bq = 2.f * E.z;
 #pragma unroll
-  for (int k = 0; k < KP; ++k) {
-    p.ax[k] = fmaf(cb, axp[k], fmaf(-sb, ayp[k], p.ax[k]));
-    p.ay[k] = fmaf(sb, axp[k], fmaf(cb, ayp[k], p.ay[k]));
-    if (HESS) {
-      const float4 G = r4[5];
-      const float u2sc2 = D.z, u2st2 = D.w;
-      const float ymx = y2[k] - x2[k];
+    for (int k = 0; k < KP; ++k) {
       const float Dc = fmaf(Ec[k], Ec[k], u2x2[k]), Dt = fmaf(Et[k], Et[k], u2x2[k]);
-      const float fc = rcp_a(psc[k] * Dc), ft = rcp_a(pst[k] * Dt);
-      const float fd = fc - ft;
-      const float g1d = fmaf(ymx, fd, -fmaf(u2sc2, fc, -u2st2 * ft));
-      const float g2d = fd * (x[k] * y[k]);
-      p.k[k] = fmaf(E.z, ic[k] - it[k], p.k[k]);
-      p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
-      p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
+      const float lg = fmaf(sc, __log2f(Dc), -st * __log2f(Dt));  // sc log2 Dc - st log2 Dt
+      p.k[k] = fmaf(bq, fmaf(x[k], axp[k], fmaf(y[k], ayp[k], -0.346573590f * lg)), p.k[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      p.ax[k] = fmaf(cb, axp[k], fmaf(-sb, ayp[k], p.ax[k]));
+      p.ay[k] = fmaf(sb, axp[k], fmaf(cb, ayp[k], p.ay[k]));
+      if (HESS) {
+        const float4 G = r4[5];
+        const float u2sc2 = D.z, u2st2 = D.w;
+        const float ymx = y2[k] - x2[k];
+        const float Dc = fmaf(Ec[k], Ec[k], u2x2[k]), Dt = fmaf(Et[k], Et[k], u2x2[k]);
+        const float fc = rcp_a(psc[k] * Dc), ft = rcp_a(pst[k] * Dt);
+        const float fd = fc - ft;
+        const float g1d = fmaf(ymx, fd, -fmaf(u2sc2, fc, -u2st2 * ft));
+        const float g2d = fd * (x[k] * y[k]);
+        p.k[k] = fmaf(E.z, ic[k] - it[k], p.k[k]);
+        p.g1[k] = fmaf(G.x, g1d, fmaf(G.y, g2d, p.g1[k]));
+        p.g2[k] = fmaf(G.z, g1d, fmaf(G.w, g2d, p.g2[k]));
+      }
     }
   }
 }
 
 // SIS / point mass (FP32): circular, evaluated directly on (dX, dY).
-template <bool HESS, int KP, bool POINT, typename DX>
+// POT: the potential b r (SIS) or b ln r (point mass, b = theta_E^2; 0 at
+// the centre) into p.k.
+template <bool HESS, int KP, bool POINT, bool POT = false, typename DX>
 __device__ __forceinline__ void circ32(const float4 *__restrict__ r4, const DX &dX, const float (&dY)[KP],
-                                       Acc<HESS, KP> &p) {
+                                       Acc<HESS || POT, KP> &p) {
   const float b = r4[7].y;
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     const float x = dx_of(dX, k), y = dY[k];
     const float r2 = fmaf(x, x, y * y);
+    if constexpr (POT) {
+      if (POINT)
+        p.k[k] = fmaf(b, r2 > 0.f ? 0.346573590f * __log2f(r2) : 0.f, p.k[k]);
+      else
+        p.k[k] = fmaf(b, r2 > 0.f ? r2 * rsqrt_a(r2) : 0.f, p.k[k]);
+      continue;
+    }
     if (POINT) {
       const float ir2 = r2 > 0.f ? rcp_a(r2) : 0.f;
       const float f = b * ir2;

@@ -305,6 +305,9 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
 int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
                     cudaStream_t st, int row0 = 0, int rows = -1);
 int map_tile_rows(bool hess);  // rows per CTA tile of the mixed map kernel
+// potential map (and, when beta is not NULL, the Fermat potential about beta)
+int launch_pot_map(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, int32_t precision,
+                   const double *beta, void *out, cudaStream_t st);
 int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st);
 int launch_math_selftest(const double *x, int n, double *out, cudaStream_t st);
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);

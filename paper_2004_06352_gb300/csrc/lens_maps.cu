@@ -84,11 +84,18 @@ struct MapArgs {
   float *out;   // [planes][ny][nx] for the launch's rows
   long long plane;
   int *err;
+  int tau;          // potential map: also the Fermat potential about (bx, by)
+  double bx, by;
+  double *out64;    // potential map: [1 or 2][ny][nx] doubles
 };
 
-template <bool HESS, int KP>
-__global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD)
+// What a map computes: deflection, deflection + Hessian, or the potential.
+enum MapMode : int { MAP_GRAD = 0, MAP_HESS = 1, MAP_POT = 2 };
+
+template <int MODE, int KP>
+__global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD)
     k_map_mixed(const MapArgs a) {
+  constexpr bool HESS = MODE == MAP_HESS, POT = MODE == MAP_POT, ACC5 = HESS || POT;
   constexpr int MAP_THREADS = map_threads(HESS), MAP_WARPS = MAP_THREADS / 32;
   __shared__ __align__(128) float s_rec[2][CH * REC32];
   // Offsets of the tile from each staged potential's centre: X - x0 at the
@@ -103,7 +110,7 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
   __shared__ __align__(8) float2 s_offx[2][KP == 2 ? 1 : CH];
   __shared__ float2 s_ly[ROWS];  // row r's offset r dy inside the tile, hi/lo
   __shared__ __align__(8) uint64_t s_bar[2];
-  constexpr int NC = HESS ? 5 : 2;
+  constexpr int NC = HESS ? 5 : POT ? 1 : 2;
   __shared__ double s_hv[MAP_THREADS][KP][NC];  // FP64 potentials' sums per point
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -120,7 +127,7 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
     s_ly[tid] = make_float2(h, (float)(ly - (double)h));
   }
 
-  Acc<HESS, KP> tot, cmp, part;
+  Acc<ACC5, KP> tot, cmp, part;  // POT: the potential in .k
   tot.zero();
   cmp.zero();
   part.zero();
@@ -137,10 +144,14 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
 #pragma unroll
       for (int c = 0; c < NC; ++c) v[c] = 0.0;
       for (int h = 0; h < a.n_heavy; ++h) {
+        if constexpr (POT) {
+          v[0] += pot64(a.heavy + (size_t)h * REC64, X, Y);
+          continue;
+        }
         double ax, ay, kk = 0, q1 = 0, q2 = 0;
         eval64<HESS>(a.heavy + (size_t)h * REC64, X, Y, ax, ay, kk, q1, q2);
         v[0] += ax;
-        v[1] += ay;
+        v[NC > 1 ? 1 : 0] += ay;
         if (HESS) {
           v[NC > 2 ? 2 : 0] += kk;
           v[NC > 3 ? 3 : 0] += q1;
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
       if (base + CH + hs < a.n_light) pxy = reinterpret_cast<const double2 *>(a.pos64)[2 * (base + CH + hs)];
     }
     const float4 *recs = reinterpret_cast<const float4 *>(&s_rec[buf][0]);
-    if constexpr (HESS ? LENS_MAP_SEGMENTS : LENS_MAP_SEGMENTS_GRAD) {
+    if constexpr (HESS ? LENS_MAP_SEGMENTS : (POT || LENS_MAP_SEGMENTS_GRAD)) {
       // the potentials are sorted by kind: each kind's run inside this chunk is
       // a loop without a per-potential dispatch (Hessian kernel: 6 % faster;
       // the deflection-only kernel spills with it and keeps the plain loop)
@@ -257,11 +268,11 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
             float dX, dY[KP];
             tile_offsets(buf, h, dX, dY);
             if (KIND == K32_DPIE)
-              dpie32<HESS, KP, false>(r4, dX, dY, part);
+              dpie32<HESS, KP, false, false, POT>(r4, dX, dY, part);
             else if (KIND == K32_DPIE_SERIES)
-              dpie32<HESS, KP, true>(r4, dX, dY, part);
+              dpie32<HESS, KP, true, false, POT>(r4, dX, dY, part);
             else
-              circ32<HESS, KP, KIND == K32_POINT>(r4, dX, dY, part);
+              circ32<HESS, KP, KIND == K32_POINT, POT>(r4, dX, dY, part);
           }
           if (seen == SUB) {
             fold(tot, cmp, part);
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
       if (h0 < h1) run(std::integral_constant<int, K32_SIS>(), h0, h1);
       seg(K32_POINT, h0, h1);
       if (h0 < h1) run(std::integral_constant<int, K32_POINT>(), h0, h1);
-    } else {
+    } else if constexpr (!POT) {
       for (int h = 0; h < cnt;) {
         const int he = min(h + (SUB - seen), cnt);
         seen += he - h;
@@ -307,8 +318,20 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
 #pragma unroll
   for (int k = 0; k < KP; ++k) {
     const int j = j0 + warp * KP + k;
+    if constexpr (POT) {
+      if (i < a.nx && j < a.ny) {
+        const long long o = (long long)j * a.nx + i;
+        const double phi = a.dls * ((double)tot.k[k] - (double)cmp.k[k] + s_hv[tid][k][0]);
+        a.out64[o] = phi;
+        if (a.tau) {
+          const double X = a.xmin + i * a.dx - a.bx, Y = a.ymin + (a.row0 + j) * a.dy - a.by;
+          a.out64[a.plane + o] = 0.5 * (X * X + Y * Y) - phi;
+        }
+      }
+      continue;
+    }
     const double AX = (double)tot.ax[k] - (double)cmp.ax[k] + s_hv[tid][k][0];
-    const double AY = (double)tot.ay[k] - (double)cmp.ay[k] + s_hv[tid][k][1];
+    const double AY = (double)tot.ay[k] - (double)cmp.ay[k] + s_hv[tid][k][NC > 1 ? 1 : 0];
     double KA = 0, G1 = 0, G2 = 0;
     if (HESS) {
       KA = (double)tot.k[k] - (double)cmp.k[k] + s_hv[tid][k][NC > 2 ? 2 : 0];
@@ -331,14 +354,24 @@ __global__ void __launch_bounds__(map_threads(HESS), HESS ? LENS_MAP_MINB : LENS
   }
 }
 
-template <bool HESS>
+template <int MODE>
 __global__ void __launch_bounds__(256) k_map_fp64(const double *__restrict__ all64, int n, double xmin, double ymin,
                                                   double dx, double dy, int nx, int row0, double dls,
-                                                  double *__restrict__ out, long long plane) {
+                                                  double *__restrict__ out, long long plane, int tau = 0,
+                                                  double bx = 0.0, double by = 0.0) {
+  constexpr bool HESS = MODE == MAP_HESS;
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= plane) return;
   const int i = (int)(p % nx), j = (int)(p / nx);
   const double X = xmin + i * dx, Y = ymin + (row0 + j) * dy;
+  if constexpr (MODE == MAP_POT) {
+    double PHI = 0;
+    for (int h = 0; h < n; ++h) PHI += pot64(all64 + (size_t)h * REC64, X, Y);
+    const double phi = dls * PHI;
+    out[p] = phi;
+    if (tau) out[plane + p] = 0.5 * ((X - bx) * (X - bx) + (Y - by) * (Y - by)) - phi;
+    return;
+  }
   double AX = 0, AY = 0, KA = 0, G1 = 0, G2 = 0;
   for (int h = 0; h < n; ++h) {
     double ax, ay, kk = 0, q1 = 0, q2 = 0;
@@ -425,15 +458,18 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.out = (float *)out;
   a.plane = (long long)g->nx * rows;
   a.err = ctx->d_err;
+  a.tau = 0;
+  a.bx = a.by = 0.0;
+  a.out64 = nullptr;
   constexpr int KPG = LENS_KP_GRAD, KPH = LENS_KP_HESS;
   if (hess) {
     const int th = map_tile_rows(true);
     dim3 grid((g->nx + 31) / 32, (rows + th - 1) / th);
-    k_map_mixed<true, KPH><<<grid, map_threads(true), 0, st>>>(a);
+    k_map_mixed<MAP_HESS, KPH><<<grid, map_threads(true), 0, st>>>(a);
   } else {
     const int th = map_tile_rows(false);
     dim3 grid((g->nx + 31) / 32, (rows + th - 1) / th);
-    k_map_mixed<false, KPG><<<grid, map_threads(false), 0, st>>>(a);
+    k_map_mixed<MAP_GRAD, KPG><<<grid, map_threads(false), 0, st>>>(a);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "map kernel launch: %s", cudaGetErrorString(e));
@@ -449,13 +485,56 @@ int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dl
   const double dx = (g->xmax - g->xmin) / (g->nx - 1), dy = (g->ymax - g->ymin) / (g->ny - 1);
   const unsigned blocks = (unsigned)((plane + 255) / 256);
   if (hess)
-    k_map_fp64<true><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, row0, dls,
+    k_map_fp64<MAP_HESS><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, row0, dls,
                                               (double *)out, plane);
   else
-    k_map_fp64<false><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, row0, dls,
+    k_map_fp64<MAP_GRAD><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, row0, dls,
                                                (double *)out, plane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "FP64 map kernel launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+int launch_pot_map(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, int32_t precision,
+                   const double *beta, void *out, cudaStream_t st) {
+  const int rows = g->ny;
+  const double dx = (g->xmax - g->xmin) / (g->nx - 1), dy = (g->ymax - g->ymin) / (g->ny - 1);
+  const long long plane = (long long)g->nx * rows;
+  if (precision == LENS_FP64) {
+    const unsigned blocks = (unsigned)((plane + 255) / 256);
+    k_map_fp64<MAP_POT><<<blocks, 256, 0, st>>>(m->all64, m->n, g->xmin, g->ymin, dx, dy, g->nx, 0, dls,
+                                                 (double *)out, plane, beta != nullptr, beta ? beta[0] : 0.0,
+                                                 beta ? beta[1] : 0.0);
+  } else {
+    MapArgs a;
+    a.rec32 = m->rec32;
+    a.pos64 = m->pos64;
+    a.n_light = m->n_light;
+    for (int k = 0; k < 5; ++k) a.koff[k] = m->koff[k];
+    a.heavy = m->heavy;
+    a.n_heavy = m->n_heavy;
+    a.xmin = g->xmin;
+    a.ymin = g->ymin;
+    a.dx = dx;
+    a.dy = dy;
+    a.nx = g->nx;
+    a.ny = rows;
+    a.row0 = 0;
+    a.dls = dls;
+    a.out = nullptr;
+    a.out64 = (double *)out;
+    a.plane = plane;
+    a.err = ctx->d_err;
+    a.tau = beta != nullptr;
+    a.bx = beta ? beta[0] : 0.0;
+    a.by = beta ? beta[1] : 0.0;
+    constexpr int KPG = LENS_KP_GRAD;
+    const int th = map_tile_rows(false);
+    dim3 grid((g->nx + 31) / 32, (rows + th - 1) / th);
+    k_map_mixed<MAP_POT, KPG><<<grid, map_threads(false), 0, st>>>(a);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "potential map launch: %s", cudaGetErrorString(e));
   return LENS_OK;
 }
 

@@ -15,6 +15,13 @@ LENS_MIXED maps (FP32 bulk):
           as FP32 alone costs 6e-8 |det|).
 LENS_FP64 maps: relative 1e-11 (floor 1e-3 x peak) on every plane.
 chi2: relative 1e-8 (FP64 on both sides), absolute floor 1e-12 for chi2 ~ 0.
+Potential maps (phi is defined up to a constant; its additive part
+b q s_t ln s_t is large next to its variation over the field):
+  LENS_FP64: |d phi| <= 1e-11 * max|phi_ref|;
+  LENS_MIXED: |d phi| <= 1e-6 * (max phi_ref - min phi_ref) + 1e-9 * max|phi_ref|
+          -- each FP32 member carries ~1e-7 of its own b q s_t ln D_t term
+          (~1e-5 arcsec^2 for the members of a cluster model), a few 1e-4
+          over 1000 of them, against a variation of ~1e3-1e4 arcsec^2.
 """
 import numpy as np
 
@@ -23,6 +30,14 @@ ALPHA_FLOOR_FRAC = 0.05
 HESS_ABS = 1e-5
 DET_ABS = 3e-5
 CHI2_REL = 1e-8
+POT_FP64_REL = 1e-11
+POT_RANGE_REL = 1e-6
+POT_ABS_REL = 1e-9
+
+
+def pot_mixed_tol(ref):
+    """Absolute bound on |d phi| of a LENS_MIXED potential map (see above)."""
+    return POT_RANGE_REL * (ref.max() - ref.min()) + POT_ABS_REL * np.abs(ref).max()
 
 
 def alpha_violations(ax, ay, rx, ry, rel=ALPHA_REL, floor_frac=ALPHA_FLOOR_FRAC):
