@@ -363,6 +363,29 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P,
                          "ms_default_shape": t_default, "autotuned_shape": cfg, "graph_replay": True,
                          "workload": "source-plane chi2, 4096 parameter sets, 1000 potentials"}
+    # Metropolis sampling on the device: 4096 chains over the two cluster
+    # halos' 14 parameters, one step = proposals + batched chi2 + acceptance
+    walk = params.clone()
+    wchi2 = torch.empty(P, dtype=torch.float64, device=dev)
+    ctx.chi2_source(cs, walk, P, 0, wchi2, stream)
+    sig = torch.tensor([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1] * 2, dtype=torch.float64, device=dev)
+    scratch = torch.empty(16 * P, dtype=torch.float64, device=dev)
+    acc = torch.empty(P, dtype=torch.int32, device=dev)
+    nsteps = 20
+    state = {"k": 0, "acc": 0}
+
+    def mcmc_steps():
+        for _ in range(nsteps):
+            ctx.mcmc_step(cs, walk, wchi2, P, sig, 2000.0, 2024, state["k"], scratch, acc, stream=stream)
+            state["k"] += 1
+
+    t = timed(mcmc_steps, 1) / nsteps
+    ctx.mcmc_step(cs, walk, wchi2, P, sig, 2000.0, 2024, state["k"], scratch, acc, stream=stream)
+    torch.cuda.synchronize()
+    ex["mcmc_step"] = {"ms": t, "steps_per_s": 1e3 / t, "models_per_s": P / (t * 1e-3), "chains": P,
+                       "accept_frac_last_step": float(acc.float().mean()),
+                       "workload": "Metropolis step of 4096 chains (Philox proposals, source-plane chi2, "
+                                   "acceptance), 1000 potentials, temperature 2000"}
     # the same without the static cache: every potential at every image for
     # every set (double-float), the per-model cost when any potential may vary
     t = timed(lambda: ctx.chi2_source_nocache(cs, params, P, 0, chi2, stream), 1)

@@ -213,6 +213,27 @@ int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
 int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                      double *d_chi2, void *stream);
 
+/* One Metropolis step of W independent Markov chains over the 14 varying
+ * parameters (the Bayesian fit of Sec. 2.2: likelihood exp(-chi2/2) of the
+ * source-plane chi2 of Eq. 6, flat prior over the dPIE domain).  d_params
+ * (DEVICE double [W][14], as for lens_chi2_source) and d_chi2 (DEVICE double
+ * [W], each chain's current chi2; NaN makes the chain take any valid
+ * proposal) are updated in place.  Chain w proposes theta' = theta + sigma z
+ * with d_sigma DEVICE double [14] (standard deviations) and z standard normal,
+ * and moves when ln u < -(chi2' - chi2) / (2 temperature); a proposal outside
+ * the dPIE domain is refused.  z and u are drawn from Philox4x64-10 (Salmon
+ * et al. 2011) with key (seed, 0) and counters (step, w, j, 0), j = 0..3:
+ * word x gives ((x >> 11) + 1/2) 2^-53, words 0..13 the 7 Box-Muller pairs
+ * (sqrt(-2 ln u_2i) (cos, sin)(2 pi u_2i+1)), word 14 u; the same (seed, step)
+ * replays the same step.  d_scratch: DEVICE double [16 W] (proposals, then
+ * the uniforms and the proposals' chi2); d_accepted: DEVICE int32 [W] (1 =
+ * moved) or NULL.  temperature > 0; variant as for lens_chi2_source.
+ * Asynchronous on `stream`; three launches (proposals, the batched chi2,
+ * acceptance), capturable in a CUDA graph. */
+int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
+                   const double *d_sigma, double temperature, uint64_t seed, uint64_t step, int32_t variant,
+                   double *d_scratch, int32_t *d_accepted, void *stream);
+
 /* lens_chi2_source without the static cache: the deflection and Hessian of
  * every static potential at every image are recomputed for every parameter
  * set (double-float, summed in FP64; batches of 512 sets in the context's

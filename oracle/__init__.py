@@ -267,6 +267,82 @@ def chi2_source_batch(table, cons, var_halo, params, variant=0):
     return out
 
 
+# ---------------------------------------------------------------- sampling
+# Metropolis steps over the varying potentials' parameters (the Bayesian fit
+# of Sec. 2.2: likelihood exp(-chi2/2) of the source-plane chi2, Eq. 6) with
+# the counter-based generator Philox4x64-10 of Salmon, Moraes, Dror and Shaw
+# ("Parallel random numbers: as easy as 1, 2, 3", SC 2011), written here in
+# plain Python integers from that definition.
+
+_PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)
+_PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)
+_M64 = (1 << 64) - 1
+
+
+def philox4x64_10(counter, key):
+    """Philox4x64 with 10 rounds: four 64-bit counter words, two key words."""
+    c0, c1, c2, c3 = (int(v) & _M64 for v in counter)
+    k0, k1 = (int(v) & _M64 for v in key)
+    for _ in range(10):
+        p0, p1 = _PHILOX_M[0] * c0, _PHILOX_M[1] * c2
+        c0, c1, c2, c3 = (p1 >> 64) ^ c1 ^ k0, p1 & _M64, (p0 >> 64) ^ c3 ^ k1, p0 & _M64
+        k0, k1 = (k0 + _PHILOX_W[0]) & _M64, (k1 + _PHILOX_W[1]) & _M64
+    return c0, c1, c2, c3
+
+
+def mcmc_uniforms(seed, step, W):
+    """[W][16] uniforms in (0, 1): chain w's 16 words are Philox with counter
+    (step, w, j, 0), j = 0..3, key (seed, 0); word x gives ((x >> 11) + 1/2) 2^-53."""
+    out = np.empty((W, 16))
+    for w in range(W):
+        words = []
+        for j in range(4):
+            words.extend(philox4x64_10((step, w, j, 0), (seed, 0)))
+        out[w] = [((x >> 11) + 0.5) * 2.0 ** -53 for x in words]
+    return out
+
+
+def params_in_domain(table, var_halo, p14):
+    """The parameter set is inside the model's domain: every field finite,
+    b0 > 0, and for a dPIE 0 <= eps < 1 and 0 < rcore < rcut."""
+    table = np.asarray(table)
+    for v in range(2):
+        x0, y0, eps, theta, rcore, rcut, b0 = (float(t) for t in p14[7 * v: 7 * v + 7])
+        if not all(np.isfinite([x0, y0, eps, theta, rcore, rcut, b0])) or not b0 > 0:
+            return False
+        if int(table[var_halo[v], 0]) == 0 and not (0.0 <= eps < 1.0 and 0.0 < rcore < rcut):
+            return False
+    return True
+
+
+def mcmc_step(table, cons, var_halo, params, chi2, sigma, temperature, seed, step, variant=0):
+    """One Metropolis step of W chains: proposals theta + sigma z with z
+    from Box-Muller pairs of the uniforms, chi2 of the proposals (NaN outside
+    the domain), move when ln u < -(chi2' - chi2) / (2 T) (any valid proposal
+    when chi2 is NaN).  Returns (params', chi2', accepted, proposals, chi2 of
+    the proposals)."""
+    params = np.asarray(params, dtype=np.float64).reshape(-1, 14)
+    chi2 = np.asarray(chi2, dtype=np.float64)
+    W = len(params)
+    u = mcmc_uniforms(seed, step, W)
+    z = np.empty((W, 14))
+    for i in range(7):
+        rad = np.sqrt(-2.0 * np.log(u[:, 2 * i]))
+        ang = 2.0 * np.pi * u[:, 2 * i + 1]
+        z[:, 2 * i] = rad * np.cos(ang)
+        z[:, 2 * i + 1] = rad * np.sin(ang)
+    prop = params + np.asarray(sigma, dtype=np.float64) * z
+    ok = np.array([params_in_domain(table, var_halo, p) for p in prop])
+    chi2p = np.full(W, np.nan)
+    if ok.any():
+        chi2p[ok] = chi2_source_batch(table, cons, var_halo, prop[ok], variant)
+    take = np.isfinite(chi2p) & (~np.isfinite(chi2) |
+                                 (np.log(u[:, 14]) < -(chi2p - chi2) / (2.0 * temperature)))
+    new_p = np.where(take[:, None], prop, params)
+    new_c = np.where(take, chi2p, chi2)
+    return new_p, new_c, take, prop, chi2p
+
+
 def newton(table, r, beta_s, theta0, maxit=40, tol=1e-6, step_max=0.0):
     """Newton solve of beta_s = theta - r alpha(theta); returns (theta, iters or -1)."""
     lib = _load()

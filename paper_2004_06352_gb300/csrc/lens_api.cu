@@ -667,6 +667,22 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
   return launch_chi2_source(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
 }
 
+int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
+                   const double *d_sigma, double temperature, uint64_t seed, uint64_t step, int32_t variant,
+                   double *d_scratch, int32_t *d_accepted, void *stream) {
+  if (!ctx || !d_params || !d_chi2 || !d_sigma || !d_scratch) return fail(LENS_EINVAL, "NULL argument");
+  if (W < 1) return fail(LENS_EINVAL, "W must be >= 1");
+  if (!(std::isfinite(temperature) && temperature > 0.0)) return fail(LENS_EINVAL, "temperature must be > 0");
+  if (variant < 0 || variant > 2) return fail(LENS_EINVAL, "variant must be 0, 1 or 2");
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  Model *m = find_model(ctx, c->model);
+  if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
+  cudaSetDevice(ctx->device);
+  return launch_mcmc_step(ctx, m, c, d_params, d_chi2, W, d_sigma, temperature, seed, step, variant, d_scratch,
+                          d_accepted, (cudaStream_t)stream);
+}
+
 int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                              double *d_chi2, void *stream) {
   if (!ctx || !d_params || !d_chi2) return fail(LENS_EINVAL, "NULL argument");

@@ -1,0 +1,106 @@
+// Metropolis sampling of the batched source-plane chi2 on the device: the
+// Bayesian fit of Sec. 2.2 (the likelihood exp(-chi2 / 2) of Eq. 6 explored
+// by a Markov chain over the parameters of the varying potentials) run as W
+// independent chains, one parameter set each, advanced together.
+//
+// One step: every chain proposes theta' = theta + sigma * z (z standard
+// normal), the batch of proposals goes through the source-plane chi2 kernel,
+// and each chain moves to theta' when ln u < -(chi2' - chi2) / (2 T)
+// (u uniform in (0, 1), T the temperature; a proposal outside the dPIE
+// domain has chi2' = NaN and is refused).
+//
+// Random numbers: Philox4x64-10 (Salmon, Moraes, Dror and Shaw, "Parallel
+// random numbers: as easy as 1, 2, 3", SC 2011), a counter-based generator:
+// the words for chain w at step s are Philox(counter = (s, w, j, 0),
+// key = (seed, 0)) for j = 0..3, 16 64-bit words; each word x gives the
+// uniform ((x >> 11) + 1/2) 2^-53; words 0..13 make 7 Box-Muller pairs,
+// word 14 the acceptance uniform.
+#include "lens_device.cuh"
+
+namespace lens {
+namespace {
+
+struct U4 {
+  unsigned long long w[4];
+};
+
+// Philox4x64 with 10 rounds: per round two 64 x 64 -> 128-bit products mix
+// the counter words with the key, which is bumped by the Weyl constants.
+__device__ __forceinline__ U4 philox4x64_10(U4 c, unsigned long long k0, unsigned long long k1) {
+  constexpr unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  constexpr unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long hi0 = __umul64hi(M0, c.w[0]), lo0 = M0 * c.w[0];
+    const unsigned long long hi1 = __umul64hi(M1, c.w[2]), lo1 = M1 * c.w[2];
+    c = U4{{hi1 ^ c.w[1] ^ k0, lo1, hi0 ^ c.w[3] ^ k1, lo0}};
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double unit_open(unsigned long long x) {
+  return ((double)(x >> 11) + 0.5) * 0x1.0p-53;
+}
+
+// Proposals into prop [W][14] and the acceptance uniforms into ua [W].
+__global__ void k_mcmc_propose(const double *__restrict__ params, const double *__restrict__ sigma, int W,
+                               unsigned long long seed, unsigned long long step, double *__restrict__ prop,
+                               double *__restrict__ ua) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  double u[16];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const U4 r = philox4x64_10(U4{{step, (unsigned long long)w, (unsigned long long)j, 0ull}}, seed, 0ull);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[4 * j + q] = unit_open(r.w[q]);
+  }
+  const double two_pi = 6.283185307179586;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const double rad = sqrt(-2.0 * log(u[2 * i])), ang = two_pi * u[2 * i + 1];
+    const size_t o = (size_t)w * 14 + 2 * i;
+    prop[o] = params[o] + sigma[2 * i] * (rad * cos(ang));
+    prop[o + 1] = params[o + 1] + sigma[2 * i + 1] * (rad * sin(ang));
+  }
+  ua[w] = u[14];
+}
+
+// Metropolis acceptance; accepted[w] (when not NULL) records the decision.
+__global__ void k_mcmc_accept(double *__restrict__ params, double *__restrict__ chi2,
+                              const double *__restrict__ prop, const double *__restrict__ ua,
+                              const double *__restrict__ chi2_prop, int W, double temperature,
+                              int32_t *__restrict__ accepted) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const double cp = chi2_prop[w], c0 = chi2[w];
+  bool take = false;
+  if (isfinite(cp)) take = !isfinite(c0) || log(ua[w]) < -(cp - c0) / (2.0 * temperature);
+  if (take) {
+    for (int q = 0; q < 14; ++q) params[(size_t)w * 14 + q] = prop[(size_t)w * 14 + q];
+    chi2[w] = cp;
+  }
+  if (accepted) accepted[w] = take ? 1 : 0;
+}
+
+}  // namespace
+
+int launch_mcmc_step(lens_ctx *ctx, const Model *m, const CSet *c, double *d_params, double *d_chi2, int32_t W,
+                     const double *d_sigma, double temperature, unsigned long long seed, unsigned long long step,
+                     int32_t variant, double *d_scratch, int32_t *d_accepted, cudaStream_t st) {
+  double *prop = d_scratch, *ua = d_scratch + (size_t)W * 14, *chi2_prop = ua + W;
+  const int blocks = (W + 127) / 128;
+  k_mcmc_propose<<<blocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "proposal launch: %s", cudaGetErrorString(e));
+  const int rc = launch_chi2_source(ctx, m, c, prop, W, variant, chi2_prop, st);
+  if (rc) return rc;
+  k_mcmc_accept<<<blocks, 128, 0, st>>>(d_params, d_chi2, prop, ua, chi2_prop, W, temperature, d_accepted);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "acceptance launch: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
+}  // namespace lens

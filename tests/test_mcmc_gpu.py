@@ -1,0 +1,93 @@
+"""Metropolis sampling on the device (the Bayesian fit of Sec. 2.2 over the
+batched source-plane chi2) against the oracle's sampler, which draws the same
+Philox4x64-10 stream: proposals, chi2 and every move decision agree step by
+step."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2004_06352_gb300 import inputs as I
+from tests import tolerances as T
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def test_mcmc_steps_match_oracle(lens):
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    W = 40
+    params = I.perturbed_params(m, var, W, seed=81)
+    params[3, 2] = 0.995                    # eps next to 1: proposals leave the domain
+    chi2 = oracle.chi2_source_batch(m, cons, var, params, 0)
+    chi2[5] = np.nan                        # takes any valid proposal
+    sigma = np.tile([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1], 2)
+    sig_gpu = sigma.copy()
+    T_ = 2000.0                             # chi2 ~ 1e5: moves of a few 1e3 are taken at times
+    seed = 0xC0FFEE
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        c = torch.tensor(chi2, device=DEV)
+        sg = torch.tensor(sig_gpu, device=DEV)
+        scratch = torch.empty(16 * W, dtype=torch.float64, device=DEV)
+        acc = torch.empty(W, dtype=torch.int32, device=DEV)
+        po, co = params.copy(), chi2.copy()
+        n_acc = 0
+        for step in range(4):
+            ctx.mcmc_step(cs, p, c, W, sg, T_, seed, step, scratch, acc)
+            ctx.wait()
+            po2, co2, take, prop, cp = oracle.mcmc_step(m, cons, var, po, co, sigma, T_, seed, step)
+            got_take = acc.cpu().numpy().astype(bool)
+            u = oracle.mcmc_uniforms(seed, step, W)[:, 14]
+            margin = np.log(u) + (cp - co) / (2 * T_)
+            sure = ~np.isfinite(margin) | (np.abs(margin) > 1e-6)   # decisions far from the threshold
+            assert np.array_equal(got_take[sure], take[sure]), step
+            # keep the oracle in step with the device on the (unseen so far) borderline cases
+            po2 = np.where(got_take[:, None], prop, po)
+            co2 = np.where(got_take, cp, co)
+            gp, gc = p.cpu().numpy(), c.cpu().numpy()
+            assert np.allclose(gp, po2, rtol=1e-13, atol=1e-13), step
+            fin = np.isfinite(co2)
+            assert np.array_equal(np.isfinite(gc), fin)
+            assert np.all(np.abs(gc[fin] - co2[fin]) <= T.CHI2_REL * np.abs(co2[fin])), step
+            po, co = po2, co2
+            n_acc += int(got_take.sum())
+        assert 0 < n_acc < 4 * W                                    # some moves taken, some refused
+        assert np.isfinite(co[5])                                   # the NaN chain moved
+
+
+def test_mcmc_step_replays_and_zero_step(lens):
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    W = 300
+    params = I.perturbed_params(m, var, W, seed=82)
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p0 = torch.tensor(params, device=DEV)
+        c0 = torch.empty(W, dtype=torch.float64, device=DEV)
+        ctx.chi2_source(cs, p0, W, 0, c0)
+        sg = torch.tensor(np.tile([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1], 2), device=DEV)
+        scratch = torch.empty(16 * W, dtype=torch.float64, device=DEV)
+        runs = []
+        for _ in range(2):
+            p, c = p0.clone(), c0.clone()
+            ctx.mcmc_step(cs, p, c, W, sg, 500.0, 99, 17, scratch)
+            runs.append((p, c))
+        ctx.wait()
+        assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+        p, c = p0.clone(), c0.clone()
+        acc = torch.empty(W, dtype=torch.int32, device=DEV)
+        ctx.mcmc_step(cs, p, c, W, torch.zeros_like(sg), 1.0, 99, 18, scratch, acc)
+        ctx.wait()
+        assert torch.equal(p, p0) and torch.equal(c, c0) and bool(acc.all())
+        with pytest.raises(lens.LensError) as e:
+            ctx.mcmc_step(cs, p, c, W, sg, 0.0, 1, 0, scratch)
+        assert e.value.code == lens.LENS_EINVAL
