@@ -394,6 +394,14 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
                                  "pair_per_s": nimg * (N_HALO - 2) * P / (t * 1e-3),
                                  "workload": "source-plane chi2 without the static cache, 4096 sets x 372 images "
                                              "x 1000 potentials, double-float with Hessian"}
+    # members' scaling relations free as well: 16 parameters per set, the
+    # static sums recomputed per set (double-float)
+    p16 = torch.cat([params, torch.tensor(np.random.default_rng(36).uniform(0.8, 1.2, (P, 2)), device=dev)], 1)
+    t = timed(lambda: ctx.chi2_source_scaled(cs, p16, P, 0, chi2, stream), 1)
+    ex["chi2_source_scaled"] = {"ms": t, "models_per_s": P / (t * 1e-3), "P": P,
+                                "pair_per_s": nimg * (N_HALO - 2) * P / (t * 1e-3),
+                                "workload": "source-plane chi2 with the members' b0 and r_cut factors free, 4096 "
+                                            "sets x 372 images x 1000 potentials, double-float with Hessian"}
     Pi = 256
     gi = I.grid(1024)
     chi2i = torch.empty(Pi, dtype=torch.float64, device=dev)

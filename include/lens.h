@@ -213,6 +213,20 @@ int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
 int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                      double *d_chi2, void *stream);
 
+/* Source-plane chi2 with the cluster members' scaling relations free as
+ * well (Sec. 2.2: a cluster model's free parameters include the members'
+ * scaling relations, b0_i = b0* s_i and r_cut,i = r_cut* s_i): d_params is
+ * DEVICE double [P][16], the 14 parameters of lens_chi2_source followed by
+ * f_b and f_t, which multiply b0 of every static potential and r_cut of every
+ * static dPIE (r_core stays).  The static sums are recomputed for every set
+ * in double-float (~1e-13 relative per potential; the r_cut-dependent
+ * constants rebuilt from f_t r_cut in double-float; FP64 where that fails)
+ * in batches of 512 sets, into the context's scratch (as
+ * lens_chi2_source_nocache).  NaN for a set outside the domain (f_b or f_t
+ * not positive, or f_t r_cut <= r_core for a member). */
+int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
+                            double *d_chi2, void *stream);
+
 /* One Metropolis step of W independent Markov chains over the 14 varying
  * parameters (the Bayesian fit of Sec. 2.2: likelihood exp(-chi2/2) of the
  * source-plane chi2 of Eq. 6, flat prior over the dPIE domain).  d_params

@@ -236,6 +236,35 @@ def apply_params(table, var_halo, p14):
     return np.array([[o.type, o.x0, o.y0, o.theta, o.eps, o.rcore, o.rcut, o.b0] for o in out])
 
 
+def apply_params_scaled(table, var_halo, p16):
+    """Model with the two varying halos from p16[0:14], and the members'
+    scaling relations moved (Sec. 2.2: b0_i = b0* s_i, r_cut,i = r_cut* s_i):
+    every other potential's b0 times p16[14], every other dPIE's r_cut times
+    p16[15]."""
+    t = apply_params(table, var_halo, p16[:14])
+    others = np.array([i for i in range(len(t)) if i not in tuple(var_halo)], dtype=int)
+    t[others, 7] *= p16[14]
+    dp = others[t[others, 0] == 0]
+    t[dp, 6] *= p16[15]
+    return t
+
+
+def chi2_source_scaled_batch(table, cons, var_halo, params16, variant=0):
+    """Source-plane chi2 of each 16-parameter set; NaN outside the domain
+    (f_b or f_t not positive, a member's r_cut not above its r_core, or the
+    varying halos' own domain)."""
+    params16 = np.asarray(params16, dtype=np.float64).reshape(-1, 16)
+    out = np.full(len(params16), np.nan)
+    for k, p in enumerate(params16):
+        if not (p[14] > 0 and p[15] > 0 and params_in_domain(table, var_halo, p[:14])):
+            continue
+        t = apply_params_scaled(table, var_halo, p)
+        if np.any((t[:, 0] == 0) & ~(t[:, 6] > t[:, 5])):
+            continue
+        out[k] = chi2_source(t, cons, variant)
+    return out
+
+
 def backtrace(table, cons):
     """beta_ij = theta_ij - alpha(theta_ij) (Sec. 2.1 Eq. 1) and per-source
     barycentres (Sec. 2.2, Fig. 3).  Returns (beta [nimg, 2], bary [nsrc, 2])."""

@@ -26,7 +26,7 @@ EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_u
            "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_potential_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
-           "lens_chi2_source", "lens_chi2_source_nocache", "lens_mcmc_step", "lens_chi2_autotune", "lens_chi2_image",
+           "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_source_scaled", "lens_mcmc_step", "lens_chi2_autotune", "lens_chi2_image",
            "lens_find_images", "lens_chi2_image_noalloc", "lens_selftest_wait", "lens_selftest_math", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
            "lens_server_progress", "lens_server_cancel", "lens_server_stats")
@@ -97,6 +97,7 @@ def load_library(path=LIB_PATH):
         "lens_cset_release": (C.c_int, [vp, i64]),
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_source_nocache": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
+        "lens_chi2_source_scaled": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_mcmc_step": (C.c_int, [vp, i64, vp, vp, C.c_int32, vp, C.c_double, C.c_uint64, C.c_uint64,
                                      C.c_int32, vp, vp, vp]),
         "lens_chi2_autotune": (C.c_int, [vp, i64, vp, C.c_int32, vp, vp, C.POINTER(C.c_int32),
@@ -266,6 +267,13 @@ class Context:
         _check(_lib.lens_chi2_source(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(chi2),
                                      _stream(stream)), "lens_chi2_source")
         return chi2
+
+    def chi2_source_scaled(self, cset, params, P, variant, out, stream=None):
+        """chi2 of P sets of 16 parameters: the 14 of chi2_source, then the
+        members' b0 and r_cut factors (see lens.h)."""
+        _check(_lib.lens_chi2_source_scaled(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(out),
+                                            _stream(stream)), "lens_chi2_source_scaled")
+        return out
 
     def mcmc_step(self, cset, params, chi2, W, sigma, temperature, seed, step, scratch, accepted=None,
                   variant=0, stream=None):

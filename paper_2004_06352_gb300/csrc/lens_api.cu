@@ -667,6 +667,21 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
   return launch_chi2_source(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
 }
 
+int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
+                            double *d_chi2, void *stream) {
+  if (!ctx || !d_params || !d_chi2) return fail(LENS_EINVAL, "NULL argument");
+  if (P < 1) return fail(LENS_EINVAL, "P must be >= 1");
+  if (variant < 0 || variant > 2) return fail(LENS_EINVAL, "variant must be 0, 1 or 2");
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  Model *m = find_model(ctx, c->model);
+  if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
+  cudaSetDevice(ctx->device);
+  const int rc = ensure_scratch(ctx, chi2_nocache_scratch_bytes(c));
+  if (rc) return rc;
+  return launch_chi2_source_scaled(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
+}
+
 int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
                    const double *d_sigma, double temperature, uint64_t seed, uint64_t step, int32_t variant,
                    double *d_scratch, int32_t *d_accepted, void *stream) {

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(CACHE_THREADS) k_static_cache(const double *__
 struct Chi2SrcArgs {
   const double *stat, *x, *y, *sigma, *ratio, *params;
   long long stat_stride;  // doubles between the static sums of consecutive sets (0: one shared cache)
+  int pstride;            // doubles per parameter set (14; 16 with the members' scaling factors)
   const int32_t *img_off, *src_of;
   int nsrc, nimg, P, variant;
   int type0, type1;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
       const int k = threadIdx.x >> 1, v = threadIdx.x & 1;
       const long long p = p0 + (long long)k * gridDim.x;
       if (p < a.P) {
-        const double *q = a.params + p * 14;
+        const double *q = a.params + p * a.pstride;
         const double *w = q + 7 * v;  // x0, y0, eps, theta, rcore, rcut, b0
         s_ok[k][v] = load_var_rec64(q, a.type0, a.type1, v, s_rec[k]);
         make_recdf(v == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rdf[k] + v * RECDF);
@@ -140,7 +141,7 @@ int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c) {
 template <int T>
 static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, int32_t P, int32_t variant,
                           double *d_chi2, cudaStream_t st, int blocks_per_sm, const double *stat = nullptr,
-                          long long stat_stride = 0) {
+                          long long stat_stride = 0, int pstride = 14) {
   const size_t smem = sizeof(double) * (5 * (size_t)c->nimg + 2 * (size_t)c->nsrc + T / 32);
   if (smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
   cudaFuncSetAttribute(k_chi2_source<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -158,6 +159,7 @@ static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, 
   a.sigma = c->sigma;
   a.ratio = c->ratio;
   a.params = d_params;
+  a.pstride = pstride;
   a.img_off = c->img_off;
   a.src_of = c->src_of;
   a.nsrc = c->nsrc;
@@ -252,6 +254,97 @@ int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, con
     if (e != cudaSuccess) return fail(LENS_ECUDA, "static sums launch: %s", cudaGetErrorString(e));
     const int rc = launch_src_cfg<128>(ctx, c, d_params + (size_t)p0 * 14, B, variant, d_chi2 + p0, st, 0, stat,
                                        (long long)c->nimg * 5);
+    if (rc) return rc;
+  }
+  return LENS_OK;
+}
+
+// Static sums with the members' scaling relations applied, grid (nimg, sets):
+// every static potential's b0 times f_b = params[14] and every static dPIE's
+// r_cut times f_t = params[15] (b0_i = b0* s_i, r_cut,i = r_cut* s_i: varying
+// b0* and r_cut*).  The sum is linear in b0, so f_b scales the result; the
+// r_cut-dependent fields of each double-float record are rebuilt from
+// st' = f_t st in double-float (q^2 st', q^2 st'^2, (1+q^2) st'^2, u^2 st'^2,
+// st' + sc, q^2 (st' +- sc), q^2 (st'^2 - sc^2)).  FP64 (a record rescaled the
+// same way) where the double-float evaluation fails.  Outside the domain
+// (f_b <= 0, f_t r_cut,i <= r_core,i) the set's sums are NaN.
+__global__ void __launch_bounds__(CACHE_THREADS) k_static_scaled(const float2 *__restrict__ recdf,
+                                                                 const double *__restrict__ all64, int n, int v0,
+                                                                 int v1, const double *__restrict__ x,
+                                                                 const double *__restrict__ y,
+                                                                 const double *__restrict__ params, double *stat) {
+  __shared__ double s_red[(CACHE_THREADS / 32) * 5];
+  const int img = blockIdx.x;
+  stat += (size_t)blockIdx.y * gridDim.x * 5;
+  const double fb = params[(size_t)blockIdx.y * 16 + 14], ft = params[(size_t)blockIdx.y * 16 + 15];
+  const double X = x[img], Y = y[img];
+  const df Xd = df_from_double(X), Yd = df_from_double(Y), fd = df_from_double(ft), f2 = df_mul(fd, fd);
+  double v[5] = {0, 0, 0, 0, 0};
+  df sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  bool bad = !(fb > 0.0 && ft > 0.0 && isfinite(fb) && isfinite(ft));
+  for (int h = threadIdx.x; h < n && !bad; h += CACHE_THREADS) {
+    if (h == v0 || h == v1) continue;
+    const float2 *g = recdf + h;
+    df ax, ay, hh[3];
+    bool ok = true;
+    if (g[F_U2 * n].x < 0.f) {
+      circ_df<true>(g, n, Xd, Yd, ax, ay, hh);
+    } else {
+      float2 r[RECDF];
+#pragma unroll
+      for (int k = 0; k < RECDF; ++k) r[k] = g[k * n];
+      auto D = [&](int k) { return df{r[k].x, r[k].y}; };
+      auto put = [&](int k, df d) { r[k] = make_float2(d.hi, d.lo); };
+      const df st = df_mul(D(F_ST), fd), sc = D(F_SC), q2st = df_mul(D(F_Q2ST), fd);
+      const df ss = df_add_ss(st, sc), q2ds = df_sub(q2st, D(F_Q2SC));
+      if (!(st.hi > sc.hi)) bad = true;  // r_cut' <= r_core
+      put(F_ST, st);
+      put(F_Q2ST, q2st);
+      put(F_SS, ss);
+      put(F_Q2SS, df_add_ss(q2st, D(F_Q2SC)));
+      put(F_Q2DS, q2ds);
+      put(F_KT, df_mul(D(F_KT), f2));
+      put(F_DT0, df_mul(D(F_DT0), f2));
+      put(F_U2ST2, df_mul(D(F_U2ST2), f2));
+      put(F_KTC, df_mul(q2ds, ss));
+      ok = dpie_df<true, true>(r, 1, Xd, Yd, ax, ay, hh);
+    }
+    if (ok) {
+      sum[0] = df_add(sum[0], ax);
+      sum[1] = df_add(sum[1], ay);
+      sum[2] = df_add(sum[2], hh[0]);
+      sum[3] = df_add(sum[3], hh[1]);
+      sum[4] = df_add(sum[4], hh[2]);
+    } else {
+      double q[REC64], e[5] = {0, 0, 0, 0, 0};
+      for (int k = 0; k < REC64; ++k) q[k] = all64[(size_t)h * REC64 + k];
+      q[D_ST] *= ft;
+      q[D_DS] = q[D_ST] - q[D_SC];
+      q[D_SS] = q[D_ST] + q[D_SC];
+      eval64<true>(q, X, Y, e[0], e[1], e[2], e[3], e[4]);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] += e[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) v[k] = fb * (v[k] + df_to_double(sum[k]));
+  const int any_bad = __syncthreads_or(bad);
+  block_sum<5, CACHE_THREADS>(v, s_red);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 5; ++k) stat[(size_t)img * 5 + k] = any_bad ? __longlong_as_double(0x7ff8000000000000ll) : v[k];
+}
+
+int launch_chi2_source_scaled(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                              int32_t variant, double *d_chi2, cudaStream_t st) {
+  double *stat = (double *)ctx->scratch;
+  for (int32_t p0 = 0; p0 < P; p0 += NOCACHE_BATCH) {
+    const int B = std::min(NOCACHE_BATCH, P - p0);
+    k_static_scaled<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1],
+                                                                 c->x, c->y, d_params + (size_t)p0 * 16, stat);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LENS_ECUDA, "scaled static sums launch: %s", cudaGetErrorString(e));
+    const int rc = launch_src_cfg<128>(ctx, c, d_params + (size_t)p0 * 16, B, variant, d_chi2 + p0, st, 0, stat,
+                                       (long long)c->nimg * 5, 16);
     if (rc) return rc;
   }
   return LENS_OK;

@@ -317,6 +317,8 @@ int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);
 size_t chi2_nocache_scratch_bytes(const CSet *c);
+int launch_chi2_source_scaled(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
+                              int32_t variant, double *d_chi2, cudaStream_t st);
 int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                                int32_t variant, double *d_chi2, cudaStream_t st);
 int autotune_chi2_source(lens_ctx *ctx, CSet *c, const double *d_params, int32_t P, double *d_chi2, cudaStream_t st,

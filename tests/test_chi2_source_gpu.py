@@ -134,3 +134,36 @@ def test_chi2_source_nocache_matches_cache_and_oracle(lens):
             sample = [0, 1, 513, 1099]
             ref = oracle.chi2_source_batch(m, cons, var, params[sample], variant)
             assert np.all(np.abs(b[sample] - ref) <= T.CHI2_REL * np.abs(ref))
+
+
+def test_chi2_source_scaled_members_matches_oracle(lens):
+    """16 parameters per set: the two cluster halos plus the members' b0 and
+    r_cut factors (their scaling relations); P spans two batches of 512 and
+    a ragged tail; sets outside the domain are NaN; unit factors give the
+    no-cache chi2."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    P = 1100
+    rng = np.random.default_rng(62)
+    p14 = I.perturbed_params(m, var, P, seed=63)
+    params = np.hstack([p14, rng.uniform(0.8, 1.2, (P, 1)), rng.uniform(0.7, 1.3, (P, 1))])
+    params[5, 14] = -1.0        # f_b <= 0
+    params[6, 15] = 1e-3        # members' r_cut below r_core
+    params[7, 14:] = 1.0        # unit factors
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        out = torch.full((P,), float("nan"), dtype=torch.float64, device=DEV)
+        ctx.chi2_source_scaled(cs, p, P, 0, out)
+        plain = torch.empty(1, dtype=torch.float64, device=DEV)
+        ctx.chi2_source_nocache(cs, torch.tensor(p14[7:8], device=DEV), 1, 0, plain)
+        ctx.wait()
+        got, plain = out.cpu().numpy(), float(plain.cpu()[0])
+    assert np.isnan(got[5]) and np.isnan(got[6])
+    assert abs(got[7] - plain) <= 1e-10 * plain
+    sample = [0, 1, 7, 511, 512, 1023, 1024, 1099]
+    ref = oracle.chi2_source_scaled_batch(m, cons, var, params[sample], 0)
+    assert np.all(np.abs(got[sample] - ref) <= T.CHI2_REL * np.abs(ref)), np.max(np.abs(got[sample] - ref) / ref)

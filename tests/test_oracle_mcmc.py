@@ -79,3 +79,49 @@ def test_outside_domain_refused_and_nan_start_moves(small_fit):
     bad = ~np.array([oracle.params_in_domain(m, var, p) for p in prop])
     assert bad.any() and np.all(np.isnan(cp[bad])) and not take[bad].any()
     assert take[1] == np.isfinite(cp[1])
+
+
+# ------------------------------------------------- members' scaling relations
+
+def test_scaled_chi2_reduces_to_plain_at_unit_factors(small_fit):
+    m, cons, var, params, chi2, sigma = small_fit
+    p16 = np.hstack([params, np.ones((len(params), 2))])
+    got = oracle.chi2_source_scaled_batch(m, cons, var, p16, 0)
+    assert np.allclose(got, chi2, rtol=1e-13, atol=0)
+
+
+def test_scaled_factors_act_on_the_static_potentials_only():
+    """f_b multiplies the static potentials' deflection (the model is linear
+    in b0); f_t moves a circular member's cut radius and not its core (the
+    circular dPIE's closed-form deflection)."""
+    m = np.stack([I.halo_row(I.DPIE, 0.0, 0.0, 0.3, 0.2, 4.0, 500.0, 20.0),
+                  I.halo_row(I.DPIE, 5.0, -3.0, 1.0, 0.1, 3.0, 300.0, 15.0),
+                  I.halo_row(I.DPIE, 2.0, 7.0, 0.0, 0.0, 0.2, 10.0, 1.5),
+                  I.halo_row(I.SIS, -6.0, 1.0, 0, 0, 0, 0, 0.8)])
+    var = (0, 1)
+    base = np.hstack([m[0, [1, 2, 4, 3, 5, 6, 7]], m[1, [1, 2, 4, 3, 5, 6, 7]]])
+    X, Y = np.array([30.0, -12.0, 4.0]), np.array([-8.0, 22.0, 40.0])
+    stat = lambda t: oracle.model_eval(t[2:], X, Y)
+    one = stat(oracle.apply_params_scaled(m, var, np.hstack([base, 1.0, 1.0])))
+    two = stat(oracle.apply_params_scaled(m, var, np.hstack([base, 2.0, 1.0])))
+    assert np.allclose(two, 2 * one, rtol=1e-13, atol=0)
+    # varying halos untouched
+    t = oracle.apply_params_scaled(m, var, np.hstack([base, 3.0, 0.5]))
+    assert np.array_equal(t[:2], oracle.apply_params(m, var, base)[:2])
+    # circular member alone: alpha_r = b0 [(sqrt(rc^2 + r^2) - rc) - (sqrt(rt^2 + r^2) - rt)] / r
+    for ft in (0.6, 1.7):
+        t = oracle.apply_params_scaled(m, var, np.hstack([base, 1.0, ft]))
+        for r in (0.1, 3.0, 25.0):
+            a = oracle.model_eval(t[2:3], 2.0 + r, 7.0)[0]
+            rc, rt = 0.2, ft * 10.0
+            exact = 1.5 * ((np.hypot(rc, r) - rc) - (np.hypot(rt, r) - rt)) / r
+            assert abs(a[0] - exact) <= 1e-12 * abs(exact) and abs(a[1]) < 1e-15
+
+
+def test_scaled_outside_domain_is_nan(small_fit):
+    m, cons, var, params, chi2, sigma = small_fit
+    p16 = np.hstack([params[:3], np.ones((3, 2))])
+    p16[0, 14] = -1.0           # f_b <= 0
+    p16[1, 15] = 1e-4           # members' r_cut below their r_core
+    got = oracle.chi2_source_scaled_batch(m, cons, var, p16, 0)
+    assert np.isnan(got[0]) and np.isnan(got[1]) and np.isfinite(got[2])
