@@ -382,6 +382,16 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     t = timed(mcmc_steps, 1) / nsteps
     ctx.mcmc_step(cs, walk, wchi2, P, sig, 2000.0, 2024, state["k"], scratch, acc, stream=stream)
     torch.cuda.synchronize()
+    # the same with the members' scaling factors moving too (16 parameters)
+    walk16 = torch.cat([params, torch.ones((P, 2), dtype=torch.float64, device=dev)], 1)
+    wchi16 = torch.empty(P, dtype=torch.float64, device=dev)
+    ctx.chi2_source_scaled(cs, walk16, P, 0, wchi16, stream)
+    sig16 = torch.cat([sig, torch.tensor([0.02, 0.05], dtype=torch.float64, device=dev)])
+    scratch16 = torch.empty(18 * P, dtype=torch.float64, device=dev)
+    t16 = timed(lambda: ctx.mcmc_step(cs, walk16, wchi16, P, sig16, 2000.0, 7, 0, scratch16, acc, stream=stream), 1)
+    ex["mcmc_step_scaled"] = {"ms": t16, "steps_per_s": 1e3 / t16, "models_per_s": P / (t16 * 1e-3), "chains": P,
+                              "workload": "Metropolis step of 4096 chains over 16 parameters (the members' "
+                                          "scaling factors too; chi2 with every static potential per set)"}
     ex["mcmc_step"] = {"ms": t, "steps_per_s": 1e3 / t, "models_per_s": P / (t * 1e-3), "chains": P,
                        "accept_frac_last_step": float(acc.float().mean()),
                        "workload": "Metropolis step of 4096 chains (Philox proposals, source-plane chi2, "

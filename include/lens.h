@@ -227,24 +227,27 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
 int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                             double *d_chi2, void *stream);
 
-/* One Metropolis step of W independent Markov chains over the 14 varying
+/* One Metropolis step of W independent Markov chains over the varying
  * parameters (the Bayesian fit of Sec. 2.2: likelihood exp(-chi2/2) of the
- * source-plane chi2 of Eq. 6, flat prior over the dPIE domain).  d_params
- * (DEVICE double [W][14], as for lens_chi2_source) and d_chi2 (DEVICE double
- * [W], each chain's current chi2; NaN makes the chain take any valid
- * proposal) are updated in place.  Chain w proposes theta' = theta + sigma z
- * with d_sigma DEVICE double [14] (standard deviations) and z standard normal,
- * and moves when ln u < -(chi2' - chi2) / (2 temperature); a proposal outside
- * the dPIE domain is refused.  z and u are drawn from Philox4x64-10 (Salmon
- * et al. 2011) with key (seed, 0) and counters (step, w, j, 0), j = 0..3:
- * word x gives ((x >> 11) + 1/2) 2^-53, words 0..13 the 7 Box-Muller pairs
- * (sqrt(-2 ln u_2i) (cos, sin)(2 pi u_2i+1)), word 14 u; the same (seed, step)
- * replays the same step.  d_scratch: DEVICE double [16 W] (proposals, then
- * the uniforms and the proposals' chi2); d_accepted: DEVICE int32 [W] (1 =
- * moved) or NULL.  temperature > 0; variant as for lens_chi2_source.
- * Asynchronous on `stream`; three launches (proposals, the batched chi2,
- * acceptance), capturable in a CUDA graph. */
-int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
+ * source-plane chi2 of Eq. 6, flat prior over the domain).  nparams = 14:
+ * the two varying potentials, chi2 as lens_chi2_source; nparams = 16: also
+ * the members' scaling factors, chi2 as lens_chi2_source_scaled.  d_params
+ * (DEVICE double [W][nparams]) and d_chi2 (DEVICE double [W], each chain's
+ * current chi2; NaN makes the chain take any valid proposal) are updated in
+ * place.  Chain w proposes theta' = theta + sigma z with d_sigma DEVICE
+ * double [nparams] (standard deviations) and z standard normal, and moves
+ * when ln u < -(chi2' - chi2) / (2 temperature); a proposal outside the
+ * domain is refused.  z and u come from Philox4x64-10 (Salmon et al. 2011)
+ * with key (seed, 0) and counters (step, w, j, 0): word x gives
+ * ((x >> 11) + 1/2) 2^-53; j = 0..3 give 16 words, 8 Box-Muller pairs
+ * (sqrt(-2 ln u_2i) (cos, sin)(2 pi u_2i+1)) of which the first nparams
+ * normals are used, and word 0 of j = 4 is u; the same (seed, step) replays
+ * the same step.  d_scratch: DEVICE double [(nparams + 2) W] (proposals, the
+ * uniforms, the proposals' chi2); d_accepted: DEVICE int32 [W] (1 = moved)
+ * or NULL.  temperature > 0; variant as for lens_chi2_source.  Asynchronous
+ * on `stream`; three launches for nparams = 14 (capturable in a CUDA graph),
+ * the scaled chi2's batches for 16. */
+int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W, int32_t nparams,
                    const double *d_sigma, double temperature, uint64_t seed, uint64_t step, int32_t variant,
                    double *d_scratch, int32_t *d_accepted, void *stream);
 

@@ -320,13 +320,16 @@ def philox4x64_10(counter, key):
 
 
 def mcmc_uniforms(seed, step, W):
-    """[W][16] uniforms in (0, 1): chain w's 16 words are Philox with counter
-    (step, w, j, 0), j = 0..3, key (seed, 0); word x gives ((x >> 11) + 1/2) 2^-53."""
-    out = np.empty((W, 16))
+    """[W][17] uniforms in (0, 1): chain w's words are Philox with counter
+    (step, w, j, 0), key (seed, 0): the 16 words of j = 0..3 (the Box-Muller
+    inputs), then word 0 of j = 4 (the acceptance uniform); word x gives
+    ((x >> 11) + 1/2) 2^-53."""
+    out = np.empty((W, 17))
     for w in range(W):
         words = []
         for j in range(4):
             words.extend(philox4x64_10((step, w, j, 0), (seed, 0)))
+        words.append(philox4x64_10((step, w, 4, 0), (seed, 0))[0])
         out[w] = [((x >> 11) + 0.5) * 2.0 ** -53 for x in words]
     return out
 
@@ -345,28 +348,35 @@ def params_in_domain(table, var_halo, p14):
 
 
 def mcmc_step(table, cons, var_halo, params, chi2, sigma, temperature, seed, step, variant=0):
-    """One Metropolis step of W chains: proposals theta + sigma z with z
-    from Box-Muller pairs of the uniforms, chi2 of the proposals (NaN outside
-    the domain), move when ln u < -(chi2' - chi2) / (2 T) (any valid proposal
+    """One Metropolis step of W chains over 14 parameters (chi2 as
+    chi2_source_batch) or 16 (with the members' scaling factors, chi2 as
+    chi2_source_scaled_batch): proposals theta + sigma z with z from
+    Box-Muller pairs of the uniforms, chi2 of the proposals (NaN outside the
+    domain), move when ln u < -(chi2' - chi2) / (2 T) (any valid proposal
     when chi2 is NaN).  Returns (params', chi2', accepted, proposals, chi2 of
     the proposals)."""
-    params = np.asarray(params, dtype=np.float64).reshape(-1, 14)
+    params = np.asarray(params, dtype=np.float64)
+    npar = params.shape[-1]
+    params = params.reshape(-1, npar)
     chi2 = np.asarray(chi2, dtype=np.float64)
     W = len(params)
     u = mcmc_uniforms(seed, step, W)
-    z = np.empty((W, 14))
-    for i in range(7):
+    z = np.empty((W, npar))
+    for i in range(npar // 2):
         rad = np.sqrt(-2.0 * np.log(u[:, 2 * i]))
         ang = 2.0 * np.pi * u[:, 2 * i + 1]
         z[:, 2 * i] = rad * np.cos(ang)
         z[:, 2 * i + 1] = rad * np.sin(ang)
     prop = params + np.asarray(sigma, dtype=np.float64) * z
-    ok = np.array([params_in_domain(table, var_halo, p) for p in prop])
-    chi2p = np.full(W, np.nan)
-    if ok.any():
-        chi2p[ok] = chi2_source_batch(table, cons, var_halo, prop[ok], variant)
+    if npar == 16:
+        chi2p = chi2_source_scaled_batch(table, cons, var_halo, prop, variant)
+    else:
+        ok = np.array([params_in_domain(table, var_halo, p) for p in prop])
+        chi2p = np.full(W, np.nan)
+        if ok.any():
+            chi2p[ok] = chi2_source_batch(table, cons, var_halo, prop[ok], variant)
     take = np.isfinite(chi2p) & (~np.isfinite(chi2) |
-                                 (np.log(u[:, 14]) < -(chi2p - chi2) / (2.0 * temperature)))
+                                 (np.log(u[:, 16]) < -(chi2p - chi2) / (2.0 * temperature)))
     new_p = np.where(take[:, None], prop, params)
     new_c = np.where(take, chi2p, chi2)
     return new_p, new_c, take, prop, chi2p

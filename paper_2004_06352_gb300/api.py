@@ -98,8 +98,8 @@ def load_library(path=LIB_PATH):
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_source_nocache": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_source_scaled": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
-        "lens_mcmc_step": (C.c_int, [vp, i64, vp, vp, C.c_int32, vp, C.c_double, C.c_uint64, C.c_uint64,
-                                     C.c_int32, vp, vp, vp]),
+        "lens_mcmc_step": (C.c_int, [vp, i64, vp, vp, C.c_int32, C.c_int32, vp, C.c_double, C.c_uint64,
+                                     C.c_uint64, C.c_int32, vp, vp, vp]),
         "lens_chi2_autotune": (C.c_int, [vp, i64, vp, C.c_int32, vp, vp, C.POINTER(C.c_int32),
                                          C.POINTER(C.c_float)]),
         "lens_chi2_image": (C.c_int, [vp, i64, C.POINTER(lens_grid), vp, C.c_int32, vp, vp, vp]),
@@ -277,9 +277,10 @@ class Context:
 
     def mcmc_step(self, cset, params, chi2, W, sigma, temperature, seed, step, scratch, accepted=None,
                   variant=0, stream=None):
-        """One Metropolis step of W chains, params [W][14] and chi2 [W]
+        """One Metropolis step of W chains, params [W][14 or 16] and chi2 [W]
         updated in place on the device (see lens.h)."""
-        _check(_lib.lens_mcmc_step(self.h, int(cset), _ptr(params), _ptr(chi2), int(W), _ptr(sigma),
+        nparams = int(params.shape[-1])
+        _check(_lib.lens_mcmc_step(self.h, int(cset), _ptr(params), _ptr(chi2), int(W), nparams, _ptr(sigma),
                                    float(temperature), int(seed) & (2**64 - 1), int(step) & (2**64 - 1),
                                    int(variant), _ptr(scratch), None if accepted is None else _ptr(accepted),
                                    _stream(stream)), "lens_mcmc_step")

@@ -683,10 +683,11 @@ int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_par
 }
 
 int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
-                   const double *d_sigma, double temperature, uint64_t seed, uint64_t step, int32_t variant,
-                   double *d_scratch, int32_t *d_accepted, void *stream) {
+                   int32_t nparams, const double *d_sigma, double temperature, uint64_t seed, uint64_t step,
+                   int32_t variant, double *d_scratch, int32_t *d_accepted, void *stream) {
   if (!ctx || !d_params || !d_chi2 || !d_sigma || !d_scratch) return fail(LENS_EINVAL, "NULL argument");
   if (W < 1) return fail(LENS_EINVAL, "W must be >= 1");
+  if (nparams != 14 && nparams != 16) return fail(LENS_EINVAL, "nparams must be 14 or 16");
   if (!(std::isfinite(temperature) && temperature > 0.0)) return fail(LENS_EINVAL, "temperature must be > 0");
   if (variant < 0 || variant > 2) return fail(LENS_EINVAL, "variant must be 0, 1 or 2");
   CSet *c = find_cset(ctx, cset);
@@ -694,8 +695,12 @@ int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
-  return launch_mcmc_step(ctx, m, c, d_params, d_chi2, W, d_sigma, temperature, seed, step, variant, d_scratch,
-                          d_accepted, (cudaStream_t)stream);
+  if (nparams == 16) {
+    const int rc = ensure_scratch(ctx, chi2_nocache_scratch_bytes(c));
+    if (rc) return rc;
+  }
+  return launch_mcmc_step(ctx, m, c, d_params, d_chi2, W, d_sigma, temperature, seed, step, variant, nparams,
+                          d_scratch, d_accepted, (cudaStream_t)stream);
 }
 
 int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,

@@ -312,7 +312,7 @@ int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st);
 int launch_math_selftest(const double *x, int n, double *out, cudaStream_t st);
 int launch_mcmc_step(lens_ctx *ctx, const Model *m, const CSet *c, double *d_params, double *d_chi2, int32_t W,
                      const double *d_sigma, double temperature, unsigned long long seed, unsigned long long step,
-                     int32_t variant, double *d_scratch, int32_t *d_accepted, cudaStream_t st);
+                     int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st);
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);

@@ -12,9 +12,10 @@
 // Random numbers: Philox4x64-10 (Salmon, Moraes, Dror and Shaw, "Parallel
 // random numbers: as easy as 1, 2, 3", SC 2011), a counter-based generator:
 // the words for chain w at step s are Philox(counter = (s, w, j, 0),
-// key = (seed, 0)) for j = 0..3, 16 64-bit words; each word x gives the
-// uniform ((x >> 11) + 1/2) 2^-53; words 0..13 make 7 Box-Muller pairs,
-// word 14 the acceptance uniform.
+// key = (seed, 0)) for j = 0..4, 20 64-bit words; each word x gives the
+// uniform ((x >> 11) + 1/2) 2^-53; words 0..15 make 8 Box-Muller pairs (the
+// first NP normals are used: 14 parameters, or 16 with the members' scaling
+// factors), word 16 the acceptance uniform.
 #include "lens_device.cuh"
 
 namespace lens {
@@ -44,7 +45,8 @@ __device__ __forceinline__ double unit_open(unsigned long long x) {
   return ((double)(x >> 11) + 0.5) * 0x1.0p-53;
 }
 
-// Proposals into prop [W][14] and the acceptance uniforms into ua [W].
+// Proposals into prop [W][NP] and the acceptance uniforms into ua [W].
+template <int NP>
 __global__ void k_mcmc_propose(const double *__restrict__ params, const double *__restrict__ sigma, int W,
                                unsigned long long seed, unsigned long long step, double *__restrict__ prop,
                                double *__restrict__ ua) {
@@ -59,19 +61,19 @@ __global__ void k_mcmc_propose(const double *__restrict__ params, const double *
   }
   const double two_pi = 6.283185307179586;
 #pragma unroll
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < NP / 2; ++i) {
     const double rad = sqrt(-2.0 * log(u[2 * i])), ang = two_pi * u[2 * i + 1];
-    const size_t o = (size_t)w * 14 + 2 * i;
+    const size_t o = (size_t)w * NP + 2 * i;
     prop[o] = params[o] + sigma[2 * i] * (rad * cos(ang));
     prop[o + 1] = params[o + 1] + sigma[2 * i + 1] * (rad * sin(ang));
   }
-  ua[w] = u[14];
+  ua[w] = unit_open(philox4x64_10(U4{{step, (unsigned long long)w, 4ull, 0ull}}, seed, 0ull).w[0]);
 }
 
 // Metropolis acceptance; accepted[w] (when not NULL) records the decision.
 __global__ void k_mcmc_accept(double *__restrict__ params, double *__restrict__ chi2,
                               const double *__restrict__ prop, const double *__restrict__ ua,
-                              const double *__restrict__ chi2_prop, int W, double temperature,
+                              const double *__restrict__ chi2_prop, int W, int np, double temperature,
                               int32_t *__restrict__ accepted) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= W) return;
@@ -79,7 +81,7 @@ __global__ void k_mcmc_accept(double *__restrict__ params, double *__restrict__ 
   bool take = false;
   if (isfinite(cp)) take = !isfinite(c0) || log(ua[w]) < -(cp - c0) / (2.0 * temperature);
   if (take) {
-    for (int q = 0; q < 14; ++q) params[(size_t)w * 14 + q] = prop[(size_t)w * 14 + q];
+    for (int q = 0; q < np; ++q) params[(size_t)w * np + q] = prop[(size_t)w * np + q];
     chi2[w] = cp;
   }
   if (accepted) accepted[w] = take ? 1 : 0;
@@ -89,15 +91,19 @@ __global__ void k_mcmc_accept(double *__restrict__ params, double *__restrict__ 
 
 int launch_mcmc_step(lens_ctx *ctx, const Model *m, const CSet *c, double *d_params, double *d_chi2, int32_t W,
                      const double *d_sigma, double temperature, unsigned long long seed, unsigned long long step,
-                     int32_t variant, double *d_scratch, int32_t *d_accepted, cudaStream_t st) {
-  double *prop = d_scratch, *ua = d_scratch + (size_t)W * 14, *chi2_prop = ua + W;
+                     int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st) {
+  double *prop = d_scratch, *ua = d_scratch + (size_t)W * np, *chi2_prop = ua + W;
   const int blocks = (W + 127) / 128;
-  k_mcmc_propose<<<blocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+  if (np == 16)
+    k_mcmc_propose<16><<<blocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+  else
+    k_mcmc_propose<14><<<blocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "proposal launch: %s", cudaGetErrorString(e));
-  const int rc = launch_chi2_source(ctx, m, c, prop, W, variant, chi2_prop, st);
+  const int rc = np == 16 ? launch_chi2_source_scaled(ctx, m, c, prop, W, variant, chi2_prop, st)
+                          : launch_chi2_source(ctx, m, c, prop, W, variant, chi2_prop, st);
   if (rc) return rc;
-  k_mcmc_accept<<<blocks, 128, 0, st>>>(d_params, d_chi2, prop, ua, chi2_prop, W, temperature, d_accepted);
+  k_mcmc_accept<<<blocks, 128, 0, st>>>(d_params, d_chi2, prop, ua, chi2_prop, W, np, temperature, d_accepted);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "acceptance launch: %s", cudaGetErrorString(e));
   return LENS_OK;

@@ -43,7 +43,7 @@ def test_mcmc_steps_match_oracle(lens):
             ctx.wait()
             po2, co2, take, prop, cp = oracle.mcmc_step(m, cons, var, po, co, sigma, T_, seed, step)
             got_take = acc.cpu().numpy().astype(bool)
-            u = oracle.mcmc_uniforms(seed, step, W)[:, 14]
+            u = oracle.mcmc_uniforms(seed, step, W)[:, 16]
             margin = np.log(u) + (cp - co) / (2 * T_)
             sure = ~np.isfinite(margin) | (np.abs(margin) > 1e-6)   # decisions far from the threshold
             assert np.array_equal(got_take[sure], take[sure]), step
@@ -91,3 +91,44 @@ def test_mcmc_step_replays_and_zero_step(lens):
         with pytest.raises(lens.LensError) as e:
             ctx.mcmc_step(cs, p, c, W, sg, 0.0, 1, 0, scratch)
         assert e.value.code == lens.LENS_EINVAL
+
+
+def test_mcmc_steps_with_member_scaling_match_oracle(lens):
+    """16-parameter chains: the cluster halos and the members' b0 and r_cut
+    factors, chi2 as lens_chi2_source_scaled."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    W = 24
+    rng = np.random.default_rng(84)
+    params = np.hstack([I.perturbed_params(m, var, W, seed=85), rng.uniform(0.9, 1.1, (W, 2))])
+    chi2 = oracle.chi2_source_scaled_batch(m, cons, var, params, 0)
+    sigma = np.concatenate([np.tile([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1], 2), [0.02, 0.05]])
+    T_, seed = 2000.0, 77
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        c = torch.tensor(chi2, device=DEV)
+        sg = torch.tensor(sigma, device=DEV)
+        scratch = torch.empty(18 * W, dtype=torch.float64, device=DEV)
+        acc = torch.empty(W, dtype=torch.int32, device=DEV)
+        po, co = params.copy(), chi2.copy()
+        moved = 0
+        for step in range(3):
+            ctx.mcmc_step(cs, p, c, W, sg, T_, seed, step, scratch, acc)
+            ctx.wait()
+            _, _, take, prop, cp = oracle.mcmc_step(m, cons, var, po, co, sigma, T_, seed, step)
+            got_take = acc.cpu().numpy().astype(bool)
+            u = oracle.mcmc_uniforms(seed, step, W)[:, 16]
+            margin = np.log(u) + (cp - co) / (2 * T_)
+            sure = ~np.isfinite(margin) | (np.abs(margin) > 1e-6)
+            assert np.array_equal(got_take[sure], take[sure]), step
+            po = np.where(got_take[:, None], prop, po)
+            co = np.where(got_take, cp, co)
+            gp, gc = p.cpu().numpy(), c.cpu().numpy()
+            assert np.allclose(gp, po, rtol=1e-13, atol=1e-13), step
+            assert np.all(np.abs(gc - co) <= T.CHI2_REL * np.abs(co)), step
+            moved += int(got_take.sum())
+        assert 0 < moved < 3 * W
