@@ -389,6 +389,12 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     sig16 = torch.cat([sig, torch.tensor([0.02, 0.05], dtype=torch.float64, device=dev)])
     scratch16 = torch.empty(18 * P, dtype=torch.float64, device=dev)
     t16 = timed(lambda: ctx.mcmc_step(cs, walk16, wchi16, P, sig16, 2000.0, 7, 0, scratch16, acc, stream=stream), 1)
+    ctx.cset_scaling_cache(cs, 0.5, 2.0, 32)
+    ctx.chi2_source_scaled(cs, walk16, P, 0, wchi16, stream)
+    t16c = timed(lambda: ctx.mcmc_step(cs, walk16, wchi16, P, sig16, 2000.0, 7, 1, scratch16, acc, stream=stream), 5)
+    ctx.cset_scaling_cache(cs, 0.0, 0.0, 0)
+    ex["mcmc_step_scaled_cached"] = {"ms": t16c, "steps_per_s": 1e3 / t16c, "models_per_s": P / (t16c * 1e-3),
+                                     "chains": P, "workload": "as mcmc_step_scaled, chi2 from the scaling cache"}
     ex["mcmc_step_scaled"] = {"ms": t16, "steps_per_s": 1e3 / t16, "models_per_s": P / (t16 * 1e-3), "chains": P,
                               "workload": "Metropolis step of 4096 chains over 16 parameters (the members' "
                                           "scaling factors too; chi2 with every static potential per set)"}
@@ -412,6 +418,15 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
                                 "pair_per_s": nimg * (N_HALO - 2) * P / (t * 1e-3),
                                 "workload": "source-plane chi2 with the members' b0 and r_cut factors free, 4096 "
                                             "sets x 372 images x 1000 potentials, double-float with Hessian"}
+    # ... and from the scaling cache: the static sums at 32 Chebyshev nodes
+    # of the r_cut factor on [0.5, 2], interpolated per set
+    t0 = time.perf_counter()
+    ctx.cset_scaling_cache(cs, 0.5, 2.0, 32)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    t = timed(lambda: ctx.chi2_source_scaled(cs, p16, P, 0, chi2, stream), 5)
+    ex["chi2_source_scaled_cached"] = {"ms": t, "models_per_s": P / (t * 1e-3), "P": P, "cache_build_ms": build_ms,
+                                       "workload": "as chi2_source_scaled, the static sums interpolated from 32 "
+                                                   "Chebyshev nodes of the r_cut factor"}
     Pi = 256
     gi = I.grid(1024)
     chi2i = torch.empty(Pi, dtype=torch.float64, device=dev)

@@ -26,7 +26,7 @@ EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_u
            "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_potential_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
-           "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_source_scaled", "lens_mcmc_step", "lens_chi2_autotune", "lens_chi2_image",
+           "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_source_scaled", "lens_cset_scaling_cache", "lens_mcmc_step", "lens_chi2_autotune", "lens_chi2_image",
            "lens_find_images", "lens_chi2_image_noalloc", "lens_selftest_wait", "lens_selftest_math", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
            "lens_server_progress", "lens_server_cancel", "lens_server_stats")
@@ -98,6 +98,7 @@ def load_library(path=LIB_PATH):
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_source_nocache": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_source_scaled": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
+        "lens_cset_scaling_cache": (C.c_int, [vp, i64, C.c_double, C.c_double, C.c_int32]),
         "lens_mcmc_step": (C.c_int, [vp, i64, vp, vp, C.c_int32, C.c_int32, vp, C.c_double, C.c_uint64,
                                      C.c_uint64, C.c_int32, vp, vp, vp]),
         "lens_chi2_autotune": (C.c_int, [vp, i64, vp, C.c_int32, vp, vp, C.POINTER(C.c_int32),
@@ -274,6 +275,12 @@ class Context:
         _check(_lib.lens_chi2_source_scaled(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(out),
                                             _stream(stream)), "lens_chi2_source_scaled")
         return out
+
+    def cset_scaling_cache(self, cset, ft_min, ft_max, nodes=32):
+        """Static sums at Chebyshev points of the members' r_cut factor (see
+        lens.h); nodes = 0 drops them."""
+        _check(_lib.lens_cset_scaling_cache(self.h, int(cset), float(ft_min), float(ft_max), int(nodes)),
+               "lens_cset_scaling_cache")
 
     def mcmc_step(self, cset, params, chi2, W, sigma, temperature, seed, step, scratch, accepted=None,
                   variant=0, stream=None):

@@ -288,6 +288,8 @@ static void free_cset(lens_ctx *ctx, CSet *c) {
   dev_free(ctx, c->grp_ratio, c->ng * sizeof(double));
   dev_free(ctx, c->grp_ratio32, c->ng * sizeof(float));
   for (auto &g : c->grids) dev_free(ctx, g.alpha32, g.bytes);
+  dev_free(ctx, c->scale_cache, (size_t)c->scale_nodes * c->nimg * 5 * sizeof(double));
+  dev_free(ctx, c->scale_x, (size_t)c->scale_nodes * sizeof(double));
   if (c->stat_model) free_model(ctx, c->stat_model);
   delete c;
 }
@@ -680,6 +682,55 @@ int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_par
   const int rc = ensure_scratch(ctx, chi2_nocache_scratch_bytes(c));
   if (rc) return rc;
   return launch_chi2_source_scaled(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
+}
+
+int lens_cset_scaling_cache(lens_ctx *ctx, lens_cset_t cset, double ft_min, double ft_max, int32_t nodes) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  CSet *c = find_cset(ctx, cset);
+  if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
+  Model *m = find_model(ctx, c->model);
+  if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();  // calls using the old cache have finished
+  dev_free(ctx, c->scale_cache, (size_t)c->scale_nodes * c->nimg * 5 * sizeof(double));
+  dev_free(ctx, c->scale_x, (size_t)c->scale_nodes * sizeof(double));
+  c->scale_cache = c->scale_x = nullptr;
+  c->scale_nodes = 0;
+  if (nodes == 0) return LENS_OK;
+  if (nodes < 8 || nodes > 128) return fail(LENS_EINVAL, "nodes must be 0 or 8..128");
+  if (!(std::isfinite(ft_min) && std::isfinite(ft_max) && ft_min > 0.0 && ft_min < ft_max))
+    return fail(LENS_EINVAL, "need 0 < ft_min < ft_max");
+  for (int32_t i = 0; i < m->n; ++i) {
+    const lens_halo &h = m->host[i];
+    if (i == c->var[0] || i == c->var[1] || h.type != LENS_DPIE) continue;
+    if (!(ft_min * h.rcut > h.rcore)) return fail(LENS_EINVAL, "ft_min puts potential %d's r_cut below r_core", i);
+  }
+  std::vector<double> xs(nodes), p16((size_t)nodes * 16, 0.0);
+  for (int k = 0; k < nodes; ++k) {
+    xs[k] = 0.5 * (ft_min + ft_max) + 0.5 * (ft_max - ft_min) * std::cos(M_PI * k / (nodes - 1));
+    p16[(size_t)k * 16 + 14] = 1.0;
+    p16[(size_t)k * 16 + 15] = xs[k];
+  }
+  double *d_p16 = nullptr;
+  int rc = dev_alloc(ctx, (void **)&c->scale_cache, (size_t)nodes * c->nimg * 5 * sizeof(double));
+  if (!rc) rc = dev_alloc(ctx, (void **)&c->scale_x, (size_t)nodes * sizeof(double));
+  if (!rc) rc = dev_alloc(ctx, (void **)&d_p16, p16.size() * sizeof(double));
+  if (!rc && (cudaMemcpy(c->scale_x, xs.data(), nodes * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+              cudaMemcpy(d_p16, p16.data(), p16.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess))
+    rc = fail(LENS_ECUDA, "scaling cache upload failed");
+  c->scale_nodes = nodes;
+  if (!rc) rc = build_scaling_cache(ctx, m, c, d_p16, nodes);
+  dev_free(ctx, d_p16, p16.size() * sizeof(double));
+  if (rc) {
+    dev_free(ctx, c->scale_cache, (size_t)nodes * c->nimg * 5 * sizeof(double));
+    dev_free(ctx, c->scale_x, (size_t)nodes * sizeof(double));
+    c->scale_cache = c->scale_x = nullptr;
+    c->scale_nodes = 0;
+    return rc;
+  }
+  c->ft_min = ft_min;
+  c->ft_max = ft_max;
+  return LENS_OK;
 }
 
 int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,

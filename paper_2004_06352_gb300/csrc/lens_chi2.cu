@@ -334,13 +334,76 @@ __global__ void __launch_bounds__(CACHE_THREADS) k_static_scaled(const float2 *_
     for (int k = 0; k < 5; ++k) stat[(size_t)img * 5 + k] = any_bad ? __longlong_as_double(0x7ff8000000000000ll) : v[k];
 }
 
+// Static sums of each set from the scaling cache, grid (sets of the batch):
+// the barycentric Chebyshev interpolant in f_t of the cached sums (second
+// kind points xs with weights (-1)^k, halved at both ends: Berrut and
+// Trefethen, "Barycentric Lagrange interpolation", SIAM Review 2004), times
+// f_b; NaN for f_t outside the cached interval or f_b not positive.
+constexpr int MAX_SCALE_NODES = 128;
+__global__ void __launch_bounds__(CACHE_THREADS) k_scaled_interp(const double *__restrict__ cache,
+                                                                 const double *__restrict__ xs, int nodes,
+                                                                 double ft_min, double ft_max, int nimg,
+                                                                 const double *__restrict__ params, double *stat) {
+  __shared__ double s_w[MAX_SCALE_NODES];
+  __shared__ int s_hit;
+  const double fb = params[(size_t)blockIdx.x * 16 + 14], ft = params[(size_t)blockIdx.x * 16 + 15];
+  stat += (size_t)blockIdx.x * nimg * 5;
+  const bool ok = fb > 0.0 && isfinite(fb) && ft >= ft_min && ft <= ft_max;
+  if (threadIdx.x == 0) s_hit = -1;
+  __syncthreads();
+  for (int k = threadIdx.x; k < nodes; k += CACHE_THREADS) {
+    const double xk = xs[k];
+    const double wk = ((k & 1) ? -1.0 : 1.0) * ((k == 0 || k == nodes - 1) ? 0.5 : 1.0);
+    if (ft == xk) s_hit = k;
+    s_w[k] = wk / (ft - xk);
+  }
+  __syncthreads();
+  const int hit = s_hit;
+  double den = 0.0;
+  if (hit < 0)
+    for (int k = 0; k < nodes; ++k) den += s_w[k];
+  const double iden = hit < 0 ? 1.0 / den : 0.0;
+  for (int j = threadIdx.x; j < nimg; j += CACHE_THREADS) {
+    double v[5];
+    if (hit >= 0) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) v[q] = cache[((size_t)hit * nimg + j) * 5 + q];
+    } else {
+      double num[5] = {0, 0, 0, 0, 0};
+      for (int k = 0; k < nodes; ++k) {
+        const double w = s_w[k];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) num[q] = fma(w, cache[((size_t)k * nimg + j) * 5 + q], num[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) v[q] = num[q] * iden;
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) stat[(size_t)j * 5 + q] = ok ? fb * v[q] : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+int build_scaling_cache(lens_ctx *ctx, const Model *m, CSet *c, const double *d_nodes16, int32_t nodes) {
+  (void)ctx;
+  k_static_scaled<<<dim3(c->nimg, nodes), CACHE_THREADS>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1], c->x,
+                                                           c->y, d_nodes16, c->scale_cache);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(LENS_ECUDA, "scaling cache: %s", cudaGetErrorString(e));
+  return LENS_OK;
+}
+
 int launch_chi2_source_scaled(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                               int32_t variant, double *d_chi2, cudaStream_t st) {
   double *stat = (double *)ctx->scratch;
   for (int32_t p0 = 0; p0 < P; p0 += NOCACHE_BATCH) {
     const int B = std::min(NOCACHE_BATCH, P - p0);
-    k_static_scaled<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1],
-                                                                 c->x, c->y, d_params + (size_t)p0 * 16, stat);
+    if (c->scale_cache)
+      k_scaled_interp<<<B, CACHE_THREADS, 0, st>>>(c->scale_cache, c->scale_x, c->scale_nodes, c->ft_min,
+                                                    c->ft_max, c->nimg, d_params + (size_t)p0 * 16, stat);
+    else
+      k_static_scaled<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1],
+                                                                   c->x, c->y, d_params + (size_t)p0 * 16, stat);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LENS_ECUDA, "scaled static sums launch: %s", cudaGetErrorString(e));
     const int rc = launch_src_cfg<128>(ctx, c, d_params + (size_t)p0 * 16, B, variant, d_chi2 + p0, st, 0, stat,

@@ -248,6 +248,12 @@ struct CSet {
   float *grp_ratio32 = nullptr; // [ng] the same rounded to FP32 (image search)
   std::vector<GridCache> grids;
   size_t bytes = 0;
+  // members' scaling cache: the static sums at f_b = 1 and nodes Chebyshev
+  // points of f_t in [ft_min, ft_max] ([nodes][nimg][5]), or none
+  double *scale_cache = nullptr;
+  double *scale_x = nullptr;    // [nodes] the f_t points
+  int32_t scale_nodes = 0;
+  double ft_min = 0.0, ft_max = 0.0;
 };
 
 }  // namespace lens
@@ -319,6 +325,7 @@ int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const doubl
 size_t chi2_nocache_scratch_bytes(const CSet *c);
 int launch_chi2_source_scaled(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                               int32_t variant, double *d_chi2, cudaStream_t st);
+int build_scaling_cache(lens_ctx *ctx, const Model *m, CSet *c, const double *d_nodes16, int32_t nodes);
 int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                                int32_t variant, double *d_chi2, cudaStream_t st);
 int autotune_chi2_source(lens_ctx *ctx, CSet *c, const double *d_params, int32_t P, double *d_chi2, cudaStream_t st,

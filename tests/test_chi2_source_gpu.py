@@ -167,3 +167,52 @@ def test_chi2_source_scaled_members_matches_oracle(lens):
     sample = [0, 1, 7, 511, 512, 1023, 1024, 1099]
     ref = oracle.chi2_source_scaled_batch(m, cons, var, params[sample], 0)
     assert np.all(np.abs(got[sample] - ref) <= T.CHI2_REL * np.abs(ref)), np.max(np.abs(got[sample] - ref) / ref)
+
+
+def test_scaling_cache_interpolates_the_recomputed_sums(lens):
+    """The static sums interpolated in the members' r_cut factor from 32
+    Chebyshev nodes give the recomputed chi2 to the chi2 tolerance (median
+    ~1e-13, a few sets up to ~5e-9: the sums converge to 1e-12 by 32 nodes,
+    as the FP64 oracle's do, and the double-float sums' own rounding,
+    amplified ~1e3 by the residuals' cancellation, sets the floor), and the
+    oracle's, the worst set included; outside the cached interval the set is
+    NaN; dropping the cache restores the recomputed values bit for bit."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    P = 700
+    rng = np.random.default_rng(64)
+    params = np.hstack([I.perturbed_params(m, var, P, seed=65), rng.uniform(0.8, 1.2, (P, 1)),
+                        rng.uniform(0.55, 1.95, (P, 1))])
+    params[9, 15] = 2.2          # outside the cached interval
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        direct = torch.empty(P, dtype=torch.float64, device=DEV)
+        ctx.chi2_source_scaled(cs, p, P, 0, direct)
+        with pytest.raises(lens.LensError) as e:
+            ctx.cset_scaling_cache(cs, 1e-4, 2.0, 32)          # members' r_cut below r_core
+        assert e.value.code == lens.LENS_EINVAL
+        ctx.cset_scaling_cache(cs, 0.5, 2.0, 32)
+        cached = torch.empty(P, dtype=torch.float64, device=DEV)
+        ctx.chi2_source_scaled(cs, p, P, 0, cached)
+        ctx.cset_scaling_cache(cs, 0.0, 0.0, 0)
+        again = torch.empty(P, dtype=torch.float64, device=DEV)
+        ctx.chi2_source_scaled(cs, p, P, 0, again)
+        ctx.wait()
+        direct, cached, again = direct.cpu().numpy(), cached.cpu().numpy(), again.cpu().numpy()
+    assert np.isnan(cached[9]) and np.isfinite(direct[9])
+    ok = np.arange(P) != 9
+    rel = np.abs(cached[ok] - direct[ok]) / direct[ok]
+    assert rel.max() <= T.CHI2_REL and np.median(rel) <= 1e-11, (rel.max(), np.median(rel))
+    assert np.array_equal(again, direct)
+    # the oracle's comparison takes the worst well-conditioned set (chi2 up to
+    # 1e9; beyond, an image sits on a critical curve of the proposed model and
+    # the mapped chi2 divides by a vanishing det A^-1)
+    tame = ok & (direct < 1e9)
+    worst = int(np.flatnonzero(tame)[np.argmax(np.abs(cached[tame] - direct[tame]) / direct[tame])])
+    sample = [0, 1, 511, 512, 699, worst]
+    ref = oracle.chi2_source_scaled_batch(m, cons, var, params[sample], 0)
+    assert np.all(np.abs(cached[sample] - ref) <= T.CHI2_REL * np.abs(ref))
