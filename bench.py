@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the chi2 / FP64 comparison legs")
-    ap.add_argument("--profile-leg", default=None, choices=["map", "potential", "chi2_source", "chi2_image"],
+    ap.add_argument("--profile-leg", default=None,
+                    choices=["map", "potential", "chi2_source", "chi2_image", "mcmc", "scaled"],
                     help="run only this workload `--steps` times (for ncu launch lists); prints nothing")
     return ap.parse_args()
 
@@ -501,11 +502,27 @@ def profile_leg(args):
     else:
         cons = I.load_constraints(os.path.join(ROOT, "tests", "golden", "cfg2_constraints.json"))
         cs = ctx.cset_create(mid, cons, (0, 1))
-        P = 4096 if args.profile_leg == "chi2_source" else 256
+        P = 256 if args.profile_leg == "chi2_image" else 4096
         params = torch.tensor(I.perturbed_params(m, (0, 1), P, seed=35), device=dev)
         chi2 = torch.empty(P, dtype=torch.float64, device=dev)
         if args.profile_leg == "chi2_source":
             run = lambda: ctx.chi2_source(cs, params, P, 0, chi2)
+        elif args.profile_leg == "mcmc":
+            # Metropolis steps of 4096 chains (14 parameters)
+            ctx.chi2_source(cs, params, P, 0, chi2)
+            sig = torch.tensor([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1] * 2, dtype=torch.float64, device=dev)
+            scratch = torch.empty(16 * P, dtype=torch.float64, device=dev)
+            state = {"k": 0}
+
+            def run():
+                ctx.mcmc_step(cs, params, chi2, P, sig, 2000.0, 5, state["k"], scratch)
+                state["k"] += 1
+        elif args.profile_leg == "scaled":
+            # the members' scaling factors free: recomputed sums, then the cache
+            p16 = torch.cat([params, torch.full((P, 2), 1.05, dtype=torch.float64, device=dev)], 1)
+            ctx.chi2_source_scaled(cs, p16, P, 0, chi2)
+            ctx.cset_scaling_cache(cs, 0.5, 2.0, 32)
+            run = lambda: ctx.chi2_source_scaled(cs, p16, P, 0, chi2)
         else:
             gi = I.grid(1024)
             run = lambda: ctx.chi2_image(cs, gi, params, P, chi2)

@@ -45,29 +45,30 @@ __device__ __forceinline__ double unit_open(unsigned long long x) {
   return ((double)(x >> 11) + 0.5) * 0x1.0p-53;
 }
 
-// Proposals into prop [W][NP] and the acceptance uniforms into ua [W].
+// Proposals into prop [W][NP] and the acceptance uniforms into ua [W]: one
+// thread per (chain, Philox block j = 0..3), each block's four words giving
+// two Box-Muller pairs (parameters 4j .. 4j+3 where < NP); the j = 0 thread
+// also draws block 4 for the acceptance uniform.  (One thread per chain left
+// most SMs idle: 4096 chains are 32 CTAs of 128.)
 template <int NP>
 __global__ void k_mcmc_propose(const double *__restrict__ params, const double *__restrict__ sigma, int W,
                                unsigned long long seed, unsigned long long step, double *__restrict__ prop,
                                double *__restrict__ ua) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = t >> 2, j = t & 3;
   if (w >= W) return;
-  double u[16];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const U4 r = philox4x64_10(U4{{step, (unsigned long long)w, (unsigned long long)j, 0ull}}, seed, 0ull);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) u[4 * j + q] = unit_open(r.w[q]);
-  }
+  const U4 r = philox4x64_10(U4{{step, (unsigned long long)w, (unsigned long long)j, 0ull}}, seed, 0ull);
   const double two_pi = 6.283185307179586;
 #pragma unroll
-  for (int i = 0; i < NP / 2; ++i) {
-    const double rad = sqrt(-2.0 * log(u[2 * i])), ang = two_pi * u[2 * i + 1];
-    const size_t o = (size_t)w * NP + 2 * i;
-    prop[o] = params[o] + sigma[2 * i] * (rad * cos(ang));
-    prop[o + 1] = params[o + 1] + sigma[2 * i + 1] * (rad * sin(ang));
+  for (int h = 0; h < 2; ++h) {
+    const int i = 4 * j + 2 * h;  // parameters i, i + 1
+    if (i >= NP) break;
+    const double rad = sqrt(-2.0 * log(unit_open(r.w[2 * h]))), ang = two_pi * unit_open(r.w[2 * h + 1]);
+    const size_t o = (size_t)w * NP + i;
+    prop[o] = params[o] + sigma[i] * (rad * cos(ang));
+    prop[o + 1] = params[o + 1] + sigma[i + 1] * (rad * sin(ang));
   }
-  ua[w] = unit_open(philox4x64_10(U4{{step, (unsigned long long)w, 4ull, 0ull}}, seed, 0ull).w[0]);
+  if (j == 0) ua[w] = unit_open(philox4x64_10(U4{{step, (unsigned long long)w, 4ull, 0ull}}, seed, 0ull).w[0]);
 }
 
 // Metropolis acceptance; accepted[w] (when not NULL) records the decision.
@@ -93,11 +94,11 @@ int launch_mcmc_step(lens_ctx *ctx, const Model *m, const CSet *c, double *d_par
                      const double *d_sigma, double temperature, unsigned long long seed, unsigned long long step,
                      int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st) {
   double *prop = d_scratch, *ua = d_scratch + (size_t)W * np, *chi2_prop = ua + W;
-  const int blocks = (W + 127) / 128;
+  const int blocks = (W + 127) / 128, pblocks = (4 * W + 127) / 128;
   if (np == 16)
-    k_mcmc_propose<16><<<blocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+    k_mcmc_propose<16><<<pblocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
   else
-    k_mcmc_propose<14><<<blocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+    k_mcmc_propose<14><<<pblocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "proposal launch: %s", cudaGetErrorString(e));
   const int rc = np == 16 ? launch_chi2_source_scaled(ctx, m, c, prop, W, variant, chi2_prop, st)
