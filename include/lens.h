@@ -262,8 +262,8 @@ int lens_cset_scaling_cache(lens_ctx *ctx, lens_cset_t cset, double ft_min, doub
  * the same step.  d_scratch: DEVICE double [(nparams + 2) W] (proposals, the
  * uniforms, the proposals' chi2); d_accepted: DEVICE int32 [W] (1 = moved)
  * or NULL.  temperature > 0; variant as for lens_chi2_source.  Asynchronous
- * on `stream`, no allocation or host synchronisation: three launches for
- * nparams = 14, the scaled chi2's batches of 512 for 16.  A CUDA graph
+ * on `stream`: three launches for nparams = 14 (no allocation), the scaled
+ * chi2's batches of 512 for 16 (its scratch grows on first use).  A CUDA graph
  * captured from it replays the captured step's draws (seed and step are
  * launch arguments). */
 int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W, int32_t nparams,
