@@ -132,3 +132,48 @@ def test_mcmc_steps_with_member_scaling_match_oracle(lens):
             assert np.all(np.abs(gc - co) <= T.CHI2_REL * np.abs(co)), step
             moved += int(got_take.sum())
         assert 0 < moved < 3 * W
+
+
+def test_mcmc_steps_with_scaling_cache_match_oracle(lens):
+    """16-parameter chains whose chi2 comes from the scaling cache (the
+    members' sums interpolated in the r_cut factor) against the oracle's
+    sampler with the sums recomputed exactly; a proposal outside the cached
+    factor interval is refused."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    W = 24
+    rng = np.random.default_rng(86)
+    params = np.hstack([I.perturbed_params(m, var, W, seed=87), rng.uniform(0.9, 1.1, (W, 2))])
+    params[4, 15] = 1.499                  # next to the cache's upper end: f_t proposals leave it
+    chi2 = oracle.chi2_source_scaled_batch(m, cons, var, params, 0)
+    sigma = np.concatenate([np.tile([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1], 2), [0.02, 0.05]])
+    T_, seed = 2000.0, 91
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        ctx.cset_scaling_cache(cs, 0.6, 1.5, 32)
+        p = torch.tensor(params, device=DEV)
+        c = torch.tensor(chi2, device=DEV)
+        sg = torch.tensor(sigma, device=DEV)
+        scratch = torch.empty(18 * W, dtype=torch.float64, device=DEV)
+        acc = torch.empty(W, dtype=torch.int32, device=DEV)
+        po, co = params.copy(), chi2.copy()
+        for step in range(2):
+            ctx.mcmc_step(cs, p, c, W, sg, T_, seed, step, scratch, acc)
+            ctx.wait()
+            _, _, take, prop, cp = oracle.mcmc_step(m, cons, var, po, co, sigma, T_, seed, step)
+            cp = np.where((prop[:, 15] >= 0.6) & (prop[:, 15] <= 1.5), cp, np.nan)  # the cache's prior
+            take = np.isfinite(cp) & (~np.isfinite(co) | (np.log(oracle.mcmc_uniforms(seed, step, W)[:, 16])
+                                                          < -(cp - co) / (2 * T_)))
+            got_take = acc.cpu().numpy().astype(bool)
+            u = oracle.mcmc_uniforms(seed, step, W)[:, 16]
+            margin = np.log(u) + (cp - co) / (2 * T_)
+            sure = ~np.isfinite(margin) | (np.abs(margin) > 1e-5)
+            assert np.array_equal(got_take[sure], take[sure]), step
+            po = np.where(got_take[:, None], prop, po)
+            co = np.where(got_take, cp, co)
+            assert np.allclose(p.cpu().numpy(), po, rtol=1e-13, atol=1e-13), step
+            assert np.all(np.abs(c.cpu().numpy() - co) <= T.CHI2_REL * np.abs(co)), step
+        ctx.cset_scaling_cache(cs, 0.0, 0.0, 0)
