@@ -347,6 +347,34 @@ def params_in_domain(table, var_halo, p14):
     return True
 
 
+def gaussian_proposals(params, sigma, u):
+    """Random-walk proposals params + sigma z, z standard normal from the
+    Box-Muller transform of consecutive pairs of the uniforms u [W][npar]
+    (radius sqrt(-2 ln u_2i), angle 2 pi u_2i+1; cosine to parameter 2i,
+    sine to 2i+1)."""
+    params = np.asarray(params, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    z = np.empty(params.shape)
+    for i in range(params.shape[-1] // 2):
+        rad = np.sqrt(-2.0 * np.log(u[:, 2 * i]))
+        ang = 2.0 * np.pi * u[:, 2 * i + 1]
+        z[:, 2 * i] = rad * np.cos(ang)
+        z[:, 2 * i + 1] = rad * np.sin(ang)
+    return params + np.asarray(sigma, dtype=np.float64) * z
+
+
+def metropolis_accept(chi2, chi2p, u, temperature):
+    """Metropolis decision for the likelihood exp(-chi2/2) of Sec. 2.2 (Eq. 6)
+    tempered by 1/T: a chain moves to its proposal when the uniform u is below
+    the likelihood ratio (L'/L)^(1/T) = exp(-(chi2' - chi2) / (2T)), compared
+    in logarithms.  A proposal outside the domain (chi2' NaN) never moves; a
+    chain whose current chi2 is NaN takes any valid proposal."""
+    chi2 = np.asarray(chi2, dtype=np.float64)
+    chi2p = np.asarray(chi2p, dtype=np.float64)
+    return np.isfinite(chi2p) & (~np.isfinite(chi2) |
+                                 (np.log(u) < -(chi2p - chi2) / (2.0 * temperature)))
+
+
 def mcmc_step(table, cons, var_halo, params, chi2, sigma, temperature, seed, step, variant=0):
     """One Metropolis step of W chains over 14 parameters (chi2 as
     chi2_source_batch) or 16 (with the members' scaling factors, chi2 as
@@ -361,13 +389,7 @@ def mcmc_step(table, cons, var_halo, params, chi2, sigma, temperature, seed, ste
     chi2 = np.asarray(chi2, dtype=np.float64)
     W = len(params)
     u = mcmc_uniforms(seed, step, W)
-    z = np.empty((W, npar))
-    for i in range(npar // 2):
-        rad = np.sqrt(-2.0 * np.log(u[:, 2 * i]))
-        ang = 2.0 * np.pi * u[:, 2 * i + 1]
-        z[:, 2 * i] = rad * np.cos(ang)
-        z[:, 2 * i + 1] = rad * np.sin(ang)
-    prop = params + np.asarray(sigma, dtype=np.float64) * z
+    prop = gaussian_proposals(params, sigma, u[:, :npar])
     if npar == 16:
         chi2p = chi2_source_scaled_batch(table, cons, var_halo, prop, variant)
     else:
@@ -375,8 +397,7 @@ def mcmc_step(table, cons, var_halo, params, chi2, sigma, temperature, seed, ste
         chi2p = np.full(W, np.nan)
         if ok.any():
             chi2p[ok] = chi2_source_batch(table, cons, var_halo, prop[ok], variant)
-    take = np.isfinite(chi2p) & (~np.isfinite(chi2) |
-                                 (np.log(u[:, 16]) < -(chi2p - chi2) / (2.0 * temperature)))
+    take = metropolis_accept(chi2, chi2p, u[:, 16], temperature)
     new_p = np.where(take[:, None], prop, params)
     new_c = np.where(take, chi2p, chi2)
     return new_p, new_c, take, prop, chi2p

@@ -1,7 +1,8 @@
 """Pins of the oracle's Metropolis sampler (the Bayesian fit of Sec. 2.2):
 its counter-based generator against numpy's own Philox4x64-10, the
-uniforms' and Box-Muller normals' distributions, and the acceptance rule in
-its limiting cases."""
+uniforms' and Box-Muller normals' distributions, the stationary law of the
+random walk, the acceptance frequency against the likelihood ratio, and the
+acceptance rule in its limiting cases."""
 import numpy as np
 import pytest
 
@@ -31,18 +32,18 @@ def test_uniforms_and_normals_distribution():
     u = oracle.mcmc_uniforms(seed=12345, step=7, W=4000)
     assert u.min() > 0.0 and u.max() < 1.0
     assert stats.kstest(u.ravel(), "uniform").pvalue > 1e-3
-    # the sampler's Box-Muller pairs are standard normal and uncorrelated
-    rad = np.sqrt(-2.0 * np.log(u[:, 0:14:2]))
-    z = np.concatenate([(rad * np.cos(2 * np.pi * u[:, 1:14:2])).ravel(),
-                        (rad * np.sin(2 * np.pi * u[:, 1:14:2])).ravel()])
-    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # the sampler's proposal steps (params 0, sigma 1) are standard normal,
+    # each coordinate and every pair uncorrelated
+    z = oracle.gaussian_proposals(np.zeros((len(u), 14)), np.ones(14), u[:, :14])
+    assert stats.kstest(z.ravel(), "norm").pvalue > 1e-3
+    assert abs(z.var() - 1.0) < 0.02 and abs(z.mean()) < 0.02
+    assert np.all(np.abs(np.corrcoef(z.T) - np.eye(14)) < 0.06)
     assert abs(np.corrcoef(u[:-1, 3], u[1:, 3])[0, 1]) < 0.05  # neighbouring chains
     assert not np.array_equal(oracle.mcmc_uniforms(12345, 8, 4), u[:4])   # steps differ
     assert np.array_equal(oracle.mcmc_uniforms(12345, 7, 4), u[:4])       # replayable
 
 
-@pytest.fixture(scope="module")
-def small_fit():
+def make_small_fit():
     m = I.random_model(6, seed=71)
     m[0, 7], m[1, 7] = 8.0, 6.0
     cons = I.random_constraints(4, seed=72, field=30)
@@ -51,6 +52,79 @@ def small_fit():
     chi2 = oracle.chi2_source_batch(m, cons, var, params, 0)
     sigma = np.tile([0.3, 0.3, 0.01, 0.02, 0.02, 1.0, 0.05], 2)
     return m, cons, var, params, chi2, sigma
+
+
+@pytest.fixture(scope="module")
+def small_fit():
+    return make_small_fit()
+
+
+# pytest fixtures of this module, as plain builders (the mutation tests call
+# the pins directly)
+FIXTURES = {"small_fit": make_small_fit}
+
+
+def test_stationary_distribution_is_the_tempered_likelihood():
+    """The random walk built from the oracle's proposals and acceptance rule
+    samples the posterior of the likelihood exp(-chi2/2) (Sec. 2.2) at
+    temperature T: for chi2(x) = sum_k (x_k/s_k)^2 the stationary law is
+    N(0, T s_k^2) in every coordinate.  Detailed balance fixes this law
+    whatever the step size; 20000 independent chains after a burn-in of 400
+    steps give each variance to about 1 %.  Dropping the 1/2 of the
+    likelihood would halve the variances."""
+    rng = np.random.default_rng(2024)
+    W, T = 20000, 1.7
+    s = np.array([0.5, 2.0, 1.0, 0.25])
+    chi2_of = lambda x: np.sum((x / s) ** 2, axis=1)
+    x = np.zeros((W, len(s)))
+    c = chi2_of(x)
+    rates = []
+    for _ in range(400):
+        prop = oracle.gaussian_proposals(x, 1.6 * s, rng.random((W, len(s))))
+        cp = chi2_of(prop)
+        take = oracle.metropolis_accept(c, cp, rng.random(W), T)
+        rates.append(take.mean())
+        x = np.where(take[:, None], prop, x)
+        c = np.where(take, cp, c)
+    assert 0.2 < np.mean(rates[-50:]) < 0.8
+    var = x.var(axis=0) / (T * s * s)
+    assert np.all(np.abs(var - 1.0) < 0.05), var
+    assert np.all(np.abs(x.mean(axis=0)) < 5 * np.sqrt(T / W) * s)
+
+
+def test_acceptance_frequency_matches_the_likelihood_ratio():
+    """On the lens model's own chi2: bin one step's proposals by the
+    difference of chi2 it reports; the fraction accepted in each bin equals
+    the mean Metropolis probability min(1, exp(-d chi2 / (2T))) of its
+    members, within binomial error (Sec. 2.2: likelihood exp(-chi2/2)).  The
+    temperature puts the probabilities across the middle of their range."""
+    m, cons, var, params, chi2, sigma = make_small_fit()
+    W = 2400
+    base = np.repeat(params[:1], W, axis=0)
+    c0 = np.repeat(chi2[:1], W)
+    # a first step fixes the scale of d chi2; T then puts exp(-d/2T) near
+    # e^-1 at the median |d| (the same proposals: same seed and step)
+    _, _, _, _, cp = oracle.mcmc_step(m, cons, var, base, c0, 0.4 * sigma, 1.0, seed=9, step=1)
+    d = cp - c0
+    T = float(np.median(np.abs(d[np.isfinite(d)]))) / 2.0
+    _, _, take, prop, cp = oracle.mcmc_step(m, cons, var, base, c0, 0.4 * sigma, T, seed=9, step=1)
+    d = cp - c0
+    ok = np.isfinite(d)
+    p = np.minimum(1.0, np.exp(-d[ok] / (2.0 * T)))
+    t = take[ok].astype(float)
+    edges = np.quantile(p, np.linspace(0, 1, 9))
+    checked = 0
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (p >= lo) & (p <= hi)
+        if sel.sum() < 50:
+            continue
+        mean_p = p[sel].mean()
+        err = np.sqrt(max(mean_p * (1 - mean_p), 1e-3) / sel.sum())
+        assert abs(t[sel].mean() - mean_p) < 4.5 * err + 1e-9, (lo, hi, t[sel].mean(), mean_p)
+        checked += 1
+    assert checked >= 4
+    # the accepted fraction overall sits mid-range, so the test has power
+    assert 0.15 < t.mean() < 0.85
 
 
 def test_zero_step_always_moves_in_place(small_fit):

@@ -1,12 +1,17 @@
 """The pins catch plausible mistakes: each mutant below is a copy of the
 oracle with one deliberate error (dropped term, flipped sign, wrong index,
-transposed operand, wrong normalisation), compiled on the CPU; every mutant
-must fail at least one pin of test_oracle_pins.py.  Nothing here touches a GPU."""
+transposed operand, wrong normalisation).  Mutants of the C evaluator are
+compiled on the CPU; mutants of the Python sampler are executed as a copy of
+the oracle package whose functions stand in for the originals.  Every mutant
+must fail at least one pin of test_oracle_pins.py or test_oracle_mcmc.py.
+Nothing here touches a GPU."""
 import inspect
+import types
 
 import pytest
 
 import oracle
+from tests import test_oracle_mcmc as mcmc_pins
 from tests import test_oracle_pins as pins
 
 # (description, exact text in lens_oracle.c, replacement)
@@ -31,6 +36,10 @@ MUTANTS = [
     ("Newton step sign", "    x += dx;\n    y += dy;", "    x -= dx;\n    y -= dy;"),
     ("distance ratio dropped", "for (int k = 0; k < 5; ++k) out[k] = dls_ds * acc[k];",
      "for (int k = 0; k < 5; ++k) out[k] = acc[k];"),
+    ("magnification weight is det, not |mu|", "chi2 += (dbx * dbx + dby * dby) * fabs(1.0 / det) / s2;",
+     "chi2 += (dbx * dbx + dby * dby) * fabs(det) / s2;"),
+    ("magnification weight without its absolute value", "chi2 += (dbx * dbx + dby * dby) * fabs(1.0 / det) / s2;",
+     "chi2 += (dbx * dbx + dby * dby) * (1.0 / det) / s2;"),
     ("chi2 sigma not squared", "ci += bd / (c->sigma[j] * c->sigma[j]);", "ci += bd / c->sigma[j];"),
     ("grid spacing", "return g->nx > 1 ? g->xmin + i * ((g->xmax - g->xmin) / (g->nx - 1)) : g->xmin;",
      "return g->nx > 1 ? g->xmin + i * ((g->xmax - g->xmin) / g->nx) : g->xmin;"),
@@ -40,19 +49,44 @@ MUTANTS = [
 ]
 
 
+# (description, exact text in oracle/__init__.py, replacement)
+PY_MUTANTS = [
+    ("acceptance without the 1/2 of the likelihood exp(-chi2/2)",
+     "(np.log(u) < -(chi2p - chi2) / (2.0 * temperature))", "(np.log(u) < -(chi2p - chi2) / temperature)"),
+    ("acceptance with the chi2 difference reversed",
+     "(np.log(u) < -(chi2p - chi2) / (2.0 * temperature))", "(np.log(u) < -(chi2 - chi2p) / (2.0 * temperature))"),
+    ("Box-Muller radius without the factor 2", "rad = np.sqrt(-2.0 * np.log(u[:, 2 * i]))",
+     "rad = np.sqrt(-np.log(u[:, 2 * i]))"),
+]
+
+
 def pin_functions():
     out = []
-    for name, fn in inspect.getmembers(pins, inspect.isfunction):
-        if not name.startswith("test_"):
-            continue
-        marks = getattr(fn, "pytestmark", [])
-        params = [m for m in marks if m.name == "parametrize"]
-        if params:
-            for v in params[0].args[1]:
-                out.append((f"{name}[{v}]", lambda fn=fn, v=v: fn(v)))
-        else:
-            out.append((name, fn))
+    for mod in (pins, mcmc_pins):
+        fixtures = getattr(mod, "FIXTURES", {})
+        for name, fn in inspect.getmembers(mod, inspect.isfunction):
+            if not name.startswith("test_"):
+                continue
+            marks = getattr(fn, "pytestmark", [])
+            params = [m for m in marks if m.name == "parametrize"]
+            args = list(inspect.signature(fn).parameters)
+            if params:
+                for v in params[0].args[1]:
+                    out.append((f"{name}[{v}]", lambda fn=fn, v=v: fn(v)))
+            elif args:
+                out.append((name, lambda fn=fn, args=args, fx=fixtures: fn(*[fx[a]() for a in args])))
+            else:
+                out.append((name, fn))
     return out
+
+
+def first_failing_pin():
+    for name, fn in pin_functions():
+        try:
+            fn()
+        except Exception:
+            return name
+    return None
 
 
 @pytest.fixture(scope="module")
@@ -67,13 +101,25 @@ def test_mutant_fails_a_pin(desc, old, new, workdir):
     path = oracle.build_variant(src.replace(old, new), str(workdir / f"m{abs(hash(desc))}.so"))
     oracle.use_library(path)
     try:
-        failed = []
-        for name, fn in pin_functions():
-            try:
-                fn()
-            except Exception:
-                failed.append(name)
-                break
-        assert failed, f"no pin caught mutant: {desc}"
+        assert first_failing_pin() is not None, f"no pin caught mutant: {desc}"
     finally:
         oracle.use_library(None)
+
+
+@pytest.mark.parametrize("desc,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_python_mutant_fails_a_pin(desc, old, new):
+    with open(oracle.__file__) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation site not found: {desc}"
+    mutant = types.ModuleType("oracle_mutant")
+    mutant.__file__ = oracle.__file__
+    exec(compile(src.replace(old, new), oracle.__file__, "exec"), mutant.__dict__)
+    names = [n for n, v in vars(oracle).items() if inspect.isfunction(v) and not n.startswith("_")]
+    saved = {n: getattr(oracle, n) for n in names}
+    try:
+        for n in names:
+            setattr(oracle, n, getattr(mutant, n))
+        assert first_failing_pin() is not None, f"no pin caught mutant: {desc}"
+    finally:
+        for n, v in saved.items():
+            setattr(oracle, n, v)

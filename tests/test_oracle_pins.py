@@ -346,6 +346,51 @@ def test_chi2_image_plane_sis_closed_form():
     assert math.isclose(oracle.chi2_source(m, cons, 2), exp_src, rel_tol=1e-12)
 
 
+def test_chi2_source_weighted_forms_sis_closed_form():
+    """The two weighted source-plane forms on an SIS, written here from its
+    closed forms.  For an SIS of strength b (times the distance ratio), the
+    inverse magnification matrix I - H has eigenvalue 1 along the radius and
+    1 - b/|theta| across it, so det = 1 - b/|theta| and |mu| = |theta| /
+    ||theta| - b|.  Variant 1 weights |bary - beta|^2 by |mu|; variant 0 maps
+    the residual back to the image plane with A = (I - H)^-1, which leaves its
+    radial part and divides its tangential part by 1 - b/|theta|.  The
+    constraints sit on both sides of the Einstein ring, so one image has a
+    negative det (the weight is |mu|, not mu)."""
+    b, r = 2.5, 0.8
+    m = I.halo_row(SIS, 0.4, -0.3, 0, 0, 0, 0, b)[None]
+    c0 = np.array([0.4, -0.3])
+    rng = np.random.default_rng(31)
+    xs, ys, sig, off = [], [], [], [0]
+    for s in (np.array([0.5, 0.3]), np.array([-0.2, 0.9]), np.array([0.7, -0.6])):
+        for p in _sis_images(r * b, s):
+            q = c0 + p + rng.normal(0, 0.08, 2)
+            xs.append(q[0])
+            ys.append(q[1])
+            sig.append(rng.uniform(0.05, 0.2))
+        off.append(len(xs))
+    cons = I.constraints_dict(off, xs, ys, np.array(sig), np.full(3, r))
+    be = r * b
+    exp1 = exp0 = 0.0
+    dets = []
+    for i in range(3):
+        pts = [np.array([xs[j], ys[j]]) - c0 for j in range(off[i], off[i + 1])]
+        beta = [p - be * p / np.linalg.norm(p) for p in pts]
+        bary = sum(beta) / len(beta)
+        for k, (p, bt) in enumerate(zip(pts, beta)):
+            rr = np.linalg.norm(p)
+            det = 1.0 - be / rr
+            dets.append(det)
+            d = bary - bt
+            s2 = sig[off[i] + k] ** 2
+            exp1 += np.sum(d * d) * rr / abs(rr - be) / s2
+            er = p / rr
+            et = np.array([-er[1], er[0]])
+            exp0 += ((d @ er) ** 2 + (d @ et / det) ** 2) / s2
+    assert min(dets) < 0 < max(dets)
+    assert math.isclose(oracle.chi2_source(m, cons, 1), exp1, rel_tol=1e-12)
+    assert math.isclose(oracle.chi2_source(m, cons, 0), exp0, rel_tol=1e-12)
+
+
 def test_source_plane_mapped_chi2_is_first_order_image_chi2():
     """For small noise, |A (bary - beta)| approximates the image-plane
     displacement, so the mapped source-plane chi2 (variant 0) tends to the
