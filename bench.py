@@ -156,6 +156,81 @@ def oracle_map_sample(m, g, seconds):
     return pairs / t_used, rows, oracle.num_threads()
 
 
+def interp_range_fraction(m, g, sub=64):
+    """Fraction of (grid node, FP32 dPIE) pairs whose core-minus-cut
+    arguments leave the range of the map kernel's interpolants
+    (max(w_x^2, w_y^2) >= 0.16, where the kernel calls the library atan /
+    log1p), on a sub x sub lattice of grid nodes, in FP64.  w_x and w_y are
+    the tangents of the differences of the core and cut terms' atan / atanh
+    arguments; potentials with b0 >= 5" (the FP64 path) are left out.  A
+    workload diagnostic only."""
+    t = np.asarray(m, dtype=np.float64)
+    t = t[(t[:, 0] == 0) & (t[:, 7] < 5.0)]
+    X, Y = np.meshgrid(np.linspace(g["xmin"], g["xmax"], sub), np.linspace(g["ymin"], g["ymax"], sub))
+    X, Y = X.ravel()[:, None], Y.ravel()[:, None]
+    x0, y0, th, e, rc, rt = (t[:, k][None, :] for k in (1, 2, 3, 4, 5, 6))
+    c, s = np.cos(th), np.sin(th)
+    x = c * (X - x0) + s * (Y - y0)
+    y = -s * (X - x0) + c * (Y - y0)
+    q = (1 - e) / (1 + e)
+    u = 2 * np.sqrt(e) / (1 + e)
+    sc, st = rc * (1 + e), rt * (1 + e)
+    pc = np.sqrt(q * q * (sc * sc + x * x) + y * y)
+    pt = np.sqrt(q * q * (st * st + x * x) + y * y)
+    ac, at = u * x / (pc + sc), u * x / (pt + st)
+    bc, bt = u * y / (pc + q * q * sc), u * y / (pt + q * q * st)
+    wx = (ac - at) / (1 + ac * at)
+    wy = (bc - bt) / (1 - bc * bt)
+    return float(np.mean(np.maximum(wx * wx, wy * wy) >= 0.16))
+
+
+def map_errors(res, m, g, dls=1.0, n=4000, seed=7):
+    """Max error of a LENS_MIXED Hessian map (planes ax, ay, kappa, gamma1,
+    gamma2, mu; a torch tensor on the device) against the oracle, on n random
+    grid nodes, the corners, and a 48 x 48 block around the map's smallest
+    deflection (where alpha's tolerance turns absolute).  Run outside any
+    timed region."""
+    import oracle
+    import torch
+    ny, nx = g["ny"], g["nx"]
+    rng = np.random.default_rng(seed)
+    ii, jj = rng.integers(0, nx, n), rng.integers(0, ny, n)
+    ii[:4], jj[:4] = [0, nx - 1, 0, nx - 1], [0, 0, ny - 1, ny - 1]
+    j0, i0 = divmod(int(torch.argmin(torch.hypot(res[0], res[1]))), nx)
+    j0, i0 = min(max(j0 - 24, 0), max(ny - 48, 0)), min(max(i0 - 24, 0), max(nx - 48, 0))
+    jb, ib = np.meshgrid(np.arange(j0, min(j0 + 48, ny)), np.arange(i0, min(i0 + 48, nx)), indexing="ij")
+    ii, jj = np.concatenate([ii, ib.ravel()]), np.concatenate([jj, jb.ravel()])
+    dx, dy = (g["xmax"] - g["xmin"]) / (nx - 1), (g["ymax"] - g["ymin"]) / (ny - 1)
+    ev = oracle.model_eval(m, g["xmin"] + ii * dx, g["ymin"] + jj * dy, dls)
+    rk, rg1, rg2 = 0.5 * (ev[:, 2] + ev[:, 3]), 0.5 * (ev[:, 2] - ev[:, 3]), ev[:, 4]
+    rdet = (1 - rk) ** 2 - rg1 ** 2 - rg2 ** 2
+    got = res[:, torch.from_numpy(jj).to(res.device), torch.from_numpy(ii).to(res.device)].double().cpu().numpy()
+    ra = np.hypot(ev[:, 0], ev[:, 1])
+    peak = ra.max()
+    ea = np.hypot(got[0] - ev[:, 0], got[1] - ev[:, 1])
+    tol_a = 1e-6 * np.maximum(ra, 1e-3 * peak)
+    det = 1.0 / got[5]
+    big = np.abs(rdet) >= 1e-2
+    worst = int(np.argmax(ea / tol_a))
+    out = {"nodes": int(len(ii)), "sample": f"{n} random nodes + corners + 48x48 block around min |alpha|",
+           "alpha_abs_arcsec": float(ea.max()), "alpha_rel_max": float(np.max(ea / np.maximum(ra, 1e-3 * peak))),
+           "alpha_worst_node": {"i": int(ii[worst]), "j": int(jj[worst]), "alpha_ref": float(ra[worst]),
+                                "err": float(ea[worst])},
+           "kappa": float(np.max(np.abs(got[2] - rk) / np.maximum(np.abs(rk), 1))),
+           "gamma1": float(np.max(np.abs(got[3] - rg1) / np.maximum(np.abs(rg1), 1))),
+           "gamma2": float(np.max(np.abs(got[4] - rg2) / np.maximum(np.abs(rg2), 1))),
+           "det_abs": float(np.max(np.abs(det - rdet))),
+           "mu_rel_where_det_ge_1e-2": float(np.max(np.abs(got[5] * rdet - 1.0)[big])) if big.any() else None,
+           "tolerance": {"alpha": "1e-6 max(|a|, 1e-3 peak)", "kappa_gamma": "1e-5 max(|x|,1)",
+                         "det_abs": 3e-5, "chi2_rel": 1e-8},
+           "within_tolerance": bool(np.all(ea <= tol_a)
+                                    and np.all(np.abs(got[2] - rk) <= 1e-5 * np.maximum(np.abs(rk), 1))
+                                    and np.all(np.abs(got[3] - rg1) <= 1e-5 * np.maximum(np.abs(rg1), 1))
+                                    and np.all(np.abs(got[4] - rg2) <= 1e-5 * np.maximum(np.abs(rg2), 1))
+                                    and np.all(np.abs(det - rdet) <= 3e-5))}
+    return out
+
+
 def run_reference(args, rank):
     """The oracle as it stands, on the host cores: each step a bounded row
     band of the same 2048^2 x 1000 workload."""
@@ -266,8 +341,14 @@ def main():
     value = ws * pairs / (ms * 1e-3)
 
     extra = {}
+    if rank == 0:
+        # accuracy of the timed map (its last step's output) against the oracle
+        try:
+            extra["max_err"] = {"hessian_map": map_errors(out, m, g)}
+        except Exception as e:  # the line still prints without it
+            extra["max_err"] = {"hessian_map": {"error": str(e)}}
     if rank == 0 and not args.no_extra:
-        extra = extra_legs(ctx, api, I, torch, dev, m, g, mid, stream)
+        extra.update(extra_legs(ctx, api, I, torch, dev, m, g, mid, stream, extra["max_err"], out))
 
     if rank != 0:
         ctx.close()
@@ -305,9 +386,10 @@ def main():
     ctx.close()
 
 
-def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
+def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream, errs, out):
     """Secondary numbers: grad-only map, plain FP64 GPU map, batched chi2, and
-    the oracle on the host cores (bounded sample)."""
+    the oracle on the host cores (bounded sample); max errors of the chi2 and
+    potential outputs against the oracle go into errs."""
     ex = {}
 
     def timed(fn, reps):
@@ -328,12 +410,36 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     # potential + time-delay (Fermat) surface about a source position
     outp = torch.empty((2, MAP_N, MAP_N), dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.potential_map(mid, g, 1.0, api.LENS_MIXED, outp, beta=(1.0, -2.0), stream=stream), 5)
+    try:
+        import oracle
+        rng = np.random.default_rng(8)
+        ii, jj = rng.integers(0, MAP_N, 4000), rng.integers(0, MAP_N, 4000)
+        dxy = 200.0 / (MAP_N - 1)
+        ref = oracle.potential(m, -100.0 + ii * dxy, -100.0 + jj * dxy, 1.0)
+        got = outp[0, torch.from_numpy(jj).to(dev), torch.from_numpy(ii).to(dev)].cpu().numpy()
+        errs["potential_map"] = {"phi_abs": float(np.max(np.abs(got - ref))),
+                                 "phi_range": float(ref.max() - ref.min()),
+                                 "frac_of_tolerance": float(np.max(np.abs(got - ref)) /
+                                                            (1e-6 * (ref.max() - ref.min()) + 1e-9 * np.abs(ref).max())),
+                                 "nodes": 4000}
+    except Exception as e:
+        errs["potential_map"] = {"error": str(e)}
     ex["potential_map_mixed"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3),
                                  "ops_per_pair": POT_FP32_OPS_PER_PAIR,
                                  "fp32_frac": POT_FP32_OPS_PER_PAIR * pairs / (t * 1e-3)
                                  / (SMS * FP32_LANES * 2.07e9) if POT_FP32_OPS_PER_PAIR else None,
                                  "workload": "potential + Fermat surface, 2048^2 x 1000, LENS_MIXED"}
     del outp
+    # the same map with the members' cut radii at 45" (L/L*)^1/2 instead of
+    # 8" (L/L*)^1/2: more (point, member) pairs inside a cut radius
+    m45 = I.cfg2_model(rcut_star=45.0)
+    mid45 = ctx.model_upload(m45)
+    t45 = timed(lambda: ctx.hessian_map(mid45, g, 1.0, api.LENS_MIXED, out, stream), 5)
+    ex["hessian_map_rcut45"] = {"ms": t45, "pair_per_s": pairs / (t45 * 1e-3),
+                                "interp_range_frac": interp_range_fraction(m45, g),
+                                "interp_range_frac_rcut8": interp_range_fraction(m, g),
+                                "workload": "hessian_map 2048^2 x 1000, members' r_cut = 45\" (L/L*)^1/2"}
+    ctx.model_release(mid45)
     out64 = torch.empty((6, MAP_N, MAP_N), dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.hessian_map(mid, g, 1.0, api.LENS_FP64, out64, stream), 1)
     ex["hessian_map_fp64_gpu"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3)}
@@ -361,6 +467,7 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     with torch.cuda.graph(graph, stream=side):
         ctx.chi2_source(cs, params, P, 0, chi2, side)
     t = timed(lambda: graph.replay(), 20)
+    chi2_src_gpu = chi2[:64].cpu().numpy()
     ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P,
                          "ms_default_shape": t_default, "autotuned_shape": cfg, "graph_replay": True,
                          "workload": "source-plane chi2, 4096 parameter sets, 1000 potentials"}
@@ -432,6 +539,10 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
     gi = I.grid(1024)
     chi2i = torch.empty(Pi, dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.chi2_image(cs, gi, params[:Pi], Pi, chi2i, None, stream), 2)
+    nf_img = torch.empty((Pi, len(cons["img_off"]) - 1), dtype=torch.int32, device=dev)
+    ctx.chi2_image(cs, gi, params[:1], 1, chi2i, nf_img, stream)
+    torch.cuda.synchronize()
+    chi2_img_gpu, nf_img_gpu = float(chi2i[0]), nf_img[0].cpu().numpy()
     ex["chi2_image"] = {"ms": t, "models_per_s": Pi / (t * 1e-3), "P": Pi,
                         "workload": "image-plane chi2, 1024^2 triangulated grid, 256 parameter sets, 1000 potentials"}
     # request loop: mixed Poisson stream over 8 resident models
@@ -448,7 +559,12 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream):
         ex["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                               "sample": f"failed: {e}"}
     try:
-        ex["cpu_oracle_other"] = oracle_other_legs(m, g, cons, params.cpu().numpy())
+        ex["cpu_oracle_other"], ref_src, ref_img, ref_nf = oracle_other_legs(m, g, cons, params.cpu().numpy())
+        rel = np.abs(chi2_src_gpu - ref_src) / np.abs(ref_src)
+        errs["chi2_source"] = {"rel_max": float(rel.max()), "sets": len(rel), "variant": 0}
+        errs["chi2_image"] = {"rel": abs(chi2_img_gpu - ref_img) / abs(ref_img), "sets": 1,
+                              "image_counts_equal": bool(np.array_equal(nf_img_gpu, ref_nf)),
+                              "grid": "1024^2"}
     except Exception as e:
         ex["cpu_oracle_other"] = {"error": str(e)}
     return ex
@@ -470,14 +586,14 @@ def oracle_other_legs(m, g, cons, params):
     out["hessian_map_1core"] = {"pair_per_s": rate, "cores": 1, "sample": f"{rows} rows x 2048 x 1000"}
     n = 64
     t0 = time.perf_counter()
-    oracle.chi2_source_batch(m, cons, (0, 1), params[:n], 0)
+    ref_src = oracle.chi2_source_batch(m, cons, (0, 1), params[:n], 0)
     dt = time.perf_counter() - t0
     out["chi2_source"] = {"models_per_s": n / dt, "cores": thr, "sample": f"{n} parameter sets"}
     t0 = time.perf_counter()
-    oracle.chi2_image_batch(m, cons, I.grid(1024), (0, 1), params[:1])
+    ref_img, ref_nf = oracle.chi2_image_batch(m, cons, I.grid(1024), (0, 1), params[:1])
     dt = time.perf_counter() - t0
     out["chi2_image"] = {"models_per_s": 1.0 / dt, "cores": thr, "sample": "1 parameter set, 1024^2 grid"}
-    return out
+    return out, ref_src, float(ref_img[0]), ref_nf[0]
 
 
 def profile_leg(args):

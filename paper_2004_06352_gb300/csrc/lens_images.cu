@@ -43,7 +43,7 @@ namespace {
 
 constexpr int IMG_CAP = 4096;       // candidate images per parameter set
 constexpr int IMG_BATCH = 256;      // parameter sets per batch
-constexpr int MAX_SRC = 1024;
+constexpr int MAX_SRC = IMG_MAX_SRC;
 constexpr double DEDUP = 1e-3;      // images closer than this are one image (arcsec)
 constexpr double NEWTON32_TOL = 1e-4;
 constexpr double POLISH_TOL = 1e-6;  // same stopping rule as the FP64 Newton of the definition
@@ -1043,6 +1043,20 @@ size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch) { return layout(ba
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P, double *d_chi2,
                    int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st, double *d_images,
                    int32_t img_max, int32_t *d_img_count) {
+  {
+    // every caller (the entry points, the request loop, the allocation-free
+    // path) passes through here: refuse what the kernels' fixed shared
+    // arrays cannot hold before anything is launched
+    lens_grid g;
+    g.xmin = gc->xmin;
+    g.xmax = gc->xmax;
+    g.ymin = gc->ymin;
+    g.ymax = gc->ymax;
+    g.nx = gc->nx;
+    g.ny = gc->ny;
+    const int lim = check_chi2_image_limits(c, &g);
+    if (lim) return lim;
+  }
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   const Model *sm = c->stat_model;
@@ -1081,7 +1095,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   g.fdy = (float)g.dy;
   g.tiny = (float)(1e-10 * g.dx * g.dy);
   const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
-  cudaFuncSetAttribute(k_img_sources, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_img_sources, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)IMG_SRC_SMEM_MAX);
   for (int32_t p0 = 0; p0 < P; p0 += batch) {
     SetArgs a;
     a.params = d_params;
@@ -1140,14 +1154,21 @@ int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st
   return LENS_OK;
 }
 
+int check_chi2_image_limits(const CSet *c, const lens_grid *g) {
+  if (c->nsrc > MAX_SRC) return fail(LENS_EINVAL, "image-plane chi2 supports at most %d sources", MAX_SRC);
+  const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
+  if (src_smem > IMG_SRC_SMEM_MAX)
+    return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
+  if ((long long)(g->nx - 1) * (g->ny - 1) > (1ll << 30)) return fail(LENS_EINVAL, "grid too large");
+  return LENS_OK;
+}
+
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
                       double *d_chi2, int32_t *d_nfound, cudaStream_t st, double *d_images, int32_t img_max,
                       int32_t *d_img_count) {
   (void)m;
-  if (c->nsrc > MAX_SRC) return fail(LENS_EINVAL, "image-plane chi2 supports at most %d sources", MAX_SRC);
-  const size_t src_smem = sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc);
-  if (src_smem > 200 * 1024) return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
-  if ((long long)(g->nx - 1) * (g->ny - 1) > (1ll << 30)) return fail(LENS_EINVAL, "grid too large");
+  int lim = check_chi2_image_limits(c, g);
+  if (lim) return lim;
   const GridCache *gc = find_grid_cache(c, g);
   if (!gc) {
     int rc = build_grid_cache(ctx, c, g, st);

@@ -334,6 +334,15 @@ int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g
                       double *d_chi2, int32_t *d_nfound, cudaStream_t st, double *d_images = nullptr,
                       int32_t img_max = 0, int32_t *d_img_count = nullptr);
 size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch);
+// Limits of the image-plane chi2 kernels: sources per constraint set (the
+// image search keeps every source of a distance group in fixed shared
+// arrays) and the dynamic shared memory of the back-trace kernel.
+constexpr int32_t IMG_MAX_SRC = 1024;
+constexpr size_t IMG_SRC_SMEM_MAX = 200 * 1024;
+// LENS_OK when constraint set c and grid g are within those limits (and the
+// grid's triangle count fits the search's 32-bit cell indices); every path
+// into run_chi2_image checks this before anything is launched.
+int check_chi2_image_limits(const CSet *c, const lens_grid *g);
 const GridCache *find_grid_cache(const CSet *c, const lens_grid *g);
 int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st);
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P,

@@ -26,10 +26,7 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LENS_NOALLOC_SCRATCH_BYTES];
 
-// Limits of the image-plane chi2 kernels (sources per set, shared memory of
-// the back-trace kernel); the same bounds lens_chi2_image enforces.
-constexpr int32_t NOALLOC_MAX_SRC = 1024;
-constexpr size_t NOALLOC_MAX_SMEM = 200 * 1024;
+// Parameter sets per batch at most (fewer when the grid leaves less room).
 constexpr int32_t NOALLOC_MAX_BATCH = 16;
 constexpr int MAX_DEVICES = 64;
 
@@ -70,9 +67,7 @@ extern "C" int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const le
   CSet *c = find_cset(ctx, cset);
   if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
   if (!find_model(ctx, c->model)) return fail(LENS_ENOTFOUND, "model of constraint set not found");
-  if (c->nsrc > NOALLOC_MAX_SRC) return fail(LENS_EINVAL, "image-plane chi2 supports at most %d sources", NOALLOC_MAX_SRC);
-  if (sizeof(double) * (2 * REC64 + 2 * (size_t)c->nimg + 2 * (size_t)c->nsrc) > NOALLOC_MAX_SMEM)
-    return fail(LENS_EINVAL, "constraint set too large for one CTA (%d images)", c->nimg);
+  if ((rc = check_chi2_image_limits(c, grid))) return rc;
   // the static deflection of this grid, then the candidate buffers of a
   // batch of parameter sets; the batch shrinks until both fit
   const size_t grid_bytes = align256(2 * sizeof(float) * (size_t)grid->nx * grid->ny);

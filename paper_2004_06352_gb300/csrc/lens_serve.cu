@@ -234,6 +234,7 @@ int lens_server_submit(lens_server *s, const lens_request *r, int64_t *ticket) {
     else if (r->P < 1 || !r->params) rc = fail(LENS_EINVAL, "chi2 request needs P >= 1 and params");
     else if (r->kind == LENS_REQ_CHI2_SOURCE && (r->variant < 0 || r->variant > 2)) rc = fail(LENS_EINVAL, "bad variant");
     else if (r->kind == LENS_REQ_CHI2_IMAGE && (rc = check_grid(&r->grid))) {
+    } else if (r->kind == LENS_REQ_CHI2_IMAGE && (rc = check_chi2_image_limits(c, &r->grid))) {
     }
     if (!rc) {
       q->params.assign(r->params, r->params + (size_t)r->P * 14);

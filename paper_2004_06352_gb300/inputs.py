@@ -60,13 +60,14 @@ def cfg1_model(seed=1):
     return np.stack(rows)
 
 
-def cfg2_model(seed=2, n_members=998):
+def cfg2_model(seed=2, n_members=998, rcut_star=8.0):
     """2 cluster-scale dPIE halos + luminosity-scaled members (1000 halos).
 
     Members: log10(L/L*) ~ N(-0.5, 0.4) clipped to [-2, 0.7];
     b0 = 1.0"(L/L*)^1/2 (b0 ~ sigma^2, sigma ~ L^1/4), rcore = 0.15"(L/L*)^1/2,
-    rcut = 8"(L/L*)^1/2 (~45 kpc at z ~ 0.5); centres Gaussian (40") about the
-    origin clipped to the field; eps U(0, 0.6); theta U(0, pi).
+    rcut = rcut_star (L/L*)^1/2 with rcut_star = 8" by default (~45 kpc at
+    z ~ 0.5); centres Gaussian (40") about the origin clipped to the field;
+    eps U(0, 0.6); theta U(0, pi).  rcut_star changes no other draw.
     """
     rng = np.random.default_rng(seed)
     rows = []
@@ -81,7 +82,7 @@ def cfg2_model(seed=2, n_members=998):
     th = rng.uniform(0, np.pi, n_members)
     for k in range(n_members):
         s = np.sqrt(l[k])
-        rows.append(halo_row(DPIE, xy[k, 0], xy[k, 1], th[k], eps[k], 0.15 * s, 8.0 * s, 1.0 * s))
+        rows.append(halo_row(DPIE, xy[k, 0], xy[k, 1], th[k], eps[k], 0.15 * s, rcut_star * s, 1.0 * s))
     return np.stack(rows)
 
 

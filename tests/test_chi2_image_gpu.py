@@ -55,10 +55,10 @@ def chi2_from_images(cons, imgs):
     return tot
 
 
-def test_chi2_image_cfg2_model_parity(lens):
-    """1000-potential model, 100 sources / 372 images at 5 distance ratios,
-    the two cluster halos varying; 256^2 search grid (0.78" cells); 5
-    parameter sets (the first is the model itself).
+def check_chi2_image_parity(lens, n, P, seed):
+    """The 1000-potential model, 100 sources / 372 images at 5 distance
+    ratios, the two cluster halos varying, an n x n search grid over
+    [-100, 100]^2; P parameter sets, the first being the model itself.
 
     Where a cell is far from linear (a galaxy core or a fold inside it), the
     grid search is ill-conditioned: the oracle reports such images with a
@@ -66,12 +66,13 @@ def test_chi2_image_cfg2_model_parity(lens):
     oracle image must be found; an image found by only one side must be an
     ill-conditioned oracle image or, on the GPU side, a true root; such
     differences stay rare; each GPU chi2 equals Eq. 6 recomputed from the
-    GPU's own images, and the oracle's chi2 wherever the image sets agree."""
+    GPU's own images, and the oracle's chi2 wherever the image sets agree,
+    which must happen for at least one set."""
     m = I.cfg2_model()
     cons = make_constraints.load()
     var = (0, 1)
-    g = I.grid(256)
-    params = I.perturbed_params(m, var, 5, seed=41)
+    g = I.grid(n)
+    params = I.perturbed_params(m, var, P, seed=seed)
     params[0] = I.var_params_of(m, var)
     ref, nf_ref = oracle.chi2_image_batch(m, cons, g, var, params)
     with lens.Context(0) as ctx:
@@ -79,7 +80,7 @@ def test_chi2_image_cfg2_model_parity(lens):
         cs = ctx.cset_create(mid, cons, var)
         got, nf = gpu_chi2_image(lens, m, cons, var, g, params, ctx=ctx)
         imgs = gpu_images(ctx, cs, g, params)
-    differ, total = 0, 0
+    differ, total, compared = 0, 0, 0
     for p in range(len(params)):
         mp = oracle.apply_params(m, var, params[p])
         _, bary = oracle.backtrace(mp, cons)
@@ -109,7 +110,21 @@ def test_chi2_image_cfg2_model_parity(lens):
         if same:
             assert np.array_equal(nf[p], nf_ref[p])
             assert abs(got[p] - ref[p]) <= T.CHI2_REL * abs(ref[p]), (p, got[p], ref[p])
+            compared += 1
     assert differ <= 0.01 * total, (differ, total)
+    assert compared >= 1, "no parameter set had the oracle's image sets"
+    return compared
+
+
+def test_chi2_image_cfg2_model_parity(lens):
+    """256^2 search grid (0.78" cells), 5 parameter sets."""
+    check_chi2_image_parity(lens, 256, 5, seed=41)
+
+
+def test_chi2_image_cfg2_model_parity_bench_grid(lens):
+    """The benchmark's 1024^2 search grid (0.20" cells: more candidates per
+    source, and the refinement starts at a finer scale), 3 parameter sets."""
+    check_chi2_image_parity(lens, 1024, 3, seed=45)
 
 
 def test_chi2_image_noise_free_is_zero(lens):

@@ -29,8 +29,8 @@ def run_map(lens, m, g, dls, precision, hess, threshold=None):
         return out.cpu().numpy().astype(np.float64)
 
 
-def check_mixed(res, ref, hess):
-    bad, err, _ = T.alpha_violations(res[0], res[1], ref[0], ref[1])
+def check_mixed(res, ref, hess, peak=None):
+    bad, err, _ = T.alpha_violations(res[0], res[1], ref[0], ref[1], peak=peak)
     n, msg = T.report("alpha", bad, err)
     assert n == 0, msg
     if hess:
@@ -122,6 +122,20 @@ def test_full_size_cfg2_sampled(lens):
     ref = np.vstack([ref, 1 / det])
     got = res[:, jj, ii].numpy()
     check_mixed(got, ref, True)
+    # every node of a 48 x 48 block around the smallest deflection of the map
+    # (the cluster's centre of deflection, where the absolute floor of the
+    # alpha tolerance applies), against the map's peak deflection
+    peak = float(np.hypot(ref[0], ref[1]).max())
+    a = torch.hypot(res[0], res[1])
+    j0, i0 = divmod(int(torch.argmin(a)), 2048)
+    j0, i0 = min(max(j0 - 24, 0), 2048 - 48), min(max(i0 - 24, 0), 2048 - 48)
+    jb, ib = np.meshgrid(np.arange(j0, j0 + 48), np.arange(i0, i0 + 48), indexing="ij")
+    jb, ib = jb.ravel(), ib.ravel()
+    ev = oracle.model_eval(m, -100.0 + ib * dx, -100.0 + jb * dx, 1.0)
+    ref = np.stack([ev[:, 0], ev[:, 1], 0.5 * (ev[:, 2] + ev[:, 3]), 0.5 * (ev[:, 2] - ev[:, 3]), ev[:, 4]])
+    ref = np.vstack([ref, 1 / ((1 - ref[2]) ** 2 - ref[3] ** 2 - ref[4] ** 2)])
+    assert np.hypot(ref[0], ref[1]).min() < 0.05 * peak
+    check_mixed(res[:, jb, ib].numpy(), ref, True, peak=peak)
 
 
 def test_full_size_cfg2_sampled_deflection_only(lens):

@@ -180,3 +180,33 @@ def test_short_requests_go_first(lens):
         assert sorted(order[:3]) == sorted(t for t, _ in small)
         assert np.all(np.isfinite(big.numpy()[:5]))
         srv.close()
+
+
+def test_image_chi2_beyond_the_kernels_limits_is_refused_everywhere(lens):
+    """A constraint set with more sources than the image search's shared
+    arrays hold (1025 > 1024) is refused with LENS_EINVAL before anything is
+    launched: by lens_chi2_image, by the allocation-free entry point and by
+    the request loop's submit (nothing queued, nothing in flight)."""
+    m = I.cfg2_model(seed=77, n_members=8)
+    cons = I.random_constraints(1025, seed=78, mult=(2, 2), field=40)
+    params = I.perturbed_params(m, (0, 1), 2, seed=79)
+    g = I.grid(64, field=(-60, 60, -60, 60))
+    with lens.Context(0) as ctx:
+        cs = ctx.cset_create(ctx.model_upload(m), cons, (0, 1))
+        p = torch.tensor(params, dtype=torch.float64, device="cuda:0")
+        out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda:0")
+        for call in (ctx.chi2_image, ctx.chi2_image_noalloc):
+            with pytest.raises(lens.LensError) as e:
+                call(cs, g, p, 2, out)
+            assert e.value.code == lens.LENS_EINVAL
+        srv = lens.Server(ctx, slots=2, pool_bytes=256 << 20)
+        buf = pinned((2,), torch.float64)
+        with pytest.raises(lens.LensError) as e:
+            srv.submit_chi2_image(cs, g, params, buf)
+        assert e.value.code == lens.LENS_EINVAL
+        st = srv.stats()
+        assert st["queued"] == 0 and st["inflight"] == 0 and st["pool_used"] == 0
+        srv.close()
+        ctx.wait()
+        assert torch.equal(out.cpu(), torch.full((2,), -1.0, dtype=torch.float64))
+        assert torch.isnan(buf).all()
