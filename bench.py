@@ -41,6 +41,16 @@ POT_FP32_OPS_PER_PAIR = 48.9
 # when the kernel ends
 MAP_TRAFFIC_BYTES = 482816 + 39919616
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
+# FP64 FMA lanes per SM and clock (measured on this GPU: 1/64 of the FP32 rate)
+FP64_LANES = 2
+# Thread operations per model of the batched chi2 legs (ncu instruction
+# counters on the 1000-potential model, 372 images; summary under profiles/):
+# FP32 = FFMA + FADD + FMUL, FP64 = DFMA + DADD + DMUL, MUFU = XU pipe.
+# Source-plane chi2, 4096 sets (k_chi2_source):
+CHI2_SRC_OPS = {"fp32": 1.276e6, "fp64": 1.881e4, "mufu": 1.207e4}
+# Image-plane chi2, 1024^2 grid, 256 sets (k_img_sources + search + newton +
+# dedup + polish + chi2, per model):
+CHI2_IMG_OPS = {"fp32": 8.898e8, "fp64": 1.996e6, "mufu": 4.636e7}
 
 
 def hbm_peak_gbs():
@@ -154,6 +164,17 @@ def oracle_map_sample(m, g, seconds):
         pairs += band * nx * len(m)
         band = min(band * 2, 64)
     return pairs / t_used, rows, oracle.num_threads()
+
+
+def leg_roofline(ops, models_per_s, f_hz):
+    """Achieved operation rates of a chi2 leg from its per-model counts,
+    against the FP32, FP64 and MUFU pipes' peaks at clock f_hz."""
+    out = {"bound": "alu", "unit": "Top/s", "ops_per_model": ops, "source": "ncu instruction counters"}
+    for pipe, lanes in (("fp32", FP32_LANES), ("fp64", FP64_LANES), ("mufu", MUFU_LANES)):
+        ach = ops[pipe] * models_per_s / 1e12
+        peak = SMS * lanes * f_hz / 1e12
+        out[pipe] = {"achieved": ach, "peak": peak, "frac": ach / peak}
+    return out
 
 
 def interp_range_fraction(m, g, sub=64):
@@ -470,6 +491,7 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream, errs, out):
     chi2_src_gpu = chi2[:64].cpu().numpy()
     ex["chi2_source"] = {"ms": t, "models_per_s": P / (t * 1e-3), "images": int(cons["img_off"][-1]), "P": P,
                          "ms_default_shape": t_default, "autotuned_shape": cfg, "graph_replay": True,
+                         "roofline": leg_roofline(CHI2_SRC_OPS, P / (t * 1e-3), 2.07e9),
                          "workload": "source-plane chi2, 4096 parameter sets, 1000 potentials"}
     # Metropolis sampling on the device: 4096 chains over the two cluster
     # halos' 14 parameters, one step = proposals + batched chi2 + acceptance
@@ -544,6 +566,7 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream, errs, out):
     torch.cuda.synchronize()
     chi2_img_gpu, nf_img_gpu = float(chi2i[0]), nf_img[0].cpu().numpy()
     ex["chi2_image"] = {"ms": t, "models_per_s": Pi / (t * 1e-3), "P": Pi,
+                        "roofline": leg_roofline(CHI2_IMG_OPS, Pi / (t * 1e-3), 2.07e9),
                         "workload": "image-plane chi2, 1024^2 triangulated grid, 256 parameter sets, 1000 potentials"}
     # request loop: mixed Poisson stream over 8 resident models
     try:

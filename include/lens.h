@@ -34,6 +34,16 @@
  *     enqueued when a call returns an error.  lens_strerror() names a code;
  *     lens_last_error() gives a message for the calling thread's last error.
  *   - A context is not thread-safe: one host thread at a time per context.
+ *     Its calls may target different streams and run concurrently on the
+ *     GPU: a call's working memory is allocated and freed in stream order on
+ *     that call's stream (from a memory pool of the context), so calls on
+ *     different streams never share it (lens_chi2_image_noalloc excepted: see
+ *     there).  No call but lens_destroy synchronises the device: releasing a
+ *     model or constraint set, growing a buffer or replacing a cache frees
+ *     the old memory on a stream of the context that first waits for every
+ *     launch the context enqueued before the release.  Work captured into a
+ *     CUDA graph is not tracked that way: release nothing a captured graph
+ *     still reads before its last replay has finished.
  */
 #ifndef LENS_H
 #define LENS_H
@@ -111,11 +121,15 @@ typedef struct {
 
 /* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
  * device memory the context may hold (models, constraint sets, caches,
- * scratch); 0 means no bound.  *out receives the context. */
+ * working memory of the calls in progress on the host); 0 means no bound.
+ * The context allocates from a device memory pool of its own, which keeps
+ * the memory it has held for reuse until lens_destroy.  *out receives the
+ * context. */
 int lens_create(lens_ctx **out, int device, size_t mem_budget_bytes);
 
 /* Release every model, constraint set and buffer of the context and free it.
- * Synchronises the device first.  NULL is accepted. */
+ * Synchronises the device first (the one call that does).  NULL is
+ * accepted. */
 int lens_destroy(lens_ctx *ctx);
 
 /* Potentials with b0 >= threshold_b0 are evaluated in FP64 by LENS_MIXED
@@ -182,8 +196,8 @@ int lens_potential_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid,
  * host as soon as it is done, so the copy overlaps the rest of the map; the
  * values equal those of lens_grad_map / lens_hessian_map.  Asynchronous:
  * h_out is complete when `stream` reaches this point.  Uses two device band
- * buffers owned by the context (counted in lens_mem_used); calls on streams
- * that are not ordered with each other must not overlap. */
+ * buffers owned by the context (counted in lens_mem_used); calls on
+ * different streams go through them one after the other, in call order. */
 int lens_grad_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds, int32_t precision,
                        void *h_out, void *stream);
 int lens_hessian_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, double dls_ds,
@@ -195,8 +209,10 @@ int lens_hessian_map_host(lens_ctx *ctx, lens_model_t model, const lens_grid *gr
  * var_halo[0], var_halo[1] (distinct, < n) are the two potentials whose
  * parameters each parameter set replaces; every other potential is static,
  * and its FP64 deflection and Hessian at the constraint positions are
- * computed here once (the static cache).  Synchronous.  The constraint
- * table is copied. */
+ * computed here once (the static cache).  Synchronous (on a stream of the
+ * context).  The constraint table is copied.  The chi2 calls take the
+ * returned handle in place of a (model, constraints, var_halo) triple per
+ * call, so the static cache stays resident across the calls of a fit. */
 int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *c, const int32_t var_halo[2],
                      lens_cset_t *out);
 int lens_cset_release(lens_ctx *ctx, lens_cset_t cset);
@@ -221,7 +237,7 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
  * static dPIE (r_core stays).  The static sums are recomputed for every set
  * in double-float (~1e-13 relative per potential; the r_cut-dependent
  * constants rebuilt from f_t r_cut in double-float; FP64 where that fails)
- * in batches of 512 sets, into the context's scratch (as
+ * in batches of 512 sets, into working memory of the call (as
  * lens_chi2_source_nocache).  NaN for a set outside the domain (f_b or f_t
  * not positive, or f_t r_cut <= r_core for a member). */
 int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
@@ -263,21 +279,35 @@ int lens_cset_scaling_cache(lens_ctx *ctx, lens_cset_t cset, double ft_min, doub
  * uniforms, the proposals' chi2); d_accepted: DEVICE int32 [W] (1 = moved)
  * or NULL.  temperature > 0; variant as for lens_chi2_source.  Asynchronous
  * on `stream`: three launches for nparams = 14 (no allocation), the scaled
- * chi2's batches of 512 for 16 (its scratch grows on first use).  A CUDA graph
+ * chi2's batches of 512 for 16 (with its working memory).  A CUDA graph
  * captured from it replays the captured step's draws (seed and step are
- * launch arguments). */
+ * launch arguments); lens_mcmc_step_dev keeps the step in device memory. */
 int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W, int32_t nparams,
                    const double *d_sigma, double temperature, uint64_t seed, uint64_t step, int32_t variant,
                    double *d_scratch, int32_t *d_accepted, void *stream);
 
+/* lens_mcmc_step with the step counter in device memory: d_step is DEVICE
+ * uint64 [1]; the step draws its Philox counters (step, w, j, 0) with step =
+ * *d_step as the proposals are formed, and its last kernel adds 1 to
+ * *d_step.  A CUDA graph captured from one call therefore draws the next
+ * step's numbers at every replay (with lens_mcmc_step, seed and step are
+ * launch arguments and a replay repeats the captured step).  The caller
+ * sets *d_step before the first step (any value; the same value replays the
+ * same sequence).  Arguments, errors and asynchrony otherwise as
+ * lens_mcmc_step; LENS_EINVAL when d_step is NULL. */
+int lens_mcmc_step_dev(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
+                       int32_t nparams, const double *d_sigma, double temperature, uint64_t seed, uint64_t *d_step,
+                       int32_t variant, double *d_scratch, int32_t *d_accepted, void *stream);
+
 /* lens_chi2_source without the static cache: the deflection and Hessian of
  * every static potential at every image are recomputed for every parameter
- * set (double-float, summed in FP64; batches of 512 sets in the context's
- * scratch memory), as in the paper's fit, which evaluates every potential for
+ * set (double-float, summed in FP64; batches of 512 sets in working memory
+ * of the call), as in the paper's fit, which evaluates every potential for
  * every model (Sec. 2.2, Sec. 4.2).  Same arguments, results (to ~1e-10
  * relative) and errors as lens_chi2_source; the per-set cost is N potentials
- * x images instead of 2 x images.  Grows the context's scratch to 512 x
- * images x 40 bytes (LENS_ENOMEM over budget). */
+ * x images instead of 2 x images.  Working memory 512 x images x 40 bytes,
+ * allocated and freed in stream order on `stream` (LENS_ENOMEM over the
+ * budget). */
 int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
                              double *d_chi2, void *stream);
 
@@ -301,7 +331,11 @@ int lens_chi2_autotune(lens_ctx *ctx, lens_cset_t cset, const double *d_params, 
  * candidate buffer, 4096 candidates, overflowed).  A source without images,
  * or an overflow, makes that set's chi2 NaN; an overflow also sets the
  * context's error flag, which the next lens_wait reports as LENS_ECAPACITY
- * (and clears). */
+ * (and clears).  At most 1024 sources per constraint set (LENS_EINVAL
+ * beyond, nothing launched).  The first call on a (constraint set, grid)
+ * pair computes and keeps the static potentials' deflection on the grid;
+ * each call's candidate buffers are working memory allocated and freed in
+ * stream order on `stream`. */
 int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, const double *d_params, int32_t P,
                     double *d_chi2, int32_t *d_nimg_found, void *stream);
 

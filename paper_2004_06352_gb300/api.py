@@ -26,7 +26,7 @@ EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_u
            "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_potential_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
-           "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_source_scaled", "lens_cset_scaling_cache", "lens_mcmc_step", "lens_chi2_autotune", "lens_chi2_image",
+           "lens_chi2_source", "lens_chi2_source_nocache", "lens_chi2_source_scaled", "lens_cset_scaling_cache", "lens_mcmc_step", "lens_mcmc_step_dev", "lens_chi2_autotune", "lens_chi2_image",
            "lens_find_images", "lens_chi2_image_noalloc", "lens_selftest_wait", "lens_selftest_math", "lens_wait", "lens_strerror",
            "lens_last_error", "lens_server_create", "lens_server_destroy", "lens_server_submit",
            "lens_server_progress", "lens_server_cancel", "lens_server_stats")
@@ -96,6 +96,8 @@ def load_library(path=LIB_PATH):
         "lens_cset_create": (C.c_int, [vp, i64, C.POINTER(lens_constraints), C.POINTER(C.c_int32), C.POINTER(i64)]),
         "lens_cset_release": (C.c_int, [vp, i64]),
         "lens_chi2_source": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
+        "lens_mcmc_step_dev": (C.c_int, [vp, i64, vp, vp, C.c_int32, C.c_int32, vp, C.c_double, C.c_uint64,
+                                         vp, C.c_int32, vp, vp, vp]),
         "lens_chi2_source_nocache": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_chi2_source_scaled": (C.c_int, [vp, i64, vp, C.c_int32, C.c_int32, vp, vp]),
         "lens_cset_scaling_cache": (C.c_int, [vp, i64, C.c_double, C.c_double, C.c_int32]),
@@ -291,6 +293,17 @@ class Context:
                                    float(temperature), int(seed) & (2**64 - 1), int(step) & (2**64 - 1),
                                    int(variant), _ptr(scratch), None if accepted is None else _ptr(accepted),
                                    _stream(stream)), "lens_mcmc_step")
+
+    def mcmc_step_dev(self, cset, params, chi2, W, sigma, temperature, seed, step_counter, scratch, accepted=None,
+                      variant=0, stream=None):
+        """mcmc_step with the step counter in device memory (step_counter: a
+        device tensor of one int64 / uint64, advanced by 1 by every step;
+        see lens.h)."""
+        nparams = int(params.shape[-1])
+        _check(_lib.lens_mcmc_step_dev(self.h, int(cset), _ptr(params), _ptr(chi2), int(W), nparams, _ptr(sigma),
+                                       float(temperature), int(seed) & (2**64 - 1), _ptr(step_counter),
+                                       int(variant), _ptr(scratch), None if accepted is None else _ptr(accepted),
+                                       _stream(stream)), "lens_mcmc_step_dev")
 
     def chi2_source_nocache(self, cset, params, P, variant, chi2, stream=None):
         _check(_lib.lens_chi2_source_nocache(self.h, int(cset), _ptr(params), int(P), int(variant), _ptr(chi2),

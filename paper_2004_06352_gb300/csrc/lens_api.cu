@@ -39,47 +39,114 @@ CSet *find_cset(lens_ctx *ctx, lens_cset_t id) {
   return nullptr;
 }
 
+// Long-lived device memory: from the context's pool on alloc_st (memory the
+// pool holds is reused; a free of this pool that has not completed is never
+// waited for, since internal dependencies are off for the pool), ready for
+// any stream on return.
 int dev_alloc(lens_ctx *ctx, void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return LENS_OK;
   if (ctx->budget && ctx->used + bytes > ctx->budget && !ctx->block_cache.empty()) {
     // cached model blocks go first
-    for (auto &b : ctx->block_cache) {
-      cudaFree(b.first);
-      ctx->used -= std::min(ctx->used, b.second);
-    }
+    auto cached = std::move(ctx->block_cache);
     ctx->block_cache.clear();
     ctx->cached_bytes = 0;
+    for (auto &b : cached) dev_free(ctx, b.first, b.second);
   }
   if (ctx->budget && ctx->used + bytes > ctx->budget)
     return fail(LENS_ENOMEM, "device memory budget exceeded: %zu used + %zu requested > %zu", ctx->used, bytes,
                 ctx->budget);
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->alloc_st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->alloc_st);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return fail(LENS_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    cudaGetLastError();
+    return fail(LENS_ENOMEM, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
   }
   ctx->used += bytes;
   return LENS_OK;
 }
 
+cudaStream_t upload_stream(lens_ctx *ctx) {
+  if (!ctx->upload_st && cudaStreamCreateWithFlags(&ctx->upload_st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->upload_st = nullptr;
+  }
+  return ctx->upload_st;
+}
+
+void wait_marks(lens_ctx *ctx, cudaStream_t st) {
+  for (auto &mk : ctx->marks) cudaStreamWaitEvent(st, mk.second, 0);
+}
+
 void dev_free(lens_ctx *ctx, void *p, size_t bytes) {
   if (!p) return;
-  cudaFree(p);
+  if (ctx->release_gen != ctx->mark_gen) {  // new launches since release_st last caught up
+    wait_marks(ctx, ctx->release_st);
+    ctx->release_gen = ctx->mark_gen;
+  }
+  cudaFreeAsync(p, ctx->release_st);
   ctx->used -= std::min(ctx->used, bytes);
 }
 
-int ensure_scratch(lens_ctx *ctx, size_t bytes) {
-  if (ctx->scratch_bytes >= bytes) return LENS_OK;
-  if (ctx->scratch) {
-    cudaDeviceSynchronize();
-    dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
-    ctx->scratch = nullptr;
-    ctx->scratch_bytes = 0;
+void mark_stream(lens_ctx *ctx, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return;
   }
-  int rc = dev_alloc(ctx, &ctx->scratch, bytes);
-  if (rc == LENS_OK) ctx->scratch_bytes = bytes;
-  return rc;
+  if (cs != cudaStreamCaptureStatusNone) return;
+  ++ctx->mark_gen;
+  if (ctx->marks.size() > 32) {  // drop streams whose marked work has finished
+    size_t k = 0;
+    for (auto &mk : ctx->marks) {
+      if (mk.first != st && cudaEventQuery(mk.second) == cudaSuccess)
+        cudaEventDestroy(mk.second);
+      else
+        ctx->marks[k++] = mk;
+    }
+    ctx->marks.resize(k);
+    cudaGetLastError();
+  }
+  for (auto &mk : ctx->marks)
+    if (mk.first == st) {
+      cudaEventRecord(mk.second, st);
+      return;
+    }
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(st);  // cannot track this stream: let its work finish instead
+    return;
+  }
+  cudaEventRecord(ev, st);
+  ctx->marks.push_back({st, ev});
+}
+
+int CallScratch::alloc(size_t n) {
+  if (n == 0) return LENS_OK;
+  if (ctx->budget && ctx->used + n > ctx->budget)
+    return fail(LENS_ENOMEM, "device memory budget exceeded: %zu used + %zu requested > %zu", ctx->used, n,
+                ctx->budget);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) cudaGetLastError();
+  // inside a graph capture: a memory node of the graph (the device's default pool)
+  const cudaError_t e = cs != cudaStreamCaptureStatusNone ? cudaMallocAsync(&p, n, st)
+                                                          : cudaMallocFromPoolAsync(&p, n, ctx->pool, st);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    cudaGetLastError();
+    return fail(LENS_ENOMEM, "working memory of %zu bytes: %s", n, cudaGetErrorString(e));
+  }
+  bytes = n;
+  ctx->used += n;
+  return LENS_OK;
+}
+
+CallScratch::~CallScratch() {
+  if (!p) return;
+  cudaFreeAsync(p, st);
+  ctx->used -= std::min(ctx->used, bytes);
 }
 
 int check_grid(const lens_grid *g) {
@@ -133,6 +200,10 @@ static int model_block(lens_ctx *ctx, size_t bytes, void **p, size_t *got) {
     *got = ctx->block_cache[best].second;
     ctx->cached_bytes -= *got;
     ctx->block_cache.erase(ctx->block_cache.begin() + best);
+    // the released model's launches may still be reading the block: the
+    // upload that overwrites it comes after every launch enqueued so far
+    if (!upload_stream(ctx)) return fail(LENS_ECUDA, "upload stream creation failed");
+    wait_marks(ctx, ctx->upload_st);
     return LENS_OK;
   }
   *got = bytes;
@@ -256,7 +327,7 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->recdf = (float2 *)(base + offs[5]);
   cudaError_t e = cudaSuccess;
   if (n > 0) {
-    if (!ctx->upload_st) e = cudaStreamCreateWithFlags(&ctx->upload_st, cudaStreamNonBlocking);
+    if (!upload_stream(ctx)) e = cudaErrorNotReady;
     if (e == cudaSuccess) e = cudaMemcpyAsync(base + offs[6], img, staged, cudaMemcpyHostToDevice, ctx->upload_st);
     if (e == cudaSuccess) {
       k_build_records<<<(3 * n + 63) / 64, 64, 0, ctx->upload_st>>>(
@@ -325,9 +396,31 @@ int lens_create(lens_ctx **out, int device, size_t mem_budget_bytes) {
   lens_ctx *ctx = new lens_ctx();
   ctx->device = device;
   ctx->budget = mem_budget_bytes;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaError_t e = cudaMemPoolCreate(&ctx->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;  // memory the pool holds stays with it until lens_destroy
+    int no = 0;
+    e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->alloc_st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->release_st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->alloc_st) cudaStreamDestroy(ctx->alloc_st);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    delete ctx;
+    return fail(LENS_ECUDA, "memory pool / stream creation: %s", cudaGetErrorString(e));
+  }
   int rc = dev_alloc(ctx, (void **)&ctx->d_err, sizeof(int));
   if (rc != LENS_OK) {
-    delete ctx;
+    lens_destroy(ctx);
     return rc;
   }
   cudaMemset(ctx->d_err, 0, sizeof(int));
@@ -343,9 +436,13 @@ int lens_destroy(lens_ctx *ctx) {
   for (auto &p : ctx->models) free_model(ctx, p.second);
   flush_block_cache(ctx);
   if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-  dev_free(ctx, ctx->scratch, ctx->scratch_bytes);
   dev_free(ctx, ctx->band, ctx->band_bytes);
   dev_free(ctx, ctx->d_err, sizeof(int));
+  if (ctx->release_st) cudaStreamSynchronize(ctx->release_st);
+  for (auto &mk : ctx->marks) cudaEventDestroy(mk.second);
+  if (ctx->alloc_st) cudaStreamDestroy(ctx->alloc_st);
+  if (ctx->release_st) cudaStreamDestroy(ctx->release_st);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   for (int k = 0; k < 2; ++k) {
     if (ctx->pipe_cs[k]) cudaStreamDestroy(ctx->pipe_cs[k]);
     if (ctx->pipe_done[k]) cudaEventDestroy(ctx->pipe_done[k]);
@@ -398,7 +495,8 @@ int lens_model_release(lens_ctx *ctx, lens_model_t id) {
   for (size_t k = 0; k < ctx->models.size(); ++k)
     if (ctx->models[k].first == id) {
       cudaSetDevice(ctx->device);
-      cudaDeviceSynchronize();
+      // the memory is freed (or kept for reuse) in stream order, after the
+      // launches enqueued so far: no wait here
       // constraint sets bound to this model go with it
       for (size_t j = 0; j < ctx->csets.size();) {
         if (ctx->csets[j].second->model == id) {
@@ -427,6 +525,7 @@ static int map_common(lens_ctx *ctx, lens_model_t model, const lens_grid *grid, 
   if ((uintptr_t)d_out % align) return fail(LENS_EINVAL, "d_out must be aligned to its element size");
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
+  StreamMark mark(ctx, st);
   if (precision == LENS_MIXED) return launch_map_mixed(ctx, m, grid, dls_ds, hess, d_out, st);
   if (precision == LENS_FP64) return launch_map_fp64(ctx, m, grid, dls_ds, hess, d_out, st);
   return fail(LENS_EINVAL, "precision must be LENS_FP64 or LENS_MIXED");
@@ -445,6 +544,7 @@ int lens_potential_map(lens_ctx *ctx, lens_model_t model, const lens_grid *grid,
   if (beta && !(std::isfinite(beta[0]) && std::isfinite(beta[1]))) return fail(LENS_EINVAL, "beta must be finite");
   if ((uintptr_t)d_out % 8) return fail(LENS_EINVAL, "d_out must be 8-byte aligned (double planes)");
   cudaSetDevice(ctx->device);
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_pot_map(ctx, m, grid, dls_ds, precision, beta, d_out, (cudaStream_t)stream);
 }
 
@@ -480,8 +580,7 @@ static int map_host_common(lens_ctx *ctx, lens_model_t model, const lens_grid *g
   const size_t band_bytes = (size_t)rows * nx * planes * esize;
   if (ctx->band_bytes < 2 * band_bytes) {
     if (ctx->band) {
-      cudaDeviceSynchronize();
-      dev_free(ctx, ctx->band, ctx->band_bytes);
+      dev_free(ctx, ctx->band, ctx->band_bytes);  // after the bands in flight have left
       ctx->band = nullptr;
       ctx->band_bytes = 0;
     }
@@ -498,6 +597,7 @@ static int map_host_common(lens_ctx *ctx, lens_model_t model, const lens_grid *g
     LENS_CUDA_TRY(cudaEventCreateWithFlags(&ctx->pipe_start, cudaEventDisableTiming));
   }
   cudaStream_t st = (cudaStream_t)stream;
+  StreamMark mark(ctx, st);  // st joins the band streams at the end
   LENS_CUDA_TRY(cudaEventRecord(ctx->pipe_start, st));
   for (int k = 0; k < 2; ++k) LENS_CUDA_TRY(cudaStreamWaitEvent(ctx->pipe_cs[k], ctx->pipe_start, 0));
   char *host = (char *)h_out;
@@ -648,8 +748,7 @@ int lens_cset_release(lens_ctx *ctx, lens_cset_t id) {
   for (size_t k = 0; k < ctx->csets.size(); ++k)
     if (ctx->csets[k].first == id) {
       cudaSetDevice(ctx->device);
-      cudaDeviceSynchronize();
-      free_cset(ctx, ctx->csets[k].second);
+      free_cset(ctx, ctx->csets[k].second);  // freed in stream order, after the launches so far
       ctx->csets.erase(ctx->csets.begin() + k);
       return LENS_OK;
     }
@@ -666,6 +765,7 @@ int lens_chi2_source(lens_ctx *ctx, lens_cset_t cset, const double *d_params, in
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_chi2_source(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
 }
 
@@ -679,8 +779,7 @@ int lens_chi2_source_scaled(lens_ctx *ctx, lens_cset_t cset, const double *d_par
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
-  const int rc = ensure_scratch(ctx, chi2_nocache_scratch_bytes(c));
-  if (rc) return rc;
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_chi2_source_scaled(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
 }
 
@@ -691,7 +790,7 @@ int lens_cset_scaling_cache(lens_ctx *ctx, lens_cset_t cset, double ft_min, doub
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();  // calls using the old cache have finished
+  // the old cache goes once the calls enqueued with it have finished
   dev_free(ctx, c->scale_cache, (size_t)c->scale_nodes * c->nimg * 5 * sizeof(double));
   dev_free(ctx, c->scale_x, (size_t)c->scale_nodes * sizeof(double));
   c->scale_cache = c->scale_x = nullptr;
@@ -733,9 +832,9 @@ int lens_cset_scaling_cache(lens_ctx *ctx, lens_cset_t cset, double ft_min, doub
   return LENS_OK;
 }
 
-int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
-                   int32_t nparams, const double *d_sigma, double temperature, uint64_t seed, uint64_t step,
-                   int32_t variant, double *d_scratch, int32_t *d_accepted, void *stream) {
+static int mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W, int32_t nparams,
+                     const double *d_sigma, double temperature, uint64_t seed, uint64_t step, uint64_t *d_step,
+                     int32_t variant, double *d_scratch, int32_t *d_accepted, void *stream) {
   if (!ctx || !d_params || !d_chi2 || !d_sigma || !d_scratch) return fail(LENS_EINVAL, "NULL argument");
   if (W < 1) return fail(LENS_EINVAL, "W must be >= 1");
   if (nparams != 14 && nparams != 16) return fail(LENS_EINVAL, "nparams must be 14 or 16");
@@ -746,12 +845,24 @@ int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
-  if (nparams == 16) {
-    const int rc = ensure_scratch(ctx, chi2_nocache_scratch_bytes(c));
-    if (rc) return rc;
-  }
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_mcmc_step(ctx, m, c, d_params, d_chi2, W, d_sigma, temperature, seed, step, variant, nparams,
-                          d_scratch, d_accepted, (cudaStream_t)stream);
+                          d_scratch, d_accepted, (cudaStream_t)stream, (unsigned long long *)d_step);
+}
+
+int lens_mcmc_step(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
+                   int32_t nparams, const double *d_sigma, double temperature, uint64_t seed, uint64_t step,
+                   int32_t variant, double *d_scratch, int32_t *d_accepted, void *stream) {
+  return mcmc_step(ctx, cset, d_params, d_chi2, W, nparams, d_sigma, temperature, seed, step, nullptr, variant,
+                   d_scratch, d_accepted, stream);
+}
+
+int lens_mcmc_step_dev(lens_ctx *ctx, lens_cset_t cset, double *d_params, double *d_chi2, int32_t W,
+                       int32_t nparams, const double *d_sigma, double temperature, uint64_t seed, uint64_t *d_step,
+                       int32_t variant, double *d_scratch, int32_t *d_accepted, void *stream) {
+  if (!d_step) return fail(LENS_EINVAL, "d_step is NULL");
+  return mcmc_step(ctx, cset, d_params, d_chi2, W, nparams, d_sigma, temperature, seed, 0, d_step, variant,
+                   d_scratch, d_accepted, stream);
 }
 
 int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_params, int32_t P, int32_t variant,
@@ -764,8 +875,7 @@ int lens_chi2_source_nocache(lens_ctx *ctx, lens_cset_t cset, const double *d_pa
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
-  const int rc = ensure_scratch(ctx, chi2_nocache_scratch_bytes(c));
-  if (rc) return rc;
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_chi2_source_nocache(ctx, m, c, d_params, P, variant, d_chi2, (cudaStream_t)stream);
 }
 
@@ -776,6 +886,7 @@ int lens_chi2_autotune(lens_ctx *ctx, lens_cset_t cset, const double *d_params, 
   CSet *c = find_cset(ctx, cset);
   if (!c) return fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)cset);
   cudaSetDevice(ctx->device);
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return autotune_chi2_source(ctx, c, d_params, P, d_chi2, (cudaStream_t)stream, chosen, best_ms);
 }
 
@@ -790,6 +901,7 @@ int lens_chi2_image(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, cons
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_chi2_image(ctx, m, c, grid, d_params, P, d_chi2, d_nimg_found, (cudaStream_t)stream);
 }
 
@@ -804,6 +916,7 @@ int lens_find_images(lens_ctx *ctx, lens_cset_t cset, const lens_grid *grid, con
   Model *m = find_model(ctx, c->model);
   if (!m) return fail(LENS_ENOTFOUND, "model of constraint set not found");
   cudaSetDevice(ctx->device);
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_chi2_image(ctx, m, c, grid, d_params, P, nullptr, nullptr, (cudaStream_t)stream, d_images,
                            max_per_set, d_count);
 }
@@ -812,6 +925,7 @@ int lens_selftest_wait(lens_ctx *ctx, int32_t polls, void *stream) {
   if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
   if (polls < 1 || polls > (1 << 20)) return fail(LENS_EINVAL, "polls must be in 1..2^20");
   cudaSetDevice(ctx->device);
+  StreamMark mark(ctx, (cudaStream_t)stream);
   return launch_wait_selftest(ctx, (unsigned)polls, (cudaStream_t)stream);
 }
 

@@ -129,11 +129,13 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
 
 }  // namespace
 
+// Synchronous on the context's upload stream (no other stream waits).
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c) {
-  (void)ctx;
-  k_static_cache<<<c->nimg, CACHE_THREADS>>>(m->all64, m->n, c->var[0], c->var[1], c->x, c->y, c->stat);
+  cudaStream_t st = upload_stream(ctx);
+  if (!st) return fail(LENS_ECUDA, "upload stream creation failed");
+  k_static_cache<<<c->nimg, CACHE_THREADS, 0, st>>>(m->all64, m->n, c->var[0], c->var[1], c->x, c->y, c->stat);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(LENS_ECUDA, "static cache: %s", cudaGetErrorString(e));
   return LENS_OK;
 }
@@ -245,7 +247,10 @@ size_t chi2_nocache_scratch_bytes(const CSet *c) { return (size_t)NOCACHE_BATCH 
 
 int launch_chi2_source_nocache(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                                int32_t variant, double *d_chi2, cudaStream_t st) {
-  double *stat = (double *)ctx->scratch;
+  CallScratch scratch(ctx, st);  // the static sums of a batch, on this call's stream
+  int rc0 = scratch.alloc(chi2_nocache_scratch_bytes(c));
+  if (rc0) return rc0;
+  double *stat = (double *)scratch.p;
   for (int32_t p0 = 0; p0 < P; p0 += NOCACHE_BATCH) {
     const int B = std::min(NOCACHE_BATCH, P - p0);
     k_static_df<<<dim3(c->nimg, B), CACHE_THREADS, 0, st>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1], c->x,
@@ -383,19 +388,24 @@ __global__ void __launch_bounds__(CACHE_THREADS) k_scaled_interp(const double *_
   }
 }
 
+// Synchronous on the context's upload stream.
 int build_scaling_cache(lens_ctx *ctx, const Model *m, CSet *c, const double *d_nodes16, int32_t nodes) {
-  (void)ctx;
-  k_static_scaled<<<dim3(c->nimg, nodes), CACHE_THREADS>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1], c->x,
-                                                           c->y, d_nodes16, c->scale_cache);
+  cudaStream_t st = upload_stream(ctx);
+  if (!st) return fail(LENS_ECUDA, "upload stream creation failed");
+  k_static_scaled<<<dim3(c->nimg, nodes), CACHE_THREADS, 0, st>>>(m->recdf, m->all64, m->n, c->var[0], c->var[1],
+                                                                  c->x, c->y, d_nodes16, c->scale_cache);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(LENS_ECUDA, "scaling cache: %s", cudaGetErrorString(e));
   return LENS_OK;
 }
 
 int launch_chi2_source_scaled(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                               int32_t variant, double *d_chi2, cudaStream_t st) {
-  double *stat = (double *)ctx->scratch;
+  CallScratch scratch(ctx, st);  // the static sums of a batch, on this call's stream
+  int rc0 = scratch.alloc(chi2_nocache_scratch_bytes(c));
+  if (rc0) return rc0;
+  double *stat = (double *)scratch.p;
   for (int32_t p0 = 0; p0 < P; p0 += NOCACHE_BATCH) {
     const int B = std::min(NOCACHE_BATCH, P - p0);
     if (c->scale_cache)

@@ -350,38 +350,25 @@ __device__ __forceinline__ void fold(Acc<HESS, KP> &tot, Acc<HESS, KP> &cmp, Acc
 #define LENS_SERIES_DEG 4
 #endif
 constexpr float T_SERIES = 0.16f;
-__device__ __forceinline__ float atan_over_w(float t) {
+// coefficients, highest degree first
 #if LENS_SERIES_DEG == 5
-  float p = -6.186992596e-02f;
-  p = fmaf(p, t, 1.062997788e-01f);
-  p = fmaf(p, t, -1.424732623e-01f);
-  p = fmaf(p, t, 1.999858949e-01f);
-  p = fmaf(p, t, -3.333331418e-01f);
-  return fmaf(p, t, 9.999999996e-01f);
+#define LENS_ATAN_W_COEF -6.186992596e-02f, 1.062997788e-01f, -1.424732623e-01f, 1.999858949e-01f, \
+                         -3.333331418e-01f, 9.999999996e-01f
+#define LENS_ATANH_W_COEF 1.399562492e-01f, 1.014973434e-01f, 1.436870917e-01f, 1.999682206e-01f, \
+                          3.333337736e-01f, 9.999999990e-01f
 #else
-  float p = 8.147408669e-02f;
-  p = fmaf(p, t, -1.389835755e-01f);
-  p = fmaf(p, t, 1.997853999e-01f);
-  p = fmaf(p, t, -3.333291011e-01f);
-  return fmaf(p, t, 9.999999865e-01f);
+#define LENS_ATAN_W_COEF 8.147408669e-02f, -1.389835755e-01f, 1.997853999e-01f, -3.333291011e-01f, 9.999999865e-01f
+#define LENS_ATANH_W_COEF 1.572736881e-01f, 1.359152003e-01f, 2.004095578e-01f, 3.333250231e-01f, 1.000000027e+00f
 #endif
+// Horner with FMA: c[0] t^n + ... + c[n]
+template <typename... C>
+__device__ __forceinline__ float horner(float t, float c0, C... c) {
+  float p = c0;
+  ((p = fmaf(p, t, c)), ...);
+  return p;
 }
-__device__ __forceinline__ float atanh_over_w(float t) {
-#if LENS_SERIES_DEG == 5
-  float p = 1.399562492e-01f;
-  p = fmaf(p, t, 1.014973434e-01f);
-  p = fmaf(p, t, 1.436870917e-01f);
-  p = fmaf(p, t, 1.999682206e-01f);
-  p = fmaf(p, t, 3.333337736e-01f);
-  return fmaf(p, t, 9.999999990e-01f);
-#else
-  float p = 1.572736881e-01f;
-  p = fmaf(p, t, 1.359152003e-01f);
-  p = fmaf(p, t, 2.004095578e-01f);
-  p = fmaf(p, t, 3.333250231e-01f);
-  return fmaf(p, t, 1.000000027e+00f);
-#endif
-}
+__device__ __forceinline__ float atan_over_w(float t) { return horner(t, LENS_ATAN_W_COEF); }
+__device__ __forceinline__ float atanh_over_w(float t) { return horner(t, LENS_ATANH_W_COEF); }
 
 // One dPIE (FP32) at KP points.  (dX, dY) of each point relative to the
 // potential's centre are formed by the caller from hi/lo float pairs, then
@@ -582,6 +569,206 @@ __device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, const 
     circ32<HESS, KP, false>(r4, dX, dY, p);
   else
     circ32<HESS, KP, true>(r4, dX, dY, p);
+}
+
+
+// ------------------------------------------------------- paired FP32 path
+// The map kernels give each thread points in pairs that share every
+// per-potential constant (two rows of one grid column).  Blackwell executes
+// the two FP32 additions, multiplications or FMAs of a float2 as one
+// instruction (FADD2 / FMUL2 / FFMA2), so a pair is evaluated side by side:
+// the same FP32 work in half the issued instructions.  The MUFU
+// approximations (rsqrt, rcp) have no paired form and run per point.  Each
+// paired operation rounds exactly as the scalar one it replaces (a - b is
+// formed as b * (-1) + a: an exact product and one rounding), so the paired
+// evaluators below give the scalar dpie32 / circ32 results bit for bit.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrt_a(a.x), rsqrt_a(a.y)); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp_a(a.x), rcp_a(a.y)); }
+template <typename... C>
+__device__ __forceinline__ float2 horner2(float2 t, float c0, C... c) {
+  float2 p = dup2(c0);
+  ((p = fma2(p, t, dup2(c))), ...);
+  return p;
+}
+// component h (0: .x, 1: .y) of a pair, h a compile-time constant after unrolling
+__device__ __forceinline__ float &part2(float2 &v, int h) { return h ? v.y : v.x; }
+__device__ __forceinline__ float part2(const float2 &v, int h) { return h ? v.y : v.x; }
+
+// Sums of NP point pairs: point 2 j + h lives in component h of entry j.
+template <bool HESS, int NP>
+struct Acc2 {
+  float2 ax[NP], ay[NP], k[NP], g1[NP], g2[NP];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) ax[i] = ay[i] = k[i] = g1[i] = g2[i] = make_float2(0.f, 0.f);
+  }
+};
+
+__device__ __forceinline__ void kahan2(float2 &s, float2 &c, float2 v) {
+  const float2 y = sub2(v, c);
+  const float2 t = add2(s, y);
+  c = sub2(sub2(t, s), y);
+  s = t;
+}
+
+template <bool HESS, int NP>
+__device__ __forceinline__ void fold2(Acc2<HESS, NP> &tot, Acc2<HESS, NP> &cmp, Acc2<HESS, NP> &part) {
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    kahan2(tot.ax[i], cmp.ax[i], part.ax[i]);
+    kahan2(tot.ay[i], cmp.ay[i], part.ay[i]);
+    if (HESS) {
+      kahan2(tot.k[i], cmp.k[i], part.k[i]);
+      kahan2(tot.g1[i], cmp.g1[i], part.g1[i]);
+      kahan2(tot.g2[i], cmp.g2[i], part.g2[i]);
+    }
+  }
+  part.zero();
+}
+
+// One dPIE (FP32) at NP point pairs sharing dX (one grid column), with dY
+// per point: the arithmetic of dpie32 (same formulas, same order), paired.
+template <bool HESS, int NP, bool SERIES>
+__device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, float dX, const float2 (&dY)[NP],
+                                         Acc2<HESS, NP> &p) {
+  const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
+  const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
+  const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
+  const float dK = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
+  const float q2dS = D.y;
+  const float cb = E.x, sb = E.y;
+  const float2 cdX = dup2(c * dX), msdX = dup2(-(s * dX));
+  float2 x[NP], y[NP], x2[NP], y2[NP], u2x2[NP], ic[NP], it[NP], psc[NP], pst[NP], Ec[NP], Et[NP];
+  float2 Zx[NP], Zy[NP], tx[NP], ty[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    x[k] = fma2(dup2(s), dY[k], cdX);
+    y[k] = fma2(dup2(c), dY[k], msdX);
+    x2[k] = mul2(x[k], x[k]);
+    y2[k] = mul2(y[k], y[k]);
+    u2x2[k] = mul2(dup2(u2), x2[k]);
+    const float2 R = fma2(dup2(q2), x2[k], y2[k]);
+    const float2 pc2 = add2(R, dup2(Kc)), pt2 = add2(R, dup2(Kt));
+    ic[k] = rsqrt2(pc2);
+    it[k] = rsqrt2(pt2);
+    psc[k] = mul2(pc2, ic[k]);
+    pst[k] = mul2(pt2, it[k]);
+    const float2 Sp = add2(psc[k], pst[k]);
+    Ec[k] = add2(psc[k], dup2(sc));
+    Et[k] = add2(pst[k], dup2(st));
+    Zx[k] = mul2(mul2(x[k], fma2(dup2(dS), Sp, dup2(dK))), rcp2(mul2(Sp, fma2(Ec[k], Et[k], u2x2[k]))));
+    const float2 Fc = add2(psc[k], dup2(q2sc)), Ft = add2(pst[k], dup2(q2st));
+    Zy[k] = mul2(mul2(y[k], fma2(dup2(q2dS), Sp, dup2(dK))), rcp2(mul2(Sp, fma2(dup2(-u2), y2[k], mul2(Fc, Ft)))));
+    tx[k] = mul2(dup2(u2), mul2(Zx[k], Zx[k]));
+    ty[k] = mul2(dup2(u2), mul2(Zy[k], Zy[k]));
+  }
+  // the interpolants where every point's |w|^2 < T_SERIES, one branch for
+  // all points of the thread (as dpie32)
+  float2 axp[NP], ayp[NP];
+  bool poly = SERIES;
+  if (!SERIES) {
+    float t = fmaxf(fmaxf(tx[0].x, tx[0].y), fmaxf(ty[0].x, ty[0].y));
+#pragma unroll
+    for (int k = 1; k < NP; ++k) t = fmaxf(t, fmaxf(fmaxf(tx[k].x, tx[k].y), fmaxf(ty[k].x, ty[k].y)));
+    poly = t < T_SERIES;
+  }
+  if (poly) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      axp[k] = mul2(Zx[k], horner2(tx[k], LENS_ATAN_W_COEF));
+      ayp[k] = mul2(Zy[k], horner2(ty[k], LENS_ATANH_W_COEF));
+    }
+  } else {
+    const float u = r4[6].x, iu = E.w;
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float zx = part2(Zx[k], h), zy = part2(Zy[k], h), tX = part2(tx[k], h), tY = part2(ty[k], h);
+        if (fmaxf(tX, tY) < T_SERIES) {
+          part2(axp[k], h) = zx * atan_over_w(tX);
+          part2(ayp[k], h) = zy * atanh_over_w(tY);
+        } else {
+          const float wx = u * zx, wy = u * zy;
+          part2(axp[k], h) = iu * atanf(wx);
+          part2(ayp[k], h) = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
+        }
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    p.ax[k] = fma2(dup2(cb), axp[k], fma2(dup2(-sb), ayp[k], p.ax[k]));
+    p.ay[k] = fma2(dup2(sb), axp[k], fma2(dup2(cb), ayp[k], p.ay[k]));
+    if (HESS) {
+      const float4 G = r4[5];
+      const float u2sc2 = D.z, u2st2 = D.w;
+      const float2 ymx = sub2(y2[k], x2[k]);
+      const float2 Dc = fma2(Ec[k], Ec[k], u2x2[k]), Dt = fma2(Et[k], Et[k], u2x2[k]);
+      const float2 fc = rcp2(mul2(psc[k], Dc)), ft = rcp2(mul2(pst[k], Dt));
+      const float2 fd = sub2(fc, ft);
+      // -(u2sc2 fc - u2st2 ft), rounded as its negation in dpie32
+      const float2 g1d = fma2(ymx, fd, fma2(dup2(-u2sc2), fc, mul2(dup2(u2st2), ft)));
+      const float2 g2d = mul2(fd, mul2(x[k], y[k]));
+      p.k[k] = fma2(dup2(E.z), sub2(ic[k], it[k]), p.k[k]);
+      p.g1[k] = fma2(dup2(G.x), g1d, fma2(dup2(G.y), g2d, p.g1[k]));
+      p.g2[k] = fma2(dup2(G.z), g1d, fma2(dup2(G.w), g2d, p.g2[k]));
+    }
+  }
+}
+
+// SIS / point mass at NP point pairs sharing dX: circ32, paired.
+template <bool HESS, int NP, bool POINT>
+__device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, float dX, const float2 (&dY)[NP],
+                                         Acc2<HESS, NP> &p) {
+  const float b = r4[7].y;
+  const float2 x = dup2(dX);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const float2 y = dY[k];
+    const float2 r2 = fma2(x, x, mul2(y, y));
+    float2 ir;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float v = part2(r2, h);
+      part2(ir, h) = v > 0.f ? (POINT ? rcp_a(v) : rsqrt_a(v)) : 0.f;
+    }
+    const float2 f = mul2(dup2(b), ir);
+    p.ax[k] = fma2(f, x, p.ax[k]);
+    p.ay[k] = fma2(f, y, p.ay[k]);
+    if (HESS) {
+      const float2 ymx = mul2(sub2(y, x), add2(y, x));
+      if (POINT) {
+        const float2 f2 = mul2(f, ir);
+        p.g1[k] = fma2(f2, ymx, p.g1[k]);
+        p.g2[k] = fma2(mul2(dup2(-2.f), f2), mul2(x, y), p.g2[k]);
+      } else {
+        const float2 f3 = mul2(mul2(f, ir), ir);
+        p.k[k] = fma2(dup2(0.5f), f, p.k[k]);
+        p.g1[k] = fma2(mul2(dup2(0.5f), f3), ymx, p.g1[k]);
+        p.g2[k] = fma2(mul2(f3, dup2(-1.f)), mul2(x, y), p.g2[k]);
+      }
+    }
+  }
+}
+
+// Any FP32 potential at NP point pairs (kind uniform across the CTA).
+template <bool HESS, int NP>
+__device__ __forceinline__ void eval32x2_any(const float4 *__restrict__ r4, float dX, const float2 (&dY)[NP],
+                                             Acc2<HESS, NP> &p) {
+  const int kind = __float_as_int(r4[7].x);
+  if (kind == K32_DPIE)
+    dpie32x2<HESS, NP, false>(r4, dX, dY, p);
+  else if (kind == K32_DPIE_SERIES)
+    dpie32x2<HESS, NP, true>(r4, dX, dY, p);
+  else if (kind == K32_SIS)
+    circ32x2<HESS, NP, false>(r4, dX, dY, p);
+  else
+    circ32x2<HESS, NP, true>(r4, dX, dY, p);
 }
 
 

@@ -1176,9 +1176,10 @@ int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g
     gc = find_grid_cache(c, g);
   }
   const int32_t batch = std::min<int32_t>(IMG_BATCH, P);
-  const int rc = ensure_scratch(ctx, chi2_image_scratch_bytes(c, batch));
+  CallScratch scratch(ctx, st);  // this call's candidate buffers, on its own stream
+  const int rc = scratch.alloc(chi2_image_scratch_bytes(c, batch));
   if (rc) return rc;
-  return run_chi2_image(ctx, c, gc, d_params, P, d_chi2, d_nfound, ctx->scratch, batch, st, d_images, img_max,
+  return run_chi2_image(ctx, c, gc, d_params, P, d_chi2, d_nfound, scratch.p, batch, st, d_images, img_max,
                         d_img_count);
 }
 

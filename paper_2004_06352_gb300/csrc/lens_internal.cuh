@@ -266,8 +266,19 @@ struct lens_ctx {
   std::vector<std::pair<int64_t, lens::Model *>> models;
   std::vector<std::pair<int64_t, lens::CSet *>> csets;
   int *d_err = nullptr;          // device-side error word (bounded waits)
-  void *scratch = nullptr;       // growable scratch for chi2 image search
-  size_t scratch_bytes = 0;
+  // Device memory comes from a memory pool of the context's own, in stream
+  // order: long-lived blocks (models, constraint sets, caches) are allocated
+  // on alloc_st and freed on release_st once the work the context enqueued
+  // before the release has finished (release_st waits on the marks below:
+  // the GPU waits, the host and the other streams do not); a call's working
+  // memory is allocated and freed on the call's own stream, so calls on
+  // different streams never share it.
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t alloc_st = nullptr, release_st = nullptr;
+  // one event per stream the context has launched work on, recorded after
+  // the latest such launch
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> marks;
+  uint64_t mark_gen = 0, release_gen = 0;  // marks recorded / marks release_st has waited for
   // maps streamed to host memory: two device row-band buffers, two compute
   // streams and a copy stream (created on first use)
   void *band = nullptr;
@@ -297,8 +308,37 @@ int fail(int code, const char *fmt, ...);
 Model *find_model(lens_ctx *ctx, lens_model_t id);
 CSet *find_cset(lens_ctx *ctx, lens_cset_t id);
 int dev_alloc(lens_ctx *ctx, void **p, size_t bytes);
+// Frees p once every launch the context has enqueued so far has finished
+// (stream-ordered; never blocks the host or other streams).
 void dev_free(lens_ctx *ctx, void *p, size_t bytes);
-int ensure_scratch(lens_ctx *ctx, size_t bytes);
+// Records that the context enqueued work on st (no-op while st captures a
+// graph: a graph's launches happen when the caller replays it).
+void mark_stream(lens_ctx *ctx, cudaStream_t st);
+// Makes st wait for every launch the context has enqueued so far.
+void wait_marks(lens_ctx *ctx, cudaStream_t st);
+// The context's upload stream (created on first use; NULL if that fails):
+// model records and the constraint sets' caches are built on it.
+cudaStream_t upload_stream(lens_ctx *ctx);
+// Working memory of one call, in stream order on the call's stream: freed
+// (on that stream, after the call's launches) when the object goes.
+struct CallScratch {
+  lens_ctx *ctx;
+  cudaStream_t st;
+  void *p = nullptr;
+  size_t bytes = 0;
+  CallScratch(lens_ctx *c, cudaStream_t s) : ctx(c), st(s) {}
+  int alloc(size_t n);
+  ~CallScratch();
+  CallScratch(const CallScratch &) = delete;
+  CallScratch &operator=(const CallScratch &) = delete;
+};
+// Marks the stream when the entry point returns (see mark_stream).
+struct StreamMark {
+  lens_ctx *ctx;
+  cudaStream_t st;
+  StreamMark(lens_ctx *c, cudaStream_t s) : ctx(c), st(s) {}
+  ~StreamMark() { mark_stream(ctx, st); }
+};
 int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out);
 void free_model(lens_ctx *ctx, Model *m);
 int check_grid(const lens_grid *g);
@@ -318,7 +358,8 @@ int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st);
 int launch_math_selftest(const double *x, int n, double *out, cudaStream_t st);
 int launch_mcmc_step(lens_ctx *ctx, const Model *m, const CSet *c, double *d_params, double *d_chi2, int32_t W,
                      const double *d_sigma, double temperature, unsigned long long seed, unsigned long long step,
-                     int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st);
+                     int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st,
+                     unsigned long long *d_step = nullptr);
 int build_static_cache(lens_ctx *ctx, const Model *m, CSet *c);
 int launch_chi2_source(lens_ctx *ctx, const Model *m, const CSet *c, const double *d_params, int32_t P,
                        int32_t variant, double *d_chi2, cudaStream_t st);

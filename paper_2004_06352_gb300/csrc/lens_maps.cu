@@ -68,7 +68,10 @@ static_assert(map_threads(true) >= 64 && map_threads(false) >= 64 && map_threads
               "the chunk staging uses 64 threads");
 constexpr int MAP_UNROLL = LENS_MAP_UNROLL;
 constexpr int CH = 64;   // potentials per staged chunk (8 KB of records)
-constexpr int SUB = 16;  // partial sums folded into the compensated total every SUB potentials
+#ifndef LENS_MAP_SUB
+#define LENS_MAP_SUB 16
+#endif
+constexpr int SUB = LENS_MAP_SUB;  // partial sums folded into the compensated total every SUB potentials
 
 struct MapArgs {
   const float *rec32;
@@ -91,6 +94,13 @@ struct MapArgs {
 
 // What a map computes: deflection, deflection + Hessian, or the potential.
 enum MapMode : int { MAP_GRAD = 0, MAP_HESS = 1, MAP_POT = 2 };
+
+// Point k of a thread's sums: plain per-point arrays (the potential map) or
+// point pairs (the paired deflection / Hessian maps).
+template <int N>
+__device__ __forceinline__ float pt(const float (&v)[N], int k) { return v[k]; }
+template <int N>
+__device__ __forceinline__ float pt(const float2 (&v)[N], int k) { return part2(v[k >> 1], k & 1); }
 
 template <int MODE, int KP>
 __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD)
@@ -127,10 +137,20 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
     s_ly[tid] = make_float2(h, (float)(ly - (double)h));
   }
 
-  Acc<ACC5, KP> tot, cmp, part;  // POT: the potential in .k
+  // deflection / Hessian: the thread's points as KP/2 pairs on the paired
+  // FP32 path; the potential map: per point (POT: the potential in .k)
+  constexpr int NP = KP / 2;
+  using AccT = std::conditional_t<POT, Acc<true, KP>, Acc2<HESS, NP>>;
+  AccT tot, cmp, part;
   tot.zero();
   cmp.zero();
   part.zero();
+  auto fold_all = [&]() {
+    if constexpr (POT)
+      fold(tot, cmp, part);
+    else
+      fold2(tot, cmp, part);
+  };
 
   // FP64 potentials (cluster scale).  Half of the tiles evaluate them before
   // the FP32 loop, half after, so the two CTAs sharing an SM rarely load the
@@ -267,15 +287,27 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
             const float4 *r4 = recs + h * (REC32 / 4);
             float dX, dY[KP];
             tile_offsets(buf, h, dX, dY);
-            if (KIND == K32_DPIE)
-              dpie32<HESS, KP, false, false, POT>(r4, dX, dY, part);
-            else if (KIND == K32_DPIE_SERIES)
-              dpie32<HESS, KP, true, false, POT>(r4, dX, dY, part);
-            else
-              circ32<HESS, KP, KIND == K32_POINT, POT>(r4, dX, dY, part);
+            if constexpr (POT) {
+              if (KIND == K32_DPIE)
+                dpie32<false, KP, false, false, true>(r4, dX, dY, part);
+              else if (KIND == K32_DPIE_SERIES)
+                dpie32<false, KP, true, false, true>(r4, dX, dY, part);
+              else
+                circ32<false, KP, KIND == K32_POINT, true>(r4, dX, dY, part);
+            } else {
+              float2 dY2[NP];
+#pragma unroll
+              for (int j = 0; j < NP; ++j) dY2[j] = make_float2(dY[2 * j], dY[2 * j + 1]);
+              if (KIND == K32_DPIE)
+                dpie32x2<HESS, NP, false>(r4, dX, dY2, part);
+              else if (KIND == K32_DPIE_SERIES)
+                dpie32x2<HESS, NP, true>(r4, dX, dY2, part);
+              else
+                circ32x2<HESS, NP, KIND == K32_POINT>(r4, dX, dY2, part);
+            }
           }
           if (seen == SUB) {
-            fold(tot, cmp, part);
+            fold_all();
             seen = 0;
           }
         }
@@ -301,16 +333,19 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
           const float4 *r4 = recs + h * (REC32 / 4);
           float dX, dY[KP];
           tile_offsets(buf, h, dX, dY);
-          eval32_any<HESS, KP>(r4, dX, dY, part);
+          float2 dY2[NP];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) dY2[j] = make_float2(dY[2 * j], dY[2 * j + 1]);
+          eval32x2_any<HESS, NP>(r4, dX, dY2, part);
         }
         if (seen == SUB) {
-          fold(tot, cmp, part);
+          fold_all();
           seen = 0;
         }
       }
     }
   }
-  fold(tot, cmp, part);
+  fold_all();
   if (!heavy_first) heavy_pass();
 
   // per-point epilogue: FP32 totals + FP64 sums, scaled, derived maps
@@ -321,7 +356,7 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
     if constexpr (POT) {
       if (i < a.nx && j < a.ny) {
         const long long o = (long long)j * a.nx + i;
-        const double phi = a.dls * ((double)tot.k[k] - (double)cmp.k[k] + s_hv[tid][k][0]);
+        const double phi = a.dls * ((double)pt(tot.k, k) - (double)pt(cmp.k, k) + s_hv[tid][k][0]);
         a.out64[o] = phi;
         if (a.tau) {
           const double X = a.xmin + i * a.dx - a.bx, Y = a.ymin + (a.row0 + j) * a.dy - a.by;
@@ -330,13 +365,13 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
       }
       continue;
     }
-    const double AX = (double)tot.ax[k] - (double)cmp.ax[k] + s_hv[tid][k][0];
-    const double AY = (double)tot.ay[k] - (double)cmp.ay[k] + s_hv[tid][k][NC > 1 ? 1 : 0];
+    const double AX = (double)pt(tot.ax, k) - (double)pt(cmp.ax, k) + s_hv[tid][k][0];
+    const double AY = (double)pt(tot.ay, k) - (double)pt(cmp.ay, k) + s_hv[tid][k][NC > 1 ? 1 : 0];
     double KA = 0, G1 = 0, G2 = 0;
     if (HESS) {
-      KA = (double)tot.k[k] - (double)cmp.k[k] + s_hv[tid][k][NC > 2 ? 2 : 0];
-      G1 = (double)tot.g1[k] - (double)cmp.g1[k] + s_hv[tid][k][NC > 3 ? 3 : 0];
-      G2 = (double)tot.g2[k] - (double)cmp.g2[k] + s_hv[tid][k][NC > 4 ? 4 : 0];
+      KA = (double)pt(tot.k, k) - (double)pt(cmp.k, k) + s_hv[tid][k][NC > 2 ? 2 : 0];
+      G1 = (double)pt(tot.g1, k) - (double)pt(cmp.g1, k) + s_hv[tid][k][NC > 3 ? 3 : 0];
+      G2 = (double)pt(tot.g2, k) - (double)pt(cmp.g2, k) + s_hv[tid][k][NC > 4 ? 4 : 0];
     }
     if (i < a.nx && j < a.ny) {
       const long long o = (long long)j * a.nx + i;

@@ -50,13 +50,17 @@ __device__ __forceinline__ double unit_open(unsigned long long x) {
 // two Box-Muller pairs (parameters 4j .. 4j+3 where < NP); the j = 0 thread
 // also draws block 4 for the acceptance uniform.  (One thread per chain left
 // most SMs idle: 4096 chains are 32 CTAs of 128.)
+// The step's counter word is `step`, or *d_step when d_step is not NULL
+// (a counter in device memory that the acceptance kernel advances).
 template <int NP>
 __global__ void k_mcmc_propose(const double *__restrict__ params, const double *__restrict__ sigma, int W,
-                               unsigned long long seed, unsigned long long step, double *__restrict__ prop,
+                               unsigned long long seed, unsigned long long step,
+                               const unsigned long long *__restrict__ d_step, double *__restrict__ prop,
                                double *__restrict__ ua) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int w = t >> 2, j = t & 3;
   if (w >= W) return;
+  if (d_step) step = *d_step;
   const U4 r = philox4x64_10(U4{{step, (unsigned long long)w, (unsigned long long)j, 0ull}}, seed, 0ull);
   const double two_pi = 6.283185307179586;
 #pragma unroll
@@ -72,11 +76,15 @@ __global__ void k_mcmc_propose(const double *__restrict__ params, const double *
 }
 
 // Metropolis acceptance; accepted[w] (when not NULL) records the decision.
+// With a device step counter, one thread advances it: the proposal kernel of
+// this step has finished reading it (stream order), the next step reads the
+// new value.
 __global__ void k_mcmc_accept(double *__restrict__ params, double *__restrict__ chi2,
                               const double *__restrict__ prop, const double *__restrict__ ua,
                               const double *__restrict__ chi2_prop, int W, int np, double temperature,
-                              int32_t *__restrict__ accepted) {
+                              int32_t *__restrict__ accepted, unsigned long long *__restrict__ d_step) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d_step && w == 0) *d_step += 1ull;
   if (w >= W) return;
   const double cp = chi2_prop[w], c0 = chi2[w];
   bool take = false;
@@ -92,19 +100,21 @@ __global__ void k_mcmc_accept(double *__restrict__ params, double *__restrict__ 
 
 int launch_mcmc_step(lens_ctx *ctx, const Model *m, const CSet *c, double *d_params, double *d_chi2, int32_t W,
                      const double *d_sigma, double temperature, unsigned long long seed, unsigned long long step,
-                     int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st) {
+                     int32_t variant, int32_t np, double *d_scratch, int32_t *d_accepted, cudaStream_t st,
+                     unsigned long long *d_step) {
   double *prop = d_scratch, *ua = d_scratch + (size_t)W * np, *chi2_prop = ua + W;
   const int blocks = (W + 127) / 128, pblocks = (4 * W + 127) / 128;
   if (np == 16)
-    k_mcmc_propose<16><<<pblocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+    k_mcmc_propose<16><<<pblocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, d_step, prop, ua);
   else
-    k_mcmc_propose<14><<<pblocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, prop, ua);
+    k_mcmc_propose<14><<<pblocks, 128, 0, st>>>(d_params, d_sigma, W, seed, step, d_step, prop, ua);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "proposal launch: %s", cudaGetErrorString(e));
   const int rc = np == 16 ? launch_chi2_source_scaled(ctx, m, c, prop, W, variant, chi2_prop, st)
                           : launch_chi2_source(ctx, m, c, prop, W, variant, chi2_prop, st);
   if (rc) return rc;
-  k_mcmc_accept<<<blocks, 128, 0, st>>>(d_params, d_chi2, prop, ua, chi2_prop, W, np, temperature, d_accepted);
+  k_mcmc_accept<<<blocks, 128, 0, st>>>(d_params, d_chi2, prop, ua, chi2_prop, W, np, temperature, d_accepted,
+                                        d_step);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "acceptance launch: %s", cudaGetErrorString(e));
   return LENS_OK;

@@ -82,6 +82,7 @@ extern "C" int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const le
   void *base = nullptr;
   if ((rc = scratch_address(ctx->device, &base))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  StreamMark mark(ctx, st);
   GridCache gc;
   gc.xmin = grid->xmin;
   gc.xmax = grid->xmax;

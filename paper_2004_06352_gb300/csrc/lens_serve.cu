@@ -165,6 +165,7 @@ static int launch_req(lens_server *s, Slot &sl, Req *q) {
   if (cudaMemcpyAsync(r.result, base, q->out_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return fail(LENS_ECUDA, "result download failed");
   if (cudaEventRecord(sl.ev, st) != cudaSuccess) return fail(LENS_ECUDA, "cudaEventRecord failed");
+  mark_stream(ctx, st);  // releases of models and constraint sets wait for it
   return LENS_OK;
 }
 

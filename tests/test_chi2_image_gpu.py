@@ -293,3 +293,59 @@ def test_find_images_truncates_to_capacity(lens):
         for row in imgs[p]:
             same_src = full[p][full[p][:, 2] == row[2]]
             assert len(same_src) and np.min(np.hypot(same_src[:, 0] - row[0], same_src[:, 1] - row[1])) < 1e-9, (p, row)
+
+
+def test_calls_on_two_streams_of_one_context(lens):
+    """Image-plane and no-cache source-plane chi2 of different parameter
+    sets enqueued on two streams of one context at once: each call's working
+    memory is its own (stream-ordered), so every result equals the one the
+    same call gives alone; a model released while a map that reads it is in
+    flight keeps its memory until that map is done, and an upload that reuses
+    the block afterwards does not disturb it."""
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    g = I.grid(256)
+    pa = torch.tensor(I.perturbed_params(m, var, 40, seed=61), device=DEV)
+    pb = torch.tensor(I.perturbed_params(m, var, 40, seed=62), device=DEV)
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        ref = {}
+        for name, p in (("a", pa), ("b", pb)):
+            oi = torch.empty(40, dtype=torch.float64, device=DEV)
+            on = torch.empty(40, dtype=torch.float64, device=DEV)
+            ctx.chi2_image(cs, g, p, 40, oi)
+            ctx.chi2_source_nocache(cs, p, 40, 0, on)
+            ctx.wait()
+            ref[name] = (oi.clone(), on.clone())
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        outs = {k: (torch.full((40,), -1.0, dtype=torch.float64, device=DEV),
+                    torch.full((40,), -1.0, dtype=torch.float64, device=DEV)) for k in ("a", "b")}
+        torch.cuda.synchronize()
+        for _ in range(3):
+            for name, p, st in (("a", pa, s1), ("b", pb, s2)):
+                ctx.chi2_image(cs, g, p, 40, outs[name][0], stream=st)
+                ctx.chi2_source_nocache(cs, p, 40, 0, outs[name][1], stream=st)
+        torch.cuda.synchronize()
+        # (the image search appends candidates with atomics, so the last
+        # bits of an image-plane chi2 may differ from run to run)
+        for k in ("a", "b"):
+            for got, want in zip(outs[k], ref[k]):
+                rel = (got - want).abs() / want.abs()
+                assert float(rel.max()) <= T.CHI2_REL, (k, float(rel.max()))
+        # release while in flight, then reuse of the released block
+        m2 = I.random_model(300, seed=63)
+        gm = I.grid(512, field=(-60, 60, -60, 60))
+        mid2 = ctx.model_upload(m2)
+        want = torch.empty((6, 512, 512), device=DEV)
+        ctx.hessian_map(mid2, gm, 1.0, lens.LENS_MIXED, want)
+        ctx.wait()
+        got = torch.empty_like(want)
+        ctx.hessian_map(mid2, gm, 1.0, lens.LENS_MIXED, got, stream=s1)
+        ctx.model_release(mid2)                   # the map above is still running
+        mid3 = ctx.model_upload(I.random_model(290, seed=64))   # may take the released block
+        other = torch.empty_like(want)
+        ctx.hessian_map(mid3, gm, 1.0, lens.LENS_MIXED, other, stream=s2)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)

@@ -177,3 +177,56 @@ def test_mcmc_steps_with_scaling_cache_match_oracle(lens):
             assert np.allclose(p.cpu().numpy(), po, rtol=1e-13, atol=1e-13), step
             assert np.all(np.abs(c.cpu().numpy() - co) <= T.CHI2_REL * np.abs(co)), step
         ctx.cset_scaling_cache(cs, 0.0, 0.0, 0)
+
+
+def test_mcmc_step_graph_replays_advance_the_device_counter(lens):
+    """lens_mcmc_step_dev captured once in a CUDA graph: each replay reads
+    the step counter from device memory and advances it, so replay k draws
+    step s0 + k -- compared with the oracle's sampler at those steps."""
+    from tests.golden import make_constraints
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    W = 32
+    params = I.perturbed_params(m, var, W, seed=88)
+    chi2 = oracle.chi2_source_batch(m, cons, var, params, 0)
+    sigma = np.tile([0.2, 0.2, 0.005, 0.01, 0.05, 5.0, 0.1], 2)
+    T_, seed, s0 = 2000.0, 4242, 11
+    with lens.Context(0) as ctx:
+        mid = ctx.model_upload(m)
+        cs = ctx.cset_create(mid, cons, var)
+        p = torch.tensor(params, device=DEV)
+        c = torch.tensor(chi2, device=DEV)
+        sg = torch.tensor(sigma, device=DEV)
+        scratch = torch.empty(16 * W, dtype=torch.float64, device=DEV)
+        acc = torch.empty(W, dtype=torch.int32, device=DEV)
+        ctr = torch.tensor([s0], dtype=torch.int64, device=DEV)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            ctx.mcmc_step_dev(cs, p, c, W, sg, T_, seed, ctr, scratch, acc, stream=side)
+        side.synchronize()
+        # capturing ran nothing: the state is still the initial one
+        assert int(ctr.item()) == s0 and torch.equal(p.cpu(), torch.tensor(params))
+        po, co = params.copy(), chi2.copy()
+        moved = 0
+        for k in range(2):
+            graph.replay()
+            torch.cuda.synchronize()
+            _, _, take, prop, cp = oracle.mcmc_step(m, cons, var, po, co, sigma, T_, seed, s0 + k)
+            got_take = acc.cpu().numpy().astype(bool)
+            u = oracle.mcmc_uniforms(seed, s0 + k, W)[:, 16]
+            margin = np.log(u) + (cp - co) / (2 * T_)
+            sure = ~np.isfinite(margin) | (np.abs(margin) > 1e-6)
+            assert np.array_equal(got_take[sure], take[sure]), k
+            po = np.where(got_take[:, None], prop, po)
+            co = np.where(got_take, cp, co)
+            assert np.allclose(p.cpu().numpy(), po, rtol=1e-13, atol=1e-13), k
+            assert np.all(np.abs(c.cpu().numpy() - co) <= T.CHI2_REL * np.abs(co)), k
+            assert int(ctr.item()) == s0 + k + 1
+            moved += int(got_take.sum())
+        assert moved > 0
+        with pytest.raises(lens.LensError) as e:
+            ctx.mcmc_step_dev(cs, p, c, W, sg, T_, seed, None, scratch)
+        assert e.value.code == lens.LENS_EINVAL
