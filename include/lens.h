@@ -136,6 +136,23 @@ int lens_destroy(lens_ctx *ctx);
  * maps (default 5 arcsec).  Applies to models uploaded afterwards. */
 int lens_set_fp64_threshold(lens_ctx *ctx, double threshold_b0);
 
+/* LENS_MIXED deflection and Hessian maps: where the deflection at a node is
+ * small next to the summed magnitudes of its FP32 terms -- near a zero of
+ * alpha, where the terms cancel -- their rounding error (measured at about
+ * 1.6e-7 of that sum) would exceed 1e-6 |alpha|.  Such nodes (|alpha| <
+ * r x the sum of |alpha_i| over the FP32 potentials, each term's |alpha_i|
+ * taken as |alpha_x'| + |alpha_y'| in its own frame) are listed by the map
+ * kernel and recomputed, every potential in double-float (~1e-13), by a
+ * second kernel on the same stream; every plane of those nodes is
+ * rewritten.  r = LENS_REPAIR_RATIO_DEFAULT = 0.16 by default: outside the
+ * repaired nodes the measured error then stays below 0.83 of 1e-6 |alpha|
+ * (the FP32 error never exceeded 1.32e-7 of the sum on the models measured);
+ * r = 0 turns the repair off.
+ * The list is working memory of the call (4 bytes per grid point, stream
+ * ordered).  LENS_EINVAL for r < 0 or not finite. */
+int lens_set_repair_ratio(lens_ctx *ctx, double r);
+#define LENS_REPAIR_RATIO_DEFAULT 0.16
+
 /* Device bytes currently held by the context (including released model
  * blocks kept for reuse by later uploads; those are freed first when an
  * allocation would exceed the budget). */

@@ -20,9 +20,10 @@ LENS_OK, LENS_EINVAL, LENS_ENOMEM, LENS_ENOTFOUND, LENS_ECAPACITY, LENS_ECUDA, L
 LENS_DPIE, LENS_SIS, LENS_POINT = 0, 1, 2
 LENS_FP64, LENS_MIXED = 0, 1
 LENS_CHI2_SRC_MAPPED, LENS_CHI2_SRC_MU, LENS_CHI2_SRC_PLAIN = 0, 1, 2
+LENS_REPAIR_RATIO_DEFAULT = 0.16  # lens.h
 
 # Every symbol the header declares (checked by the CPU test suite).
-EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_mem_used", "lens_model_bytes",
+EXPORTS = ("lens_create", "lens_destroy", "lens_set_fp64_threshold", "lens_set_repair_ratio", "lens_mem_used", "lens_model_bytes",
            "lens_model_upload",
            "lens_model_release", "lens_grad_map", "lens_hessian_map", "lens_potential_map", "lens_grad_map_host", "lens_hessian_map_host",
            "lens_cset_create", "lens_cset_release",
@@ -83,6 +84,7 @@ def load_library(path=LIB_PATH):
         "lens_create": (C.c_int, [C.POINTER(vp), C.c_int, C.c_size_t]),
         "lens_destroy": (C.c_int, [vp]),
         "lens_set_fp64_threshold": (C.c_int, [vp, C.c_double]),
+        "lens_set_repair_ratio": (C.c_int, [vp, C.c_double]),
         "lens_mem_used": (C.c_size_t, [vp]),
         "lens_model_bytes": (C.c_size_t, [vp, i64]),
         "lens_model_upload": (C.c_int, [vp, C.POINTER(lens_halo), C.c_int32, C.POINTER(i64)]),
@@ -197,6 +199,9 @@ class Context:
 
     def set_fp64_threshold(self, b0):
         _check(_lib.lens_set_fp64_threshold(self.h, float(b0)), "lens_set_fp64_threshold")
+
+    def set_repair_ratio(self, r):
+        _check(_lib.lens_set_repair_ratio(self.h, float(r)), "lens_set_repair_ratio")
 
     def mem_used(self):
         return int(_lib.lens_mem_used(self.h))

@@ -351,6 +351,7 @@ static void free_cset(lens_ctx *ctx, CSet *c) {
   dev_free(ctx, c->x, c->nimg * sizeof(double));
   dev_free(ctx, c->y, c->nimg * sizeof(double));
   dev_free(ctx, c->sigma, c->nimg * sizeof(double));
+  dev_free(ctx, c->isig2, c->nimg * sizeof(double));
   dev_free(ctx, c->ratio, c->nsrc * sizeof(double));
   dev_free(ctx, c->stat, (size_t)c->nimg * 5 * sizeof(double));
   dev_free(ctx, c->var_base, 2 * REC64 * sizeof(double));
@@ -459,6 +460,13 @@ int lens_set_fp64_threshold(lens_ctx *ctx, double t) {
   if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
   if (std::isnan(t) || t < 0.0) return fail(LENS_EINVAL, "threshold must be >= 0");
   ctx->fp64_threshold = t;
+  return LENS_OK;
+}
+
+int lens_set_repair_ratio(lens_ctx *ctx, double r) {
+  if (!ctx) return fail(LENS_EINVAL, "ctx is NULL");
+  if (!(std::isfinite(r) && r >= 0.0)) return fail(LENS_EINVAL, "repair ratio must be finite and >= 0");
+  ctx->repair_ratio = r;
   return LENS_OK;
 }
 
@@ -683,6 +691,7 @@ int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *
       (rc = dev_alloc(ctx, (void **)&s->x, nimg * sizeof(double))) ||
       (rc = dev_alloc(ctx, (void **)&s->y, nimg * sizeof(double))) ||
       (rc = dev_alloc(ctx, (void **)&s->sigma, nimg * sizeof(double))) ||
+      (rc = dev_alloc(ctx, (void **)&s->isig2, nimg * sizeof(double))) ||
       (rc = dev_alloc(ctx, (void **)&s->ratio, c->nsrc * sizeof(double))) ||
       (rc = dev_alloc(ctx, (void **)&s->stat, (size_t)nimg * 5 * sizeof(double))) ||
       (rc = dev_alloc(ctx, (void **)&s->var_base, 2 * REC64 * sizeof(double)))) {
@@ -694,6 +703,9 @@ int lens_cset_create(lens_ctx *ctx, lens_model_t model, const lens_constraints *
   if (e == cudaSuccess) e = cudaMemcpy(s->x, c->x, nimg * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->y, c->y, nimg * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->sigma, c->sigma, nimg * sizeof(double), cudaMemcpyHostToDevice);
+  std::vector<double> isig2(nimg);
+  for (int32_t j = 0; j < nimg; ++j) isig2[j] = 1.0 / (c->sigma[j] * c->sigma[j]);
+  if (e == cudaSuccess) e = cudaMemcpy(s->isig2, isig2.data(), nimg * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->ratio, c->dls_ds, c->nsrc * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->var_base, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(CACHE_THREADS) k_static_cache(const double *__
 }
 
 struct Chi2SrcArgs {
-  const double *stat, *x, *y, *sigma, *ratio, *params;
+  const double *stat, *x, *y, *isig2, *ratio, *params;
   long long stat_stride;  // doubles between the static sums of consecutive sets (0: one shared cache)
   int pstride;            // doubles per parameter set (14; 16 with the members' scaling factors)
   const int32_t *img_off, *src_of;
@@ -105,14 +105,14 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
       for (int j = threadIdx.x; j < a.nimg; j += THREADS) {
         const int i = a.src_of[j];
         const double dbx = s_bary[2 * i] - s_beta[2 * j], dby = s_bary[2 * i + 1] - s_beta[2 * j + 1];
-        const double is2 = rcp64(a.sigma[j] * a.sigma[j]);
+        const double is2 = a.isig2[j];
         if (a.variant == LENS_CHI2_SRC_PLAIN) {
           acc[0] += (dbx * dbx + dby * dby) * is2;
         } else {
           // A^-1 = I - r H (Sec. 2.1 Eq. 4)
           const double a11 = 1.0 - s_m[3 * j], a22 = 1.0 - s_m[3 * j + 1], a12 = -s_m[3 * j + 2];
           const double det = a11 * a22 - a12 * a12;
-          const double id = 1.0 / det;
+          const double id = det != 0.0 ? rcp64(det) : 1.0 / det;
           if (a.variant == LENS_CHI2_SRC_MU) {
             acc[0] += (dbx * dbx + dby * dby) * fabs(id) * is2;
           } else {
@@ -158,7 +158,7 @@ static int launch_src_cfg(lens_ctx *ctx, const CSet *c, const double *d_params, 
   a.stat_stride = stat_stride;
   a.x = c->x;
   a.y = c->y;
-  a.sigma = c->sigma;
+  a.isig2 = c->isig2;
   a.ratio = c->ratio;
   a.params = d_params;
   a.pstride = pstride;

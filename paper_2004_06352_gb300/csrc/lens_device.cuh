@@ -600,14 +600,18 @@ __device__ __forceinline__ float &part2(float2 &v, int h) { return h ? v.y : v.x
 __device__ __forceinline__ float part2(const float2 &v, int h) { return h ? v.y : v.x; }
 
 // Sums of NP point pairs: point 2 j + h lives in component h of entry j.
+// mag: half the summed magnitudes of the terms' deflections (each term's
+// |alpha| taken as |alpha_x'| + |alpha_y'| in its own frame), the scale of
+// the FP32 rounding error of the sum (plain FP32 sum: an estimate).
 template <bool HESS, int NP>
 struct Acc2 {
-  float2 ax[NP], ay[NP], k[NP], g1[NP], g2[NP];
+  float2 ax[NP], ay[NP], k[NP], g1[NP], g2[NP], mag[NP];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) ax[i] = ay[i] = k[i] = g1[i] = g2[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < NP; ++i) ax[i] = ay[i] = k[i] = g1[i] = g2[i] = mag[i] = make_float2(0.f, 0.f);
   }
 };
+__device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 
 __device__ __forceinline__ void kahan2(float2 &s, float2 &c, float2 v) {
   const float2 y = sub2(v, c);
@@ -627,14 +631,27 @@ __device__ __forceinline__ void fold2(Acc2<HESS, NP> &tot, Acc2<HESS, NP> &cmp, 
       kahan2(tot.g1[i], cmp.g1[i], part.g1[i]);
       kahan2(tot.g2[i], cmp.g2[i], part.g2[i]);
     }
+    tot.mag[i] = add2(tot.mag[i], part.mag[i]);
   }
   part.zero();
 }
 
-// One dPIE (FP32) at NP point pairs sharing dX (one grid column), with dY
-// per point: the arithmetic of dpie32 (same formulas, same order), paired.
-template <bool HESS, int NP, bool SERIES>
-__device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, float dX, const float2 (&dY)[NP],
+// dX of pair k: one value shared by both points and all pairs (a map
+// column), or one per point (float2 per pair)
+__device__ __forceinline__ float2 dx2_of(float dX, int) { return dup2(dX); }
+template <int NP>
+__device__ __forceinline__ float2 dx2_of(const float2 (&dX)[NP], int k) { return dX[k]; }
+// c dX of pair k, rounded as the scalar c * dX
+__device__ __forceinline__ float2 cdx2(float c, float dX, int) { return dup2(c * dX); }
+template <int NP>
+__device__ __forceinline__ float2 cdx2(float c, const float2 (&dX)[NP], int k) { return mul2(dup2(c), dX[k]); }
+
+// One dPIE (FP32) at NP point pairs, dX shared (one grid column) or per
+// point, dY per point: the arithmetic of dpie32 (same formulas, same order),
+// paired.  MAG: also the magnitude sum p.mag.  FAST: outside the
+// interpolants' range, dpie32's FAST forms (decision-grade, image search).
+template <bool HESS, int NP, bool SERIES, bool MAG = true, bool FAST = false, typename DX>
+__device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX &dX, const float2 (&dY)[NP],
                                          Acc2<HESS, NP> &p) {
   const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
   const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
@@ -642,11 +659,11 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, float dX
   const float dK = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
   const float q2dS = D.y;
   const float cb = E.x, sb = E.y;
-  const float2 cdX = dup2(c * dX), msdX = dup2(-(s * dX));
   float2 x[NP], y[NP], x2[NP], y2[NP], u2x2[NP], ic[NP], it[NP], psc[NP], pst[NP], Ec[NP], Et[NP];
   float2 Zx[NP], Zy[NP], tx[NP], ty[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
+    const float2 cdX = cdx2(c, dX, k), msdX = cdx2(-s, dX, k);  // -(s dX) exactly
     x[k] = fma2(dup2(s), dY[k], cdX);
     y[k] = fma2(dup2(c), dY[k], msdX);
     x2[k] = mul2(x[k], x[k]);
@@ -695,8 +712,13 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, float dX
           part2(ayp[k], h) = zy * atanh_over_w(tY);
         } else {
           const float wx = u * zx, wy = u * zy;
-          part2(axp[k], h) = iu * atanf(wx);
-          part2(ayp[k], h) = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
+          if (FAST) {
+            part2(axp[k], h) = iu * atan_fast(wx);
+            part2(ayp[k], h) = iu * (0.346573590f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
+          } else {
+            part2(axp[k], h) = iu * atanf(wx);
+            part2(ayp[k], h) = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
+          }
         }
       }
   }
@@ -704,6 +726,7 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, float dX
   for (int k = 0; k < NP; ++k) {
     p.ax[k] = fma2(dup2(cb), axp[k], fma2(dup2(-sb), ayp[k], p.ax[k]));
     p.ay[k] = fma2(dup2(sb), axp[k], fma2(dup2(cb), ayp[k], p.ay[k]));
+    if (MAG) p.mag[k] = fma2(dup2(E.z), add2(abs2(axp[k]), abs2(ayp[k])), p.mag[k]);  // E.z = b q / 2
     if (HESS) {
       const float4 G = r4[5];
       const float u2sc2 = D.z, u2st2 = D.w;
@@ -721,14 +744,14 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, float dX
   }
 }
 
-// SIS / point mass at NP point pairs sharing dX: circ32, paired.
-template <bool HESS, int NP, bool POINT>
-__device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, float dX, const float2 (&dY)[NP],
+// SIS / point mass at NP point pairs: circ32, paired.
+template <bool HESS, int NP, bool POINT, bool MAG = true, typename DX>
+__device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, const DX &dX, const float2 (&dY)[NP],
                                          Acc2<HESS, NP> &p) {
   const float b = r4[7].y;
-  const float2 x = dup2(dX);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
+    const float2 x = dx2_of(dX, k);
     const float2 y = dY[k];
     const float2 r2 = fma2(x, x, mul2(y, y));
     float2 ir;
@@ -740,6 +763,7 @@ __device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, float dX
     const float2 f = mul2(dup2(b), ir);
     p.ax[k] = fma2(f, x, p.ax[k]);
     p.ay[k] = fma2(f, y, p.ay[k]);
+    if (MAG) p.mag[k] = fma2(dup2(0.5f), add2(abs2(mul2(f, x)), abs2(mul2(f, y))), p.mag[k]);
     if (HESS) {
       const float2 ymx = mul2(sub2(y, x), add2(y, x));
       if (POINT) {
@@ -756,19 +780,19 @@ __device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, float dX
   }
 }
 
-// Any FP32 potential at NP point pairs (kind uniform across the CTA).
-template <bool HESS, int NP>
-__device__ __forceinline__ void eval32x2_any(const float4 *__restrict__ r4, float dX, const float2 (&dY)[NP],
+// Any FP32 potential at NP point pairs.
+template <bool HESS, int NP, bool MAG = true, bool FAST = false, typename DX>
+__device__ __forceinline__ void eval32x2_any(const float4 *__restrict__ r4, const DX &dX, const float2 (&dY)[NP],
                                              Acc2<HESS, NP> &p) {
   const int kind = __float_as_int(r4[7].x);
   if (kind == K32_DPIE)
-    dpie32x2<HESS, NP, false>(r4, dX, dY, p);
+    dpie32x2<HESS, NP, false, MAG, FAST>(r4, dX, dY, p);
   else if (kind == K32_DPIE_SERIES)
-    dpie32x2<HESS, NP, true>(r4, dX, dY, p);
+    dpie32x2<HESS, NP, true, MAG>(r4, dX, dY, p);
   else if (kind == K32_SIS)
-    circ32x2<HESS, NP, false>(r4, dX, dY, p);
+    circ32x2<HESS, NP, false, MAG>(r4, dX, dY, p);
   else
-    circ32x2<HESS, NP, true>(r4, dX, dY, p);
+    circ32x2<HESS, NP, true, MAG>(r4, dX, dY, p);
 }
 
 

@@ -246,6 +246,9 @@ __device__ __forceinline__ int f2ord(float f) {
 }
 __device__ __forceinline__ float ord2f(int i) { return __int_as_float(i ^ ((i >> 31) & 0x7fffffff)); }
 
+#ifndef LENS_SEARCH_PAIRED
+#define LENS_SEARCH_PAIRED 0  // 1: two nodes per paired evaluation of the varying potentials (measured 1 % slower)
+#endif
 #ifndef LENS_SEARCH_MINB
 #define LENS_SEARCH_MINB 4  // resident CTAs per SM the search is compiled for (64 registers: 4 % faster than 1, no spills; 5 spills)
 #endif
@@ -278,6 +281,29 @@ __global__ void __launch_bounds__(SEARCH_THREADS, LENS_SEARCH_MINB) k_img_search
   for (int i = tid; i < a.nsrc; i += SEARCH_THREADS) s_src[i] = src32[i];
   __syncthreads();
   const float fdx = g.fdx, fdy = g.fdy, fTx = s_T[0], fTy = s_T[1];
+#if LENS_SEARCH_PAIRED
+  // the tile's nodes two at a time (n and n + SEARCH_THREADS) on the paired
+  // FP32 path; past the end the second is a copy of the first, not stored
+  for (int n = tid; n < NX_T * NY_T; n += 2 * SEARCH_THREADS) {
+    const int n1 = n + SEARCH_THREADS < NX_T * NY_T ? n + SEARCH_THREADS : n;
+    const int ia = min(i0 + n % NX_T, g.nx - 1), ja = min(j0 + n / NX_T, g.ny - 1);
+    const int ib = min(i0 + n1 % NX_T, g.nx - 1), jb = min(j0 + n1 / NX_T, g.ny - 1);
+    const size_t oa = (size_t)ja * g.nx + ia, ob = (size_t)jb * g.nx + ib;
+    float2 tx = make_float2(g.ax[oa], g.ax[ob]), ty = make_float2(g.ay[oa], g.ay[ob]);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const float2 dX2[1] = {make_float2(fmaf((float)(ia - i0), fdx, s_off[v].x), fmaf((float)(ib - i0), fdx, s_off[v].x))};
+      const float2 dY2[1] = {make_float2(fmaf((float)(ja - j0), fdy, s_off[v].y), fmaf((float)(jb - j0), fdy, s_off[v].y))};
+      Acc2<false, 1> acc;
+      acc.zero();
+      eval32x2_any<false, 1, false, true>(reinterpret_cast<const float4 *>(s_rec[v]), dX2, dY2, acc);
+      tx = add2(tx, acc.ax[0]);
+      ty = add2(ty, acc.ay[0]);
+    }
+    s_al[n] = make_float2(tx.x, ty.x);
+    if (n1 != n) s_al[n1] = make_float2(tx.y, ty.y);
+  }
+#else
   for (int n = tid; n < NX_T * NY_T; n += SEARCH_THREADS) {
     const int li = n % NX_T, lj = n / NX_T;
     const int ii = min(i0 + li, g.nx - 1), jj = min(j0 + lj, g.ny - 1);
@@ -294,6 +320,7 @@ __global__ void __launch_bounds__(SEARCH_THREADS, LENS_SEARCH_MINB) k_img_search
     }
     s_al[n] = make_float2(tx, ty);
   }
+#endif
   __syncthreads();
   // this thread's cells: column ci, rows cj0, cj0 + CT_Y / CPT, ...
   const int ci = tid % CT_X, cj0 = tid / CT_X;
@@ -478,6 +505,9 @@ __host__ __device__ constexpr int sub_vertex(int sb, int k) {
 #ifndef LENS_NEWTON_EXTRA
 #define LENS_NEWTON_EXTRA 0
 #endif
+#ifndef LENS_NEWTON_PAIRED
+#define LENS_NEWTON_PAIRED 0
+#endif
 #ifndef LENS_RF_THREADS
 #define LENS_RF_THREADS 128
 #endif
@@ -487,6 +517,12 @@ __host__ __device__ constexpr int sub_vertex(int sb, int k) {
 constexpr int RF_THREADS = LENS_RF_THREADS, RF_CH = 64, RF_G = LENS_RF_G, RF_CAND = RF_THREADS / RF_G;
 constexpr int RF_STRIDE4 = REC32 / 4 + 1;  // float4 slots per staged record: the pad spreads a group's 8 records over all banks
 static_assert(32 % RF_G == 0, "groups never straddle a warp");
+
+// Point k of per-point sums or of pair sums.
+template <int N>
+__device__ __forceinline__ float pt_of(const float (&v)[N], int k) { return v[k]; }
+template <int N>
+__device__ __forceinline__ float pt_of(const float2 (&v)[N], int k) { return part2(v[k >> 1], k & 1); }
 
 template <int NP, bool HESS>
 __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, float4 *s_rec, float4 *s_cen,
@@ -500,10 +536,24 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     hy[k] = (float)py[k];
     ly[k] = (float)(py[k] - (double)hy[k]);
   }
-  Acc<HESS, NP> tot, cmp, part;  // the NP points side by side (one range branch per potential)
+  // the NP points side by side (one range branch per potential); with
+  // LENS_NEWTON_PAIRED, two or more points as pairs on the paired FP32 path
+  // (an odd count padded with a copy of the last point, whose sums are not
+  // used) -- measured slower: the padded fourth point and the registers of
+  // the pairs (spills at 4 CTAs per SM) cost more than the pairing saves
+  constexpr bool PAIRED = LENS_NEWTON_PAIRED && NP >= 2;
+  constexpr int NPP = (NP + 1) / 2;
+  using AccT = std::conditional_t<PAIRED, Acc2<HESS, NPP>, Acc<HESS, NP>>;
+  AccT tot, cmp, part;
   tot.zero();
   cmp.zero();
   part.zero();
+  auto fold_all = [&]() {
+    if constexpr (PAIRED)
+      fold2(tot, cmp, part);
+    else
+      fold(tot, cmp, part);
+  };
   int seen = 0;
   const float4 *g_rec = reinterpret_cast<const float4 *>(n.rec32);
   const float4 *g_cen = reinterpret_cast<const float4 *>(n.cen32);
@@ -538,18 +588,36 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
             dX[k] = (hx[k] - c.x) + (lx[k] - c.z);
             dY[k] = (hy[k] - c.y) + (ly[k] - c.w);
           }
-          if (KIND == K32_DPIE)
-            dpie32<HESS, NP, false>(r4, dX, dY, part);
-          else if (KIND == K32_DPIE_SERIES)
-            dpie32<HESS, NP, true>(r4, dX, dY, part);
-          else if (KIND == K32_SIS || KIND == K32_POINT)
-            circ32<HESS, NP, KIND == K32_POINT>(r4, dX, dY, part);
-          else
-            eval32_any<HESS, NP>(r4, dX, dY, part);
+          if constexpr (PAIRED) {
+            float2 dX2[NPP], dY2[NPP];
+#pragma unroll
+            for (int q = 0; q < NPP; ++q) {
+              const int k1 = 2 * q + 1 < NP ? 2 * q + 1 : NP - 1;
+              dX2[q] = make_float2(dX[2 * q], dX[k1]);
+              dY2[q] = make_float2(dY[2 * q], dY[k1]);
+            }
+            if (KIND == K32_DPIE)
+              dpie32x2<HESS, NPP, false, false>(r4, dX2, dY2, part);
+            else if (KIND == K32_DPIE_SERIES)
+              dpie32x2<HESS, NPP, true, false>(r4, dX2, dY2, part);
+            else if (KIND == K32_SIS || KIND == K32_POINT)
+              circ32x2<HESS, NPP, KIND == K32_POINT, false>(r4, dX2, dY2, part);
+            else
+              eval32x2_any<HESS, NPP, false>(r4, dX2, dY2, part);
+          } else {
+            if (KIND == K32_DPIE)
+              dpie32<HESS, NP, false>(r4, dX, dY, part);
+            else if (KIND == K32_DPIE_SERIES)
+              dpie32<HESS, NP, true>(r4, dX, dY, part);
+            else if (KIND == K32_SIS || KIND == K32_POINT)
+              circ32<HESS, NP, KIND == K32_POINT>(r4, dX, dY, part);
+            else
+              eval32_any<HESS, NP>(r4, dX, dY, part);
+          }
         }
         seen += (h - hs) / RF_G;
         if (seen == 16) {
-          fold(tot, cmp, part);
+          fold_all();
           seen = 0;
         }
       }
@@ -573,14 +641,15 @@ __device__ __forceinline__ void sweep(const NewtonArgs &n, const VarRecs &var, f
     }
   }
   constexpr int NC = HESS ? 5 : 2;
-  fold(tot, cmp, part);
+  fold_all();
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     // each thread's compensated sum tot - cmp as a float pair, combined over
     // the group in double-float (TwoSum gives both partners the same bits)
-    float hi[5] = {tot.ax[k], tot.ay[k], HESS ? tot.k[k] : 0.f, HESS ? tot.g1[k] : 0.f, HESS ? tot.g2[k] : 0.f};
-    float lo[5] = {-cmp.ax[k], -cmp.ay[k], HESS ? -cmp.k[k] : 0.f, HESS ? -cmp.g1[k] : 0.f,
-                   HESS ? -cmp.g2[k] : 0.f};
+    float hi[5] = {pt_of(tot.ax, k), pt_of(tot.ay, k), HESS ? pt_of(tot.k, k) : 0.f, HESS ? pt_of(tot.g1, k) : 0.f,
+                   HESS ? pt_of(tot.g2, k) : 0.f};
+    float lo[5] = {-pt_of(cmp.ax, k), -pt_of(cmp.ay, k), HESS ? -pt_of(cmp.k, k) : 0.f,
+                   HESS ? -pt_of(cmp.g1, k) : 0.f, HESS ? -pt_of(cmp.g2, k) : 0.f};
 #pragma unroll
     for (int o = 1; o < RF_G; o <<= 1)
 #pragma unroll
@@ -1143,7 +1212,7 @@ int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st
   int rc = dev_alloc(ctx, (void **)&n.alpha32, n.bytes);
   if (rc) return rc;
   if (c->stat_model->n > 0)
-    rc = launch_map_mixed(ctx, c->stat_model, g, 1.0, false, n.alpha32, st);
+    rc = launch_map_mixed(ctx, c->stat_model, g, 1.0, false, n.alpha32, st, 0, -1, false);
   else
     rc = cudaMemsetAsync(n.alpha32, 0, n.bytes, st) == cudaSuccess ? LENS_OK : fail(LENS_ECUDA, "memset failed");
   if (rc) {

@@ -235,6 +235,7 @@ struct CSet {
   int32_t *img_off = nullptr;   // [nsrc+1]
   int32_t *src_of = nullptr;    // [nimg]
   double *x = nullptr, *y = nullptr, *sigma = nullptr;  // [nimg]
+  double *isig2 = nullptr;      // [nimg] 1 / sigma^2
   double *ratio = nullptr;      // [nsrc]
   double *stat = nullptr;       // [nimg][5]: ax, ay, hxx, hyy, hxy of the static potentials (D_ls/D_s = 1)
   double *var_base = nullptr;   // [2][16] FP64 records of the varying potentials' base types (type in D_KIND)
@@ -262,6 +263,10 @@ struct lens_ctx {
   int device = 0;
   size_t budget = 0, used = 0;
   double fp64_threshold = 5.0;
+  // LENS_MIXED deflection / Hessian maps: a node is recomputed in
+  // double-float where |alpha| < repair_ratio x the summed magnitude of its
+  // FP32 terms (0: never)
+  double repair_ratio = LENS_REPAIR_RATIO_DEFAULT;
   int64_t next_id = 1;
   std::vector<std::pair<int64_t, lens::Model *>> models;
   std::vector<std::pair<int64_t, lens::CSet *>> csets;
@@ -346,8 +351,11 @@ int check_grid(const lens_grid *g);
 // Kernel launchers (lens_maps.cu / lens_chi2.cu).
 // Maps of grid rows [row0, row0 + rows) (rows < 0: to the last row) into
 // out[planes][rows][nx]; the positions are those of the full grid.
+// repair: recompute in double-float the nodes where FP32 cancellation
+// leaves too few significant digits (working memory on st; off for the
+// image search's static deflection, which must allocate nothing there).
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                     cudaStream_t st, int row0 = 0, int rows = -1);
+                     cudaStream_t st, int row0 = 0, int rows = -1, bool repair = true);
 int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
                     cudaStream_t st, int row0 = 0, int rows = -1);
 int map_tile_rows(bool hess);  // rows per CTA tile of the mixed map kernel

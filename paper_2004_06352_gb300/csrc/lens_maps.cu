@@ -23,6 +23,8 @@
 //     evaluated in FP64; the final sum, scaling by D_ls/D_s and the derived
 //     kappa/gamma/mu are formed in FP64 per point and stored as FP32.
 // LENS_FP64 kernel: one point per thread, every potential in FP64.
+#include <algorithm>
+#include <climits>
 #include <type_traits>
 
 #include "lens_device.cuh"
@@ -72,6 +74,10 @@ constexpr int CH = 64;   // potentials per staged chunk (8 KB of records)
 #define LENS_MAP_SUB 16
 #endif
 constexpr int SUB = LENS_MAP_SUB;  // partial sums folded into the compensated total every SUB potentials
+// Repair of the Hessian maps' det = 1/mu: the FP32 terms' relative error
+// (measured below 2e-7 of each term) and the det error above which a node is
+// recomputed in double-float (a third of the 3e-5 the maps are held to)
+constexpr double DET_TERM_ERR = 2e-7, DET_REPAIR_ABS = 1e-5;
 
 struct MapArgs {
   const float *rec32;
@@ -90,6 +96,11 @@ struct MapArgs {
   int tau;          // potential map: also the Fermat potential about (bx, by)
   double bx, by;
   double *out64;    // potential map: [1 or 2][ny][nx] doubles
+  // deflection / Hessian maps: nodes where |alpha| < repair * (summed
+  // magnitude of the FP32 terms) are appended to rep_list (count in
+  // *rep_count) for the double-float repair pass; repair = 0: none
+  double repair;
+  int *rep_count, *rep_list;
 };
 
 // What a map computes: deflection, deflection + Hessian, or the potential.
@@ -105,7 +116,7 @@ __device__ __forceinline__ float pt(const float2 (&v)[N], int k) { return part2(
 template <int MODE, int KP>
 __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD)
     k_map_mixed(const MapArgs a) {
-  constexpr bool HESS = MODE == MAP_HESS, POT = MODE == MAP_POT, ACC5 = HESS || POT;
+  constexpr bool HESS = MODE == MAP_HESS, POT = MODE == MAP_POT;
   constexpr int MAP_THREADS = map_threads(HESS), MAP_WARPS = MAP_THREADS / 32;
   __shared__ __align__(128) float s_rec[2][CH * REC32];
   // Offsets of the tile from each staged potential's centre: X - x0 at the
@@ -373,12 +384,111 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
       G1 = (double)pt(tot.g1, k) - (double)pt(cmp.g1, k) + s_hv[tid][k][NC > 3 ? 3 : 0];
       G2 = (double)pt(tot.g2, k) - (double)pt(cmp.g2, k) + s_hv[tid][k][NC > 4 ? 4 : 0];
     }
+    if constexpr (!POT) {
+      // FP32 cancellation: the rounding error of the FP32 terms is ~1e-7 of
+      // their summed magnitude; where that is not well below 1e-6 |alpha|
+      // the node is recomputed in double-float (k_map_repair)
+      const double S = a.repair * 2.0 * (double)pt(tot.mag, k);
+      const bool rep = i < a.nx && j < a.ny && AX * AX + AY * AY < S * S;
+      bool rep_h = false;  // det's error: the Hessian planes need the repair as well
+      if (HESS && a.repair > 0.0) {
+        // det = (1 - kappa)^2 - gamma^2 carries 2 |1 - kappa| dkappa + 2 |gamma| dgamma;
+        // the FP32 terms' kappa are positive, so their sum bounds their
+        // magnitude, and their gamma's by that sum plus |gamma| of their sum
+        const double kl = a.dls * ((double)pt(tot.k, k) - (double)pt(cmp.k, k));
+        const double g1l = a.dls * ((double)pt(tot.g1, k) - (double)pt(cmp.g1, k));
+        const double g2l = a.dls * ((double)pt(tot.g2, k) - (double)pt(cmp.g2, k));
+        const double kap = a.dls * KA, gm = a.dls * sqrt(G1 * G1 + G2 * G2), gl = sqrt(g1l * g1l + g2l * g2l);
+        rep_h = i < a.nx && j < a.ny &&
+                2.0 * DET_TERM_ERR * (fabs(1.0 - kap) * fabs(kl) + gm * (fabs(kl) + gl)) > DET_REPAIR_ABS;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, rep || rep_h);
+      if (mask) {
+        int first = 0;
+        if (lane == __ffs(mask) - 1) first = atomicAdd(a.rep_count, __popc(mask));
+        first = __shfl_sync(0xffffffffu, first, __ffs(mask) - 1);
+        // bit 31: the Hessian planes too (else the deflection alone)
+        if (rep || rep_h)
+          a.rep_list[first + __popc(mask & ((1u << lane) - 1u))] = (j * a.nx + i) | (rep_h ? (int)0x80000000u : 0);
+      }
+    }
     if (i < a.nx && j < a.ny) {
       const long long o = (long long)j * a.nx + i;
       a.out[o] = (float)(a.dls * AX);
       a.out[a.plane + o] = (float)(a.dls * AY);
       if (HESS) {
         const double kap = a.dls * KA, g1 = a.dls * G1, g2 = a.dls * G2;
+        const double det = (1.0 - kap) * (1.0 - kap) - g1 * g1 - g2 * g2;
+        a.out[2 * a.plane + o] = (float)kap;
+        a.out[3 * a.plane + o] = (float)g1;
+        a.out[4 * a.plane + o] = (float)g2;
+        a.out[5 * a.plane + o] = (float)(1.0 / det);
+      }
+    }
+  }
+}
+
+// Double-float repair of the nodes the mixed map kernel listed: a CTA of
+// REP_WARPS warps takes REP_WARPS nodes, one per warp; the potentials' double-
+// float records are staged in shared memory 32 at a time (field-major, read
+// by all the CTA's warps) and lane l evaluates potential h0 + l of each chunk
+// at its warp's node (FP64 where double-float fails); a warp sum in FP64 and
+// the node's deflection planes -- and, for an entry with bit 31 set, its
+// Hessian planes too -- rewritten as the map kernel writes them.  A node
+// listed for its deflection alone keeps the map kernel's kappa, gamma and mu
+// (their FP32 errors are far inside their tolerances there).
+struct RepairArgs {
+  const float2 *recdf;
+  const double *all64;
+  int n;
+  double xmin, ymin, dx, dy;
+  int nx, row0;
+  double dls;
+  float *out;
+  long long plane;
+  const int *count, *list;
+};
+
+constexpr int REP_WARPS = 8, REP_THREADS = 32 * REP_WARPS;
+
+template <bool HESS>
+__global__ void __launch_bounds__(REP_THREADS) k_map_repair(const RepairArgs a) {
+  __shared__ float2 s_rdf[RECDF][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int total = *a.count;
+  for (int e0 = blockIdx.x * REP_WARPS; e0 < total; e0 += gridDim.x * REP_WARPS) {  // uniform over the CTA
+    const int e = e0 + warp;
+    const bool have = e < total;
+    const int entry = have ? a.list[e] : 0;
+    const int o = entry & 0x7fffffff;
+    const bool full = HESS && entry < 0;  // warp-uniform
+    const int i = o % a.nx, j = o / a.nx;
+    const double X = a.xmin + i * a.dx, Y = a.ymin + (a.row0 + j) * a.dy;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int h0 = 0; h0 < a.n; h0 += 32) {
+      __syncthreads();  // the previous chunk has been used
+      for (int t = threadIdx.x; t < RECDF * 32; t += REP_THREADS) {
+        const int f = t >> 5, h = h0 + (t & 31);
+        s_rdf[f][t & 31] = h < a.n ? a.recdf[(size_t)f * a.n + h] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      const int h = h0 + lane;
+      if (have && h < a.n) {
+        if (full)
+          add_potential_df<true>(&s_rdf[0][lane], 32, a.all64 + (size_t)h * REC64, X, Y, acc);
+        else
+          add_potential_df<false>(&s_rdf[0][lane], 32, a.all64 + (size_t)h * REC64, X, Y, acc);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < (HESS ? 5 : 2); ++c)
+#pragma unroll
+      for (int off = 16; off; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+    if (have && lane == 0) {
+      a.out[o] = (float)(a.dls * acc[0]);
+      a.out[a.plane + o] = (float)(a.dls * acc[1]);
+      if (full) {
+        const double kap = a.dls * acc[2], g1 = a.dls * acc[3], g2 = a.dls * acc[4];
         const double det = (1.0 - kap) * (1.0 - kap) - g1 * g1 - g2 * g2;
         a.out[2 * a.plane + o] = (float)kap;
         a.out[3 * a.plane + o] = (float)g1;
@@ -473,8 +583,17 @@ int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st) {
 int map_tile_rows(bool hess) { return map_threads(hess) / 32 * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
 
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                     cudaStream_t st, int row0, int rows) {
+                     cudaStream_t st, int row0, int rows, bool repair) {
   if (rows < 0) rows = g->ny - row0;
+  const long long nodes = (long long)g->nx * rows;
+  if (nodes > INT32_MAX) return fail(LENS_EINVAL, "map launch of more than 2^31 points");
+  repair = repair && ctx->repair_ratio > 0.0 && m->n_light > 0;
+  CallScratch rs(ctx, st);  // repair list: a count and up to one entry per node
+  if (repair) {
+    int rc = rs.alloc(sizeof(int) * (size_t)(nodes + 1));
+    if (rc) return rc;
+    if (cudaMemsetAsync(rs.p, 0, sizeof(int), st) != cudaSuccess) return fail(LENS_ECUDA, "cudaMemsetAsync failed");
+  }
   MapArgs a;
   a.rec32 = m->rec32;
   a.pos64 = m->pos64;
@@ -496,6 +615,9 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.tau = 0;
   a.bx = a.by = 0.0;
   a.out64 = nullptr;
+  a.repair = repair ? ctx->repair_ratio : 0.0;
+  a.rep_count = (int *)rs.p;
+  a.rep_list = repair ? (int *)rs.p + 1 : nullptr;
   constexpr int KPG = LENS_KP_GRAD, KPH = LENS_KP_HESS;
   if (hess) {
     const int th = map_tile_rows(true);
@@ -508,6 +630,32 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LENS_ECUDA, "map kernel launch: %s", cudaGetErrorString(e));
+  if (repair) {
+    RepairArgs r;
+    r.recdf = m->recdf;
+    r.all64 = m->all64;
+    r.n = m->n;
+    r.xmin = a.xmin;
+    r.ymin = a.ymin;
+    r.dx = a.dx;
+    r.dy = a.dy;
+    r.nx = a.nx;
+    r.row0 = row0;
+    r.dls = dls;
+    r.out = (float *)out;
+    r.plane = a.plane;
+    r.count = a.rep_count;
+    r.list = a.rep_list;
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int blocks = std::max(1, 4 * nsm);  // CTAs loop over the list: any count covers it
+    if (hess)
+      k_map_repair<true><<<blocks, REP_THREADS, 0, st>>>(r);
+    else
+      k_map_repair<false><<<blocks, REP_THREADS, 0, st>>>(r);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LENS_ECUDA, "map repair launch: %s", cudaGetErrorString(e));
+  }
   return LENS_OK;
 }
 
@@ -563,6 +711,8 @@ int launch_pot_map(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls
     a.tau = beta != nullptr;
     a.bx = beta ? beta[0] : 0.0;
     a.by = beta ? beta[1] : 0.0;
+    a.repair = 0.0;
+    a.rep_count = a.rep_list = nullptr;
     constexpr int KPG = LENS_KP_GRAD;
     const int th = map_tile_rows(false);
     dim3 grid((g->nx + 31) / 32, (rows + th - 1) / th);

@@ -93,7 +93,7 @@ extern "C" int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const le
   gc.alpha32 = (float *)base;
   gc.bytes = grid_bytes;
   if (c->stat_model->n > 0) {
-    if ((rc = launch_map_mixed(ctx, c->stat_model, grid, 1.0, false, gc.alpha32, st))) return rc;
+    if ((rc = launch_map_mixed(ctx, c->stat_model, grid, 1.0, false, gc.alpha32, st, 0, -1, false))) return rc;
   } else if (cudaMemsetAsync(gc.alpha32, 0, 2 * sizeof(float) * (size_t)grid->nx * grid->ny, st) != cudaSuccess) {
     return fail(LENS_ECUDA, "clearing the static deflection failed");
   }

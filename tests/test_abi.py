@@ -34,6 +34,13 @@ def test_binding_covers_the_header(libpath):
     assert sorted(api.EXPORTS) == declared_functions()
 
 
+def test_binding_constants_match_the_header():
+    from paper_2004_06352_gb300 import api
+    src = open(os.path.join(ROOT, "include", "lens.h")).read()
+    m = re.search(r"#define LENS_REPAIR_RATIO_DEFAULT ([0-9.]+)", src)
+    assert m and float(m.group(1)) == api.LENS_REPAIR_RATIO_DEFAULT
+
+
 def test_error_strings_without_gpu(libpath):
     from paper_2004_06352_gb300 import api
     for code in (0, -1, -2, -3, -4, -5, -6):

@@ -11,7 +11,9 @@ LENS_MIXED maps (FP32 bulk):
   kappa, gamma1, gamma2: |d| <= 1e-5 * max(|ref|, 1)  (they enter as 1 - kappa)
   mu:     |d det| <= 3e-5 absolute, det = 1/mu = (1-k)^2 - g^2 (equivalently
           mu relative 3e-5/|det|, the form that means something where
-          |det| >= 1e-2).
+          |det| >= 1e-2), plus the rounding of mu to the FP32 output plane
+          (|d det| <= 2^-24 |det| from that alone, which passes 3e-5 where
+          |det| > 500: next to the cores of concentrated FP32 potentials).
 LENS_FP64 maps: relative 1e-11 (floor 1e-3 x peak) on every plane.
 chi2: relative 1e-8 (FP64 on both sides), absolute floor 1e-12 for chi2 ~ 0.
 Potential maps (phi is defined up to a constant; its additive part
@@ -55,10 +57,13 @@ def hess_violations(k, g1, g2, rk, rg1, rg2, atol=HESS_ABS):
     return bad
 
 
-def mu_violations(mu, rmu, det_atol=DET_ABS):
+MU_STORE_REL = 2.0 ** -24   # rounding of mu (and so of det) to the FP32 plane
+
+
+def mu_violations(mu, rmu, det_atol=DET_ABS, stored_fp32=True):
     det = 1.0 / np.asarray(mu, dtype=np.float64)
     rdet = 1.0 / np.asarray(rmu, dtype=np.float64)
-    return np.abs(det - rdet) > det_atol
+    return np.abs(det - rdet) > det_atol + (MU_STORE_REL * np.abs(rdet) if stored_fp32 else 0.0)
 
 
 def report(name, bad, err=None):
