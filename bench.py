@@ -713,12 +713,15 @@ def serving_leg(ctx, api, torch):
     # same small-map requests through the mixed and the plain FP64 forms
     small = S.mixed_requests(24, seed=14, n_models=8, sides=(512, 1024, 2048))
     res = {}
-    for name, prec in (("mixed", api.LENS_MIXED), ("fp64", api.LENS_FP64)):
+    for name, prec, rr in (("mixed", api.LENS_MIXED, api.LENS_REPAIR_RATIO_DEFAULT),
+                           ("mixed_no_repair", api.LENS_MIXED, 0.0), ("fp64", api.LENS_FP64, 0.0)):
+        ctx.set_repair_ratio(rr)
         s2 = S.Session(ctx, models, precision=prec)
         srv = api.Server(ctx, slots=4, pool_bytes=4 << 30)
         lat, wall, _, _ = S.run_stream(srv, s2, small, max_outstanding=8, keep_results=False)
         res[name] = dict(S.percentiles(lat), req_per_s=len(small) / wall)
         srv.close()
+    ctx.set_repair_ratio(api.LENS_REPAIR_RATIO_DEFAULT)
     out["mixed_vs_fp64_same_requests"] = res
     out["workload"] = ("Poisson mix: 60% Hessian maps side 512-8192 (uniform over powers of 2), 8 resident models "
                        "of 10-2000 potentials; 40% source-plane chi2 with 16-4096 sets; 4 slots, 12 GiB pool")
