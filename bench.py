@@ -27,11 +27,13 @@ UNIT = "pair/s"
 MAP_N, N_HALO = 2048, 1000
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
 
-# FP32-pipe thread instructions (FFMA + FADD + FMUL) and MUFU (XU pipe)
-# instructions per point-halo pair of the LENS_MIXED Hessian map kernel,
-# measured with ncu on the 2048^2 x 1000 workload (the counter group of the
-# map kernel's summary under profiles/); the compensated-fold overhead
-# (~1 op per pair) is included.
+# FP32-pipe lane operations (FFMA + FADD + FMUL, each paired FFMA2 / FADD2 /
+# FMUL2 counting two) and MUFU (XU pipe) instructions per point-halo pair of
+# the lens arithmetic of the LENS_MIXED Hessian map kernel, from ncu on the
+# 2048^2 x 1000 workload (the counter group of the map kernel's summary
+# under profiles/: 67.0 lane operations per pair, of which 2.0 are the
+# magnitude sum that decides the double-float repair); the compensated-fold
+# overhead (~1 op per pair) is included.
 FP32_OPS_PER_PAIR = 64.9
 MUFU_OPS_PER_PAIR = 6.03
 # the same count for the potential-map kernel (ncu, same workload)
@@ -39,7 +41,7 @@ POT_FP32_OPS_PER_PAIR = 48.9
 # DRAM bytes (read + write) of one launch of that kernel on that workload,
 # from the same ncu capture; the 100.7 MB of output are partly still in L2
 # when the kernel ends
-MAP_TRAFFIC_BYTES = 482816 + 39919616
+MAP_TRAFFIC_BYTES = 728064 + 40069376
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 # FP64 FMA lanes per SM and clock (measured on this GPU: 1/64 of the FP32 rate)
 FP64_LANES = 2
@@ -718,7 +720,8 @@ def serving_leg(ctx, api, torch):
         ctx.set_repair_ratio(rr)
         s2 = S.Session(ctx, models, precision=prec)
         srv = api.Server(ctx, slots=4, pool_bytes=4 << 30)
-        lat, wall, _, _ = S.run_stream(srv, s2, small, max_outstanding=8, keep_results=False)
+        S.run_stream(srv, s2, small[:4], pool=pool, max_outstanding=8, keep_results=False)  # warm
+        lat, wall, _, _ = S.run_stream(srv, s2, small, pool=pool, max_outstanding=8, keep_results=False)
         res[name] = dict(S.percentiles(lat), req_per_s=len(small) / wall)
         srv.close()
     ctx.set_repair_ratio(api.LENS_REPAIR_RATIO_DEFAULT)

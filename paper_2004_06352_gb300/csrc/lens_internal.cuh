@@ -354,8 +354,11 @@ int check_grid(const lens_grid *g);
 // repair: recompute in double-float the nodes where FP32 cancellation
 // leaves too few significant digits (working memory on st; off for the
 // image search's static deflection, which must allocate nothing there).
+// repair_mem: memory for the repair list (map_repair_bytes), else working
+// memory of the call.
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                     cudaStream_t st, int row0 = 0, int rows = -1, bool repair = true);
+                     cudaStream_t st, int row0 = 0, int rows = -1, bool repair = true, void *repair_mem = nullptr);
+size_t map_repair_bytes(const lens_grid *g, int rows = -1);
 int launch_map_fp64(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
                     cudaStream_t st, int row0 = 0, int rows = -1);
 int map_tile_rows(bool hess);  // rows per CTA tile of the mixed map kernel

@@ -100,6 +100,7 @@ struct MapArgs {
   // magnitude of the FP32 terms) are appended to rep_list (count in
   // *rep_count) for the double-float repair pass; repair = 0: none
   double repair;
+  float repair_f;  // 2 * repair (mag holds half the magnitude sum)
   int *rep_count, *rep_list;
 };
 
@@ -388,19 +389,21 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
       // FP32 cancellation: the rounding error of the FP32 terms is ~1e-7 of
       // their summed magnitude; where that is not well below 1e-6 |alpha|
       // the node is recomputed in double-float (k_map_repair)
-      const double S = a.repair * 2.0 * (double)pt(tot.mag, k);
-      const bool rep = i < a.nx && j < a.ny && AX * AX + AY * AY < S * S;
+      // (the decisions in FP32: they only need a few significant digits)
+      const float S = a.repair_f * pt(tot.mag, k), fax = (float)AX, fay = (float)AY;
+      const bool rep = i < a.nx && j < a.ny && fmaf(fax, fax, fay * fay) < S * S;
       bool rep_h = false;  // det's error: the Hessian planes need the repair as well
       if (HESS && a.repair > 0.0) {
         // det = (1 - kappa)^2 - gamma^2 carries 2 |1 - kappa| dkappa + 2 |gamma| dgamma;
         // the FP32 terms' kappa are positive, so their sum bounds their
         // magnitude, and their gamma's by that sum plus |gamma| of their sum
-        const double kl = a.dls * ((double)pt(tot.k, k) - (double)pt(cmp.k, k));
-        const double g1l = a.dls * ((double)pt(tot.g1, k) - (double)pt(cmp.g1, k));
-        const double g2l = a.dls * ((double)pt(tot.g2, k) - (double)pt(cmp.g2, k));
-        const double kap = a.dls * KA, gm = a.dls * sqrt(G1 * G1 + G2 * G2), gl = sqrt(g1l * g1l + g2l * g2l);
+        const float d = (float)a.dls;
+        const float kl = d * pt(tot.k, k), g1l = d * pt(tot.g1, k), g2l = d * pt(tot.g2, k);
+        const float kap = d * (float)KA, g1 = d * (float)G1, g2 = d * (float)G2;
+        const float gm = sqrtf(fmaf(g1, g1, g2 * g2)), gl = sqrtf(fmaf(g1l, g1l, g2l * g2l));
         rep_h = i < a.nx && j < a.ny &&
-                2.0 * DET_TERM_ERR * (fabs(1.0 - kap) * fabs(kl) + gm * (fabs(kl) + gl)) > DET_REPAIR_ABS;
+                (float)(2.0 * DET_TERM_ERR) * (fabsf(1.f - kap) * fabsf(kl) + gm * (fabsf(kl) + gl)) >
+                    (float)DET_REPAIR_ABS;
       }
       const unsigned mask = __ballot_sync(0xffffffffu, rep || rep_h);
       if (mask) {
@@ -449,11 +452,11 @@ struct RepairArgs {
   const int *count, *list;
 };
 
-constexpr int REP_WARPS = 8, REP_THREADS = 32 * REP_WARPS;
+constexpr int REP_WARPS = 8, REP_THREADS = 32 * REP_WARPS, REP_CH = 32;  // potentials per staged chunk (one per lane)
 
 template <bool HESS>
 __global__ void __launch_bounds__(REP_THREADS) k_map_repair(const RepairArgs a) {
-  __shared__ float2 s_rdf[RECDF][32];
+  __shared__ float2 s_rdf[RECDF][REP_CH];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int total = *a.count;
   for (int e0 = blockIdx.x * REP_WARPS; e0 < total; e0 += gridDim.x * REP_WARPS) {  // uniform over the CTA
@@ -465,19 +468,19 @@ __global__ void __launch_bounds__(REP_THREADS) k_map_repair(const RepairArgs a) 
     const int i = o % a.nx, j = o / a.nx;
     const double X = a.xmin + i * a.dx, Y = a.ymin + (a.row0 + j) * a.dy;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int h0 = 0; h0 < a.n; h0 += 32) {
+    for (int h0 = 0; h0 < a.n; h0 += REP_CH) {
       __syncthreads();  // the previous chunk has been used
-      for (int t = threadIdx.x; t < RECDF * 32; t += REP_THREADS) {
-        const int f = t >> 5, h = h0 + (t & 31);
-        s_rdf[f][t & 31] = h < a.n ? a.recdf[(size_t)f * a.n + h] : make_float2(0.f, 0.f);
+      for (int t = threadIdx.x; t < RECDF * REP_CH; t += REP_THREADS) {
+        const int f = t / REP_CH, h = h0 + t % REP_CH;
+        s_rdf[f][t % REP_CH] = h < a.n ? a.recdf[(size_t)f * a.n + h] : make_float2(0.f, 0.f);
       }
       __syncthreads();
       const int h = h0 + lane;
       if (have && h < a.n) {
         if (full)
-          add_potential_df<true>(&s_rdf[0][lane], 32, a.all64 + (size_t)h * REC64, X, Y, acc);
+          add_potential_df<true>(&s_rdf[0][lane], REP_CH, a.all64 + (size_t)h * REC64, X, Y, acc);
         else
-          add_potential_df<false>(&s_rdf[0][lane], 32, a.all64 + (size_t)h * REC64, X, Y, acc);
+          add_potential_df<false>(&s_rdf[0][lane], REP_CH, a.all64 + (size_t)h * REC64, X, Y, acc);
       }
     }
 #pragma unroll
@@ -582,17 +585,27 @@ int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st) {
 
 int map_tile_rows(bool hess) { return map_threads(hess) / 32 * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
 
+size_t map_repair_bytes(const lens_grid *g, int rows) {
+  return sizeof(int) * ((size_t)g->nx * (size_t)(rows < 0 ? g->ny : rows) + 1);
+}
+
 int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls, bool hess, void *out,
-                     cudaStream_t st, int row0, int rows, bool repair) {
+                     cudaStream_t st, int row0, int rows, bool repair, void *repair_mem) {
   if (rows < 0) rows = g->ny - row0;
   const long long nodes = (long long)g->nx * rows;
   if (nodes > INT32_MAX) return fail(LENS_EINVAL, "map launch of more than 2^31 points");
   repair = repair && ctx->repair_ratio > 0.0 && m->n_light > 0;
   CallScratch rs(ctx, st);  // repair list: a count and up to one entry per node
   if (repair) {
-    int rc = rs.alloc(sizeof(int) * (size_t)(nodes + 1));
-    if (rc) return rc;
-    if (cudaMemsetAsync(rs.p, 0, sizeof(int), st) != cudaSuccess) return fail(LENS_ECUDA, "cudaMemsetAsync failed");
+    if (repair_mem) {
+      rs.p = nullptr;  // the caller's memory (the request loop's arena)
+    } else {
+      int rc = rs.alloc(map_repair_bytes(g, rows));
+      if (rc) return rc;
+      repair_mem = rs.p;
+    }
+    if (cudaMemsetAsync(repair_mem, 0, sizeof(int), st) != cudaSuccess)
+      return fail(LENS_ECUDA, "cudaMemsetAsync failed");
   }
   MapArgs a;
   a.rec32 = m->rec32;
@@ -616,8 +629,9 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.bx = a.by = 0.0;
   a.out64 = nullptr;
   a.repair = repair ? ctx->repair_ratio : 0.0;
-  a.rep_count = (int *)rs.p;
-  a.rep_list = repair ? (int *)rs.p + 1 : nullptr;
+  a.repair_f = (float)(2.0 * a.repair);
+  a.rep_count = repair ? (int *)repair_mem : nullptr;
+  a.rep_list = repair ? (int *)repair_mem + 1 : nullptr;
   constexpr int KPG = LENS_KP_GRAD, KPH = LENS_KP_HESS;
   if (hess) {
     const int th = map_tile_rows(true);
@@ -712,6 +726,7 @@ int launch_pot_map(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls
     a.bx = beta ? beta[0] : 0.0;
     a.by = beta ? beta[1] : 0.0;
     a.repair = 0.0;
+    a.repair_f = 0.f;
     a.rep_count = a.rep_list = nullptr;
     constexpr int KPG = LENS_KP_GRAD;
     const int th = map_tile_rows(false);

@@ -143,8 +143,9 @@ static int launch_req(lens_server *s, Slot &sl, Req *q) {
     if (!m) return fail(LENS_ENOTFOUND, "model released while its request was queued");
     if (r.precision == LENS_FP64)
       rc = launch_map_fp64(ctx, m, &r.grid, r.dls_ds, r.hessian != 0, base, st);
-    else
-      rc = launch_map_mixed(ctx, m, &r.grid, r.dls_ds, r.hessian != 0, base, st);
+    else  // the repair list in the request's own arena memory, after its output
+      rc = launch_map_mixed(ctx, m, &r.grid, r.dls_ds, r.hessian != 0, base, st, 0, -1, true,
+                            base + up(q->out_bytes));
   } else {
     CSet *c = find_cset(ctx, r.handle);
     Model *m = c ? find_model(ctx, c->model) : nullptr;
@@ -229,6 +230,7 @@ int lens_server_submit(lens_server *s, const lens_request *r, int64_t *ticket) {
     } else if (!(std::isfinite(r->dls_ds) && r->dls_ds > 0)) rc = fail(LENS_EINVAL, "dls_ds must be > 0");
     else if (r->precision != LENS_FP64 && r->precision != LENS_MIXED) rc = fail(LENS_EINVAL, "bad precision");
     q->out_bytes = map_out_bytes(*r);
+    if (r->precision == LENS_MIXED) q->scratch_bytes = map_repair_bytes(&r->grid);
   } else if (r->kind == LENS_REQ_CHI2_SOURCE || r->kind == LENS_REQ_CHI2_IMAGE) {
     CSet *c = find_cset(ctx, r->handle);
     if (!c) rc = fail(LENS_ENOTFOUND, "constraint set %lld not found", (long long)r->handle);

@@ -21,11 +21,15 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
 
-def test_noalloc_matches_allocating_entry_point_twice(lens):
+@pytest.mark.parametrize("n", [256, 1400])
+def test_noalloc_matches_allocating_entry_point_twice(lens, n):
+    """256^2: the 12 sets in one batch.  1400^2: the grid's static
+    deflection takes 15.7 MB of the 16 MiB array, so the batch halves from 12
+    to 3 sets and the call runs four batches through the space left."""
     m = I.cfg2_model()
     cons = make_constraints.load()
     var = (0, 1)
-    g = I.grid(256)
+    g = I.grid(n)
     P = 12
     params = torch.tensor(I.perturbed_params(m, var, P, seed=61), dtype=torch.float64, device=DEV)
     nsrc = len(cons["img_off"]) - 1
