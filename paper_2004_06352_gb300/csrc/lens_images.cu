@@ -924,9 +924,6 @@ __global__ void __launch_bounds__(DD_THREADS) k_img_dedup(const SetArgs a) {
 }
 
 // ----------------------------------------------------------------- 5. polish
-#ifndef LENS_POLISH_PAIRED
-#define LENS_POLISH_PAIRED 0  // 1: pairs of static dPIEs side by side in double-float (measured 29 % slower)
-#endif
 #ifndef LENS_POLISH_MINB
 #define LENS_POLISH_MINB 2  // resident CTAs per SM the polish is compiled for (3: same speed, spills)
 #endif
@@ -977,53 +974,31 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
         fx = df_add(fx, gx);
         fy = df_add(fy, gy);
       };
-      // potentials base + lane and base + 32 + lane: a pair of static dPIEs
-      // side by side in double-float (dpie_df2), any other alone; each lane
-      // adds them in index order (j, j + 32, j + 64, ...) and the queue of
-      // the potentials outside the interpolants' range fills in index order
-      for (int base = 0; base < ntot; base += 64) {
-        const int jj[2] = {base + lane, base + 32 + lane};
-        bool need[2] = {false, false};
-        df g2x[2], g2y[2];
-        bool got[2] = {false, false};
-        if (LENS_POLISH_PAIRED && jj[1] < n.n_stat && n.recdf[F_U2 * n.n_stat + jj[0]].x >= 0.f &&
-            n.recdf[F_U2 * n.n_stat + jj[1]].x >= 0.f) {
-          df2 px, py;
-          dpie_df2<false>(n.recdf + jj[0], n.recdf + jj[1], n.n_stat, X, Y, px, py, nullptr, got);
-#pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            g2x[v] = df_part2(px, v);
-            g2y[v] = df_part2(py, v);
+      for (int base = 0; base < ntot; base += 32) {
+        const int j = base + lane;
+        bool need = false;
+        if (j < ntot) {
+          const bool st = j < n.n_stat;
+          const float2 *rec = st ? n.recdf + j : s_vdf[w] + (j - n.n_stat) * RECDF;
+          const int stride = st ? n.n_stat : 1;
+          df gx, gy;
+          if (rec[F_U2 * stride].x >= 0.f && dpie_df<false>(rec, stride, X, Y, gx, gy)) {
+            // one-TwoSum accumulation: absolute error 2^-47 sum |alpha_i|,
+            // a few 1e-13 arcsec over a cluster
+            fx = df_add_ss(fx, gx);
+            fy = df_add_ss(fy, gy);
+          } else {
+            need = true;
           }
         }
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          const int j = jj[v];
-          if (j < ntot) {
-            if (!got[v]) {
-              const bool st = j < n.n_stat;
-              const float2 *rec = st ? n.recdf + j : s_vdf[w] + (j - n.n_stat) * RECDF;
-              const int stride = st ? n.n_stat : 1;
-              got[v] = rec[F_U2 * stride].x >= 0.f && dpie_df<false>(rec, stride, X, Y, g2x[v], g2y[v]);
-            }
-            if (got[v]) {
-              // one-TwoSum accumulation: absolute error 2^-47 sum |alpha_i|,
-              // a few 1e-13 arcsec over a cluster
-              fx = df_add_ss(fx, g2x[v]);
-              fy = df_add_ss(fy, g2y[v]);
-            } else {
-              need[v] = true;
-            }
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, need[v]);
-          if (need[v]) s_q[w][nq + __popc(m & ((1u << lane) - 1u))] = j;
-          nq += __popc(m);
-          if (nq >= 32) {
-            __syncwarp();
-            queued(s_q[w][nq - 32 + lane]);
-            nq -= 32;
-            __syncwarp();
-          }
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) s_q[w][nq + __popc(m & ((1u << lane) - 1u))] = j;
+        nq += __popc(m);
+        if (nq >= 32) {
+          __syncwarp();
+          queued(s_q[w][nq - 32 + lane]);
+          nq -= 32;
+          __syncwarp();
         }
       }
       __syncwarp();
