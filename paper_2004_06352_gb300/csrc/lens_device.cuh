@@ -646,6 +646,9 @@ __device__ __forceinline__ float2 cdx2(float c, float dX, int) { return dup2(c *
 template <int NP>
 __device__ __forceinline__ float2 cdx2(float c, const float2 (&dX)[NP], int k) { return mul2(dup2(c), dX[k]); }
 
+#ifndef LENS_MAP_FOLD_U
+#define LENS_MAP_FOLD_U 1  // paired evaluator: u folded into the general kind's constants
+#endif
 // One dPIE (FP32) at NP point pairs, dX shared (one grid column) or per
 // point, dY per point: the arithmetic of dpie32 (same formulas, same order),
 // paired.  MAG: also the magnitude sum p.mag.  FAST: outside the
@@ -656,9 +659,14 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX
   const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
   const float c = A.x, s = A.y, q2 = A.z, u2 = A.w;
   const float Kc = B.x, Kt = B.y, sc = B.z, st = B.w;
-  const float dK = Cq.x, dS = Cq.y, q2sc = Cq.z, q2st = Cq.w;
-  const float q2dS = D.y;
-  const float cb = E.x, sb = E.y;
+  // FOLD (the general kind, u >= U_SERIES32): Zx, Zy below carry the factor
+  // u (the numerators' constants times u), so t = Z^2 needs no u^2 and the
+  // rotation and magnitude constants carry 1/u instead
+  constexpr bool FOLD = LENS_MAP_FOLD_U && !SERIES;
+  const float4 F6 = FOLD ? r4[6] : make_float4(0.f, 0.f, 0.f, 0.f), F7 = FOLD ? r4[7] : F6;
+  const float dK = FOLD ? D.x : Cq.x, dS = FOLD ? F6.y : Cq.y, q2sc = Cq.z, q2st = Cq.w;
+  const float q2dS = FOLD ? F6.z : D.y;
+  const float cb = FOLD ? F6.w : E.x, sb = FOLD ? F7.z : E.y, kmag = FOLD ? F7.w : E.z;
   float2 x[NP], y[NP], x2[NP], y2[NP], u2x2[NP], ic[NP], it[NP], psc[NP], pst[NP], Ec[NP], Et[NP];
   float2 Zx[NP], Zy[NP], tx[NP], ty[NP];
 #pragma unroll
@@ -681,8 +689,13 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX
     Zx[k] = mul2(mul2(x[k], fma2(dup2(dS), Sp, dup2(dK))), rcp2(mul2(Sp, fma2(Ec[k], Et[k], u2x2[k]))));
     const float2 Fc = add2(psc[k], dup2(q2sc)), Ft = add2(pst[k], dup2(q2st));
     Zy[k] = mul2(mul2(y[k], fma2(dup2(q2dS), Sp, dup2(dK))), rcp2(mul2(Sp, fma2(dup2(-u2), y2[k], mul2(Fc, Ft)))));
-    tx[k] = mul2(dup2(u2), mul2(Zx[k], Zx[k]));
-    ty[k] = mul2(dup2(u2), mul2(Zy[k], Zy[k]));
+    if (FOLD) {
+      tx[k] = mul2(Zx[k], Zx[k]);
+      ty[k] = mul2(Zy[k], Zy[k]);
+    } else {
+      tx[k] = mul2(dup2(u2), mul2(Zx[k], Zx[k]));
+      ty[k] = mul2(dup2(u2), mul2(Zy[k], Zy[k]));
+    }
   }
   // the interpolants where every point's |w|^2 < T_SERIES, one branch for
   // all points of the thread (as dpie32)
@@ -711,13 +724,14 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX
           part2(axp[k], h) = zx * atan_over_w(tX);
           part2(ayp[k], h) = zy * atanh_over_w(tY);
         } else {
-          const float wx = u * zx, wy = u * zy;
+          // folded: z is already w = u Z, and the 1/u rides on the constants
+          const float wx = FOLD ? zx : u * zx, wy = FOLD ? zy : u * zy, iw = FOLD ? 1.f : iu;
           if (FAST) {
-            part2(axp[k], h) = iu * atan_fast(wx);
-            part2(ayp[k], h) = iu * (0.346573590f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
+            part2(axp[k], h) = iw * atan_fast(wx);
+            part2(ayp[k], h) = iw * (0.346573590f * __log2f((1.f + wy) * rcp_a(1.f - wy)));
           } else {
-            part2(axp[k], h) = iu * atanf(wx);
-            part2(ayp[k], h) = (0.5f * iu) * log1pf((wy + wy) * rcp_a(1.f - wy));
+            part2(axp[k], h) = iw * atanf(wx);
+            part2(ayp[k], h) = (0.5f * iw) * log1pf((wy + wy) * rcp_a(1.f - wy));
           }
         }
       }
@@ -726,7 +740,7 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX
   for (int k = 0; k < NP; ++k) {
     p.ax[k] = fma2(dup2(cb), axp[k], fma2(dup2(-sb), ayp[k], p.ax[k]));
     p.ay[k] = fma2(dup2(sb), axp[k], fma2(dup2(cb), ayp[k], p.ay[k]));
-    if (MAG) p.mag[k] = fma2(dup2(E.z), add2(abs2(axp[k]), abs2(ayp[k])), p.mag[k]);  // E.z = b q / 2
+    if (MAG) p.mag[k] = fma2(dup2(kmag), add2(abs2(axp[k]), abs2(ayp[k])), p.mag[k]);  // b q / 2 (/ u folded)
     if (HESS) {
       const float4 G = r4[5];
       const float u2sc2 = D.z, u2st2 = D.w;

@@ -33,12 +33,13 @@ enum Rec32 : int {
   R_C = 0, R_S, R_Q2, R_U2,          // rotation, q^2, u^2
   R_KC, R_KT, R_SC, R_ST,            // q^2 sc^2, q^2 st^2, sc, st
   R_DK, R_DS, R_Q2SC, R_Q2ST,       // q^2 (st^2 - sc^2), st-sc, q^2 sc, q^2 st
-  R_PAD0, R_Q2DS, R_U2SC2, R_U2ST2,  // -, q^2 (st-sc), u^2 sc^2, u^2 st^2
+  R_UDK, R_Q2DS, R_U2SC2, R_U2ST2,   // u dK, q^2 (st-sc), u^2 sc^2, u^2 st^2
   R_CB, R_SB, R_KAPS, R_IU,          // rotation times b q, kappa scale b q / 2, 1/u
   R_C1, R_C2, R_C3, R_C4,            // shear rotation by 2 theta with the scale folded in
-  R_U, R_PAD1, R_PAD2, R_PAD3,       // u
-  R_KIND, R_B, R_PAD4, R_PAD5        // kind, SIS b / point-mass b^2
+  R_U, R_UDS, R_UQ2DS, R_CBU,        // u, u dS, u q^2 dS, R_CB / u
+  R_KIND, R_B, R_SBU, R_KAPSU        // kind, SIS b / point-mass b^2, R_SB / u, R_KAPS / u
 };
+// (the u-folded fields are set for K32_DPIE only: its u >= U_SERIES32)
 constexpr int REC32 = 32;
 
 // FP64 record (16 doubles).
@@ -124,6 +125,14 @@ __host__ __device__ inline void make_rec32(int type, double theta, double eps, d
     r[R_KAPS] = (float)(0.5 * bq);
     r[R_IU] = (float)(series ? 0.0 : 1.0 / u);
     r[R_U] = (float)u;
+    if (!series) {
+      r[R_UDK] = (float)(u * q2 * (st - sc) * (st + sc));
+      r[R_UDS] = (float)(u * (st - sc));
+      r[R_UQ2DS] = (float)(u * q2 * (st - sc));
+      r[R_CBU] = (float)(cos(theta) * bq / u);
+      r[R_SBU] = (float)(sin(theta) * bq / u);
+      r[R_KAPSU] = (float)(0.5 * bq / u);
+    }
     r[R_C1] = (float)(c2 * 0.5 * bq);
     r[R_C2] = (float)(s2 * bq);
     r[R_C3] = (float)(s2 * 0.5 * bq);
