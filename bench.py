@@ -31,17 +31,20 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
 # FMUL2 counting two) and MUFU (XU pipe) instructions per point-halo pair of
 # the lens arithmetic of the LENS_MIXED Hessian map kernel, from ncu on the
 # 2048^2 x 1000 workload (the counter group of the map kernel's summary
-# under profiles/: 67.0 lane operations per pair, of which 2.0 are the
+# under profiles/: 65.0 lane operations per pair, of which 2.0 are the
 # magnitude sum that decides the double-float repair); the compensated-fold
 # overhead (~1 op per pair) is included.
-FP32_OPS_PER_PAIR = 64.9
+FP32_OPS_PER_PAIR = 63.0
 MUFU_OPS_PER_PAIR = 6.03
+# every FP32 lane operation of the map call per pair: the kernel's 65.0 and
+# the double-float repair kernel's 1.24 (same capture)
+CALL_FP32_OPS_PER_PAIR = 66.2
 # the same count for the potential-map kernel (ncu, same workload)
 POT_FP32_OPS_PER_PAIR = 48.9
 # DRAM bytes (read + write) of one launch of that kernel on that workload,
 # from the same ncu capture; the 100.7 MB of output are partly still in L2
 # when the kernel ends
-MAP_TRAFFIC_BYTES = 728064 + 40069376
+MAP_TRAFFIC_BYTES = 619264 + 39801856
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 # FP64 FMA lanes per SM and clock (measured on this GPU: 1/64 of the FP32 rate)
 FP64_LANES = 2
@@ -49,7 +52,7 @@ FP64_LANES = 2
 # counters on the 1000-potential model, 372 images; summary under profiles/):
 # FP32 = FFMA + FADD + FMUL, FP64 = DFMA + DADD + DMUL, MUFU = XU pipe.
 # Source-plane chi2, 4096 sets (k_chi2_source):
-CHI2_SRC_OPS = {"fp32": 1.276e6, "fp64": 1.881e4, "mufu": 1.207e4}
+CHI2_SRC_OPS = {"fp32": 1.276e6, "fp64": 1.658e4, "mufu": 1.168e4}
 # Image-plane chi2, 1024^2 grid, 256 sets (k_img_sources + search + newton +
 # dedup + polish + chi2, per model):
 CHI2_IMG_OPS = {"fp32": 8.898e8, "fp64": 1.996e6, "mufu": 4.636e7}
@@ -383,6 +386,9 @@ def main():
         peak = SMS * FP32_LANES * f_max / 1e12
         roof.update({"achieved": ach, "peak": peak, "frac": ach / peak,
                      "ops_per_pair": FP32_OPS_PER_PAIR, "pipe": "fp32 (FFMA/FADD/FMUL lanes)"})
+        # the FP32 pipe's use by the whole call (magnitude sum and repair too)
+        roof["call_ops_per_pair"] = CALL_FP32_OPS_PER_PAIR
+        roof["call_frac"] = CALL_FP32_OPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12 / peak
         if MUFU_OPS_PER_PAIR:
             mach = MUFU_OPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12
             roof["mufu"] = {"achieved": mach, "peak": SMS * MUFU_LANES * f_max / 1e12,

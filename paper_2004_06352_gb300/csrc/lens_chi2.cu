@@ -67,8 +67,23 @@ struct Chi2SrcArgs {
 // instead of on two threads per set).
 constexpr int SRC_BATCH = 16;
 
+// resident warps per SM the source-plane kernel is compiled for (0: as its
+// registers allow, 118 at 128 threads; 20 warps: 96 registers and spills,
+// same speed; 24: 80 registers, 5 % slower)
+#ifndef LENS_SRC_WARPS
+#define LENS_SRC_WARPS 0
+#endif
+// both records of varying potential v of a parameter set, out of line
+__device__ __noinline__ bool var_recs_cold(const double *q, int type0, int type1, int v, double *s_rec,
+                                           float2 *s_rdf) {
+  const double *w = q + 7 * v;
+  const bool ok = load_var_rec64(q, type0, type1, v, s_rec);
+  make_recdf(v == 0 ? type0 : type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rdf + v * RECDF);
+  return ok;
+}
+
 template <int THREADS>
-__global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
+__global__ void __launch_bounds__(THREADS, LENS_SRC_WARPS * 32 / THREADS) k_chi2_source(const Chi2SrcArgs a) {
   static_assert(THREADS >= 2 * SRC_BATCH, "one thread per record of a batch");
   extern __shared__ double sm[];
   double *s_beta = sm;                   // [nimg][2]
@@ -87,8 +102,12 @@ __global__ void __launch_bounds__(THREADS) k_chi2_source(const Chi2SrcArgs a) {
       if (p < a.P) {
         const double *q = a.params + p * a.pstride;
         const double *w = q + 7 * v;  // x0, y0, eps, theta, rcore, rcut, b0
-        s_ok[k][v] = load_var_rec64(q, a.type0, a.type1, v, s_rec[k]);
-        make_recdf(v == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rdf[k] + v * RECDF);
+        if (LENS_COLD_CALLS) {
+          s_ok[k][v] = var_recs_cold(q, a.type0, a.type1, v, s_rec[k], s_rdf[k]);
+        } else {
+          s_ok[k][v] = load_var_rec64(q, a.type0, a.type1, v, s_rec[k]);
+          make_recdf(v == 0 ? a.type0 : a.type1, w[0], w[1], w[3], w[2], w[4], w[5], w[6], s_rdf[k] + v * RECDF);
+        }
       }
     }
     __syncthreads();
