@@ -214,11 +214,12 @@ static int model_block(lens_ctx *ctx, size_t bytes, void **p, size_t *got) {
 // three threads per potential (the FP64 arithmetic runs at 1/64 of the FP32
 // rate, so the work is spread): part 0 the FP64 record (upload order) and,
 // for a heavy potential (slot = -1 - heavy index), its copy in the heavy
-// table; part 1 the double-float record; part 2, for a light potential
+// table; part 1 the double-float record (and, for a heavy potential, its
+// copy in the heavy table, record-major); part 2, for a light potential
 // (slot >= 0, the kind-sorted order), the FP32 record and position data.
 __global__ void k_build_records(const lens_halo *__restrict__ h, const int32_t *__restrict__ slot, int n,
                                 float *rec32, double *pos64, float *cen32, double *heavy, double *all64,
-                                float2 *recdf) {
+                                float2 *recdf, float2 *heavydf) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
   const int k = t / 3, part = t % 3;
@@ -232,6 +233,8 @@ __global__ void k_build_records(const lens_halo *__restrict__ h, const int32_t *
       for (int q = 0; q < REC64; ++q) heavy[(size_t)(-1 - s) * REC64 + q] = r[q];
   } else if (part == 1) {
     make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, recdf + k, n);
+    if (s < 0)
+      make_recdf(a.type, a.x0, a.y0, a.theta, a.eps, a.rcore, a.rcut, a.b0, heavydf + (size_t)(-1 - s) * RECDF);
   } else if (s >= 0) {
     make_rec32(a.type, a.theta, a.eps, a.rcore, a.rcut, a.b0, rec32 + (size_t)s * REC32);
     const bool circ = a.type != LENS_DPIE;
@@ -274,15 +277,15 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->koff[4] = m->n_light;
   const size_t nl = (size_t)m->n_light, nh = (size_t)m->n_heavy, na = (size_t)n;
   // records (built on the device), then the staged halo table and slots
-  const size_t sizes[8] = {nl * REC32 * sizeof(float),  nl * 4 * sizeof(double),     nl * 4 * sizeof(float),
+  const size_t sizes[9] = {nl * REC32 * sizeof(float),  nl * 4 * sizeof(double),     nl * 4 * sizeof(float),
                            nh * REC64 * sizeof(double), na * REC64 * sizeof(double),   na * RECDF * sizeof(float2),
-                           na * sizeof(lens_halo),      na * sizeof(int32_t)};
-  size_t offs[8], total = 0;
-  for (int k = 0; k < 8; ++k) {
+                           nh * RECDF * sizeof(float2), na * sizeof(lens_halo),        na * sizeof(int32_t)};
+  size_t offs[9], total = 0;
+  for (int k = 0; k < 9; ++k) {
     offs[k] = total;
     total += (sizes[k] + 255) & ~(size_t)255;
   }
-  const size_t staged = total - offs[6];
+  const size_t staged = total - offs[7];
   // host image of the staged part: the context's page-locked staging buffer
   // (pageable if that cannot be had)
   std::vector<unsigned char> pageable;
@@ -305,7 +308,7 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
     img = pageable.data();
   }
   if (n > 0) std::memcpy(img, h, na * sizeof(lens_halo));
-  int32_t *slot = (int32_t *)(img + (offs[7] - offs[6]));
+  int32_t *slot = (int32_t *)(img + (offs[8] - offs[7]));
   for (int32_t k = 0; k < m->n_light; ++k) slot[light[k]] = k;
   for (int32_t k = 0; k < m->n_heavy; ++k) slot[heavy[k]] = -1 - k;
   int rc = total ? model_block(ctx, total, &m->block, &m->bytes) : LENS_OK;
@@ -325,14 +328,15 @@ int build_model(lens_ctx *ctx, const lens_halo *h, int32_t n, Model **out) {
   m->heavy = (double *)(base + offs[3]);
   m->all64 = (double *)(base + offs[4]);
   m->recdf = (float2 *)(base + offs[5]);
+  m->heavydf = (float2 *)(base + offs[6]);
   cudaError_t e = cudaSuccess;
   if (n > 0) {
     if (!upload_stream(ctx)) e = cudaErrorNotReady;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(base + offs[6], img, staged, cudaMemcpyHostToDevice, ctx->upload_st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(base + offs[7], img, staged, cudaMemcpyHostToDevice, ctx->upload_st);
     if (e == cudaSuccess) {
       k_build_records<<<(3 * n + 63) / 64, 64, 0, ctx->upload_st>>>(
-          (const lens_halo *)(base + offs[6]), (const int32_t *)(base + offs[7]), n, m->rec32, m->pos64, m->cen32,
-          m->heavy, m->all64, m->recdf);
+          (const lens_halo *)(base + offs[7]), (const int32_t *)(base + offs[8]), n, m->rec32, m->pos64, m->cen32,
+          m->heavy, m->all64, m->recdf, m->heavydf);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload_st);

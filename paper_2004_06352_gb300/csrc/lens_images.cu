@@ -93,13 +93,35 @@ struct __align__(16) VarRecs {
   double r64[2][REC64];
 };
 
+// Refinement state of a candidate (step 3, point-list form), beside its hit.
+struct Ref {
+  double th[3][2];  // vertices of the current (sub-)triangle
+  double be[3][2];  // their images in the source plane
+  double mo[6];     // evaluations: alpha at the three edge midpoints, or alpha, kappa, gamma1, gamma2 at the Newton point
+  double tiny;      // degenerate-area threshold at the current level
+  int nit, settled; // Newton steps taken; steps below the tolerance
+};
+// Point lists of step 3 (entries slot << 2 | m: m < 3 edge midpoint m of the
+// slot's triangle, m = 3 its Newton point), slots per candidate slot: two
+// alternating subdivision lists of 3, two Newton rounds and the stragglers.
+constexpr int LST_PER_SLOT = 9;
+#ifndef LENS_NEWTON_ROUNDS
+#define LENS_NEWTON_ROUNDS 2  // Newton steps taken by the point-list form before the rest go to k_ref_straggle
+#endif
+constexpr int NEWTON_ROUNDS = LENS_NEWTON_ROUNDS;
+static_assert(NEWTON_ROUNDS >= 1, "the subdivision hands its candidates to Newton round 0");
+constexpr int LCNT = 16;  // list counters: subdivision levels, Newton rounds, stragglers; the last: straggler fetches
+static_assert(SUBDIV_LEVELS + NEWTON_ROUNDS + 1 < LCNT, "list counters");
+
 struct Layout {
-  size_t cnt, valid, nuniq, bary, src32, hits, uniq, var, total;
+  size_t cnt, valid, nuniq, bary, src32, hits, uniq, var, ref, lst, lcnt, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-__host__ __device__ inline Layout layout(int B, int nsrc) {
+// lists = false: no point-list refinement state (step 3 then runs as
+// k_img_newton, in less memory)
+__host__ __device__ inline Layout layout(int B, int nsrc, bool lists = true) {
   Layout L;
   size_t o = 0;
   L.cnt = o;
@@ -118,6 +140,12 @@ __host__ __device__ inline Layout layout(int B, int nsrc) {
   o = align_up(o + (size_t)B * IMG_CAP * sizeof(int));
   L.var = o;
   o = align_up(o + (size_t)B * sizeof(VarRecs));
+  L.ref = o;
+  o = align_up(o + (lists ? (size_t)B * IMG_CAP * sizeof(Ref) : 0));
+  L.lst = o;
+  o = align_up(o + (lists ? (size_t)B * IMG_CAP * LST_PER_SLOT * sizeof(int) : 0));
+  L.lcnt = o;
+  o = align_up(o + LCNT * sizeof(int));
   L.total = o;
   return L;
 }
@@ -128,10 +156,13 @@ struct Bufs {
   float2 *src32;  // barycentres rounded to FP32 (search)
   Hit *hits;
   VarRecs *var;
+  Ref *ref;       // [B][IMG_CAP], beside hits
+  int *lst;       // point lists, LST_PER_SLOT x B x IMG_CAP entries
+  int *lcnt;      // their counters
 };
 
-__host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc) {
-  Layout L = layout(B, nsrc);
+__host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc, bool lists = true) {
+  Layout L = layout(B, nsrc, lists);
   char *b = (char *)scratch;
   Bufs r;
   r.cnt = (int *)(b + L.cnt);
@@ -142,6 +173,9 @@ __host__ __device__ inline Bufs bufs(void *scratch, int B, int nsrc) {
   r.hits = (Hit *)(b + L.hits);
   r.uniq = (int *)(b + L.uniq);
   r.var = (VarRecs *)(b + L.var);
+  r.ref = (Ref *)(b + L.ref);
+  r.lst = (int *)(b + L.lst);
+  r.lcnt = (int *)(b + L.lcnt);
   return r;
 }
 
@@ -439,6 +473,7 @@ struct NewtonArgs {
   int n_light;
   int koff[5];                 // the FP32 ones by kind: Kind32 k occupies [koff[k], koff[k+1])
   const double *heavy;         // static potentials on the FP64 path
+  const float2 *heavydf;       // the same in double-float, record-major (point-list refinement)
   int n_heavy;
   const double *all64;         // every static potential in FP64 (polish)
   const float2 *recdf;         // every static potential in double-float, field-major [RECDF][n_stat] (polish)
@@ -447,6 +482,7 @@ struct NewtonArgs {
   double xmin, ymin, dx, dy;   // search grid
   int nx;
   const float *gax, *gay;      // static deflection at the grid nodes [ny][nx] (D_ls/D_s = 1)
+  int *err;                    // the context's error word
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -877,6 +913,574 @@ __global__ void __launch_bounds__(RF_THREADS, LENS_NEWTON_MINB) k_img_newton(con
   }
 }
 
+// ---------------------------------------------- 3'. refinement, point lists
+// Step 3 as a sequence of dense evaluations (LENS_REFINE_LISTS): every
+// subdivision level evaluates the edge midpoints of all refining candidates
+// of the batch in one launch, and every Newton round the Newton points of
+// all active candidates, with the map kernel's structure -- one thread per
+// KP points (two-point pairs on the paired FP32 path), the static FP32
+// potentials streamed chunk by chunk into shared memory by bulk copies and
+// read by every thread at once, Kahan folds every SUB potentials, the
+// static cluster-scale potentials in FP64 and the two varying potentials
+// per point; small kernels between the evaluations take the decisions per
+// candidate (the same ones as k_img_newton) and append the next points.
+// Candidates still iterating after NEWTON_ROUNDS Newton steps (0.9 % of them
+// on the 1000-potential model) finish in k_ref_straggle, one CTA each.
+#ifndef LENS_REFINE_LISTS
+#define LENS_REFINE_LISTS 1
+#endif
+constexpr int PE_THREADS = 128, PE_CH = 64, PE_SUB = 16;
+#ifndef LENS_PE_MINB_GRAD
+#define LENS_PE_MINB_GRAD 4
+#endif
+#ifndef LENS_PE_MINB_HESS
+#define LENS_PE_MINB_HESS 4
+#endif
+__host__ __device__ constexpr int pe_points(bool hess) { return PE_THREADS * (hess ? 2 : 4); }
+
+// The compiler may not see through v: it has to keep it in registers.
+__device__ __forceinline__ void opaque2(float2 &v) { asm volatile("" : "+f"(v.x), "+f"(v.y)); }
+
+// Position of list entry e: an edge midpoint of the slot's current triangle
+// or its Newton point.
+__device__ __forceinline__ void entry_point(const Bufs &s, int e, double &X, double &Y) {
+  const int slot = e >> 2, m = e & 3;
+  if (m == 3) {
+    X = s.hits[slot].tx;
+    Y = s.hits[slot].ty;
+  } else {
+    const Ref &r = s.ref[slot];
+    const int m1 = m == 2 ? 0 : m + 1;
+    X = 0.5 * (r.th[m][0] + r.th[m1][0]);
+    Y = 0.5 * (r.th[m][1] + r.th[m1][1]);
+  }
+}
+
+template <bool HESS>
+__global__ void __launch_bounds__(PE_THREADS, HESS ? LENS_PE_MINB_HESS : LENS_PE_MINB_GRAD)
+    k_pts_eval(const SetArgs a, const NewtonArgs n, const int *__restrict__ lst, const int *__restrict__ count) {
+  constexpr int KP = HESS ? 2 : 4, NP = KP / 2, NC = HESS ? 5 : 2;
+  __shared__ __align__(128) float s_rec[2][PE_CH * REC32];
+  __shared__ __align__(16) float4 s_cen[2][PE_CH];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ double s_hv[PE_THREADS][KP][NC];
+  const int npts = *count, p0 = blockIdx.x * pe_points(HESS);
+  if (p0 >= npts) return;  // uniform over the CTA
+  const int tid = threadIdx.x;
+  int ent[KP];
+  bool live[KP];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int p = p0 + k * PE_THREADS + tid;
+    live[k] = p < npts;
+    ent[k] = lst[live[k] ? p : p0];  // past the end: the tile's first point again, not stored
+  }
+  // hi/lo float pairs of the positions: (hi - centre hi) is exact next to a
+  // centre (Sterbenz), as in k_img_newton's sweeps.  Made opaque, so that
+  // the compiler keeps them rather than re-deriving them from the doubles
+  // inside the potential loop (conversions run on the FP64 pipe, at 1/64 of
+  // the FP32 rate: that re-derivation made the kernel FP64-bound).
+  float2 hx[NP], lx[NP], hy[NP], ly[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double x, y;
+      entry_point(a.s, ent[2 * j + h], x, y);
+      const float fx = (float)x, fy = (float)y;
+      part2(hx[j], h) = fx;
+      part2(lx[j], h) = (float)(x - (double)fx);
+      part2(hy[j], h) = fy;
+      part2(ly[j], h) = (float)(y - (double)fy);
+    }
+    opaque2(hx[j]);
+    opaque2(lx[j]);
+    opaque2(hy[j]);
+    opaque2(ly[j]);
+  }
+  // static cluster-scale potentials in double-float (FP64 where that
+  // fails), before or after the FP32 sweep by tile parity.  Not FP64: at the
+  // images these potentials mostly take the atan/atanh reductions, and in
+  // FP64 (1/64 of the FP32 rate) that alone kept the FP64 pipe 84 % busy
+  // for 2.5 times the sweep's FP32 time.
+  auto heavy_pass = [&]() {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      double X, Y;
+      entry_point(a.s, ent[k], X, Y);
+      for (int j = 0; j < n.n_heavy; ++j)
+        add_potential_df<HESS>(n.heavydf + (size_t)j * RECDF, 1, n.heavy + (size_t)j * REC64, X, Y, v);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) s_hv[tid][k][c] = v[c];
+    }
+  };
+  const bool heavy_first = (blockIdx.x & 1) != 0;
+  if (heavy_first) heavy_pass();
+
+  Acc2<HESS, NP> tot, cmp, part;
+  tot.zero();
+  cmp.zero();
+  part.zero();
+  const int nl = n.n_light, nch = (nl + PE_CH - 1) / PE_CH;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int ch) {  // thread 0: chunk ch's records and centres into buffer ch & 1
+    const int base = ch * PE_CH, cnt = min(PE_CH, nl - base), buf = ch & 1;
+    mbar_expect_tx(&s_bar[buf], cnt * (REC32 * 4 + 16));
+    bulk_g2s(&s_rec[buf][0], n.rec32 + (size_t)base * REC32, cnt * REC32 * 4, &s_bar[buf]);
+    bulk_g2s(&s_cen[buf][0], n.cen32 + (size_t)base * 4, cnt * 16, &s_bar[buf]);
+  };
+  if (tid == 0 && nch > 0) issue(0);
+  int seen = 0;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int buf = ch & 1, base = ch * PE_CH, cnt = min(PE_CH, nl - base);
+    const bool ok = mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) {
+        atomicOr(n.err, ERRBIT_WAIT);
+        mbar_wait_bounded(&s_bar[buf], (ch >> 1) & 1);  // let the copy in flight land before leaving
+      }
+      return;
+    }
+    if (tid == 0 && ch + 1 < nch) {
+      fence_proxy_async();
+      issue(ch + 1);
+    }
+    const float4 *recs = reinterpret_cast<const float4 *>(&s_rec[buf][0]);
+    const float4 *cens = &s_cen[buf][0];
+    auto run = [&](auto kind_tag, int h0, int h1) {
+      constexpr int KIND = decltype(kind_tag)::value;
+      for (int h = h0; h < h1;) {
+        const int he = min(h + (PE_SUB - seen), h1);
+        seen += he - h;
+#pragma unroll 2
+        for (; h < he; ++h) {
+          const float4 *r4 = recs + h * (REC32 / 4);
+          const float4 c = cens[h];
+          float2 dX[NP], dY[NP];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            dX[j] = add2(sub2(hx[j], dup2(c.x)), sub2(lx[j], dup2(c.z)));
+            dY[j] = add2(sub2(hy[j], dup2(c.y)), sub2(ly[j], dup2(c.w)));
+          }
+          if (KIND == K32_DPIE)
+            dpie32x2<HESS, NP, false, false>(r4, dX, dY, part);
+          else if (KIND == K32_DPIE_SERIES)
+            dpie32x2<HESS, NP, true, false>(r4, dX, dY, part);
+          else
+            circ32x2<HESS, NP, KIND == K32_POINT, false>(r4, dX, dY, part);
+        }
+        if (seen == PE_SUB) {
+          fold2(tot, cmp, part);
+          seen = 0;
+        }
+      }
+    };
+    auto seg = [&](int k, int &h0, int &h1) {
+      h0 = max(n.koff[k] - base, 0);
+      h1 = min(n.koff[k + 1] - base, cnt);
+    };
+    int h0, h1;
+    seg(K32_DPIE, h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_DPIE>(), h0, h1);
+    seg(K32_DPIE_SERIES, h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_DPIE_SERIES>(), h0, h1);
+    seg(K32_SIS, h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_SIS>(), h0, h1);
+    seg(K32_POINT, h0, h1);
+    if (h0 < h1) run(std::integral_constant<int, K32_POINT>(), h0, h1);
+  }
+  fold2(tot, cmp, part);
+  if (!heavy_first) heavy_pass();
+
+  // the two varying potentials of each point's parameter set: FP32 in the
+  // subdivision (as k_img_newton's sweeps), double-float with FP64 fallback
+  // in the Newton steps
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int slot = ent[k] >> 2;
+    const VarRecs &var = a.s.var[slot / IMG_CAP];
+    double Xk, Yk;
+    entry_point(a.s, ent[k], Xk, Yk);
+    double o[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) o[c] = c < NC ? s_hv[tid][k][c] : 0.0;
+    const float2 *tt[5] = {tot.ax, tot.ay, tot.k, tot.g1, tot.g2};
+    const float2 *cc[5] = {cmp.ax, cmp.ay, cmp.k, cmp.g1, cmp.g2};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) o[c] += (double)part2(tt[c][k >> 1], k & 1) - (double)part2(cc[c][k >> 1], k & 1);
+    if (!HESS) {
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        Acc<false, 1> acc;
+        acc.zero();
+        const float dY[1] = {(float)(Yk - ((double)var.cen[v][1] + (double)var.cen[v][3]))};
+        eval32_any<false, 1>(reinterpret_cast<const float4 *>(var.r32[v]),
+                             (float)(Xk - ((double)var.cen[v][0] + (double)var.cen[v][2])), dY, acc);
+        o[0] += acc.ax[0];
+        o[1] += acc.ay[0];
+      }
+    } else {
+      const df Xd = df_from_double(Xk), Yd = df_from_double(Yk);
+#pragma unroll 1
+      for (int v = 0; v < 2; ++v) {
+        const float2 *rec = var.rdf[v];
+        df ax, ay, hh[3];
+        bool okv = true;
+        if (rec[F_U2].x < 0.f)
+          circ_df<true>(rec, 1, Xd, Yd, ax, ay, hh);
+        else
+          okv = dpie_df<true, true>(rec, 1, Xd, Yd, ax, ay, hh);
+        if (okv) {
+          o[0] += df_to_double(ax);
+          o[1] += df_to_double(ay);
+          o[2] += df_to_double(hh[0]);
+          o[3] += df_to_double(hh[1]);
+          o[4] += df_to_double(hh[2]);
+        } else {
+          double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+          eval64<true>(var.r64[v], Xk, Yk, e[0], e[1], e[2], e[3], e[4]);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) o[c] += e[c];
+        }
+      }
+    }
+    if (!live[k]) continue;
+    Ref &r = a.s.ref[slot];
+    const int m = ent[k] & 3;
+    if (m == 3) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) r.mo[c] = o[c];
+    } else {
+      r.mo[2 * m] = o[0];
+      r.mo[2 * m + 1] = o[1];
+    }
+  }
+}
+
+// The source position, ratio and grid spacing a candidate's decisions use.
+struct CandCtx {
+  double P[2], r, tiny0, step_max, local;
+};
+__device__ __forceinline__ CandCtx cand_ctx(const SetArgs &a, const NewtonArgs &n, int slot) {
+  CandCtx c;
+  const int b = slot / IMG_CAP, src = a.s.hits[slot].src;
+  c.r = n.ratio[src];
+  c.P[0] = a.s.bary[((size_t)b * a.nsrc + src) * 2];
+  c.P[1] = a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1];
+  c.tiny0 = 1e-14 * n.dx * n.dy;
+  c.step_max = fmax(n.dx, n.dy);
+  c.local = LOCAL_CELLS * fmax(n.dx, n.dy);
+  return c;
+}
+
+// Newton start from the barycentric weights of P in the current triangle
+// (the centroid where they are degenerate); the slot joins round 0.
+__device__ __forceinline__ void newton_start(const SetArgs &a, int slot, const CandCtx &c, bool weigh, int *lst0,
+                                             int *cnt0) {
+  Ref &R = a.s.ref[slot];
+  Hit &h = a.s.hits[slot];
+  double wgt[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+  if (weigh && !bary_w(R.be[0], R.be[1], R.be[2], c.P, R.tiny, wgt)) wgt[0] = wgt[1] = wgt[2] = 1.0 / 3;
+  h.tx = wgt[0] * R.th[0][0] + wgt[1] * R.th[1][0] + wgt[2] * R.th[2][0];
+  h.ty = wgt[0] * R.th[0][1] + wgt[1] * R.th[1][1] + wgt[2] * R.th[2][1];
+  h.h11 = h.h22 = h.h12 = 0.f;
+  h.status = ST_FAILED;
+  R.nit = 0;
+  R.settled = 0;
+  lst0[atomicAdd(cnt0, 1)] = slot << 2 | 3;
+}
+
+constexpr int RL_THREADS = 128;
+
+// Initial triangle of every candidate: vertices from the grid, their source
+// images from the grid cache plus the varying potentials (FP32), as
+// k_img_newton; the three edge midpoints join subdivision level 0.
+__global__ void __launch_bounds__(RL_THREADS) k_ref_init(const SetArgs a, const NewtonArgs n) {
+  const int b = blockIdx.y;
+  if (!a.s.valid[b]) return;
+  const int k = blockIdx.x * RL_THREADS + threadIdx.x;
+  if (k >= min(a.s.cnt[b], IMG_CAP)) return;
+  const int slot = b * IMG_CAP + k;
+  const Hit &h = a.s.hits[slot];
+  const CandCtx c = cand_ctx(a, n, slot);
+  const VarRecs &var = a.s.var[b];
+  const int cell = h.cell, tri = cell & 1, ci = (cell >> 1) % (n.nx - 1), cj = (cell >> 1) / (n.nx - 1);
+  // triangle 0: (i,j),(i+1,j),(i+1,j+1); triangle 1: (i,j),(i+1,j+1),(i,j+1)
+  const int oi[2][3] = {{ci, ci + 1, ci + 1}, {ci, ci + 1, ci}}, oj[2][3] = {{cj, cj, cj + 1}, {cj, cj + 1, cj + 1}};
+  Ref &R = a.s.ref[slot];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int ii = oi[tri][q], jj = oj[tri][q];
+    const double tx = n.xmin + ii * n.dx, ty = n.ymin + jj * n.dy;
+    const size_t o = (size_t)jj * n.nx + ii;
+    float ax = n.gax[o], ay = n.gay[o];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      Acc<false, 1> acc;
+      acc.zero();
+      const float dY[1] = {(float)(ty - ((double)var.cen[v][1] + (double)var.cen[v][3]))};
+      eval32_any<false, 1>(reinterpret_cast<const float4 *>(var.r32[v]),
+                           (float)(tx - ((double)var.cen[v][0] + (double)var.cen[v][2])), dY, acc);
+      ax += acc.ax[0];
+      ay += acc.ay[0];
+    }
+    R.th[q][0] = tx;
+    R.th[q][1] = ty;
+    R.be[q][0] = tx - c.r * ax;
+    R.be[q][1] = ty - c.r * ay;
+  }
+  R.tiny = c.tiny0;
+  int *cnt = a.s.lcnt;
+  if (SUBDIV_LEVELS > 0) {
+    const int base = atomicAdd(&cnt[0], 3);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) a.s.lst[base + m] = slot << 2 | m;
+  } else {
+    const size_t N = (size_t)a.B * IMG_CAP;
+    newton_start(a, slot, c, true, a.s.lst + 6 * N, &cnt[SUBDIV_LEVELS]);
+  }
+}
+
+// Subdivision level `lev` after its midpoints were evaluated: keep the
+// sub-triangle that best contains the source, or stop refining (k_img_newton's
+// rule); the next level's midpoints, or the Newton start, are appended.
+__global__ void __launch_bounds__(RL_THREADS) k_ref_level(const SetArgs a, const NewtonArgs n, int lev) {
+  const size_t N = (size_t)a.B * IMG_CAP;
+  const int *lst = a.s.lst + ((lev & 1) ? 3 * N : 0);
+  int *nxt = a.s.lst + ((lev & 1) ? 0 : 3 * N);
+  int *cnt = a.s.lcnt;
+  const int npts = cnt[lev];
+  for (int p = blockIdx.x * RL_THREADS + threadIdx.x; p < npts; p += gridDim.x * RL_THREADS) {
+    const int e = lst[p];
+    if ((e & 3) != 0) continue;  // one thread per candidate: its first midpoint's
+    const int slot = e >> 2;
+    const CandCtx c = cand_ctx(a, n, slot);
+    Ref &R = a.s.ref[slot];
+    double t6[6][2], b6[6][2];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int q1 = q == 2 ? 0 : q + 1;
+      t6[q][0] = R.th[q][0];
+      t6[q][1] = R.th[q][1];
+      t6[3 + q][0] = 0.5 * (R.th[q][0] + R.th[q1][0]);
+      t6[3 + q][1] = 0.5 * (R.th[q][1] + R.th[q1][1]);
+      b6[q][0] = R.be[q][0];
+      b6[q][1] = R.be[q][1];
+      b6[3 + q][0] = t6[3 + q][0] - c.r * R.mo[2 * q];
+      b6[3 + q][1] = t6[3 + q][1] - c.r * R.mo[2 * q + 1];
+    }
+    const double tiny_sub = 0.25 * R.tiny;
+    int best = -1;
+    double best_score = -INFINITY;
+#pragma unroll
+    for (int sb = 0; sb < 4; ++sb) {
+      double ww[3];
+      if (!bary_w(b6[sub_vertex(sb, 0)], b6[sub_vertex(sb, 1)], b6[sub_vertex(sb, 2)], c.P, tiny_sub, ww)) continue;
+      const double score = fmin(ww[0], fmin(ww[1], ww[2]));
+      if (score > best_score) {
+        best_score = score;
+        best = sb;
+      }
+    }
+    if (best < 0 || best_score < -SUBDIV_TOL) {
+      newton_start(a, slot, c, true, a.s.lst + 6 * N, &cnt[SUBDIV_LEVELS]);
+      continue;
+    }
+    R.tiny = tiny_sub;
+#pragma unroll
+    for (int sb = 0; sb < 4; ++sb)
+      if (sb == best)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          R.th[q][0] = t6[sub_vertex(sb, q)][0];
+          R.th[q][1] = t6[sub_vertex(sb, q)][1];
+          R.be[q][0] = b6[sub_vertex(sb, q)][0];
+          R.be[q][1] = b6[sub_vertex(sb, q)][1];
+        }
+    if (lev + 1 < SUBDIV_LEVELS) {
+      const int base = atomicAdd(&cnt[lev + 1], 3);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) nxt[base + m] = slot << 2 | m;
+    } else {
+      newton_start(a, slot, c, true, a.s.lst + 6 * N, &cnt[SUBDIV_LEVELS]);
+    }
+  }
+}
+
+// One Newton step of a candidate from its evaluation o (alpha, kappa, gamma1,
+// gamma2 at (tx, ty)): k_img_newton's step, limited to one cell.  Returns
+// true while the candidate iterates; otherwise its status is final.
+__device__ __forceinline__ bool newton_step(const SetArgs &a, int slot, const CandCtx &c, const double *o) {
+  Ref &R = a.s.ref[slot];
+  Hit &h = a.s.hits[slot];
+  double tx = h.tx, ty = h.ty;
+  int status = ST_FAILED;
+  bool active = true;
+  const double fx = c.P[0] - (tx - c.r * o[0]), fy = c.P[1] - (ty - c.r * o[1]);
+  const double m11 = c.r * (o[2] + o[3]), m22 = c.r * (o[2] - o[3]), m12 = c.r * o[4];
+  const double a11 = 1.0 - m11, a22 = 1.0 - m22, a12 = -m12;
+  const double det = a11 * a22 - a12 * a12;
+  if (!(det != 0.0) || !isfinite(det)) {
+    active = false;
+  } else {
+    double dx = (a22 * fx - a12 * fy) / det, dy = (a11 * fy - a12 * fx) / det;
+    const double len = sqrt(dx * dx + dy * dy);
+    if (len > c.step_max) {
+      dx *= c.step_max / len;
+      dy *= c.step_max / len;
+    }
+    tx += dx;
+    ty += dy;
+    h.tx = tx;
+    h.ty = ty;
+    h.h11 = (float)m11;
+    h.h22 = (float)m22;
+    h.h12 = (float)m12;
+    if (!isfinite(tx) || !isfinite(ty)) {
+      active = false;
+    } else if (len < NEWTON32_TOL && ++R.settled > LENS_NEWTON_EXTRA) {
+      status = ST_NEWTON;
+      active = false;
+    }
+  }
+  if (active && ++R.nit < NEWTON_MAXIT) return true;
+  // a root far from its triangle belongs to another triangle's search
+  if (status == ST_NEWTON && hypot(tx - h.cx, ty - h.cy) > c.local) status = ST_FAR;
+  h.status = status;
+  return false;
+}
+
+// Newton round `round` after its points were evaluated: a step per
+// candidate; those still iterating join the next round, after the last
+// round the stragglers.
+__global__ void __launch_bounds__(RL_THREADS) k_ref_newton(const SetArgs a, const NewtonArgs n, int round) {
+  const size_t N = (size_t)a.B * IMG_CAP;
+  // rounds alternate between the lists at 6N and 7N; the stragglers' is at 8N
+  const int *lst = a.s.lst + (6 + (round & 1)) * N;
+  int *nxt = a.s.lst + (round + 1 < NEWTON_ROUNDS ? 6 + ((round + 1) & 1) : 8) * N;
+  int *cnt = a.s.lcnt;
+  int *ncnt = &cnt[round + 1 < NEWTON_ROUNDS ? SUBDIV_LEVELS + round + 1 : SUBDIV_LEVELS + NEWTON_ROUNDS];
+  const int npts = cnt[SUBDIV_LEVELS + round];
+  for (int p = blockIdx.x * RL_THREADS + threadIdx.x; p < npts; p += gridDim.x * RL_THREADS) {
+    const int slot = lst[p] >> 2;
+    const CandCtx c = cand_ctx(a, n, slot);
+    if (newton_step(a, slot, c, a.s.ref[slot].mo)) nxt[atomicAdd(ncnt, 1)] = slot << 2 | 3;
+  }
+}
+
+// The stragglers: RS_GROUPS groups of RS_GROUP threads per CTA, each group
+// one candidate at a time, each evaluation a group-wide sweep -- the threads
+// split the static FP32 potentials (records staged in shared memory once per
+// CTA when they fit, else read from global memory), threads j < n_heavy take
+// the static cluster-scale ones in double-float, the group's last two
+// threads the varying ones in FP32 (here the step's latency matters more
+// than the root's last digits: the polish refines it in double-float) -- a
+// fixed-order group sum in FP64, then the same Newton step.  Its pace is the
+// latency of a step times the steps of the group's candidates (~40 for one
+// that never converges), so the CTA runs several groups side by side.
+constexpr int RS_THREADS = 256, RS_GROUP = 128, RS_GROUPS = RS_THREADS / RS_GROUP, RS_GWARPS = RS_GROUP / 32;
+constexpr size_t RS_SMEM_MAX = 200 * 1024;
+__host__ __device__ constexpr size_t straggle_smem(int n_light) { return (size_t)n_light * (REC32 * 4 + 16); }
+// barrier of group g (barrier 0 is __syncthreads)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "n"(RS_GROUP) : "memory"); }
+
+__global__ void __launch_bounds__(RS_THREADS) k_ref_straggle(const SetArgs a, const NewtonArgs n, int staged) {
+  extern __shared__ __align__(16) float4 s_dyn[];
+  __shared__ float2 s_red[RS_GROUPS][RS_GWARPS][5];
+  __shared__ int s_go[RS_GROUPS], s_next[RS_GROUPS];
+  const size_t N = (size_t)a.B * IMG_CAP;
+  const int *lst = a.s.lst + 8 * N;
+  const int nst = a.s.lcnt[SUBDIV_LEVELS + NEWTON_ROUNDS];
+  if ((int)blockIdx.x * RS_GROUPS >= nst) return;  // uniform over the CTA
+  const int nl = n.n_light;
+  const float4 *g_rec = reinterpret_cast<const float4 *>(n.rec32);
+  const float4 *g_cen = reinterpret_cast<const float4 *>(n.cen32);
+  const float4 *recs = g_rec, *cens = g_cen;
+  if (staged) {
+    float4 *sr = s_dyn, *sc = s_dyn + (size_t)nl * (REC32 / 4);
+    for (int i = threadIdx.x; i < nl * (REC32 / 4); i += RS_THREADS) sr[i] = g_rec[i];
+    for (int i = threadIdx.x; i < nl; i += RS_THREADS) sc[i] = g_cen[i];
+    __syncthreads();
+    recs = sr;
+    cens = sc;
+  }
+  const int g = threadIdx.x / RS_GROUP, tid = threadIdx.x % RS_GROUP, lane = tid & 31, w = tid >> 5;
+  int *next = &a.s.lcnt[LCNT - 1];  // the next straggler a group takes (groups that finish early take more)
+  for (;;) {
+    if (tid == 0) s_next[g] = atomicAdd(next, 1);
+    group_sync(g);
+    const int p = s_next[g];
+    group_sync(g);  // s_next is rewritten by the group's next fetch
+    if (p >= nst) break;  // uniform over the group
+    const int slot = lst[p] >> 2;
+    const CandCtx c = cand_ctx(a, n, slot);
+    const VarRecs &var = a.s.var[slot / IMG_CAP];
+    for (;;) {
+      const double X = a.s.hits[slot].tx, Y = a.s.hits[slot].ty;
+      const float hx = (float)X, lx = (float)(X - (double)hx), hy = (float)Y, ly = (float)(Y - (double)hy);
+      Acc<true, 1> tot, cmp, part;
+      tot.zero();
+      cmp.zero();
+      part.zero();
+      int seen = 0;
+      for (int j = tid; j < nl; j += RS_GROUP) {
+        const float4 cc = cens[j];
+        const float dY[1] = {(hy - cc.y) + (ly - cc.w)};
+        eval32_any<true, 1>(recs + (size_t)j * (REC32 / 4), (hx - cc.x) + (lx - cc.z), dY, part);
+        if (++seen == PE_SUB) {
+          fold(tot, cmp, part);
+          seen = 0;
+        }
+      }
+      if (tid >= RS_GROUP - 2) {  // the varying potentials join the FP32 sums
+        const int vv = tid - (RS_GROUP - 2);
+        const float dY[1] = {(float)(Y - ((double)var.cen[vv][1] + (double)var.cen[vv][3]))};
+        eval32_any<true, 1>(reinterpret_cast<const float4 *>(var.r32[vv]),
+                            (float)(X - ((double)var.cen[vv][0] + (double)var.cen[vv][2])), dY, part);
+      }
+      fold(tot, cmp, part);
+      // each thread's compensated sum as a float pair, summed over the group
+      // in double-float (FP32 pipe) in a fixed order: warp butterflies, then
+      // the group's warps in order
+      df v2[5] = {{tot.ax[0], -cmp.ax[0]}, {tot.ay[0], -cmp.ay[0]}, {tot.k[0], -cmp.k[0]},
+                  {tot.g1[0], -cmp.g1[0]}, {tot.g2[0], -cmp.g2[0]}};
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const df t = {__shfl_xor_sync(0xffffffffu, v2[q].hi, o), __shfl_xor_sync(0xffffffffu, v2[q].lo, o)};
+          v2[q] = df_add(v2[q], t);
+        }
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s_red[g][w][q] = make_float2(v2[q].hi, v2[q].lo);
+      group_sync(g);
+      if (tid == 0) {
+        double v[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          df t = {s_red[g][0][q].x, s_red[g][0][q].y};
+          for (int k = 1; k < RS_GWARPS; ++k) t = df_add(t, df{s_red[g][k][q].x, s_red[g][k][q].y});
+          v[q] = df_to_double(t);
+        }
+        for (int j = 0; j < n.n_heavy; ++j)  // static cluster-scale potentials (double-float)
+          add_potential_df<true>(n.heavydf + (size_t)j * RECDF, 1, n.heavy + (size_t)j * REC64, X, Y, v);
+        s_go[g] = newton_step(a, slot, c, v) ? 1 : 0;
+      }
+      group_sync(g);
+      const bool go = s_go[g] != 0;
+      group_sync(g);  // s_red and s_go are rewritten by the next step
+      if (!go) break;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ 4. dedup
 constexpr int DD_THREADS = 256;
 
@@ -1107,11 +1711,13 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
 
 }  // namespace
 
-size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch) { return layout(batch, c->nsrc).total; }
+size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch, bool lists) {
+  return layout(batch, c->nsrc, lists).total;
+}
 
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P, double *d_chi2,
                    int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st, double *d_images,
-                   int32_t img_max, int32_t *d_img_count) {
+                   int32_t img_max, int32_t *d_img_count, bool lists) {
   {
     // every caller (the entry points, the request loop, the allocation-free
     // path) passes through here: refuse what the kernels' fixed shared
@@ -1135,6 +1741,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   n.n_light = sm->n_light;
   for (int k = 0; k < 5; ++k) n.koff[k] = sm->koff[k];
   n.heavy = sm->heavy;
+  n.heavydf = sm->heavydf;
   n.n_heavy = sm->n_heavy;
   n.all64 = sm->all64;
   n.recdf = sm->recdf;
@@ -1147,6 +1754,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
   n.nx = gc->nx;
   n.gax = gc->alpha32;
   n.gay = gc->alpha32 + (size_t)gc->nx * gc->ny;
+  n.err = ctx->d_err;
   SearchArgs g;
   g.ax = gc->alpha32;
   g.ay = gc->alpha32 + (size_t)gc->nx * gc->ny;
@@ -1174,11 +1782,37 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
     a.type1 = c->var_type[1];
     a.nsrc = c->nsrc;
     a.nimg = c->nimg;
-    a.s = bufs(scratch, batch, c->nsrc);
+    a.s = bufs(scratch, batch, c->nsrc, lists);
     k_img_sources<<<a.B, SRC_THREADS, src_smem, st>>>(a, c->stat, c->x, c->y, c->ratio, c->src_of, c->img_off);
     dim3 sg((gc->nx - 1 + CT_X - 1) / CT_X, (gc->ny - 1 + CT_Y - 1) / CT_Y, a.B);
     k_img_search<<<sg, SEARCH_THREADS, 0, st>>>(a, g);
-    k_img_newton<<<dim3(IMG_CAP / RF_CAND, a.B), RF_THREADS, 0, st>>>(a, n);
+    if (LENS_REFINE_LISTS && lists) {
+      // step 3 as point lists: the list counters, the initial triangles,
+      // one evaluation + decision pair per subdivision level and Newton
+      // round (the grids of the evaluations cover the largest lists; CTAs
+      // past a list's end return at once), the stragglers
+      if (cudaMemsetAsync(a.s.lcnt, 0, LCNT * sizeof(int), st) != cudaSuccess)
+        return fail(LENS_ECUDA, "cudaMemsetAsync failed");
+      k_ref_init<<<dim3((IMG_CAP + RL_THREADS - 1) / RL_THREADS, a.B), RL_THREADS, 0, st>>>(a, n);
+      const size_t N = (size_t)a.B * IMG_CAP;
+      const unsigned gsub = (unsigned)((3 * N + pe_points(false) - 1) / pe_points(false));
+      const unsigned gnew = (unsigned)((N + pe_points(true) - 1) / pe_points(true));
+      for (int lev = 0; lev < SUBDIV_LEVELS; ++lev) {
+        k_pts_eval<false><<<gsub, PE_THREADS, 0, st>>>(a, n, a.s.lst + ((lev & 1) ? 3 * N : 0), a.s.lcnt + lev);
+        k_ref_level<<<4 * nsm, RL_THREADS, 0, st>>>(a, n, lev);
+      }
+      for (int r = 0; r < NEWTON_ROUNDS; ++r) {
+        k_pts_eval<true><<<gnew, PE_THREADS, 0, st>>>(a, n, a.s.lst + (6 + (r & 1)) * N,
+                                                      a.s.lcnt + SUBDIV_LEVELS + r);
+        k_ref_newton<<<4 * nsm, RL_THREADS, 0, st>>>(a, n, r);
+      }
+      const size_t rs_smem = straggle_smem(sm->n_light);
+      const int staged = rs_smem <= RS_SMEM_MAX;
+      if (staged) cudaFuncSetAttribute(k_ref_straggle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM_MAX);
+      k_ref_straggle<<<nsm, RS_THREADS, staged ? rs_smem : 0, st>>>(a, n, staged);
+    } else {
+      k_img_newton<<<dim3(IMG_CAP / RF_CAND, a.B), RF_THREADS, 0, st>>>(a, n);
+    }
     k_img_dedup<<<a.B, DD_THREADS, 0, st>>>(a);
     k_img_polish<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
     k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err,

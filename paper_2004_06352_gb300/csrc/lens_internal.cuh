@@ -226,6 +226,7 @@ struct Model {
   double *heavy = nullptr;
   double *all64 = nullptr;
   float2 *recdf = nullptr;  // [RECDF][n] double-float records, field-major, upload order (image polish)
+  float2 *heavydf = nullptr;  // [n_heavy][RECDF] double-float records of the heavy potentials (image refinement)
   std::vector<lens_halo> host;
   size_t bytes = 0;
 };
@@ -394,7 +395,8 @@ int autotune_chi2_source(lens_ctx *ctx, CSet *c, const double *d_params, int32_t
 int launch_chi2_image(lens_ctx *ctx, const Model *m, CSet *c, const lens_grid *g, const double *d_params, int32_t P,
                       double *d_chi2, int32_t *d_nfound, cudaStream_t st, double *d_images = nullptr,
                       int32_t img_max = 0, int32_t *d_img_count = nullptr);
-size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch);
+// lists = false: the smaller scratch of the single-kernel refinement
+size_t chi2_image_scratch_bytes(const CSet *c, int32_t batch, bool lists = true);
 // Limits of the image-plane chi2 kernels: sources per constraint set (the
 // image search keeps every source of a distance group in fixed shared
 // arrays) and the dynamic shared memory of the back-trace kernel.
@@ -408,7 +410,8 @@ const GridCache *find_grid_cache(const CSet *c, const lens_grid *g);
 int build_grid_cache(lens_ctx *ctx, CSet *c, const lens_grid *g, cudaStream_t st);
 int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_params, int32_t P,
                    double *d_chi2, int32_t *d_nfound, void *scratch, int32_t batch, cudaStream_t st,
-                   double *d_images = nullptr, int32_t img_max = 0, int32_t *d_img_count = nullptr);
+                   double *d_images = nullptr, int32_t img_max = 0, int32_t *d_img_count = nullptr,
+                   bool lists = true);
 
 // device error word bits (read and cleared by lens_wait)
 constexpr int ERRBIT_WAIT = 1;

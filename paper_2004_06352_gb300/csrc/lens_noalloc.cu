@@ -71,13 +71,17 @@ extern "C" int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const le
   // the static deflection of this grid, then the candidate buffers of a
   // batch of parameter sets; the batch shrinks until both fit
   const size_t grid_bytes = align256(2 * sizeof(float) * (size_t)grid->nx * grid->ny);
+  // (the point-list refinement's state while one set of it fits, else the
+  // single-kernel refinement's smaller buffers)
+  const bool lists = grid_bytes + chi2_image_scratch_bytes(c, 1, true) <= LENS_NOALLOC_SCRATCH_BYTES;
   int32_t batch = std::min<int32_t>(NOALLOC_MAX_BATCH, P);
-  while (batch > 1 && grid_bytes + chi2_image_scratch_bytes(c, batch) > LENS_NOALLOC_SCRATCH_BYTES) batch /= 2;
-  if (grid_bytes + chi2_image_scratch_bytes(c, batch) > LENS_NOALLOC_SCRATCH_BYTES)
+  while (batch > 1 && grid_bytes + chi2_image_scratch_bytes(c, batch, lists) > LENS_NOALLOC_SCRATCH_BYTES) batch /= 2;
+  if (grid_bytes + chi2_image_scratch_bytes(c, batch, lists) > LENS_NOALLOC_SCRATCH_BYTES)
     return fail(LENS_EINVAL,
                 "grid %d x %d needs %zu bytes of fixed scratch (plus %zu for one parameter set); the maximum is %zu "
                 "bytes (LENS_NOALLOC_SCRATCH_BYTES)",
-                grid->nx, grid->ny, grid_bytes, chi2_image_scratch_bytes(c, 1), (size_t)LENS_NOALLOC_SCRATCH_BYTES);
+                grid->nx, grid->ny, grid_bytes, chi2_image_scratch_bytes(c, 1, false),
+                (size_t)LENS_NOALLOC_SCRATCH_BYTES);
   if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(LENS_ECUDA, "cudaSetDevice(%d) failed", ctx->device);
   void *base = nullptr;
   if ((rc = scratch_address(ctx->device, &base))) return rc;
@@ -97,5 +101,6 @@ extern "C" int lens_chi2_image_noalloc(lens_ctx *ctx, lens_cset_t cset, const le
   } else if (cudaMemsetAsync(gc.alpha32, 0, 2 * sizeof(float) * (size_t)grid->nx * grid->ny, st) != cudaSuccess) {
     return fail(LENS_ECUDA, "clearing the static deflection failed");
   }
-  return run_chi2_image(ctx, c, &gc, d_params, P, d_chi2, d_nimg_found, (char *)base + grid_bytes, batch, st);
+  return run_chi2_image(ctx, c, &gc, d_params, P, d_chi2, d_nimg_found, (char *)base + grid_bytes, batch, st,
+                        nullptr, 0, nullptr, lists);
 }
