@@ -1211,6 +1211,9 @@ __device__ __forceinline__ void add_potential_df(const float2 *__restrict__ rdf,
   }
 }
 
+#ifndef LENS_SRC_UNROLL_V
+#define LENS_SRC_UNROLL_V 0  // 1: both evaluations inlined side by side (0.363 -> 0.41 ms: the code outgrows the caches)
+#endif
 #ifndef LENS_DF_PAIRED
 #define LENS_DF_PAIRED 0  // 1: the two varying potentials side by side (dpie_df2): measured 30 % slower
 #endif
@@ -1239,7 +1242,11 @@ __device__ __forceinline__ void add_varying_df(const float2 *__restrict__ rdf, c
   df2 pax, pay, ph[3];
   if (LENS_DF_PAIRED && rdf[F_U2].x >= 0.f && rdf[RECDF + F_U2].x >= 0.f)
     dpie_df2<HESS>(rdf, rdf + RECDF, 1, Xd, Yd, pax, pay, ph, pok);
+#if LENS_SRC_UNROLL_V
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
   for (int v = 0; v < 2; ++v) {  // not unrolled: one copy of the (large) evaluator in the code
     const float2 *r = rdf + v * RECDF;
     df ax, ay, h[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -1284,7 +1291,7 @@ __device__ __forceinline__ void add_varying_df(const float2 *__restrict__ rdf, c
 // s_bary [nsrc][2] and, when s_m is not NULL, r H at every image in
 // s_m [nimg][3] (hxx, hyy, hxy).  Must be called by all THREADS threads of
 // the CTA; ends synchronised.
-template <int THREADS>
+template <int THREADS, int HESS = -1>
 __device__ __forceinline__ void backtrace_set(const double *__restrict__ stat, const double *__restrict__ x,
                                               const double *__restrict__ y, const double *__restrict__ ratio,
                                               const int32_t *__restrict__ src_of, const int32_t *__restrict__ img_off,
@@ -1295,7 +1302,7 @@ __device__ __forceinline__ void backtrace_set(const double *__restrict__ stat, c
     const double *st = stat + (size_t)j * 5;
     double acc[5] = {st[0], st[1], st[2], st[3], st[4]};
     if (s_rdf) {
-      if (s_m)
+      if (HESS == 1 || (HESS < 0 && s_m))
         add_varying_df<true>(s_rdf, s_rec, X, Y, acc);
       else
         add_varying_df<false>(s_rdf, s_rec, X, Y, acc);
