@@ -25,7 +25,8 @@ DEV = "cuda:0"
 def test_noalloc_matches_allocating_entry_point_twice(lens, n):
     """256^2: the 12 sets in one batch.  1400^2: the grid's static
     deflection takes 15.7 MB of the 16 MiB array, so the batch halves from 12
-    to 3 sets and the call runs four batches through the space left."""
+    to a single set (~1.0 MB of candidate buffers and refinement lists) and
+    the call runs twelve batches through the space left."""
     m = I.cfg2_model()
     cons = make_constraints.load()
     var = (0, 1)
