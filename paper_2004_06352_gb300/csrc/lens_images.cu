@@ -1029,6 +1029,12 @@ __global__ void __launch_bounds__(RF_THREADS, LENS_NEWTON_MINB) k_img_newton(con
 #ifndef LENS_REFINE_LISTS
 #define LENS_REFINE_LISTS 1
 #endif
+// The refinement's Newton steps solve their 2 x 2 systems in FP32 (1:
+// 13.11 -> 12.93 ms per 256 sets, the stragglers' steps being chains of
+// FP64 divisions and roots), the residual staying in FP64
+#ifndef LENS_NEWTON_STEP32
+#define LENS_NEWTON_STEP32 1
+#endif
 constexpr int PE_THREADS = 128, PE_CH = 64, PE_SUB = 16;
 #ifndef LENS_PE_MINB_GRAD
 #define LENS_PE_MINB_GRAD 4
@@ -1414,15 +1420,53 @@ __global__ void __launch_bounds__(RL_THREADS) k_ref_level(const SetArgs a, const
 }
 
 // One Newton step of a candidate from its evaluation o (alpha, kappa, gamma1,
-// gamma2 at (tx, ty)): k_img_newton's step, limited to one cell.  Returns
-// true while the candidate iterates; otherwise its status is final.
-__device__ __forceinline__ bool newton_step(const SetArgs &a, int slot, const CandCtx &c, const double *o) {
-  Ref &R = a.s.ref[slot];
+// gamma2 at (tx, ty)): k_img_newton's step, limited to one cell; tx, ty
+// and the step counters are the caller's (the hit receives the position,
+// r H and, at the end, the status).  Returns true while the candidate
+// iterates; otherwise its status is final.
+__device__ __forceinline__ bool newton_step(const SetArgs &a, int slot, const CandCtx &c, const double *o, double &tx,
+                                            double &ty, int &nit, int &settled) {
   Hit &h = a.s.hits[slot];
-  double tx = h.tx, ty = h.ty;
   int status = ST_FAILED;
   bool active = true;
   const double fx = c.P[0] - (tx - c.r * o[0]), fy = c.P[1] - (ty - c.r * o[1]);
+#if LENS_NEWTON_STEP32
+  // the residual in FP64 (it is a small difference of large numbers), the
+  // 2 x 2 solve in FP32: the step needs only FP32's relative precision, and
+  // a chain of FP64 divisions and roots is slow on this GPU's FP64 unit
+  const float rf = (float)c.r, k = (float)o[2], g1 = (float)o[3], g2 = (float)o[4];
+  const float m11 = rf * (k + g1), m22 = rf * (k - g1), m12 = rf * g2;
+  const float a11 = 1.f - m11, a22 = 1.f - m22, a12 = -m12;
+  const float det = a11 * a22 - a12 * a12;
+  if (!(det != 0.f) || !isfinite(det)) {
+    active = false;
+  } else {
+    const float fxf = (float)fx, fyf = (float)fy, idet = 1.f / det;
+    float dx = (a22 * fxf - a12 * fyf) * idet, dy = (a11 * fyf - a12 * fxf) * idet;
+    const float len = sqrtf(dx * dx + dy * dy), smax = (float)c.step_max;
+    if (len > smax) {
+      dx *= smax / len;
+      dy *= smax / len;
+    }
+    tx += (double)dx;
+    ty += (double)dy;
+    h.tx = tx;
+    h.ty = ty;
+    h.h11 = m11;
+    h.h22 = m22;
+    h.h12 = m12;
+    if (!isfinite(tx) || !isfinite(ty)) {
+      active = false;
+    } else if (len < (float)NEWTON32_TOL && ++settled > LENS_NEWTON_EXTRA) {
+      status = ST_NEWTON;
+      active = false;
+    }
+  }
+  if (active && ++nit < NEWTON_MAXIT) return true;
+  if (status == ST_NEWTON && hypotf((float)(tx - h.cx), (float)(ty - h.cy)) > (float)c.local) status = ST_FAR;
+  h.status = status;
+  return false;
+#else
   const double m11 = c.r * (o[2] + o[3]), m22 = c.r * (o[2] - o[3]), m12 = c.r * o[4];
   const double a11 = 1.0 - m11, a22 = 1.0 - m22, a12 = -m12;
   const double det = a11 * a22 - a12 * a12;
@@ -1444,16 +1488,17 @@ __device__ __forceinline__ bool newton_step(const SetArgs &a, int slot, const Ca
     h.h12 = (float)m12;
     if (!isfinite(tx) || !isfinite(ty)) {
       active = false;
-    } else if (len < NEWTON32_TOL && ++R.settled > LENS_NEWTON_EXTRA) {
+    } else if (len < NEWTON32_TOL && ++settled > LENS_NEWTON_EXTRA) {
       status = ST_NEWTON;
       active = false;
     }
   }
-  if (active && ++R.nit < NEWTON_MAXIT) return true;
+  if (active && ++nit < NEWTON_MAXIT) return true;
   // a root far from its triangle belongs to another triangle's search
   if (status == ST_NEWTON && hypot(tx - h.cx, ty - h.cy) > c.local) status = ST_FAR;
   h.status = status;
   return false;
+#endif
 }
 
 // Newton round `round` after its points were evaluated: a step per
@@ -1470,7 +1515,13 @@ __global__ void __launch_bounds__(RL_THREADS) k_ref_newton(const SetArgs a, cons
   for (int p = blockIdx.x * RL_THREADS + threadIdx.x; p < npts; p += gridDim.x * RL_THREADS) {
     const int slot = lst[p] >> 2;
     const CandCtx c = cand_ctx(a, n, slot);
-    if (newton_step(a, slot, c, a.s.ref[slot].mo)) nxt[atomicAdd(ncnt, 1)] = slot << 2 | 3;
+    Ref &R = a.s.ref[slot];
+    double tx = a.s.hits[slot].tx, ty = a.s.hits[slot].ty;
+    int nit = R.nit, settled = R.settled;
+    const bool go = newton_step(a, slot, c, R.mo, tx, ty, nit, settled);
+    R.nit = nit;
+    R.settled = settled;
+    if (go) nxt[atomicAdd(ncnt, 1)] = slot << 2 | 3;
   }
 }
 
@@ -1494,6 +1545,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_ref_straggle(const SetArgs a, co
   extern __shared__ __align__(16) float4 s_dyn[];
   __shared__ float2 s_red[RS_GROUPS][RS_GWARPS][5];
   __shared__ int s_go[RS_GROUPS], s_next[RS_GROUPS];
+  __shared__ double s_pos[RS_GROUPS][2];                         // the candidate's position
+  __shared__ __align__(16) float s_var[RS_GROUPS][2][REC32 + 4];  // its varying potentials' FP32 records + centres
   const size_t N = (size_t)a.B * IMG_CAP;
   const int *lst = a.s.lst + 8 * N;
   const int nst = a.s.lcnt[SUBDIV_LEVELS + NEWTON_ROUNDS];
@@ -1501,14 +1554,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_ref_straggle(const SetArgs a, co
   const int nl = n.n_light;
   const float4 *g_rec = reinterpret_cast<const float4 *>(n.rec32);
   const float4 *g_cen = reinterpret_cast<const float4 *>(n.cen32);
-  const float4 *recs = g_rec, *cens = g_cen;
   if (staged) {
     float4 *sr = s_dyn, *sc = s_dyn + (size_t)nl * (REC32 / 4);
     for (int i = threadIdx.x; i < nl * (REC32 / 4); i += RS_THREADS) sr[i] = g_rec[i];
     for (int i = threadIdx.x; i < nl; i += RS_THREADS) sc[i] = g_cen[i];
     __syncthreads();
-    recs = sr;
-    cens = sc;
   }
   const int g = threadIdx.x / RS_GROUP, tid = threadIdx.x % RS_GROUP, lane = tid & 31, w = tid >> 5;
   int *next = &a.s.lcnt[LCNT - 1];  // the next straggler a group takes (groups that finish early take more)
@@ -1521,28 +1571,54 @@ __global__ void __launch_bounds__(RS_THREADS) k_ref_straggle(const SetArgs a, co
     const int slot = lst[p] >> 2;
     const CandCtx c = cand_ctx(a, n, slot);
     const VarRecs &var = a.s.var[slot / IMG_CAP];
+    // the iteration state lives on chip: thread 0 keeps the counters, the
+    // group reads the position and the varying records from shared memory
+    double tx = 0.0, ty = 0.0;
+    int nit = 0, settled = 0;
+    if (tid == 0) {
+      tx = a.s.hits[slot].tx;
+      ty = a.s.hits[slot].ty;
+      nit = a.s.ref[slot].nit;
+      settled = a.s.ref[slot].settled;
+      s_pos[g][0] = tx;
+      s_pos[g][1] = ty;
+    }
+    for (int i = tid; i < 2 * (REC32 + 4); i += RS_GROUP) {
+      const int v = i / (REC32 + 4), k = i % (REC32 + 4);
+      s_var[g][v][k] = k < REC32 ? var.r32[v][k] : var.cen[v][k - REC32];
+    }
+    group_sync(g);
     for (;;) {
-      const double X = a.s.hits[slot].tx, Y = a.s.hits[slot].ty;
+      const double X = s_pos[g][0], Y = s_pos[g][1];
       const float hx = (float)X, lx = (float)(X - (double)hx), hy = (float)Y, ly = (float)(Y - (double)hy);
       Acc<true, 1> tot, cmp, part;
       tot.zero();
       cmp.zero();
       part.zero();
       int seen = 0;
-      for (int j = tid; j < nl; j += RS_GROUP) {
-        const float4 cc = cens[j];
-        const float dY[1] = {(hy - cc.y) + (ly - cc.w)};
-        eval32_any<true, 1>(recs + (size_t)j * (REC32 / 4), (hx - cc.x) + (lx - cc.z), dY, part);
-        if (++seen == PE_SUB) {
-          fold(tot, cmp, part);
-          seen = 0;
+      // the static potentials: from the staged copy through shared-memory
+      // loads (a pointer that may be either would compile to generic loads)
+      auto sweep = [&](const float4 *rc, const float4 *cn) {
+        for (int j = tid; j < nl; j += RS_GROUP) {
+          const float4 cc = cn[j];
+          const float dY[1] = {(hy - cc.y) + (ly - cc.w)};
+          eval32_any<true, 1>(rc + (size_t)j * (REC32 / 4), (hx - cc.x) + (lx - cc.z), dY, part);
+          if (++seen == PE_SUB) {
+            fold(tot, cmp, part);
+            seen = 0;
+          }
         }
-      }
+      };
+      if (staged)
+        sweep(s_dyn, s_dyn + (size_t)nl * (REC32 / 4));
+      else
+        sweep(g_rec, g_cen);
       if (tid >= RS_GROUP - 2) {  // the varying potentials join the FP32 sums
         const int vv = tid - (RS_GROUP - 2);
-        const float dY[1] = {(float)(Y - ((double)var.cen[vv][1] + (double)var.cen[vv][3]))};
-        eval32_any<true, 1>(reinterpret_cast<const float4 *>(var.r32[vv]),
-                            (float)(X - ((double)var.cen[vv][0] + (double)var.cen[vv][2])), dY, part);
+        const float *cv = &s_var[g][vv][REC32];
+        const float dY[1] = {(float)(Y - ((double)cv[1] + (double)cv[3]))};
+        eval32_any<true, 1>(reinterpret_cast<const float4 *>(&s_var[g][vv][0]),
+                            (float)(X - ((double)cv[0] + (double)cv[2])), dY, part);
       }
       fold(tot, cmp, part);
       // each thread's compensated sum as a float pair, summed over the group
@@ -1571,11 +1647,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_ref_straggle(const SetArgs a, co
         }
         for (int j = 0; j < n.n_heavy; ++j)  // static cluster-scale potentials (double-float)
           add_potential_df<true>(n.heavydf + (size_t)j * RECDF, 1, n.heavy + (size_t)j * REC64, X, Y, v);
-        s_go[g] = newton_step(a, slot, c, v) ? 1 : 0;
+        const bool more = newton_step(a, slot, c, v, tx, ty, nit, settled);
+        s_pos[g][0] = tx;
+        s_pos[g][1] = ty;
+        s_go[g] = more ? 1 : 0;
+        if (!more) {
+          a.s.ref[slot].nit = nit;
+          a.s.ref[slot].settled = settled;
+        }
       }
       group_sync(g);
       const bool go = s_go[g] != 0;
-      group_sync(g);  // s_red and s_go are rewritten by the next step
+      group_sync(g);  // s_red, s_go and s_pos are rewritten by the next step
       if (!go) break;
     }
   }
