@@ -1732,9 +1732,11 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
     const double r = n.ratio[src];
     const double bx = a.s.bary[((size_t)b * a.nsrc + src) * 2], by = a.s.bary[((size_t)b * a.nsrc + src) * 2 + 1];
     const double a11 = 1.0 - h->h11, a22 = 1.0 - h->h22, a12 = -h->h12;
-    const double det = a11 * a22 - a12 * a12;
-    double tx = h->tx, ty = h->ty, step = 1e30;
-    for (int it = 0; it < POLISH_MAXIT && step >= POLISH_TOL; ++it) {
+    const double det = a11 * a22 - a12 * a12, idet = 1.0 / det;
+    // (steps compared squared: no FP64 root or division in the iteration,
+    // whose FP64 tail is a serial chain on this GPU's narrow FP64 unit)
+    double tx = h->tx, ty = h->ty, step2 = 1e60;
+    for (int it = 0; it < POLISH_MAXIT && step2 >= POLISH_TOL * POLISH_TOL; ++it) {
       // alpha(tx, ty): dPIE terms inside the polynomial range in
       // double-float; the rest (cores: |w|^2 >= 0.16, SIS, point masses)
       // queued and evaluated 32 at a time, so the warp stays converged, by
@@ -1794,15 +1796,15 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
       sx = warp_sum(sx + df_to_double(fx));
       sy = warp_sum(sy + df_to_double(fy));
       const double fxr = bx - (tx - r * sx), fyr = by - (ty - r * sy);
-      const double dx = (a22 * fxr - a12 * fyr) / det, dy = (a11 * fyr - a12 * fxr) / det;
+      const double dx = (a22 * fxr - a12 * fyr) * idet, dy = (a11 * fyr - a12 * fxr) * idet;
       tx += dx;
       ty += dy;
-      step = sqrt(dx * dx + dy * dy);
+      step2 = dx * dx + dy * dy;
     }
     if (lane == 0) {
       h->tx = tx;
       h->ty = ty;
-      h->status = (step < ACCEPT_TOL && isfinite(tx) && isfinite(ty)) ? ST_FINAL : ST_NO_POLISH;
+      h->status = (step2 < ACCEPT_TOL * ACCEPT_TOL && isfinite(tx) && isfinite(ty)) ? ST_FINAL : ST_NO_POLISH;
     }
     __syncwarp();
   }

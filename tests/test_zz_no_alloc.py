@@ -65,3 +65,33 @@ def test_noalloc_rejects_grid_beyond_fixed_scratch(lens):
             ctx.chi2_image_noalloc(cs, I.grid(2048), params, 1, out)   # 32 MiB of node deflections
         assert e.value.code == lens.LENS_EINVAL
         assert "LENS_NOALLOC_SCRATCH_BYTES" in str(e.value)
+
+
+def test_noalloc_single_kernel_refinement_matches_oracle(lens):
+    """1420^2: the grid's static deflection takes 16.13 MB of the 16 MiB
+    array, which leaves room for one set's candidate buffers (~0.22 MB) but
+    not for the point-list refinement's (~1.0 MB): the call refines with the
+    single-kernel Newton.  Its image counts and chi2 must agree with the
+    oracle's (Sec. 2.2 Eq. 6, Sec. 2.3) where the image sets agree, for at
+    least one of the two sets, and image counts may differ only rarely."""
+    import oracle
+    m = I.cfg2_model()
+    cons = make_constraints.load()
+    var = (0, 1)
+    g = I.grid(1420)
+    params = I.perturbed_params(m, var, 2, seed=63)
+    params[0] = I.var_params_of(m, var)
+    ref, nf_ref = oracle.chi2_image_batch(m, cons, g, var, params)
+    nsrc = len(cons["img_off"]) - 1
+    with lens.Context(0) as ctx:
+        cs = ctx.cset_create(ctx.model_upload(m), cons, var)
+        got = torch.full((2,), -1.0, dtype=torch.float64, device=DEV)
+        nf = torch.full((2, nsrc), -7, dtype=torch.int32, device=DEV)
+        ctx.chi2_image_noalloc(cs, g, torch.tensor(params, dtype=torch.float64, device=DEV), 2, got, nf)
+        ctx.wait()
+        got, nf = got.cpu().numpy(), nf.cpu().numpy()
+    assert np.abs(nf - nf_ref).sum() <= 0.01 * nf_ref.sum(), (nf - nf_ref)
+    same = [p for p in range(2) if np.array_equal(nf[p], nf_ref[p])]
+    assert same, "no parameter set had the oracle's image counts"
+    for p in same:
+        assert abs(got[p] - ref[p]) <= T.CHI2_REL * abs(ref[p]), (p, got[p], ref[p])
