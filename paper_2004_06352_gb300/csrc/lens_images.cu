@@ -1812,11 +1812,12 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
 
 // ------------------------------------------------------------- 6. match, chi2
 constexpr int C2_THREADS = 128;
+constexpr int C2_LIST = 128, C2_KEEP = 16;  // polished images listed, kept positions held, per source
 
 __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const double *__restrict__ x,
                                                          const double *__restrict__ y,
                                                          const double *__restrict__ sigma,
-                                                         const int32_t *__restrict__ src_of, double *chi2,
+                                                         const int32_t *__restrict__ img_off, double *chi2,
                                                          int32_t *nfound, int *err, double *images, int img_max,
                                                          int32_t *img_count) {
   __shared__ double s_red[C2_THREADS / 32];
@@ -1838,18 +1839,85 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
   // Final images: polished, and not within DEDUP of an earlier final image of
   // the same source (candidates of one highly magnified image can end the
   // FP32 Newton further apart than DEDUP and meet only after the polish).
+  // Each image's source is staged (-1: not polished); a thread per source
+  // collects its images' indices in candidate order (a scan without global
+  // loads; up to C2_LIST of them), keeps those not within DEDUP of one it
+  // already kept -- the rule of the definition's image search -- counts
+  // them and matches its constraints to them (the first C2_KEEP kept
+  // positions held by the thread, any further ones re-read).  A source with
+  // more than C2_LIST polished images re-scans the staged sources instead.
   __shared__ unsigned char s_use[IMG_CAP];
+  __shared__ int s_isrc[IMG_CAP];
   for (int u = threadIdx.x; u < nu; u += C2_THREADS) {
     const Hit &h = hits[uniq[u]];
-    bool use = h.status == ST_FINAL;
-    for (int v = 0; v < u && use; ++v) {
-      const Hit &g = hits[uniq[v]];
-      const double ex = g.tx - h.tx, ey = g.ty - h.ty;
-      if (g.status == ST_FINAL && g.src == h.src && ex * ex + ey * ey < DEDUP * DEDUP) use = false;
-    }
-    s_use[u] = use;
+    s_isrc[u] = h.status == ST_FINAL ? h.src : -1;
+    s_use[u] = 0;
   }
   __syncthreads();
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) {
+    int lst[C2_LIST];
+    int nl = 0;
+    for (int u = 0; u < nu; ++u)
+      if (s_isrc[u] == i) {
+        if (nl < C2_LIST) lst[nl] = u;
+        ++nl;
+      }
+    const bool listed = nl <= C2_LIST;
+    const int nc = listed ? nl : nu;  // candidates walked: the list, or every staged image
+    auto cand = [&](int k) { return listed ? lst[k] : k; };
+    double kx[C2_KEEP], ky[C2_KEEP];
+    int nk = 0;
+    auto near_kept = [&](double tx, double ty, int before) {  // within DEDUP of a kept image?
+      for (int k = 0; k < nk && k < C2_KEEP; ++k) {
+        const double ex = kx[k] - tx, ey = ky[k] - ty;
+        if (ex * ex + ey * ey < DEDUP * DEDUP) return true;
+      }
+      if (nk > C2_KEEP)  // kept images past the first C2_KEEP
+        for (int k = 0, seen = 0; k < before; ++k) {
+          const int v = cand(k);
+          if (s_isrc[v] != i || !s_use[v] || ++seen <= C2_KEEP) continue;
+          const double ex = hits[uniq[v]].tx - tx, ey = hits[uniq[v]].ty - ty;
+          if (ex * ex + ey * ey < DEDUP * DEDUP) return true;
+        }
+      return false;
+    };
+    for (int k = 0; k < nc; ++k) {
+      const int u = cand(k);
+      if (s_isrc[u] != i) continue;
+      const Hit &h = hits[uniq[u]];
+      if (near_kept(h.tx, h.ty, k)) continue;
+      s_use[u] = 1;
+      if (nk < C2_KEEP) {
+        kx[nk] = h.tx;
+        ky[nk] = h.ty;
+      }
+      ++nk;
+    }
+    if (nfound) nfound[(size_t)p * a.nsrc + i] = overflow ? -1 : nk;
+    // each constraint of the source: the nearest kept image (ties: lower y,
+    // then lower x)
+    for (int j = img_off[i]; j < img_off[i + 1]; ++j) {
+      double best = INFINITY, bx = 0.0, by = 0.0;
+      auto consider = [&](double tx, double ty) {
+        const double ex = x[j] - tx, ey = y[j] - ty, d2 = ex * ex + ey * ey;
+        if (d2 < best || (d2 == best && (ty < by || (ty == by && tx < bx)))) {
+          best = d2;
+          bx = tx;
+          by = ty;
+        }
+      };
+      for (int k = 0; k < nk && k < C2_KEEP; ++k) consider(kx[k], ky[k]);
+      if (nk > C2_KEEP)
+        for (int k = 0, seen = 0; k < nc; ++k) {
+          const int v = cand(k);
+          if (s_isrc[v] != i || !s_use[v] || ++seen <= C2_KEEP) continue;
+          consider(hits[uniq[v]].tx, hits[uniq[v]].ty);
+        }
+      acc[0] += best / (sigma[j] * sigma[j]);  // no image of this source: +inf -> NaN below
+    }
+  }
+  __syncthreads();  // s_use complete
   if (images && threadIdx.x == 0) {  // predicted images, in candidate order
     int c = 0;
     for (int u = 0; u < nu; ++u) {
@@ -1864,28 +1932,6 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
       ++c;
     }
     img_count[p] = overflow ? -1 : c;
-  }
-  if (nfound)
-    for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) {
-      int c = 0;
-      for (int u = 0; u < nu; ++u) c += (s_use[u] && hits[uniq[u]].src == i);
-      nfound[(size_t)p * a.nsrc + i] = overflow ? -1 : c;
-    }
-  double acc[1] = {0.0};
-  for (int j = threadIdx.x; j < a.nimg; j += C2_THREADS) {
-    const int i = src_of[j];
-    double best = INFINITY, bx = 0.0, by = 0.0;
-    for (int u = 0; u < nu; ++u) {
-      const Hit &h = hits[uniq[u]];
-      if (!s_use[u] || h.src != i) continue;
-      const double ex = x[j] - h.tx, ey = y[j] - h.ty, d2 = ex * ex + ey * ey;
-      if (d2 < best || (d2 == best && (h.ty < by || (h.ty == by && h.tx < bx)))) {
-        best = d2;
-        bx = h.tx;
-        by = h.ty;
-      }
-    }
-    acc[0] += best / (sigma[j] * sigma[j]);  // no image of this source: +inf -> NaN below
   }
   block_sum<1, C2_THREADS>(acc, s_red);
   if (threadIdx.x == 0) {
@@ -2000,7 +2046,7 @@ int run_chi2_image(lens_ctx *ctx, CSet *c, const GridCache *gc, const double *d_
     }
     k_img_dedup<<<a.B, DD_THREADS, 0, st>>>(a);
     k_img_polish<<<nsm * 8, NW_THREADS, 0, st>>>(a, n);
-    k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->src_of, d_chi2, d_nfound, ctx->d_err,
+    k_img_chi2<<<a.B, C2_THREADS, 0, st>>>(a, c->x, c->y, c->sigma, c->img_off, d_chi2, d_nfound, ctx->d_err,
                                            d_images, img_max, d_img_count);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LENS_ECUDA, "image-plane chi2 launch: %s", cudaGetErrorString(e));
