@@ -1665,34 +1665,93 @@ __global__ void __launch_bounds__(RS_THREADS) k_ref_straggle(const SetArgs a, co
 }
 
 // ------------------------------------------------------------------ 4. dedup
+// The walk of one source's candidates in candidate order that keeps those
+// not within DEDUP of a candidate it already kept (the definition's rule for
+// the images it finds).  s_src[u] is candidate u's source (-1: not taken);
+// pos(u, x, y) its position; kept candidates get s_flag[u] = 1.  Up to
+// KW_LIST candidates are listed first (a scan of shared memory only); the
+// first KW_KEEP kept positions are held in w.kx, w.ky, later ones re-read.
+constexpr int KW_LIST = 128, KW_KEEP = 16;
+struct KeepWalk {
+  int lst[KW_LIST];
+  double kx[KW_KEEP], ky[KW_KEEP];
+  int nl, nc, nk;
+  bool listed;
+  __device__ __forceinline__ int cand(int k) const { return listed ? lst[k] : k; }
+};
+template <class Pos>
+__device__ __forceinline__ void keep_walk(KeepWalk &w, int i, int n, const int *s_src, unsigned char *s_flag,
+                                          Pos pos) {
+  w.nl = 0;
+  for (int u = 0; u < n; ++u)
+    if (s_src[u] == i) {
+      if (w.nl < KW_LIST) w.lst[w.nl] = u;
+      ++w.nl;
+    }
+  w.listed = w.nl <= KW_LIST;
+  w.nc = w.listed ? w.nl : n;  // candidates walked: the list, or every staged one
+  w.nk = 0;
+  for (int k = 0; k < w.nc; ++k) {
+    const int u = w.cand(k);
+    if (s_src[u] != i) continue;
+    double tx, ty;
+    pos(u, tx, ty);
+    bool near = false;
+    for (int q = 0; q < w.nk && q < KW_KEEP && !near; ++q) {
+      const double ex = w.kx[q] - tx, ey = w.ky[q] - ty;
+      near = ex * ex + ey * ey < DEDUP * DEDUP;
+    }
+    if (w.nk > KW_KEEP)  // kept candidates past the first KW_KEEP
+      for (int q = 0, seen = 0; q < k && !near; ++q) {
+        const int v = w.cand(q);
+        if (s_src[v] != i || !s_flag[v] || ++seen <= KW_KEEP) continue;
+        double vx, vy;
+        pos(v, vx, vy);
+        const double ex = vx - tx, ey = vy - ty;
+        near = ex * ex + ey * ey < DEDUP * DEDUP;
+      }
+    if (near) continue;
+    s_flag[u] = 1;
+    if (w.nk < KW_KEEP) {
+      w.kx[w.nk] = tx;
+      w.ky[w.nk] = ty;
+    }
+    ++w.nk;
+  }
+}
+
 constexpr int DD_THREADS = 256;
 
+// Candidates that reached a root: a thread per source keeps, in candidate
+// order, those not within DEDUP of one it kept (keep_walk); the kept ones'
+// indices are then compacted in candidate order.
 __global__ void __launch_bounds__(DD_THREADS) k_img_dedup(const SetArgs a) {
   __shared__ int s_scan[DD_THREADS];
   __shared__ int s_base;
+  __shared__ int s_isrc[IMG_CAP];
+  __shared__ unsigned char s_keep[IMG_CAP];
   const int b = blockIdx.x;
   if (!a.s.valid[b]) return;
   const int n = min(a.s.cnt[b], IMG_CAP);
   const Hit *hits = a.s.hits + (size_t)b * IMG_CAP;
   int *uniq = a.s.uniq + (size_t)b * IMG_CAP;
+  for (int k = threadIdx.x; k < n; k += DD_THREADS) {
+    s_isrc[k] = hits[k].status == ST_NEWTON ? hits[k].src : -1;
+    s_keep[k] = 0;
+  }
   if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.nsrc; i += DD_THREADS) {
+    KeepWalk w;
+    keep_walk(w, i, n, s_isrc, s_keep, [&](int u, double &x, double &y) {
+      x = hits[u].tx;
+      y = hits[u].ty;
+    });
+  }
   __syncthreads();
   for (int k0 = 0; k0 < n; k0 += DD_THREADS) {
     const int k = k0 + threadIdx.x;
-    int keep = 0;
-    if (k < n && hits[k].status == ST_NEWTON) {
-      keep = 1;
-      const int src = hits[k].src;
-      const double x = hits[k].tx, y = hits[k].ty;
-      for (int j = 0; j < k; ++j) {
-        if (hits[j].status != ST_NEWTON || hits[j].src != src) continue;
-        const double ex = hits[j].tx - x, ey = hits[j].ty - y;
-        if (ex * ex + ey * ey < DEDUP * DEDUP) {
-          keep = 0;
-          break;
-        }
-      }
-    }
+    const int keep = k < n ? s_keep[k] : 0;
     // inclusive scan of keep flags (Hillis-Steele), keeps the candidates' order
     s_scan[threadIdx.x] = keep;
     __syncthreads();
@@ -1812,7 +1871,6 @@ __global__ void __launch_bounds__(NW_THREADS, LENS_POLISH_MINB) k_img_polish(con
 
 // ------------------------------------------------------------- 6. match, chi2
 constexpr int C2_THREADS = 128;
-constexpr int C2_LIST = 128, C2_KEEP = 16;  // polished images listed, kept positions held, per source
 
 __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const double *__restrict__ x,
                                                          const double *__restrict__ y,
@@ -1840,12 +1898,8 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
   // the same source (candidates of one highly magnified image can end the
   // FP32 Newton further apart than DEDUP and meet only after the polish).
   // Each image's source is staged (-1: not polished); a thread per source
-  // collects its images' indices in candidate order (a scan without global
-  // loads; up to C2_LIST of them), keeps those not within DEDUP of one it
-  // already kept -- the rule of the definition's image search -- counts
-  // them and matches its constraints to them (the first C2_KEEP kept
-  // positions held by the thread, any further ones re-read).  A source with
-  // more than C2_LIST polished images re-scans the staged sources instead.
+  // keeps its images (keep_walk: in candidate order, those not within DEDUP
+  // of one already kept), counts them and matches its constraints to them.
   __shared__ unsigned char s_use[IMG_CAP];
   __shared__ int s_isrc[IMG_CAP];
   for (int u = threadIdx.x; u < nu; u += C2_THREADS) {
@@ -1855,46 +1909,14 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
   }
   __syncthreads();
   double acc[1] = {0.0};
+  auto pos = [&](int u, double &x, double &y) {
+    x = hits[uniq[u]].tx;
+    y = hits[uniq[u]].ty;
+  };
   for (int i = threadIdx.x; i < a.nsrc; i += C2_THREADS) {
-    int lst[C2_LIST];
-    int nl = 0;
-    for (int u = 0; u < nu; ++u)
-      if (s_isrc[u] == i) {
-        if (nl < C2_LIST) lst[nl] = u;
-        ++nl;
-      }
-    const bool listed = nl <= C2_LIST;
-    const int nc = listed ? nl : nu;  // candidates walked: the list, or every staged image
-    auto cand = [&](int k) { return listed ? lst[k] : k; };
-    double kx[C2_KEEP], ky[C2_KEEP];
-    int nk = 0;
-    auto near_kept = [&](double tx, double ty, int before) {  // within DEDUP of a kept image?
-      for (int k = 0; k < nk && k < C2_KEEP; ++k) {
-        const double ex = kx[k] - tx, ey = ky[k] - ty;
-        if (ex * ex + ey * ey < DEDUP * DEDUP) return true;
-      }
-      if (nk > C2_KEEP)  // kept images past the first C2_KEEP
-        for (int k = 0, seen = 0; k < before; ++k) {
-          const int v = cand(k);
-          if (s_isrc[v] != i || !s_use[v] || ++seen <= C2_KEEP) continue;
-          const double ex = hits[uniq[v]].tx - tx, ey = hits[uniq[v]].ty - ty;
-          if (ex * ex + ey * ey < DEDUP * DEDUP) return true;
-        }
-      return false;
-    };
-    for (int k = 0; k < nc; ++k) {
-      const int u = cand(k);
-      if (s_isrc[u] != i) continue;
-      const Hit &h = hits[uniq[u]];
-      if (near_kept(h.tx, h.ty, k)) continue;
-      s_use[u] = 1;
-      if (nk < C2_KEEP) {
-        kx[nk] = h.tx;
-        ky[nk] = h.ty;
-      }
-      ++nk;
-    }
-    if (nfound) nfound[(size_t)p * a.nsrc + i] = overflow ? -1 : nk;
+    KeepWalk w;
+    keep_walk(w, i, nu, s_isrc, s_use, pos);
+    if (nfound) nfound[(size_t)p * a.nsrc + i] = overflow ? -1 : w.nk;
     // each constraint of the source: the nearest kept image (ties: lower y,
     // then lower x)
     for (int j = img_off[i]; j < img_off[i + 1]; ++j) {
@@ -1907,12 +1929,14 @@ __global__ void __launch_bounds__(C2_THREADS) k_img_chi2(const SetArgs a, const 
           by = ty;
         }
       };
-      for (int k = 0; k < nk && k < C2_KEEP; ++k) consider(kx[k], ky[k]);
-      if (nk > C2_KEEP)
-        for (int k = 0, seen = 0; k < nc; ++k) {
-          const int v = cand(k);
-          if (s_isrc[v] != i || !s_use[v] || ++seen <= C2_KEEP) continue;
-          consider(hits[uniq[v]].tx, hits[uniq[v]].ty);
+      for (int k = 0; k < w.nk && k < KW_KEEP; ++k) consider(w.kx[k], w.ky[k]);
+      if (w.nk > KW_KEEP)
+        for (int k = 0, seen = 0; k < w.nc; ++k) {
+          const int v = w.cand(k);
+          if (s_isrc[v] != i || !s_use[v] || ++seen <= KW_KEEP) continue;
+          double vx, vy;
+          pos(v, vx, vy);
+          consider(vx, vy);
         }
       acc[0] += best / (sigma[j] * sigma[j]);  // no image of this source: +inf -> NaN below
     }
