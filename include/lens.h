@@ -98,7 +98,9 @@ typedef struct {
   double x0, y0, theta, eps, rcore, rcut, b0;
 } lens_halo;
 
-/* Rectangular grid, inclusive corners; nx, ny >= 2, xmax > xmin, ymax > ymin. */
+/* Rectangular grid, inclusive corners; nx, ny >= 2, xmax > xmin, ymax > ymin,
+ * at most 2^31 - 1 nodes (node indices are 32-bit) and at most 524 280 rows
+ * (65 535 CTA rows of 8 grid rows); a grid beyond these is LENS_EINVAL. */
 typedef struct {
   double xmin, xmax, ymin, ymax;
   int32_t nx, ny;

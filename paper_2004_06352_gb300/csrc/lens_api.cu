@@ -155,6 +155,12 @@ int check_grid(const lens_grid *g) {
     return fail(LENS_EINVAL, "grid corners must be finite");
   if (g->nx < 2 || g->ny < 2) return fail(LENS_EINVAL, "grid needs nx, ny >= 2 (got %d x %d)", g->nx, g->ny);
   if (!(g->xmax > g->xmin && g->ymax > g->ymin)) return fail(LENS_EINVAL, "grid needs xmax > xmin and ymax > ymin");
+  // node indices (the map repair list, the image search's cells) are 32-bit,
+  // and a map launch has one CTA row per map_tile_rows grid rows
+  if ((long long)g->nx * g->ny > INT32_MAX)
+    return fail(LENS_EINVAL, "grid of %d x %d has more than 2^31 - 1 nodes", g->nx, g->ny);
+  const long long max_rows = 65535LL * std::min(map_tile_rows(true), map_tile_rows(false));
+  if (g->ny > max_rows) return fail(LENS_EINVAL, "grid has %d rows; at most %lld", g->ny, max_rows);
   return LENS_OK;
 }
 

@@ -167,7 +167,11 @@ def test_invalid_inputs_rejected(lens):
         mid = ctx.model_upload(I.random_model(3, seed=1))
         out = torch.empty((2, 4, 4), device=DEV)
         for g in (dict(xmin=0, xmax=1, ymin=0, ymax=1, nx=1, ny=4), dict(xmin=1, xmax=0, ymin=0, ymax=1, nx=4, ny=4),
-                  dict(xmin=0, xmax=np.inf, ymin=0, ymax=1, nx=4, ny=4)):
+                  dict(xmin=0, xmax=np.inf, ymin=0, ymax=1, nx=4, ny=4),
+                  # beyond 2^31 - 1 nodes and beyond the launch's rows: refused
+                  # on the host before anything is launched
+                  dict(xmin=0, xmax=1, ymin=0, ymax=1, nx=65536, ny=32769),
+                  dict(xmin=0, xmax=1, ymin=0, ymax=1, nx=2, ny=524281)):
             with pytest.raises(lens.LensError) as e:
                 ctx.grad_map(mid, g, 1.0, lens.LENS_MIXED, out)
             assert e.value.code == lens.LENS_EINVAL
