@@ -636,6 +636,16 @@ __device__ __forceinline__ void fold2(Acc2<HESS, NP> &tot, Acc2<HESS, NP> &cmp, 
   part.zero();
 }
 
+// The potential sums alone (p.k) folded into the compensated total.
+template <bool HESS, int NP>
+__device__ __forceinline__ void fold2_pot(Acc2<HESS, NP> &tot, Acc2<HESS, NP> &cmp, Acc2<HESS, NP> &part) {
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    kahan2(tot.k[i], cmp.k[i], part.k[i]);
+    part.k[i] = make_float2(0.f, 0.f);
+  }
+}
+
 // dX of pair k: one value shared by both points and all pairs (a map
 // column), or one per point (float2 per pair)
 __device__ __forceinline__ float2 dx2_of(float dX, int) { return dup2(dX); }
@@ -653,7 +663,9 @@ __device__ __forceinline__ float2 cdx2(float c, const float2 (&dX)[NP], int k) {
 // point, dY per point: the arithmetic of dpie32 (same formulas, same order),
 // paired.  MAG: also the magnitude sum p.mag.  FAST: outside the
 // interpolants' range, dpie32's FAST forms (decision-grade, image search).
-template <bool HESS, int NP, bool SERIES, bool MAG = true, bool FAST = false, typename DX>
+// POT: the potential (dpie32's POT form, paired) into p.k, on the plain
+// (unfolded) record constants.
+template <bool HESS, int NP, bool SERIES, bool MAG = true, bool FAST = false, bool POT = false, typename DX>
 __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX &dX, const float2 (&dY)[NP],
                                          Acc2<HESS, NP> &p) {
   const float4 A = r4[0], B = r4[1], Cq = r4[2], D = r4[3], E = r4[4];
@@ -662,7 +674,7 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX
   // FOLD (the general kind, u >= U_SERIES32): Zx, Zy below carry the factor
   // u (the numerators' constants times u), so t = Z^2 needs no u^2 and the
   // rotation and magnitude constants carry 1/u instead
-  constexpr bool FOLD = LENS_MAP_FOLD_U && !SERIES;
+  constexpr bool FOLD = LENS_MAP_FOLD_U && !SERIES && !POT;
   const float4 F6 = FOLD ? r4[6] : make_float4(0.f, 0.f, 0.f, 0.f), F7 = FOLD ? r4[7] : F6;
   const float dK = FOLD ? D.x : Cq.x, dS = FOLD ? F6.y : Cq.y, q2sc = Cq.z, q2st = Cq.w;
   const float q2dS = FOLD ? F6.z : D.y;
@@ -736,30 +748,45 @@ __device__ __forceinline__ void dpie32x2(const float4 *__restrict__ r4, const DX
         }
       }
   }
+  if constexpr (POT) {
+    // b q (x alpha_x' + y alpha_y') - b q (sc ln sqrt(Dc) - st ln sqrt(Dt)),
+    // rounded as dpie32's POT form
+    const float bq = 2.f * E.z;
 #pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    p.ax[k] = fma2(dup2(cb), axp[k], fma2(dup2(-sb), ayp[k], p.ax[k]));
-    p.ay[k] = fma2(dup2(sb), axp[k], fma2(dup2(cb), ayp[k], p.ay[k]));
-    if (MAG) p.mag[k] = fma2(dup2(kmag), add2(abs2(axp[k]), abs2(ayp[k])), p.mag[k]);  // b q / 2 (/ u folded)
-    if (HESS) {
-      const float4 G = r4[5];
-      const float u2sc2 = D.z, u2st2 = D.w;
-      const float2 ymx = sub2(y2[k], x2[k]);
+    for (int k = 0; k < NP; ++k) {
       const float2 Dc = fma2(Ec[k], Ec[k], u2x2[k]), Dt = fma2(Et[k], Et[k], u2x2[k]);
-      const float2 fc = rcp2(mul2(psc[k], Dc)), ft = rcp2(mul2(pst[k], Dt));
-      const float2 fd = sub2(fc, ft);
-      // -(u2sc2 fc - u2st2 ft), rounded as its negation in dpie32
-      const float2 g1d = fma2(ymx, fd, fma2(dup2(-u2sc2), fc, mul2(dup2(u2st2), ft)));
-      const float2 g2d = mul2(fd, mul2(x[k], y[k]));
-      p.k[k] = fma2(dup2(E.z), sub2(ic[k], it[k]), p.k[k]);
-      p.g1[k] = fma2(dup2(G.x), g1d, fma2(dup2(G.y), g2d, p.g1[k]));
-      p.g2[k] = fma2(dup2(G.z), g1d, fma2(dup2(G.w), g2d, p.g2[k]));
+      const float2 l2c = make_float2(__log2f(Dc.x), __log2f(Dc.y)), l2t = make_float2(__log2f(Dt.x), __log2f(Dt.y));
+      const float2 lg = fma2(dup2(sc), l2c, mul2(dup2(-st), l2t));
+      const float2 v = fma2(x[k], axp[k], fma2(y[k], ayp[k], mul2(dup2(-0.346573590f), lg)));
+      p.k[k] = fma2(dup2(bq), v, p.k[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      p.ax[k] = fma2(dup2(cb), axp[k], fma2(dup2(-sb), ayp[k], p.ax[k]));
+      p.ay[k] = fma2(dup2(sb), axp[k], fma2(dup2(cb), ayp[k], p.ay[k]));
+      if (MAG) p.mag[k] = fma2(dup2(kmag), add2(abs2(axp[k]), abs2(ayp[k])), p.mag[k]);  // b q / 2 (/ u folded)
+      if (HESS) {
+        const float4 G = r4[5];
+        const float u2sc2 = D.z, u2st2 = D.w;
+        const float2 ymx = sub2(y2[k], x2[k]);
+        const float2 Dc = fma2(Ec[k], Ec[k], u2x2[k]), Dt = fma2(Et[k], Et[k], u2x2[k]);
+        const float2 fc = rcp2(mul2(psc[k], Dc)), ft = rcp2(mul2(pst[k], Dt));
+        const float2 fd = sub2(fc, ft);
+        // -(u2sc2 fc - u2st2 ft), rounded as its negation in dpie32
+        const float2 g1d = fma2(ymx, fd, fma2(dup2(-u2sc2), fc, mul2(dup2(u2st2), ft)));
+        const float2 g2d = mul2(fd, mul2(x[k], y[k]));
+        p.k[k] = fma2(dup2(E.z), sub2(ic[k], it[k]), p.k[k]);
+        p.g1[k] = fma2(dup2(G.x), g1d, fma2(dup2(G.y), g2d, p.g1[k]));
+        p.g2[k] = fma2(dup2(G.z), g1d, fma2(dup2(G.w), g2d, p.g2[k]));
+      }
     }
   }
 }
 
 // SIS / point mass at NP point pairs: circ32, paired.
-template <bool HESS, int NP, bool POINT, bool MAG = true, typename DX>
+// POT: the potential b r (SIS) or b ln r (point mass) into p.k, as circ32.
+template <bool HESS, int NP, bool POINT, bool MAG = true, bool POT = false, typename DX>
 __device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, const DX &dX, const float2 (&dY)[NP],
                                          Acc2<HESS, NP> &p) {
   const float b = r4[7].y;
@@ -768,27 +795,37 @@ __device__ __forceinline__ void circ32x2(const float4 *__restrict__ r4, const DX
     const float2 x = dx2_of(dX, k);
     const float2 y = dY[k];
     const float2 r2 = fma2(x, x, mul2(y, y));
-    float2 ir;
+    if constexpr (POT) {
+      float2 f;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float v = part2(r2, h);
-      part2(ir, h) = v > 0.f ? (POINT ? rcp_a(v) : rsqrt_a(v)) : 0.f;
-    }
-    const float2 f = mul2(dup2(b), ir);
-    p.ax[k] = fma2(f, x, p.ax[k]);
-    p.ay[k] = fma2(f, y, p.ay[k]);
-    if (MAG) p.mag[k] = fma2(dup2(0.5f), add2(abs2(mul2(f, x)), abs2(mul2(f, y))), p.mag[k]);
-    if (HESS) {
-      const float2 ymx = mul2(sub2(y, x), add2(y, x));
-      if (POINT) {
-        const float2 f2 = mul2(f, ir);
-        p.g1[k] = fma2(f2, ymx, p.g1[k]);
-        p.g2[k] = fma2(mul2(dup2(-2.f), f2), mul2(x, y), p.g2[k]);
-      } else {
-        const float2 f3 = mul2(mul2(f, ir), ir);
-        p.k[k] = fma2(dup2(0.5f), f, p.k[k]);
-        p.g1[k] = fma2(mul2(dup2(0.5f), f3), ymx, p.g1[k]);
-        p.g2[k] = fma2(mul2(f3, dup2(-1.f)), mul2(x, y), p.g2[k]);
+      for (int h = 0; h < 2; ++h) {
+        const float v = part2(r2, h);
+        part2(f, h) = v > 0.f ? (POINT ? 0.346573590f * __log2f(v) : v * rsqrt_a(v)) : 0.f;
+      }
+      p.k[k] = fma2(dup2(b), f, p.k[k]);
+    } else {
+      float2 ir;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float v = part2(r2, h);
+        part2(ir, h) = v > 0.f ? (POINT ? rcp_a(v) : rsqrt_a(v)) : 0.f;
+      }
+      const float2 f = mul2(dup2(b), ir);
+      p.ax[k] = fma2(f, x, p.ax[k]);
+      p.ay[k] = fma2(f, y, p.ay[k]);
+      if (MAG) p.mag[k] = fma2(dup2(0.5f), add2(abs2(mul2(f, x)), abs2(mul2(f, y))), p.mag[k]);
+      if (HESS) {
+        const float2 ymx = mul2(sub2(y, x), add2(y, x));
+        if (POINT) {
+          const float2 f2 = mul2(f, ir);
+          p.g1[k] = fma2(f2, ymx, p.g1[k]);
+          p.g2[k] = fma2(mul2(dup2(-2.f), f2), mul2(x, y), p.g2[k]);
+        } else {
+          const float2 f3 = mul2(mul2(f, ir), ir);
+          p.k[k] = fma2(dup2(0.5f), f, p.k[k]);
+          p.g1[k] = fma2(mul2(dup2(0.5f), f3), ymx, p.g1[k]);
+          p.g2[k] = fma2(mul2(f3, dup2(-1.f)), mul2(x, y), p.g2[k]);
+        }
       }
     }
   }

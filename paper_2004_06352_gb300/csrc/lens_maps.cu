@@ -47,6 +47,9 @@ namespace {
 #ifndef LENS_MAP_SEGMENTS_GRAD
 #define LENS_MAP_SEGMENTS_GRAD 0  // the same in the deflection-only kernel (measured slower: it spills)
 #endif
+#ifndef LENS_POT_PAIRED
+#define LENS_POT_PAIRED 1  // potential map on the paired FP32 path
+#endif
 #ifndef LENS_MAP_UNROLL
 #define LENS_MAP_UNROLL 2  // potentials per iteration of those loops (2: 0.6 % faster than 4 at 128 threads)
 #endif
@@ -152,14 +155,17 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
   // deflection / Hessian: the thread's points as KP/2 pairs on the paired
   // FP32 path; the potential map: per point (POT: the potential in .k)
   constexpr int NP = KP / 2;
-  using AccT = std::conditional_t<POT, Acc<true, KP>, Acc2<HESS, NP>>;
+  constexpr bool POT1 = POT && !LENS_POT_PAIRED;  // the potential point by point
+  using AccT = std::conditional_t<POT1, Acc<true, KP>, Acc2<HESS, NP>>;
   AccT tot, cmp, part;
   tot.zero();
   cmp.zero();
   part.zero();
   auto fold_all = [&]() {
-    if constexpr (POT)
+    if constexpr (POT1)
       fold(tot, cmp, part);
+    else if constexpr (POT)
+      fold2_pot(tot, cmp, part);
     else
       fold2(tot, cmp, part);
   };
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
             const float4 *r4 = recs + h * (REC32 / 4);
             float dX, dY[KP];
             tile_offsets(buf, h, dX, dY);
-            if constexpr (POT) {
+            if constexpr (POT1) {
               if (KIND == K32_DPIE)
                 dpie32<false, KP, false, false, true>(r4, dX, dY, part);
               else if (KIND == K32_DPIE_SERIES)
@@ -311,11 +317,11 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
 #pragma unroll
               for (int j = 0; j < NP; ++j) dY2[j] = make_float2(dY[2 * j], dY[2 * j + 1]);
               if (KIND == K32_DPIE)
-                dpie32x2<HESS, NP, false>(r4, dX, dY2, part);
+                dpie32x2<HESS, NP, false, !POT, false, POT>(r4, dX, dY2, part);
               else if (KIND == K32_DPIE_SERIES)
-                dpie32x2<HESS, NP, true>(r4, dX, dY2, part);
+                dpie32x2<HESS, NP, true, !POT, false, POT>(r4, dX, dY2, part);
               else
-                circ32x2<HESS, NP, KIND == K32_POINT>(r4, dX, dY2, part);
+                circ32x2<HESS, NP, KIND == K32_POINT, !POT, POT>(r4, dX, dY2, part);
             }
           }
           if (seen == SUB) {
