@@ -41,6 +41,9 @@ namespace {
 #ifndef LENS_MAP_MINB_GRAD
 #define LENS_MAP_MINB_GRAD 6  // deflection-only kernel (128-thread CTAs)
 #endif
+#ifndef LENS_MAP_MINB_POT
+#define LENS_MAP_MINB_POT 4  // potential kernel (126 registers; 6 CTAs/SM at 80: 8.37 against 7.98 ms)
+#endif
 #ifndef LENS_MAP_SEGMENTS
 #define LENS_MAP_SEGMENTS 1  // kind-uniform loops over each chunk's potentials
 #endif
@@ -118,7 +121,9 @@ template <int N>
 __device__ __forceinline__ float pt(const float2 (&v)[N], int k) { return part2(v[k >> 1], k & 1); }
 
 template <int MODE, int KP>
-__global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HESS ? LENS_MAP_MINB : LENS_MAP_MINB_GRAD)
+__global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HESS  ? LENS_MAP_MINB
+                                                                  : MODE == MAP_POT ? LENS_MAP_MINB_POT
+                                                                                    : LENS_MAP_MINB_GRAD)
     k_map_mixed(const MapArgs a) {
   constexpr bool HESS = MODE == MAP_HESS, POT = MODE == MAP_POT;
   constexpr int MAP_THREADS = map_threads(HESS), MAP_WARPS = MAP_THREADS / 32;
