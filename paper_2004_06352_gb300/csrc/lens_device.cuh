@@ -1268,6 +1268,36 @@ template <bool HESS>
 __device__ __noinline__ void eval64_cold(const double *__restrict__ r, double X, double Y, double *e) {
   eval64<HESS>(r, X, Y, e[0], e[1], e[2], e[3], e[4]);
 }
+// The same with the sum kept in double-float: acc[0..4] pairs (one-TwoSum
+// accumulation, absolute error 2^-47 of the summed magnitudes), the point
+// also given as pairs (Xd, Yd), so that a term costs no FP64 operation
+// unless its double-float evaluation fails.
+template <bool HESS>
+__device__ __forceinline__ void add_potential_dfs(const float2 *__restrict__ rdf, int stride,
+                                                  const double *__restrict__ r64, double X, double Y, df Xd, df Yd,
+                                                  df *acc) {
+  df ax, ay, h[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  bool ok = true;
+  if (rdf[F_U2 * stride].x < 0.f)
+    circ_df<HESS>(rdf, stride, Xd, Yd, ax, ay, h);
+  else
+    ok = dpie_df<true, HESS>(rdf, stride, Xd, Yd, ax, ay, h);
+  if (!ok) {
+    double e[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    eval64_cold<HESS>(r64, X, Y, e);
+    ax = df_from_double(e[0]);
+    ay = df_from_double(e[1]);
+    h[0] = df_from_double(e[2]);
+    h[1] = df_from_double(e[3]);
+    h[2] = df_from_double(e[4]);
+  }
+  acc[0] = df_add_ss(acc[0], ax);
+  acc[1] = df_add_ss(acc[1], ay);
+  if (HESS)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) acc[2 + q] = df_add_ss(acc[2 + q], h[q]);
+}
+
 template <bool HESS>
 __device__ __forceinline__ void add_varying_df(const float2 *__restrict__ rdf, const double *__restrict__ r64,
                                                double X, double Y, double *acc) {

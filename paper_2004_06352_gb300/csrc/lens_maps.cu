@@ -463,6 +463,12 @@ struct RepairArgs {
   const int *count, *list;
 };
 
+// LENS_REPAIR_DFSUM: each lane sums its terms in double-float and converts
+// once (0: every term converted and added in FP64, 20 FP64-pipe operations
+// per term with the Hessian)
+#ifndef LENS_REPAIR_DFSUM
+#define LENS_REPAIR_DFSUM 1
+#endif
 constexpr int REP_WARPS = 8, REP_THREADS = 32 * REP_WARPS, REP_CH = 32;  // potentials per staged chunk (one per lane)
 
 template <bool HESS>
@@ -478,6 +484,10 @@ __global__ void __launch_bounds__(REP_THREADS) k_map_repair(const RepairArgs a) 
     const bool full = HESS && entry < 0;  // warp-uniform
     const int i = o % a.nx, j = o / a.nx;
     const double X = a.xmin + i * a.dx, Y = a.ymin + (a.row0 + j) * a.dy;
+#if LENS_REPAIR_DFSUM
+    const df Xd = df_from_double(X), Yd = df_from_double(Y);
+    df sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#endif
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int h0 = 0; h0 < a.n; h0 += REP_CH) {
       __syncthreads();  // the previous chunk has been used
@@ -488,12 +498,23 @@ __global__ void __launch_bounds__(REP_THREADS) k_map_repair(const RepairArgs a) 
       __syncthreads();
       const int h = h0 + lane;
       if (have && h < a.n) {
+#if LENS_REPAIR_DFSUM
+        if (full)
+          add_potential_dfs<true>(&s_rdf[0][lane], REP_CH, a.all64 + (size_t)h * REC64, X, Y, Xd, Yd, sum);
+        else
+          add_potential_dfs<false>(&s_rdf[0][lane], REP_CH, a.all64 + (size_t)h * REC64, X, Y, Xd, Yd, sum);
+#else
         if (full)
           add_potential_df<true>(&s_rdf[0][lane], REP_CH, a.all64 + (size_t)h * REC64, X, Y, acc);
         else
           add_potential_df<false>(&s_rdf[0][lane], REP_CH, a.all64 + (size_t)h * REC64, X, Y, acc);
+#endif
       }
     }
+#if LENS_REPAIR_DFSUM
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc[c] = df_to_double(sum[c]);
+#endif
 #pragma unroll
     for (int c = 0; c < (HESS ? 5 : 2); ++c)
 #pragma unroll
