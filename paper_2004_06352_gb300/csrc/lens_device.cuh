@@ -892,7 +892,23 @@ __device__ __forceinline__ df df_add_ss(df a, df b) {
 }
 // a / b: MUFU reciprocal of b.hi, then two exact remainders a - b q
 // correct the quotient (its first term may be off by a few 2^-24).
-__device__ __forceinline__ df df_div(df a, df b) {
+// Code size of the double-float evaluators: their longer operations as
+// called functions (one copy per kernel) or inlined at every use.
+#ifndef LENS_DF_NOINLINE_DIV
+#define LENS_DF_NOINLINE_DIV 0
+#endif
+#ifndef LENS_DF_NOINLINE_SQRT
+#define LENS_DF_NOINLINE_SQRT 0
+#endif
+#ifndef LENS_DF_NOINLINE_POLY
+#define LENS_DF_NOINLINE_POLY 0
+#endif
+#if LENS_DF_NOINLINE_DIV
+static __device__ __noinline__
+#else
+__device__ __forceinline__
+#endif
+df df_div(df a, df b) {
   const float ib = rcp_a(b.hi);
   const float q1 = a.hi * ib;
   df r = df_sub(a, df_mulf(b, q1));
@@ -903,7 +919,12 @@ __device__ __forceinline__ df df_div(df a, df b) {
 }
 // sqrt(a): MUFU reciprocal square root y of a.hi, s = a.hi y, one Newton
 // correction (a - s^2) y / 2 with the residual from an FMA.
-__device__ __forceinline__ df df_sqrt(df a) {
+#if LENS_DF_NOINLINE_SQRT
+static __device__ __noinline__
+#else
+__device__ __forceinline__
+#endif
+df df_sqrt(df a) {
   if (!(a.hi > 0.f)) return {0.f, 0.f};
   const float y = rsqrt_a(a.hi);
   const float s = a.hi * y;
@@ -919,7 +940,12 @@ __device__ __forceinline__ df df_from_double(double d) {
 // atan(w)/w, atanh(w)/w on t = w^2 < T_SERIES64 in double-float: the FP64
 // interpolants' terms t^7.. (below 5e-7 of the result) in FP32, the rest in
 // double-float Horner.
-__device__ __forceinline__ df df_poly(df t, const float (*c)[2]) {
+#if LENS_DF_NOINLINE_POLY
+static __device__ __noinline__
+#else
+__device__ __forceinline__
+#endif
+df df_poly(df t, const float (*c)[2]) {
   float tail = c[11][0];
 #pragma unroll
   for (int k = 10; k >= 7; --k) tail = fmaf(tail, t.hi, c[k][0]);
@@ -1027,7 +1053,17 @@ __device__ __constant__ const float PI_2_DF[2] = {1.570796371e+00f, -4.371138829
 // atan(w) and atanh(w) in double-float for any argument (|w| < 1 for
 // atanh), by the reductions of atan64 / atanh64 (pairs instead of doubles);
 // atanh returns NaN beyond the table (|w| within ~1e-15 of 1).
-__device__ __forceinline__ df df_atan(df w) {
+// LENS_DF_NOINLINE_ATAN: df_atan / df_atanh as called functions (one copy
+// of their code per kernel instead of one per call site)
+#ifndef LENS_DF_NOINLINE_ATAN
+#define LENS_DF_NOINLINE_ATAN 0
+#endif
+#if LENS_DF_NOINLINE_ATAN
+#define LENS_DF_ATAN_INLINE static __device__ __noinline__
+#else
+#define LENS_DF_ATAN_INLINE __device__ __forceinline__
+#endif
+LENS_DF_ATAN_INLINE df df_atan(df w) {
   const bool neg = w.hi < 0.f;
   const df a = neg ? df_neg(w) : w;
   const bool inv = a.hi > 1.f;
@@ -1041,7 +1077,7 @@ __device__ __forceinline__ df df_atan(df w) {
   if (inv) r = df_sub(df{PI_2_DF[0], PI_2_DF[1]}, r);
   return neg ? df_neg(r) : r;
 }
-__device__ __forceinline__ df df_atanh(df w) {
+LENS_DF_ATAN_INLINE df df_atanh(df w) {
   const bool neg = w.hi < 0.f;
   const df a = neg ? df_neg(w) : w;
   df r;
