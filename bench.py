@@ -37,14 +37,14 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2, written between timed steps
 FP32_OPS_PER_PAIR = 63.0
 MUFU_OPS_PER_PAIR = 6.03
 # every FP32 lane operation of the map call per pair: the kernel's 65.0 and
-# the double-float repair kernel's 1.24 (same capture)
-CALL_FP32_OPS_PER_PAIR = 66.2
+# the double-float repair kernel's 1.27 (same capture)
+CALL_FP32_OPS_PER_PAIR = 66.3
 # the same count for the potential-map kernel (ncu, same workload)
 POT_FP32_OPS_PER_PAIR = 48.9
 # DRAM bytes (read + write) of one launch of that kernel on that workload,
 # from the same ncu capture; the 100.7 MB of output are partly still in L2
 # when the kernel ends
-MAP_TRAFFIC_BYTES = 619264 + 39801856
+MAP_TRAFFIC_BYTES = 352000 + 39027968
 SMS, FP32_LANES, MUFU_LANES = 152, 128, 16
 # FP64 FMA lanes per SM and clock (measured on this GPU: 1/64 of the FP32 rate)
 FP64_LANES = 2
