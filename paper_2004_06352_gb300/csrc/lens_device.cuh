@@ -580,8 +580,9 @@ __device__ __forceinline__ void eval32_any(const float4 *__restrict__ r4, const 
 // the same FP32 work in half the issued instructions.  The MUFU
 // approximations (rsqrt, rcp) have no paired form and run per point.  Each
 // paired operation rounds exactly as the scalar one it replaces (a - b is
-// formed as b * (-1) + a: an exact product and one rounding), so the paired
-// evaluators below give the scalar dpie32 / circ32 results bit for bit.
+// formed as b * (-1) + a: an exact product and one rounding); a product and
+// a sum that the compiler fuses into one FMA in the scalar dpie32 / circ32
+// stay two roundings here, so the two forms can differ in the last bits.
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
