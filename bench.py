@@ -443,6 +443,24 @@ def extra_legs(ctx, api, I, torch, dev, m, g, mid, stream, errs, out):
     out2 = torch.empty((2, MAP_N, MAP_N), dtype=torch.float32, device=dev)
     t = timed(lambda: ctx.grad_map(mid, g, 1.0, api.LENS_MIXED, out2, stream), 5)
     ex["grad_map_mixed"] = {"ms": t, "pair_per_s": pairs / (t * 1e-3)}
+    del out2
+    # the paper's own map benchmark shape (Sec. 5: a 5000^2 gradient map over
+    # 150" x 150" of a 217-potential cluster model), with a synthetic model of
+    # that size in place of its data: 2 cluster-scale halos + 215 members
+    mp = I.cfg2_model(n_members=215)
+    midp = ctx.model_upload(mp)
+    gp = I.grid(5000, field=(-75.0, 75.0, -75.0, 75.0))
+    out5 = torch.empty((2, 5000, 5000), dtype=torch.float32, device=dev)
+    t = timed(lambda: ctx.grad_map(midp, gp, 1.0, api.LENS_MIXED, out5, stream), 5)
+    pp = 5000 * 5000 * len(mp)
+    ex["grad_map_paper_shape"] = {"ms": t, "pair_per_s": pp / (t * 1e-3),
+                                  "workload": "gradient map 5000^2 over 150\" x 150\", 217 potentials "
+                                              "(2 cluster + 215 members, synthetic), LENS_MIXED",
+                                  "paper_p100_s": 0.93,
+                                  "note": "the paper's 1-GPU time for its 217-potential model on this grid "
+                                          "(P100, precision unstated; context, not a like-for-like comparison)"}
+    del out5
+    ctx.model_release(midp)
     # potential + time-delay (Fermat) surface about a source position
     outp = torch.empty((2, MAP_N, MAP_N), dtype=torch.float64, device=dev)
     t = timed(lambda: ctx.potential_map(mid, g, 1.0, api.LENS_MIXED, outp, beta=(1.0, -2.0), stream=stream), 5)
