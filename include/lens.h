@@ -135,7 +135,11 @@ int lens_create(lens_ctx **out, int device, size_t mem_budget_bytes);
 int lens_destroy(lens_ctx *ctx);
 
 /* Potentials with b0 >= threshold_b0 are evaluated in FP64 by LENS_MIXED
- * maps (default 5 arcsec).  Applies to models uploaded afterwards. */
+ * maps (default 5 arcsec) -- in double-float on the FP32 pipe instead (about
+ * 1e-13 relative, FP64 where that fails) by the deflection and Hessian maps
+ * of a model with fewer than 400 other potentials per such potential, where
+ * the FP64 unit (1/64 of the FP32 rate) would set the pace.  Applies to
+ * models uploaded afterwards. */
 int lens_set_fp64_threshold(lens_ctx *ctx, double threshold_b0);
 
 /* LENS_MIXED deflection and Hessian maps: where the deflection at a node is

@@ -91,7 +91,9 @@ struct MapArgs {
   int n_light;
   int koff[5];  // light potentials of kind k (Kind32 order) are [koff[k], koff[k+1])
   const double *heavy;
+  const float2 *heavydf;  // the same in double-float, record-major
   int n_heavy;
+  int heavy_df;           // evaluate them in double-float instead of FP64 (deflection / Hessian maps)
   double xmin, ymin, dx, dy;
   int nx, ny;   // ny: rows computed by this launch
   int row0;     // grid row of the launch's first row (row bands of one grid)
@@ -175,11 +177,30 @@ __global__ void __launch_bounds__(map_threads(MODE == MAP_HESS), MODE == MAP_HES
       fold2(tot, cmp, part);
   };
 
-  // FP64 potentials (cluster scale).  Half of the tiles evaluate them before
-  // the FP32 loop, half after, so the two CTAs sharing an SM rarely load the
-  // FP64 pipe at the same time.
+  // FP64 potentials (cluster scale), in FP64 or, when the model has few FP32
+  // potentials per FP64 one, in double-float.  Half of the tiles evaluate
+  // them before the FP32 loop, half after, so the CTAs sharing an SM rarely
+  // load the FP64 pipe at the same time.
   auto heavy_pass = [&]() {
     const double X = a.xmin + (i0 + lane) * a.dx;
+    if constexpr (!POT) {
+      if (a.heavy_df) {
+        // in double-float on the FP32 pipe (FP64 where that fails)
+        const df Xd = df_from_double(X);
+#pragma unroll 1
+        for (int k = 0; k < KP; ++k) {
+          const double Y = a.ymin + (a.row0 + j0 + warp * KP + k) * a.dy;
+          const df Yd = df_from_double(Y);
+          df sum[5] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+          for (int h = 0; h < a.n_heavy; ++h)
+            add_potential_dfs<HESS>(a.heavydf + (size_t)h * RECDF, 1, a.heavy + (size_t)h * REC64, X, Y, Xd, Yd,
+                                    sum);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s_hv[tid][k][c] = df_to_double(sum[c]);
+        }
+        return;
+      }
+    }
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       const double Y = a.ymin + (a.row0 + j0 + warp * KP + k) * a.dy;
@@ -615,6 +636,18 @@ int launch_wait_selftest(lens_ctx *ctx, unsigned polls, cudaStream_t st) {
   return LENS_OK;
 }
 
+// The FP64 pipe runs at 1/64 of the FP32 rate: with few FP32 potentials per
+// FP64 one the cluster-scale potentials' FP64 work outlasts the FP32 sweep
+// it overlaps, and their double-float evaluation on the FP32 pipe is faster
+// (2 cluster-scale + 215 members: 13.85 -> 9.94 ms per 5000^2 deflection
+// map; 2 + 998: 10.00 against 10.17 ms per 2048^2 Hessian map in FP64).
+#ifndef LENS_HEAVY_DF_RATIO
+#define LENS_HEAVY_DF_RATIO 400
+#endif
+static int heavy_in_df(const Model *m) {
+  return m->n_heavy > 0 && (long long)m->n_light < (long long)LENS_HEAVY_DF_RATIO * m->n_heavy;
+}
+
 int map_tile_rows(bool hess) { return map_threads(hess) / 32 * (hess ? LENS_KP_HESS : LENS_KP_GRAD); }
 
 size_t map_repair_bytes(const lens_grid *g, int rows) {
@@ -645,7 +678,9 @@ int launch_map_mixed(lens_ctx *ctx, const Model *m, const lens_grid *g, double d
   a.n_light = m->n_light;
   for (int k = 0; k < 5; ++k) a.koff[k] = m->koff[k];
   a.heavy = m->heavy;
+  a.heavydf = m->heavydf;
   a.n_heavy = m->n_heavy;
+  a.heavy_df = heavy_in_df(m);
   a.xmin = g->xmin;
   a.ymin = g->ymin;
   a.dx = (g->xmax - g->xmin) / (g->nx - 1);
@@ -741,7 +776,9 @@ int launch_pot_map(lens_ctx *ctx, const Model *m, const lens_grid *g, double dls
     a.n_light = m->n_light;
     for (int k = 0; k < 5; ++k) a.koff[k] = m->koff[k];
     a.heavy = m->heavy;
+    a.heavydf = m->heavydf;
     a.n_heavy = m->n_heavy;
+    a.heavy_df = 0;  // the potential kernel keeps them in FP64 (no double-float potential form)
     a.xmin = g->xmin;
     a.ymin = g->ymin;
     a.dx = dx;

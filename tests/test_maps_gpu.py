@@ -87,6 +87,19 @@ def test_mixed_map_all_heavy_and_all_light(lens):
     check_mixed(run_map(lens, m, g, 1.0, lens.LENS_MIXED, True, threshold=1e9), oracle.maps(m, g, 1.0, 6), True)
 
 
+@pytest.mark.parametrize("members", [998, 215])
+def test_mixed_map_cluster_potentials_fp64_and_double_float(lens, members):
+    """The two cluster-scale potentials take the FP64 path when the model has
+    400 or more FP32 potentials per cluster-scale one (998 members: 499) and
+    the double-float path below that (215 members: 107.5); both against the
+    oracle, deflection and Hessian, on a ragged grid over the cluster."""
+    m = I.cfg2_model(n_members=members)
+    g = I.grid(97, field=(-100, 100, -100, 100), ny=83)
+    for hess in (False, True):
+        res = run_map(lens, m, g, 0.7, lens.LENS_MIXED, hess)
+        check_mixed(res, oracle.maps(m, g, 0.7, 6 if hess else 2), hess)
+
+
 def test_mixed_map_single_halo_and_minimal_grid(lens):
     m = I.halo_row(I.DPIE, 0.3, -0.2, 0.4, 0.35, 0.5, 30.0, 2.0)[None]
     for g in (I.grid(2, field=(-1, 1, -1, 1)), I.grid(33, field=(-10, 10, -3, 3), ny=2)):
