@@ -165,6 +165,39 @@ def test_full_size_cfg2_sampled_deflection_only(lens):
     check_mixed(res[:, jj, ii], np.stack([ev[:, 0], ev[:, 1]]), False)
 
 
+def test_largest_grids_sampled(lens):
+    """The largest maps: the request loop's biggest (an 8192^2 Hessian map of a
+    2000-potential model) and a deflection map of 46341 x 46340 nodes, just
+    under the 2^31 - 1 node limit of the 32-bit node indices (the repair
+    list's entries), against the oracle at sampled nodes, the grid's corners
+    and last row included; sampled on the device (the big map is 17 GB)."""
+    big = dict(xmin=-100.0, xmax=100.0, ymin=-100.0, ymax=100.0, nx=46341, ny=46340)
+    assert big["nx"] * big["ny"] < 2 ** 31 - 1
+    cases = [(I.cfg2_model(n_members=1998), I.grid(8192), True), (I.cfg1_model(), big, False)]
+    rng = np.random.default_rng(26)
+    with lens.Context(0) as ctx:
+        for m, g, hess in cases:
+            mid = ctx.model_upload(m)
+            nx, ny = g["nx"], g["ny"]
+            out = torch.empty((6 if hess else 2, ny, nx), dtype=torch.float32, device=DEV)
+            (ctx.hessian_map if hess else ctx.grad_map)(mid, g, 1.0, lens.LENS_MIXED, out)
+            ctx.wait()
+            n = 3000
+            ii, jj = rng.integers(0, nx, n), rng.integers(0, ny, n)
+            ii[:6], jj[:6] = [0, nx - 1, 0, nx - 1, nx // 2, nx - 2], [0, 0, ny - 1, ny - 1, ny - 1, ny - 1]
+            got = out[:, torch.from_numpy(jj).to(DEV), torch.from_numpy(ii).to(DEV)].cpu().numpy()
+            del out
+            dx, dy = (g["xmax"] - g["xmin"]) / (nx - 1), (g["ymax"] - g["ymin"]) / (ny - 1)
+            ev = oracle.model_eval(m, g["xmin"] + ii * dx, g["ymin"] + jj * dy, 1.0)
+            if hess:
+                ref = np.stack([ev[:, 0], ev[:, 1], 0.5 * (ev[:, 2] + ev[:, 3]), 0.5 * (ev[:, 2] - ev[:, 3]), ev[:, 4]])
+                ref = np.vstack([ref, 1 / ((1 - ref[2]) ** 2 - ref[3] ** 2 - ref[4] ** 2)])
+            else:
+                ref = np.stack([ev[:, 0], ev[:, 1]])
+            check_mixed(got.astype(np.float64), ref, hess)
+            ctx.model_release(mid)
+
+
 def test_invalid_inputs_rejected(lens):
     with lens.Context(0) as ctx:
         bad = [I.halo_row(I.DPIE, 0, 0, 0, 1.0, 1, 10, 1),      # eps = 1
