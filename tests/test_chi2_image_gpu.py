@@ -127,6 +127,27 @@ def test_chi2_image_cfg2_model_parity_bench_grid(lens):
     check_chi2_image_parity(lens, 1024, 3, seed=45)
 
 
+def test_chi2_image_at_the_source_limit(lens):
+    """1024 sources, as many as the image search's shared arrays hold, on a
+    smooth lens (the two varying cluster halos scaled down, four members far
+    outside the field: no galaxy core inside a search cell, few multiple
+    images): per-source image counts equal to the oracle's and the chi2
+    within 1e-8, for the model itself and a perturbed set."""
+    m = I.cfg2_model(seed=85, n_members=4)
+    m[:2, 7] *= 0.15
+    m[2:, 1] += 400.0
+    cons = I.random_constraints(1024, seed=86, mult=(2, 2), field=40)
+    var = (0, 1)
+    params = I.perturbed_params(m, var, 2, seed=87)
+    params[0] = I.var_params_of(m, var)
+    g = I.grid(256, field=(-60, 60, -60, 60))
+    ref, nf_ref = oracle.chi2_image_batch(m, cons, g, var, params)
+    got, nf = gpu_chi2_image(lens, m, cons, var, g, params)
+    assert np.all(nf_ref >= 1)
+    assert np.array_equal(nf, nf_ref)
+    assert np.all(np.abs(got - ref) <= T.CHI2_REL * np.abs(ref)), (got, ref)
+
+
 def test_chi2_image_noise_free_is_zero(lens):
     """Constraints placed exactly on the predicted images of a source give chi2 ~ 0."""
     m = np.vstack([I.halo_row(I.DPIE, 0.3, -0.2, 0.5, 0.3, 1.5, 300.0, 12.0),

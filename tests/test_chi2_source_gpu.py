@@ -46,6 +46,33 @@ def test_chi2_source_cfg2_sampled_sets(lens):
     assert np.all(np.abs(got - ref) <= T.CHI2_REL * np.abs(ref)), np.max(np.abs(got - ref) / ref)
 
 
+def test_chi2_source_largest_constraint_set(lens):
+    """The largest constraint set one CTA holds (its back-traced positions,
+    Hessians and barycentres in shared memory, at most 200 KB: here 1000
+    sources and 4496 images, 196 KB) against the oracle, all three variants;
+    one with 5000 images (216 KB) is refused with LENS_EINVAL, its output
+    untouched."""
+    m = I.cfg2_model(seed=81, n_members=30)
+    var = (0, 1)
+    params = I.perturbed_params(m, var, 6, seed=82)
+    cons = I.random_constraints(1000, seed=83, mult=(4, 5), field=60)
+    assert 5 * (len(cons["x"])) + 2 * 1000 + 4 <= 200 * 1024 // 8
+    for variant in (0, 1, 2):
+        ref = oracle.chi2_source_batch(m, cons, var, params, variant)
+        got = gpu_chi2(lens, m, cons, var, params, variant)
+        assert np.all(np.abs(got - ref) <= T.CHI2_REL * np.abs(ref)), (variant, np.max(np.abs(got - ref) / ref))
+    big = I.random_constraints(1000, seed=84, mult=(5, 5), field=60)
+    with lens.Context(0) as ctx:
+        cs = ctx.cset_create(ctx.model_upload(m), big, var)
+        p = torch.tensor(params, dtype=torch.float64, device=DEV)
+        out = torch.full((len(params),), -1.0, dtype=torch.float64, device=DEV)
+        with pytest.raises(lens.LensError) as e:
+            ctx.chi2_source(cs, p, len(params), 0, out)
+        assert e.value.code == lens.LENS_EINVAL
+        ctx.wait()
+        assert torch.equal(out.cpu(), torch.full((len(params),), -1.0, dtype=torch.float64))
+
+
 def test_chi2_source_invalid_sets_are_nan_and_base_set_matches(lens):
     m = I.random_model(12, seed=36)
     cons = I.random_constraints(3, seed=37, field=40)
