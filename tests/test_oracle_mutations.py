@@ -44,6 +44,10 @@ MUTANTS = [
     ("grid spacing", "return g->nx > 1 ? g->xmin + i * ((g->xmax - g->xmin) / (g->nx - 1)) : g->xmin;",
      "return g->nx > 1 ? g->xmin + i * ((g->xmax - g->xmin) / g->nx) : g->xmin;"),
     ("potential log term", "return x * ax + y * ay - b * q * s * 0.5 * log(w);", "return x * ax + y * ay - b * q * 0.5 * log(w);"),
+    ("point-mass potential ln r^2 for ln r", "return r2 > 0.0 ? h->b0 * h->b0 * 0.5 * log(r2) : 0.0;",
+     "return r2 > 0.0 ? h->b0 * h->b0 * log(r2) : 0.0;"),
+    ("SIS potential with the strength halved", "if (h->type == OR_SIS) return h->b0 * sqrt(r2);",
+     "if (h->type == OR_SIS) return 0.5 * h->b0 * sqrt(r2);"),
     ("series used outside its range", "static double atan_over_u(double u, double t) {\n  if (u < 1e-4) {",
      "static double atan_over_u(double u, double t) {\n  if (u < 0.5) {"),
 ]

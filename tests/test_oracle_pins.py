@@ -139,6 +139,43 @@ def test_finite_differences_potential_alpha_hessian():
     assert np.max(np.abs(hxy_b - ev[:, 4])) < 1e-6 * hs
 
 
+def test_potential_differences_are_line_integrals_of_alpha():
+    """psi(B) - psi(A) equals the line integral of alpha from A to B (Sec. 2.1:
+    alpha = grad psi), by Gauss-Legendre quadrature along paths that pass
+    within a core radius of dPIE centres and across the whole field, so that
+    a constant that differed between branches or regions of the potential
+    (which finite differences at isolated points would not see) fails; the
+    SIS and point-mass potentials are b r and b^2 ln r exactly."""
+    m = I.random_model(9, seed=7, types=(DPIE, DPIE, DPIE, SIS, POINT))
+    m[0, 4] = 0.002  # one dPIE on the small-ellipticity series branch
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    rng = np.random.default_rng(8)
+    for k in range(12):
+        # from a random point to a point next to a dPIE centre (or across the field)
+        A = rng.uniform(-70, 70, 2)
+        B = m[k % 3, 1:3] + rng.normal(0, 0.5 * m[k % 3, 5] + 1e-3, 2) if k < 9 else rng.uniform(-70, 70, 2)
+        # piecewise straight path avoiding SIS / point-mass centres: 64 segments
+        nodes = np.linspace(0.0, 1.0, 65)
+        total = 0.0
+        for a0, a1 in zip(nodes[:-1], nodes[1:]):
+            t = 0.5 * (a1 - a0) * xg + 0.5 * (a1 + a0)
+            P = A[None, :] + t[:, None] * (B - A)[None, :]
+            ev = oracle.model_eval(m, P[:, 0], P[:, 1])
+            total += 0.5 * (a1 - a0) * np.sum(wg * (ev[:, 0] * (B - A)[0] + ev[:, 1] * (B - A)[1]))
+        dpsi = oracle.potential(m, B[0], B[1])[0] - oracle.potential(m, A[0], A[1])[0]
+        scale = np.abs(oracle.model_eval(m, np.array([A[0], B[0]]), np.array([A[1], B[1]]))[:, :2]).max() * np.hypot(*(B - A))
+        assert abs(dpsi - total) < 1e-9 * scale + 1e-12, (k, dpsi, total)
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        b = rng.uniform(0.5, 5)
+        dx, dy = rng.normal(0, 10, 2)
+        r = math.hypot(dx, dy)
+        ps = oracle.potential(I.halo_row(SIS, 3.0, 4.0, 0, 0, 0, 0, b)[None], 3.0 + dx, 4.0 + dy)[0]
+        assert math.isclose(ps, b * r, rel_tol=1e-13)
+        pp = oracle.potential(I.halo_row(POINT, 3.0, 4.0, 0, 0, 0, 0, b)[None], 3.0 + dx, 4.0 + dy)[0]
+        assert math.isclose(pp, b * b * math.log(r), rel_tol=1e-12, abs_tol=1e-12)
+
+
 def test_magnification_from_finite_difference_jacobian():
     """mu = 1/det(d beta/d theta) (Sec. 2.1 Eqs. 4-5), with the sign of the
     shear term as in det = (1-k)^2 - g^2 (the sum in Sec. 2.4 Eq. 9 is a typo)."""
