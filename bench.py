@@ -717,9 +717,14 @@ def serving_leg(ctx, api, torch):
     sess = S.Session(ctx, models)
     srv = api.Server(ctx, slots=4, pool_bytes=12 << 30)
     pool = S.PinnedPool()
-    for side in S.MAP_SIDES:   # page-lock the result buffers before timing
-        for _ in range(6 if side == 8192 else 12):
+    # page-lock the result buffers before timing (on demand, page-locking a
+    # 1.6 GB 8192^2 result blocks the submitting loop for a good part of a
+    # second, which an open stream near capacity never recovers from)
+    for side in S.MAP_SIDES:
+        for _ in range(8 if side == 8192 else 12 if side == 4096 else 16):
             pool.give(torch.empty((6, side, side), dtype=torch.float32, pin_memory=True))
+    for _ in range(48):
+        pool.give(torch.empty((S.PinnedPool.VEC_CAP,), dtype=torch.float64, pin_memory=True))
     warm = S.mixed_requests(8, seed=12, n_models=8, sides=(512, 1024))
     S.run_stream(srv, sess, warm, pool=pool, max_outstanding=8, keep_results=False)
     # one request list (400 requests) for the capacity and every load level;

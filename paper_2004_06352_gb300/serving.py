@@ -64,7 +64,11 @@ def percentiles(lat_ms):
 class PinnedPool:
     """Reusable page-locked host buffers keyed by (shape, dtype).  `misses`
     counts buffers that had to be page-locked on demand (slow: the call
-    blocks the submitting thread)."""
+    blocks the submitting thread).  Vectors (chi2 results) come as the first
+    n elements of a buffer of at least VEC_CAP, so that requests of any batch
+    size share the same buffers."""
+
+    VEC_CAP = 4096
 
     def __init__(self):
         self.free = {}
@@ -79,7 +83,12 @@ class PinnedPool:
         self.misses += 1
         return torch.empty(shape, dtype=dtype, pin_memory=True)
 
+    def take_vec(self, n, dtype):
+        return self.take((max(n, self.VEC_CAP),), dtype)[:n]
+
     def give(self, t):
+        if t._base is not None:  # a vector handed out by take_vec: its whole buffer
+            t = t._base
         self.free.setdefault((tuple(t.shape), t.dtype), []).append(t)
 
 
@@ -105,7 +114,7 @@ class Session:
         else:
             P = req[2]
             params = I.perturbed_params(self.models[req[1]], (0, 1), P, seed=req[3])
-            buf = pool.take((P,), torch.float64)
+            buf = pool.take_vec(P, torch.float64)
             t = server.submit_chi2_source(self.csets[req[1]], params, 0, buf)
         return t, buf
 
