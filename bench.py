@@ -55,7 +55,7 @@ FP64_LANES = 2
 CHI2_SRC_OPS = {"fp32": 1.276e6, "fp64": 1.658e4, "mufu": 1.168e4}
 # Image-plane chi2, 1024^2 grid, 256 sets (k_img_sources + search + the
 # refinement's point-list kernels + dedup + polish + chi2, per model):
-CHI2_IMG_OPS = {"fp32": 1.014e9, "fp64": 1.34e6, "mufu": 5.67e7}
+CHI2_IMG_OPS = {"fp32": 1.014e9, "fp64": 1.20e6, "mufu": 5.67e7}
 
 
 def hbm_peak_gbs():
